@@ -1,0 +1,332 @@
+#!/usr/bin/env python3
+"""Benchmark of the ABCS hot path on GB300.
+
+Workload (the batched sensing/reconstruction configuration): 64 synthetic
+512x512 uint8 greyscale images (seeded generator, paper_2001_09632_gb300.synth),
+B = 16, AL-DCT-BBV, subrate 0.3, FP32.  One step = abcs_sense +
+abcs_reconstruct over the whole batch (pilot BBV, exact allocation, packed
+zigzag DCT measurements, block inverse DCT).  `value` is whole-job
+Mpixel/s with the inputs resident in HBM; L2 (129 MB) is flushed between
+timed steps by writing a 512 MB buffer.  A second timed region measures IDA
+(plain TI-DCT denoiser, D_F = 2) in Mpixel*iteration/s on the same batch.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl abcs|reference]
+
+With torchrun (N > 1) every rank senses its own 64-image batch (replicas,
+no data-path collective); the time is the max over ranks.
+`--impl reference` times the FP64 CPU oracle (test infrastructure) on a
+bounded sample of the same workload, on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s ABCS sense+recon and IDA/iter; learned vs plain IDA at equal PSNR"
+N_IMG, H, W, B, SUBRATE, SEED = 64, 512, 512, 16, 0.3, 1000
+IDA_ITERS, LAMBDA, DF = 10, 2.7, 2.0
+FLUSH_BYTES = 512 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="abcs", choices=["abcs", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling in the background (every 100 ms)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        self.t0 = time.time()
+
+    def mark(self):
+        return time.time()
+
+    def stop(self, t_start, t_end):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        # rows are sampled at ~100 ms; keep the ones inside [t_start, t_end]
+        n = len(rows)
+        dt = (time.time() - self.t0) / max(n, 1)
+        sel = [r for i, r in enumerate(rows) if t_start - dt <= self.t0 + i * dt <= t_end + dt] or rows
+        sm = [float(r[1]) for r in sel if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in sel if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in sel:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip() == "Active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sel)}
+
+
+def _oracle_sense_recon(imgs):
+    import oracle as O
+    for im in imgs:
+        out = O.sense(im, B, SUBRATE, O.BBV)
+        O.reconstruct(out["counts"], out["y"], im.shape[0], im.shape[1], B)
+
+
+def cpu_baseline(imgs, budget_s=6.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample:
+    images of the batch in order (wrapping around) until budget_s elapses."""
+    t0, c0 = time.perf_counter(), time.process_time()
+    done = 0
+    while time.perf_counter() - t0 < budget_s and done < 20 * len(imgs):
+        _oracle_sense_recon(imgs[done % len(imgs):done % len(imgs) + 1])
+        done += 1
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    px = done * imgs.shape[1] * imgs.shape[2]
+    return {"value": px / wall / 1e6, "unit": "Mpixel/s", "cores": max(1, round(cpu / wall)),
+            "kind": "oracle",
+            "sample": f"{done} images of 512x512 (the batch, in order), sense (BBV r=0.3 B=16) + "
+                      f"IDCT, FP64 numpy, {wall:.1f} s"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_2001_09632_gb300 import synth
+    img = synth.gen_image(H, W, SEED)
+    t = time.perf_counter()
+    _oracle_sense_recon(img[None])
+    per_img = time.perf_counter() - t
+    # a step is a crop of `rows` rows of one image, sized so K + W steps take <~ 120 s
+    rows = H
+    while rows > B and (a.steps + a.warmup) * per_img * rows / H > 120.0:
+        rows //= 2
+    sample = img[:rows]
+    for _ in range(a.warmup):
+        _oracle_sense_recon(sample[None])
+    t0, c0 = time.perf_counter(), time.process_time()
+    for _ in range(a.steps):
+        _oracle_sense_recon(sample[None])
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    v = a.steps * rows * W / wall / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpixel/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": wall / a.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "64 x 512x512 uint8, B=16, BBV, subrate 0.3: sense + IDCT",
+                       "sample_per_step": f"{rows}x{W} crop of one image"},
+            "cpu_baseline": {"value": v, "unit": "Mpixel/s", "cores": max(1, round(cpu / wall)),
+                             "kind": "oracle", "sample": f"{rows}x{W} crop per step"},
+            "e2e": {"value": v, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2001_09632_gb300 import abcs, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    imgs = synth.gen_batch(N_IMG, H, W, SEED + rank * N_IMG)
+    plan = abcs.abcs_plan(H, W, B, SUBRATE, abcs.BBV)
+    nB = plan["n_blocks"]
+    cap = N_IMG * plan["M"]
+    h = abcs.abcs_create()
+    d_img = torch.from_numpy(imgs).to(dev)
+    counts = torch.empty(N_IMG * nB, dtype=torch.int32, device=dev)
+    offsets = torch.empty(N_IMG * nB + 1, dtype=torch.int64, device=dev)
+    coeffs = torch.empty(cap, dtype=torch.float32, device=dev)
+    rec = torch.empty((N_IMG, H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    s = stream.cuda_stream
+
+    def step():
+        abcs.abcs_sense(h, d_img, N_IMG, H, W, W, H * W, B, SUBRATE, abcs.BBV, abcs.FP32,
+                        counts, offsets, coeffs, cap, None, s)
+        abcs.abcs_reconstruct(h, counts, offsets, coeffs, N_IMG, H, W, B, abcs.FP32, rec, None, s)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(max(3, a.warmup)):
+        step()
+    assert abcs.abcs_sync_status(h, s) == 0
+    total_coeffs = int(offsets[-1].item())
+
+    clk = Clocks(local)
+    time.sleep(0.3)
+    K = a.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    barrier()
+    t_start = time.time()
+    for i in range(K):
+        flush.fill_(i & 0xFF)                      # evict L2 between timed steps
+        e0, e1, e2 = ev[i]
+        e0.record(stream)
+        abcs.abcs_sense(h, d_img, N_IMG, H, W, W, H * W, B, SUBRATE, abcs.BBV, abcs.FP32,
+                        counts, offsets, coeffs, cap, None, s)
+        e1.record(stream)
+        abcs.abcs_reconstruct(h, counts, offsets, coeffs, N_IMG, H, W, B, abcs.FP32, rec, None, s)
+        e2.record(stream)
+    barrier()
+    t_end = time.time()
+    sense_ms = [e0.elapsed_time(e1) for e0, e1, _ in ev]
+    recon_ms = [e1.elapsed_time(e2) for _, e1, e2 in ev]
+    step_ms = sum(sense_ms) / K + sum(recon_ms) / K
+    step_ms = max_over_ranks(step_ms)
+    px = N_IMG * plan["N"]
+    value = world * px / (step_ms * 1e-3) / 1e6
+
+    # ---- IDA, plain TI-DCT denoiser --------------------------------------
+    x = torch.empty((N_IMG, H, W), dtype=torch.float32, device=dev)
+    for _ in range(2):
+        abcs.abcs_ida(h, counts, offsets, coeffs, N_IMG, H, W, B, IDA_ITERS, DF, abcs.DEN_TIDCT,
+                      LAMBDA, None, x, None, s)
+    reps = 5
+    ida_ms = []
+    barrier()
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        abcs.abcs_ida(h, counts, offsets, coeffs, N_IMG, H, W, B, IDA_ITERS, DF, abcs.DEN_TIDCT,
+                      LAMBDA, None, x, None, s)
+        e1.record(stream)
+        ida_ms.append((e0, e1))
+    barrier()
+    t_end2 = time.time()
+    ida_ms = max_over_ranks(statistics.median(e0.elapsed_time(e1) for e0, e1 in ida_ms))
+    assert abcs.abcs_sync_status(h, s) == 0
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    h_img = torch.from_numpy(imgs).pin_memory()
+    h_rec = torch.empty((N_IMG, H, W), dtype=torch.float32).pin_memory()
+    Ke = K
+    eve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Ke)]
+    barrier()
+    for i in range(Ke):
+        flush.fill_(i & 0xFF)
+        e0, e1 = eve[i]
+        e0.record(stream)
+        d_img.copy_(h_img, non_blocking=True)
+        step()
+        h_rec.copy_(rec, non_blocking=True)
+        e1.record(stream)
+    barrier()
+    t_end3 = time.time()
+    e2e_ms = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in eve) / Ke)
+    clocks = clk.stop(t_start, t_end3)
+
+    if rank != 0:
+        abcs.abcs_destroy(h)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    hbm_peak, peak_kind = _peaks()
+    recon_bytes = 4 * total_coeffs + 12 * N_IMG * nB + 4 * px
+    sense_bytes = px + 4 * total_coeffs + 12 * N_IMG * nB
+    recon_avg = sum(recon_ms) / K
+    sense_avg = sum(sense_ms) / K
+    achieved = recon_bytes / (recon_avg * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": K,
+        "warmup": a.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "64 x 512x512 uint8 greyscale (seeded shapes + 1/f^2 texture), "
+                               "B=16, AL-DCT-BBV, subrate 0.3, FP32: sense + IDCT reconstruct",
+                   "value_is": "sense+reconstruct Mpixel/s", "l2": "flushed between timed steps (512 MB write)",
+                   "measurements_per_step": total_coeffs, "parallelism": f"replicas x{world}"},
+        "roofline": {"kernel": "recon_kernel<16>", "bound": "hbm", "achieved": achieved,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": recon_bytes},
+        "kernels": {"sense_ms": sense_avg, "reconstruct_ms": recon_avg,
+                    "sense_GBps_algorithmic": sense_bytes / (sense_avg * 1e-3) / 1e9,
+                    "sense_frac_hbm": sense_bytes / (sense_avg * 1e-3) / 1e9 / hbm_peak,
+                    "sense_plus_recon_frac_hbm": (sense_bytes + recon_bytes) / (step_ms * 1e-3) / 1e9 / hbm_peak},
+        "ida": {"value": world * px * IDA_ITERS / (ida_ms * 1e-3) / 1e6, "unit": "Mpixel*iter/s",
+                "iters": IDA_ITERS, "denoiser": "tidct", "lambda": LAMBDA, "damping": DF,
+                "ms_per_call": ida_ms},
+        "e2e": {"value": world * px / (e2e_ms * 1e-3) / 1e6, "unit": "Mpixel/s",
+                "h2d_bytes_per_step": int(h_img.numel()), "d2h_bytes_per_step": int(h_rec.numel() * 4),
+                "ms_per_step": e2e_ms},
+        "gpu_launches": 4 * K,
+        "clocks": clocks,
+    }
+    if world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(imgs)
+    abcs.abcs_destroy(h)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

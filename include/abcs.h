@@ -1,0 +1,190 @@
+/*
+ * abcs.h -- C ABI of the GB300 (sm_103a) adaptive block compressive sensing
+ * (ABCS) library, libabcs.so.
+ *
+ * The operations follow Zammit & Wassell, "Adaptive Block Compressive
+ * Sensing: towards a real-time and low-complexity implementation"
+ * (arXiv 2001.09632):
+ *   abcs_plan ............ derived scalars, Eqs. 16-18, 20-21, Alg. 2 step 2, Table 1
+ *   abcs_sense ........... Alg. 1 (AL-DCT-BBV) / Alg. 2 (AL-DCT-DD) / L-DCT-ZZ (Sec. IV):
+ *                          pilot estimate (Eq. 19 or Sec. V-B), allocation (Eqs. 22-23),
+ *                          zigzag-ordered 2D-DCT measurements (Eq. 26 rows)
+ *   abcs_reconstruct ..... the real-time decoder output I_o of Fig. 1: block inverse
+ *                          2D-DCT of the zero-filled measurements (Sec. VII-D)
+ *   abcs_ida ............. IDA, Eqs. 13, 15, 25 with alpha = 1/D_F (Eq. 28)
+ *   abcs_denoise_tidct ... the plain denoiser D_sigma used inside IDA (Sec. VI-4 names
+ *                          BM3D / DnCNN; this library's plain stand-in is
+ *                          shift-averaged 8x8 DCT hard thresholding)
+ *   abcs_cnn_* ........... the learned residual CNN denoiser (DnCNN-style, Sec. VI-4)
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers marked [device] are CUDA device pointers (or managed memory)
+ *     allocated and owned by the caller; the library never frees them and
+ *     keeps no reference after the call returns.  [host] pointers are read or
+ *     written before the call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work of a call is enqueued on that stream in
+ *     order; the call does not synchronise unless stated.
+ *   - Images are greyscale uint8, row-major; image k of a batch starts at
+ *     img + k * img_stride and row r at + r * pitch (both in bytes).  Only the
+ *     top-left floor(H/B)*B x floor(W/B)*B crop is sensed (Alg. 1/2 step 1).
+ *   - Blocks are numbered row-major inside an image; image k's blocks follow
+ *     image k-1's.  counts[k*n_B + i] = m_i of block i of image k;
+ *     offsets has n_img*n_B + 1 entries, offsets[j] = sum of counts before
+ *     block j (global over the batch), offsets[last] = total measurements.
+ *     coeffs[offsets[j] + t], t < counts[j], is block j's zigzag-rank-t
+ *     orthonormal DCT coefficient (JPEG zigzag orientation).
+ *   - Float images written by the library are dense float32
+ *     [n_img][floor(H/B)*B][floor(W/B)*B].
+ *   - Return values are abcs_status; no exception crosses the ABI.  A
+ *     non-OK return leaves a message for abcs_last_error() (thread-local).
+ *     Argument errors are detected before any device work is enqueued.
+ *     Conditions only the device can see (capacity overrun, non-finite
+ *     IDA residual, undecidable DD tie, spin timeout) set bits in the
+ *     handle's device status word, read by abcs_sync_status().
+ */
+#ifndef ABCS_H
+#define ABCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ABCS_API_VERSION 1
+
+typedef enum abcs_status {
+    ABCS_OK = 0,
+    ABCS_ERR_INVALID_ARG = 1,   /* bad pointer, size, enum or geometry */
+    ABCS_ERR_UNSUPPORTED = 2,   /* valid request the method does not define (e.g. BBV with L = 1) */
+    ABCS_ERR_CAPACITY = 3,      /* an output buffer is smaller than the bound the call needs */
+    ABCS_ERR_OOM = 4,           /* library workspace allocation failed */
+    ABCS_ERR_CUDA = 5,          /* a CUDA runtime call failed (message has the CUDA error) */
+    ABCS_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    ABCS_ERR_NONFINITE = 7,     /* IDA met a non-finite residual norm */
+    ABCS_ERR_DEVICE = 8         /* abcs_sync_status: device status bits were set */
+} abcs_status;
+
+/* Bits of the device status word (abcs_sync_status). */
+#define ABCS_DEV_CAPACITY  0x1u  /* a kernel skipped writes beyond coeff_capacity */
+#define ABCS_DEV_AMBIGUOUS 0x2u  /* a DD pilot coefficient within 1e-9 of T that is not exactly decidable */
+#define ABCS_DEV_NONFINITE 0x4u  /* IDA: ||z||^2 not finite for some image */
+#define ABCS_DEV_TIMEOUT   0x8u  /* a bounded spin-wait expired */
+#define ABCS_DEV_BADCOUNT  0x10u /* a count outside [0, B*B] was clamped */
+
+typedef enum abcs_variant {
+    ABCS_ZZ = 0,    /* non-adaptive L-DCT-ZZ: floor(B^2 subrate) coefficients per block (Eq. 26) */
+    ABCS_BBV = 1,   /* AL-DCT-BBV, Alg. 1 */
+    ABCS_DD = 2     /* AL-DCT-DD, Alg. 2 */
+} abcs_variant;
+
+typedef enum abcs_precision {
+    ABCS_FP32 = 0,        /* FP32 CUDA-core transforms */
+    ABCS_TC_FP16X2 = 1,   /* tensor-core FP16 hi+lo split products, FP32 accumulate (B = 16) */
+    ABCS_TC_BF16X2 = 2,   /* tensor-core BF16 hi+lo split products, FP32 accumulate (B = 16) */
+    ABCS_TC_BF16 = 3      /* tensor-core single BF16 product, FP32 accumulate (B = 16) */
+} abcs_precision;
+
+typedef enum abcs_denoiser {
+    ABCS_DEN_NONE = 0,    /* identity: x^{t+1} = x^t + A^T z^t (used to check the linear part) */
+    ABCS_DEN_TIDCT = 1,   /* plain: shift-averaged 8x8 DCT hard thresholding at lambda * sigma */
+    ABCS_DEN_CNN = 2      /* learned: residual CNN, weights from abcs_cnn_* */
+} abcs_denoiser;
+
+typedef struct abcs_handle abcs_handle;
+
+/* Derived scalars of one image (abcs_plan). */
+typedef struct abcs_plan_info {
+    int32_t H, W, B, variant;
+    int32_t nbh, nbw;          /* blocks per column / row after cropping (Eq. 20) */
+    int64_t n_blocks;          /* n_B = nbh * nbw */
+    int64_t N;                 /* cropped pixels n_B * B^2 */
+    int64_t M;                 /* floor(subrate * N) measurement budget */
+    double CF;                 /* compression factor 1 / subrate */
+    int32_t L, X0, nS;         /* Eqs. 16-18 (BBV sampling stride, offset, samples per side) */
+    int32_t m1;                /* phase-1 measurements per block: BBV 2 n_S, DD floor(B^2/(2 C_F)), ZZ 0 */
+    int32_t m_zz;              /* floor(B^2 subrate): L-DCT-ZZ count */
+    int32_t T;                 /* DD threshold (Table 1); 0 otherwise */
+    int32_t cap;               /* cap of m_i^2: B^2 - m1 */
+    int64_t M_bbv;             /* pixel differences measured by BBV (Eq. 21 as measured) */
+    int64_t R;                 /* phase-2 budget: BBV M - M_bbv, DD n_B m1 */
+    int64_t max_coeffs;        /* upper bound of sum m_i for this image (== M) */
+} abcs_plan_info;
+
+/* Create a handle bound to the current CUDA device.  It owns a device
+ * status word and a workspace grown on demand (cudaMalloc; growing waits
+ * for the device).  Uploads the DCT and zigzag tables to this device. */
+abcs_status abcs_create(abcs_handle** out);
+
+/* Free the handle's device memory.  Waits for the device first.  NULL is a no-op. */
+void abcs_destroy(abcs_handle* h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* abcs_last_error(void);
+
+/* Host only, no device work.  Computes the scalars of one H x W image for
+ * block size B (4, 8, 16 or 32), subrate in (0, 1] and a variant.
+ * INVALID_ARG: H < B, W < B, bad B or subrate, NULL out.
+ * UNSUPPORTED: BBV with L = floor(1/subrate) = 1 (Eq. 17 puts the first
+ * sample at column 0, outside the block). */
+abcs_status abcs_plan(int H, int W, int B, double subrate, int variant, abcs_plan_info* out);
+
+/* Sense a batch of n_img equally sized images (Alg. 1 / Alg. 2).
+ *   img      [device] uint8, see conventions (pitch, img_stride in bytes)
+ *   counts   [device] int32  [n_img * n_B]      out: m_i per block
+ *   offsets  [device] int64  [n_img * n_B + 1]  out: exclusive prefix of counts
+ *   coeffs   [device] float  [coeff_capacity]   out: packed measurements
+ *   pilot    [device] int32  [n_img * n_B] or NULL; out: BBV_i (BBV) or n_i (DD)
+ * coeff_capacity must be >= n_img * plan.M (the sum of m_i never exceeds M
+ * per image), else ABCS_ERR_CAPACITY before any work.  Counts are exact
+ * integers; the DD decisions |c| > T are taken on the exact coefficient.
+ * precision selects how the measured coefficients are computed; pilot
+ * decisions do not depend on it. */
+abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int W,
+                       int64_t pitch, int64_t img_stride, int B, double subrate,
+                       int variant, int precision, int32_t* counts, int64_t* offsets,
+                       float* coeffs, int64_t coeff_capacity, int32_t* pilot, void* stream);
+
+/* Block inverse 2D-DCT of the zero-filled measurements (A^T y, Fig. 1 I_o).
+ *   counts, offsets, coeffs [device] as written by abcs_sense
+ *   out     [device] float [n_img][Hc][Wc] (Hc = floor(H/B) B, Wc = floor(W/B) B), or NULL
+ *   out_u8  [device] uint8 [n_img][Hc][Wc] rounded half-to-even and clipped to [0,255], or NULL
+ * At least one of out / out_u8 must be non-NULL.  Counts outside [0, B^2]
+ * are clamped and flagged (ABCS_DEV_BADCOUNT). */
+abcs_status abcs_reconstruct(abcs_handle* h, const int32_t* counts, const int64_t* offsets,
+                             const float* coeffs, int n_img, int H, int W, int B, int precision,
+                             float* out, uint8_t* out_u8, void* stream);
+
+/* IDA (Sec. VI): x^0 = 0, z^{-1} = 0; for t < iters:
+ *   z^t = y - A x^t + z^{t-1} / damping,   sigma^t = sqrt(||z^t||^2 / m_img),
+ *   x^{t+1} = D_{sigma^t}(x^t + A^T z^t).
+ *   counts, offsets, y [device] as written by abcs_sense (m_img = the image's
+ *                      number of measurements)
+ *   denoiser           abcs_denoiser; lambda is the TI-DCT threshold factor
+ *   cnn_weights        [device] packed weights of abcs_cnn_* (ABCS_DEN_CNN) or NULL
+ *   x_out              [device] float [n_img][Hc][Wc], out: x^iters
+ *   sigma_trace        [device] float [n_img][iters] or NULL, out: sigma^t
+ * A non-finite sigma sets ABCS_DEV_NONFINITE; that image's later iterates
+ * are not meaningful. */
+abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offsets,
+                     const float* y, int n_img, int H, int W, int B, int iters, double damping,
+                     int denoiser, double lambda, const void* cnn_weights,
+                     float* x_out, float* sigma_trace, void* stream);
+
+/* The plain denoiser alone: for every image k, out = TI-DCT(in, lambda * sigma[k]).
+ *   in, out [device] float [n_img][H][W] (dense, H, W >= 1; in != out)
+ *   sigma   [device] float [n_img] */
+abcs_status abcs_denoise_tidct(abcs_handle* h, const float* in, int n_img, int H, int W,
+                               const float* sigma, double lambda, float* out, void* stream);
+
+/* Wait for `stream`, read and clear the device status word.  Returns
+ * ABCS_OK if no bit was set, else ABCS_ERR_DEVICE with the bits in *bits
+ * (bits may be NULL). */
+abcs_status abcs_sync_status(abcs_handle* h, void* stream, uint32_t* bits);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABCS_H */

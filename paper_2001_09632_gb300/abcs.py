@@ -1,0 +1,142 @@
+"""ctypes binding of libabcs.so (C ABI in include/abcs.h).
+
+Every function here has the name of the C entry point it calls and does
+argument marshalling only: torch tensors become device pointers, a torch
+stream becomes a cudaStream_t, non-OK statuses become AbcsError.  All
+compute happens in the library's CUDA kernels; there is no fallback, and
+importing this module fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libabcs.so")
+
+ZZ, BBV, DD = 0, 1, 2
+FP32, TC_FP16X2, TC_BF16X2, TC_BF16 = 0, 1, 2, 3
+DEN_NONE, DEN_TIDCT, DEN_CNN = 0, 1, 2
+VARIANTS = {"zz": ZZ, "bbv": BBV, "dd": DD}
+PRECISIONS = {"fp32": FP32, "fp16x2": TC_FP16X2, "bf16x2": TC_BF16X2, "bf16": TC_BF16}
+
+DEV_CAPACITY, DEV_AMBIGUOUS, DEV_NONFINITE, DEV_TIMEOUT, DEV_BADCOUNT = 0x1, 0x2, 0x4, 0x8, 0x10
+
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CAPACITY", 4: "OOM", 5: "CUDA",
+                6: "TIMEOUT", 7: "NONFINITE", 8: "DEVICE"}
+
+
+class AbcsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ABCS_{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class abcs_plan_info(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("B", C.c_int32), ("variant", C.c_int32),
+                ("nbh", C.c_int32), ("nbw", C.c_int32), ("n_blocks", C.c_int64), ("N", C.c_int64),
+                ("M", C.c_int64), ("CF", C.c_double), ("L", C.c_int32), ("X0", C.c_int32),
+                ("nS", C.c_int32), ("m1", C.c_int32), ("m_zz", C.c_int32), ("T", C.c_int32),
+                ("cap", C.c_int32), ("M_bbv", C.c_int64), ("R", C.c_int64), ("max_coeffs", C.c_int64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built: run `python -m paper_2001_09632_gb300.build` "
+                      "(there is no non-CUDA fallback)")
+lib = C.CDLL(LIB_PATH)
+
+_P, _I, _L, _D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+_SIGS = {
+    "abcs_create": [C.POINTER(C.c_void_p)],
+    "abcs_destroy": [_P],
+    "abcs_last_error": [],
+    "abcs_plan": [_I, _I, _I, _D, _I, C.POINTER(abcs_plan_info)],
+    "abcs_sense": [_P, _P, _I, _I, _I, _L, _L, _I, _D, _I, _I, _P, _P, _P, _L, _P, _P],
+    "abcs_reconstruct": [_P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P],
+    "abcs_ida": [_P, _P, _P, _P, _I, _I, _I, _I, _I, _D, _I, _D, _P, _P, _P, _P],
+    "abcs_denoise_tidct": [_P, _P, _I, _I, _I, _P, _D, _P, _P],
+    "abcs_sync_status": [_P, _P, C.POINTER(C.c_uint32)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_char_p if _name == "abcs_last_error" else (None if _name == "abcs_destroy" else C.c_int)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(status: int):
+    if status != 0:
+        raise AbcsError(status, lib.abcs_last_error().decode())
+
+
+def abcs_last_error() -> str:
+    return lib.abcs_last_error().decode()
+
+
+def abcs_create() -> int:
+    h = C.c_void_p()
+    _check(lib.abcs_create(C.byref(h)))
+    return h.value
+
+
+def abcs_destroy(h: int) -> None:
+    lib.abcs_destroy(h)
+
+
+def abcs_plan(H: int, W: int, B: int, subrate: float, variant: int) -> dict:
+    info = abcs_plan_info()
+    _check(lib.abcs_plan(H, W, B, subrate, variant, C.byref(info)))
+    return info.as_dict()
+
+
+def abcs_sense(h, img, n_img, H, W, pitch, img_stride, B, subrate, variant, precision,
+               counts, offsets, coeffs, coeff_capacity, pilot=None, stream=None) -> None:
+    _check(lib.abcs_sense(h, _ptr(img), n_img, H, W, pitch, img_stride, B, subrate, variant,
+                          precision, _ptr(counts), _ptr(offsets), _ptr(coeffs), coeff_capacity,
+                          _ptr(pilot), _stream(stream)))
+
+
+def abcs_reconstruct(h, counts, offsets, coeffs, n_img, H, W, B, precision, out=None, out_u8=None,
+                     stream=None) -> None:
+    _check(lib.abcs_reconstruct(h, _ptr(counts), _ptr(offsets), _ptr(coeffs), n_img, H, W, B,
+                                precision, _ptr(out), _ptr(out_u8), _stream(stream)))
+
+
+def abcs_ida(h, counts, offsets, y, n_img, H, W, B, iters, damping, denoiser, lam, cnn_weights,
+             x_out, sigma_trace=None, stream=None) -> None:
+    _check(lib.abcs_ida(h, _ptr(counts), _ptr(offsets), _ptr(y), n_img, H, W, B, iters, damping,
+                        denoiser, lam, _ptr(cnn_weights), _ptr(x_out), _ptr(sigma_trace),
+                        _stream(stream)))
+
+
+def abcs_denoise_tidct(h, inp, n_img, H, W, sigma, lam, out, stream=None) -> None:
+    _check(lib.abcs_denoise_tidct(h, _ptr(inp), n_img, H, W, _ptr(sigma), lam, _ptr(out),
+                                  _stream(stream)))
+
+
+def abcs_sync_status(h, stream=None) -> int:
+    """Waits for the stream; returns the device status bits (0 = clean)."""
+    bits = C.c_uint32(0)
+    st = lib.abcs_sync_status(h, _stream(stream), C.byref(bits))
+    if st not in (0, 8):
+        _check(st)
+    return bits.value

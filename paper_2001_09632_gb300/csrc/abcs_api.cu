@@ -1,0 +1,377 @@
+// C ABI of libabcs.so: argument checking, derived parameters, workspace,
+// and the enqueue order of the kernels of each call.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "abcs_common.cuh"
+
+using namespace abcs;
+
+struct abcs_handle {
+    int device = 0;
+    uint32_t* status = nullptr;   // device status word
+    void* ws = nullptr;           // workspace, grown on demand
+    size_t ws_bytes = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+abcs_status fail(abcs_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+abcs_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(ABCS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define ABCS_CUDA(call, what)                        \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool valid_B(int B) { return B == 4 || B == 8 || B == 16 || B == 32; }
+
+// Table 1: T by image height and C_F.  Columns exist for H = 256 and 512;
+// H >= 512 uses the 512 column, smaller images the 256 column.
+int dd_threshold(int H, double CF) {
+    if (CF <= 2.0) return 15;
+    if (H >= 512) return CF < 10.0 ? 30 : 60;
+    return CF < 3.33 ? 30 : 60;
+}
+
+abcs_status make_plan(int H, int W, int B, double subrate, int variant, abcs_plan_info* p) {
+    if (!p) return fail(ABCS_ERR_INVALID_ARG, "plan: NULL output");
+    if (!valid_B(B)) return fail(ABCS_ERR_INVALID_ARG, "B must be 4, 8, 16 or 32 (got %d)", B);
+    if (H < B || W < B) return fail(ABCS_ERR_INVALID_ARG, "image %dx%d smaller than one block", H, W);
+    if (!(subrate > 0.0 && subrate <= 1.0))
+        return fail(ABCS_ERR_INVALID_ARG, "subrate must be in (0, 1] (got %g)", subrate);
+    if (variant < ABCS_ZZ || variant > ABCS_DD) return fail(ABCS_ERR_INVALID_ARG, "bad variant %d", variant);
+    memset(p, 0, sizeof *p);
+    p->H = H; p->W = W; p->B = B; p->variant = variant;
+    p->nbh = H / B; p->nbw = W / B;
+    p->n_blocks = (int64_t)p->nbh * p->nbw;
+    p->N = p->n_blocks * B * B;
+    p->CF = 1.0 / subrate;                                      // C_F
+    const double Lf = std::floor(p->CF);                        // Eq. 16
+    p->L = Lf > 1e9 ? 1000000000 : (int)Lf;
+    p->X0 = p->L / 2;                                           // Eq. 17
+    p->nS = B / p->L;                                           // Eq. 18
+    p->M = (int64_t)std::floor(subrate * (double)p->N);
+    p->m_zz = (int)std::floor((double)(B * B) * subrate);       // Eq. 26: floor(n C_R)
+    p->max_coeffs = p->M;
+    if (variant == ABCS_BBV) {
+        if (p->L < 2)
+            return fail(ABCS_ERR_UNSUPPORTED, "BBV needs L = floor(1/subrate) >= 2 (Eq. 17 gives X0 = 0)");
+        p->m1 = 2 * p->nS;
+        p->M_bbv = 2LL * p->nS * p->n_blocks + (int64_t)p->nS * (p->nbh + p->nbw);
+        p->R = p->M > p->M_bbv ? p->M - p->M_bbv : 0;
+        p->cap = B * B - p->m1;
+    } else if (variant == ABCS_DD) {
+        p->m1 = (int)std::floor((double)(B * B) / (2.0 * p->CF));  // Alg. 2 step 2
+        p->T = dd_threshold(H, p->CF);
+        p->R = p->n_blocks * p->m1;                             // Eq. 23
+        p->cap = B * B - p->m1;
+    }
+    return ABCS_OK;
+}
+
+ImgGeom make_geom(int n_img, int H, int W, int B, int64_t pitch, int64_t img_stride) {
+    ImgGeom g;
+    g.n_img = n_img; g.H = H; g.W = W; g.B = B;
+    g.nbh = H / B; g.nbw = W / B;
+    g.Hc = g.nbh * B; g.Wc = g.nbw * B;
+    g.n_blocks = (int64_t)g.nbh * g.nbw;
+    g.pitch = pitch; g.img_stride = img_stride;
+    return g;
+}
+
+// Workspace carving: 256-byte aligned slices of one device allocation.
+struct Carver {
+    size_t off = 0;
+    template <typename T>
+    size_t take(size_t n) {
+        const size_t o = off;
+        off += (n * sizeof(T) + 255) & ~size_t(255);
+        return o;
+    }
+};
+
+abcs_status ensure_ws(abcs_handle* h, size_t bytes) {
+    if (bytes <= h->ws_bytes) return ABCS_OK;
+    if (h->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    const size_t want = bytes + bytes / 4;
+    if (cudaMalloc(&h->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ABCS_ERR_OOM, "workspace allocation of %zu bytes failed", want);
+    }
+    h->ws_bytes = want;
+    return ABCS_OK;
+}
+
+template <typename T>
+T* at(abcs_handle* h, size_t off) {
+    return reinterpret_cast<T*>(static_cast<char*>(h->ws) + off);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* abcs_last_error(void) { return g_err.c_str(); }
+
+abcs_status abcs_plan(int H, int W, int B, double subrate, int variant, abcs_plan_info* out) {
+    return make_plan(H, W, B, subrate, variant, out);
+}
+
+abcs_status abcs_create(abcs_handle** out) {
+    if (!out) return fail(ABCS_ERR_INVALID_ARG, "create: NULL output");
+    *out = nullptr;
+    int dev;
+    ABCS_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    ABCS_CUDA(upload_tables_pilot(), "upload tables");
+    ABCS_CUDA(upload_tables_dct(), "upload tables");
+    ABCS_CUDA(upload_tables_ida(), "upload tables");
+    abcs_handle* h = new abcs_handle;
+    h->device = dev;
+    if (cudaMalloc(&h->status, sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(ABCS_ERR_OOM, "status word allocation failed");
+    }
+    cudaMemset(h->status, 0, sizeof(uint32_t));
+    *out = h;
+    return ABCS_OK;
+}
+
+void abcs_destroy(abcs_handle* h) {
+    if (!h) return;
+    DeviceGuard dg(h->device);
+    cudaDeviceSynchronize();
+    if (h->ws) cudaFree(h->ws);
+    if (h->status) cudaFree(h->status);
+    delete h;
+}
+
+abcs_status abcs_sync_status(abcs_handle* h, void* stream, uint32_t* bits) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    DeviceGuard dg(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ABCS_CUDA(cudaStreamSynchronize(s), "stream sync");
+    uint32_t v = 0;
+    ABCS_CUDA(cudaMemcpy(&v, h->status, sizeof v, cudaMemcpyDeviceToHost), "status read");
+    ABCS_CUDA(cudaMemset(h->status, 0, sizeof(uint32_t)), "status reset");
+    if (bits) *bits = v;
+    if (v) return fail(ABCS_ERR_DEVICE, "device status bits 0x%x", v);
+    return ABCS_OK;
+}
+
+abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int W, int64_t pitch,
+                       int64_t img_stride, int B, double subrate, int variant, int precision,
+                       int32_t* counts, int64_t* offsets, float* coeffs, int64_t coeff_capacity,
+                       int32_t* pilot, void* stream) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    abcs_plan_info p;
+    abcs_status st = make_plan(H, W, B, subrate, variant, &p);
+    if (st) return st;
+    if (n_img < 1 || n_img > 65535) return fail(ABCS_ERR_INVALID_ARG, "n_img must be in [1, 65535]");
+    if (!img || !counts || !offsets || !coeffs) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (pitch < W) return fail(ABCS_ERR_INVALID_ARG, "pitch %lld < W %d", (long long)pitch, W);
+    if (n_img > 1 && img_stride < pitch * H)
+        return fail(ABCS_ERR_INVALID_ARG, "img_stride smaller than pitch * H");
+    if (precision != ABCS_FP32)
+        return fail(ABCS_ERR_UNSUPPORTED, "precision %d is not built for sensing", precision);
+    if (coeff_capacity < (int64_t)n_img * p.M)
+        return fail(ABCS_ERR_CAPACITY, "coeff_capacity %lld < n_img * M = %lld",
+                    (long long)coeff_capacity, (long long)n_img * p.M);
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(ABCS_ERR_CUDA, "cannot select the handle's device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    const int64_t nb_all = (int64_t)n_img * p.n_blocks;
+    Carver c;
+    const size_t o_w = c.take<int32_t>(pilot ? 1 : nb_all);
+    const size_t o_wsum = c.take<unsigned long long>(n_img);
+    const size_t o_tot = c.take<int64_t>(n_img);
+    st = ensure_ws(h, c.off);
+    if (st) return st;
+
+    SenseArgs a{};
+    a.g = make_geom(n_img, H, W, B, pitch, img_stride);
+    a.img = img;
+    a.variant = variant;
+    a.precision = precision;
+    a.L = p.L; a.X0 = p.X0; a.nS = p.nS; a.m1 = p.m1; a.m_zz = p.m_zz; a.T = p.T; a.cap = p.cap;
+    a.R = p.R;
+    a.counts = counts;
+    a.offsets = offsets;
+    a.coeffs = coeffs;
+    a.capacity = coeff_capacity;
+    a.w = pilot ? pilot : at<int32_t>(h, o_w);
+    a.wsum = at<unsigned long long>(h, o_wsum);
+    a.img_total = at<int64_t>(h, o_tot);
+    a.status = h->status;
+
+    ABCS_CUDA(cudaMemsetAsync(a.wsum, 0, n_img * sizeof(unsigned long long), s), "memset");
+    int mode = 0;
+    if (variant == ABCS_BBV && p.nS > 0) {
+        ABCS_CUDA(launch_bbv_pilot(a, s), "bbv_pilot launch");
+        mode = 1;
+    } else if (variant == ABCS_DD) {
+        ABCS_CUDA(launch_dd_pilot(a, s), "dd_pilot launch");
+        mode = 2;
+    } else {
+        mode = (variant == ABCS_BBV) ? 3 : 0;
+        if (pilot) ABCS_CUDA(cudaMemsetAsync(pilot, 0, nb_all * sizeof(int32_t), s), "memset");
+    }
+    ABCS_CUDA(launch_allocate(a, mode, s), "allocate launch");
+    ABCS_CUDA(launch_sense_pack(a, s), "sense_pack launch");
+    return ABCS_OK;
+}
+
+abcs_status abcs_reconstruct(abcs_handle* h, const int32_t* counts, const int64_t* offsets,
+                             const float* coeffs, int n_img, int H, int W, int B, int precision,
+                             float* out, uint8_t* out_u8, void* stream) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    if (!valid_B(B)) return fail(ABCS_ERR_INVALID_ARG, "B must be 4, 8, 16 or 32");
+    if (H < B || W < B) return fail(ABCS_ERR_INVALID_ARG, "image smaller than one block");
+    if (n_img < 1 || n_img > 65535) return fail(ABCS_ERR_INVALID_ARG, "n_img must be in [1, 65535]");
+    if (!counts || !offsets || !coeffs || (!out && !out_u8))
+        return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (precision != ABCS_FP32)
+        return fail(ABCS_ERR_UNSUPPORTED, "precision %d is not built for reconstruction", precision);
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(ABCS_ERR_CUDA, "cannot select the handle's device");
+    ReconArgs a{};
+    a.g = make_geom(n_img, H, W, B, W, 0);
+    a.precision = precision;
+    a.counts = counts;
+    a.offsets = offsets;
+    a.coeffs = coeffs;
+    a.out = out;
+    a.out_u8 = out_u8;
+    a.status = h->status;
+    ABCS_CUDA(launch_reconstruct(a, static_cast<cudaStream_t>(stream)), "reconstruct launch");
+    return ABCS_OK;
+}
+
+abcs_status abcs_denoise_tidct(abcs_handle* h, const float* in, int n_img, int H, int W,
+                               const float* sigma, double lambda, float* out, void* stream) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    if (!in || !out || !sigma) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (in == out) return fail(ABCS_ERR_INVALID_ARG, "in and out must differ");
+    if (H < 1 || W < 1 || n_img < 1 || n_img > 65535) return fail(ABCS_ERR_INVALID_ARG, "bad size");
+    if (!(lambda >= 0.0)) return fail(ABCS_ERR_INVALID_ARG, "lambda must be >= 0");
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(ABCS_ERR_CUDA, "cannot select the handle's device");
+    ABCS_CUDA(launch_tidct(in, out, n_img, H, W, sigma, (float)lambda, static_cast<cudaStream_t>(stream)),
+              "tidct launch");
+    return ABCS_OK;
+}
+
+abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offsets, const float* y,
+                     int n_img, int H, int W, int B, int iters, double damping, int denoiser,
+                     double lambda, const void* cnn_weights, float* x_out, float* sigma_trace,
+                     void* stream) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    if (!valid_B(B)) return fail(ABCS_ERR_INVALID_ARG, "B must be 4, 8, 16 or 32");
+    if (H < B || W < B) return fail(ABCS_ERR_INVALID_ARG, "image smaller than one block");
+    if (n_img < 1 || n_img > 65535) return fail(ABCS_ERR_INVALID_ARG, "n_img must be in [1, 65535]");
+    if (!counts || !offsets || !y || !x_out) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (iters < 0) return fail(ABCS_ERR_INVALID_ARG, "iters must be >= 0");
+    if (!(damping > 0.0)) return fail(ABCS_ERR_INVALID_ARG, "damping must be > 0");
+    if (denoiser < ABCS_DEN_NONE || denoiser > ABCS_DEN_CNN)
+        return fail(ABCS_ERR_INVALID_ARG, "bad denoiser %d", denoiser);
+    if (denoiser == ABCS_DEN_TIDCT && !(lambda >= 0.0))
+        return fail(ABCS_ERR_INVALID_ARG, "lambda must be >= 0");
+    if (denoiser == ABCS_DEN_CNN) {
+        if (!cnn_weights) return fail(ABCS_ERR_INVALID_ARG, "CNN denoiser needs weights");
+        return fail(ABCS_ERR_UNSUPPORTED, "CNN denoiser is not built in this library");
+    }
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(ABCS_ERR_CUDA, "cannot select the handle's device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ImgGeom g = make_geom(n_img, H, W, B, W, 0);
+    const int64_t npx = (int64_t)n_img * g.Hc * g.Wc;
+    if (iters == 0) {
+        ABCS_CUDA(cudaMemsetAsync(x_out, 0, npx * sizeof(float), s), "memset");
+        return ABCS_OK;
+    }
+    const int cpi = ida_ctas_per_image(g);
+    Carver c;
+    const size_t o_r0 = c.take<float>(npx);
+    const size_t o_r1 = c.take<float>(npx);
+    const size_t o_z0 = c.take<float>(npx);     // sum of counts <= pixels
+    const size_t o_z1 = c.take<float>(npx);
+    const size_t o_part = c.take<double>((size_t)n_img * cpi);
+    const size_t o_sig = c.take<float>(n_img);
+    abcs_status st = ensure_ws(h, c.off);
+    if (st) return st;
+    float* rbuf[2] = {at<float>(h, o_r0), at<float>(h, o_r1)};
+    float* zbuf[2] = {at<float>(h, o_z0), at<float>(h, o_z1)};
+    float* sig = at<float>(h, o_sig);
+
+    IdaLinArgs a{};
+    a.g = g;
+    a.counts = counts;
+    a.offsets = offsets;
+    a.y = y;
+    a.partial = at<double>(h, o_part);
+    a.inv_df = (float)(1.0 / damping);
+    a.status = h->status;
+    const float* x_cur = nullptr;        // x^0 = 0
+    const float* z_prev = nullptr;       // z^{-1} = 0
+    for (int t = 0; t < iters; ++t) {
+        a.x = x_cur;
+        a.z_prev = z_prev;
+        a.z = zbuf[t & 1];
+        a.r = rbuf[t & 1];
+        ABCS_CUDA(launch_ida_linear(a, s), "ida_linear launch");
+        ABCS_CUDA(launch_ida_sigma(g, offsets, a.partial, sig, sigma_trace, iters, t, h->status, s),
+                  "ida_sigma launch");
+        if (denoiser == ABCS_DEN_TIDCT) {
+            ABCS_CUDA(launch_tidct(a.r, x_out, n_img, g.Hc, g.Wc, sig, (float)lambda, s), "tidct launch");
+            x_cur = x_out;
+        } else {
+            x_cur = a.r;                  // identity: x^{t+1} = r^t
+        }
+        z_prev = a.z;
+    }
+    if (x_cur != x_out)
+        ABCS_CUDA(cudaMemcpyAsync(x_out, x_cur, npx * sizeof(float), cudaMemcpyDeviceToDevice, s),
+                  "copy result");
+    return ABCS_OK;
+}
+
+}  // extern "C"

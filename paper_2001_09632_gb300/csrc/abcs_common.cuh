@@ -1,0 +1,182 @@
+// Shared device/host definitions of the ABCS CUDA library (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/abcs.h"
+
+#define ABCS_HD __host__ __device__ __forceinline__
+#define ABCS_D __device__ __forceinline__
+
+namespace abcs {
+
+// ---------------------------------------------------------------------------
+// DCT / zigzag tables.  Every translation unit that runs transforms keeps its
+// own copy in __constant__ memory; abcs_create() uploads them (per device).
+// Indices are compile-time constants inside the unrolled transforms, so the
+// coefficients become constant-bank operands of the FMAs.
+// ---------------------------------------------------------------------------
+struct HostTables {
+    float Df4[16], Df8[64], Df16[256], Df32[1024];          // D[k][n], orthonormal DCT-II
+    double Dd4[16], Dd8[64], Dd16[256], Dd32[1024];
+    uint16_t zzpos4[16], zzpos8[64], zzpos16[256], zzpos32[1024];   // rank -> u*B + v
+};
+const HostTables& host_tables();   // computed once on the host in double
+
+#define ABCS_TU_TABLES(NAME)                                                        \
+    static __constant__ float c_Df4[16], c_Df8[64], c_Df16[256], c_Df32[1024];       \
+    static __constant__ double c_Dd4[16], c_Dd8[64], c_Dd16[256], c_Dd32[1024];      \
+    static __constant__ uint16_t c_zz4[16], c_zz8[64], c_zz16[256], c_zz32[1024];    \
+    cudaError_t upload_tables_##NAME() {                                             \
+        const HostTables& t = host_tables();                                         \
+        cudaError_t e = cudaSuccess;                                                 \
+        if (!e) e = cudaMemcpyToSymbol(c_Df4, t.Df4, sizeof t.Df4);                  \
+        if (!e) e = cudaMemcpyToSymbol(c_Df8, t.Df8, sizeof t.Df8);                  \
+        if (!e) e = cudaMemcpyToSymbol(c_Df16, t.Df16, sizeof t.Df16);               \
+        if (!e) e = cudaMemcpyToSymbol(c_Df32, t.Df32, sizeof t.Df32);               \
+        if (!e) e = cudaMemcpyToSymbol(c_Dd4, t.Dd4, sizeof t.Dd4);                  \
+        if (!e) e = cudaMemcpyToSymbol(c_Dd8, t.Dd8, sizeof t.Dd8);                  \
+        if (!e) e = cudaMemcpyToSymbol(c_Dd16, t.Dd16, sizeof t.Dd16);               \
+        if (!e) e = cudaMemcpyToSymbol(c_Dd32, t.Dd32, sizeof t.Dd32);               \
+        if (!e) e = cudaMemcpyToSymbol(c_zz4, t.zzpos4, sizeof t.zzpos4);            \
+        if (!e) e = cudaMemcpyToSymbol(c_zz8, t.zzpos8, sizeof t.zzpos8);            \
+        if (!e) e = cudaMemcpyToSymbol(c_zz16, t.zzpos16, sizeof t.zzpos16);         \
+        if (!e) e = cudaMemcpyToSymbol(c_zz32, t.zzpos32, sizeof t.zzpos32);         \
+        return e;                                                                    \
+    }                                                                                \
+    template <int B> ABCS_D float Dc(int k, int n) {                                 \
+        if constexpr (B == 4) return c_Df4[k * 4 + n];                               \
+        else if constexpr (B == 8) return c_Df8[k * 8 + n];                          \
+        else if constexpr (B == 16) return c_Df16[k * 16 + n];                       \
+        else return c_Df32[k * 32 + n];                                              \
+    }                                                                                \
+    template <int B> ABCS_D double Dd(int k, int n) {                                \
+        if constexpr (B == 4) return c_Dd4[k * 4 + n];                               \
+        else if constexpr (B == 8) return c_Dd8[k * 8 + n];                          \
+        else if constexpr (B == 16) return c_Dd16[k * 16 + n];                       \
+        else return c_Dd32[k * 32 + n];                                              \
+    }                                                                                \
+    template <int B> ABCS_D int zz_pos(int rank) {                                   \
+        if constexpr (B == 4) return c_zz4[rank];                                    \
+        else if constexpr (B == 8) return c_zz8[rank];                               \
+        else if constexpr (B == 16) return c_zz16[rank];                             \
+        else return c_zz32[rank];                                                    \
+    }
+
+cudaError_t upload_tables_pilot();
+cudaError_t upload_tables_dct();
+cudaError_t upload_tables_ida();
+
+// zigzag rank of (u, v) in a B x B block, JPEG orientation: diagonal s = u+v;
+// odd s runs with u increasing, even s with u decreasing.
+ABCS_HD int zz_rank(int u, int v, int B) {
+    const int s = u + v;
+    if (s < B) {
+        const int base = s * (s + 1) / 2;
+        return base + ((s & 1) ? u : (s - u));
+    }
+    const int rem = 2 * B - 1 - s;                 // entries on diagonal s
+    const int base = B * B - rem * (rem + 1) / 2;
+    return base + ((s & 1) ? (u - (s - B + 1)) : (B - 1 - u));
+}
+
+// ---------------------------------------------------------------------------
+// Launch geometry shared by the block-transform kernels: a CTA covers one
+// block row of one image, 256 pixel columns wide (256 / B blocks), one
+// thread per pixel column.
+// ---------------------------------------------------------------------------
+constexpr int kTileCols = 256;
+
+struct ImgGeom {
+    int n_img;
+    int H, W;          // original image size (pixels)
+    int B;
+    int nbh, nbw;      // block grid after cropping
+    int Hc, Wc;        // cropped size
+    int64_t n_blocks;  // per image
+    int64_t pitch;     // bytes between rows (uint8 inputs)
+    int64_t img_stride;// bytes between images (uint8 inputs)
+};
+
+// Device status bits are OR-ed into one word owned by the handle.
+ABCS_D void set_status(uint32_t* st, uint32_t bits) { atomicOr(st, bits); }
+
+template <typename T>
+ABCS_D T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over a CTA of blockDim.x threads (multiple of 32, <= 1024).  `sh` needs
+// 32 elements.  The result is valid in every thread.  Fixed order.
+template <typename T>
+ABCS_D T block_sum(T v, T* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    T t = (lane < nw) ? sh[lane] : T(0);
+    t = warp_sum(t);
+    return t;
+}
+
+}  // namespace abcs
+
+// Launchers (host side, one per translation unit).
+namespace abcs {
+struct SenseArgs {
+    ImgGeom g;
+    const uint8_t* img;
+    int variant, precision;
+    int L, X0, nS, m1, m_zz, T, cap;
+    int64_t R;
+    int32_t* counts;
+    int64_t* offsets;
+    float* coeffs;
+    int64_t capacity;
+    int32_t* w;          // pilot per block (BBV_i or n_i)
+    unsigned long long* wsum;   // per image sum of w
+    int64_t* img_total;  // per image sum of counts
+    uint32_t* status;
+};
+cudaError_t launch_bbv_pilot(const SenseArgs& a, cudaStream_t s);
+cudaError_t launch_dd_pilot(const SenseArgs& a, cudaStream_t s);
+cudaError_t launch_allocate(const SenseArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_sense_pack(const SenseArgs& a, cudaStream_t s);
+
+struct ReconArgs {
+    ImgGeom g;
+    int precision;
+    const int32_t* counts;
+    const int64_t* offsets;
+    const float* coeffs;
+    float* out;
+    uint8_t* out_u8;
+    uint32_t* status;
+};
+cudaError_t launch_reconstruct(const ReconArgs& a, cudaStream_t s);
+
+struct IdaLinArgs {
+    ImgGeom g;
+    const int32_t* counts;
+    const int64_t* offsets;
+    const float* y;
+    const float* x;        // NULL: x = 0
+    const float* z_prev;   // NULL: z_prev = 0
+    float* z;
+    float* r;
+    double* partial;       // one per CTA
+    float inv_df;
+    uint32_t* status;
+};
+cudaError_t launch_ida_linear(const IdaLinArgs& a, cudaStream_t s);
+cudaError_t launch_ida_sigma(const ImgGeom& g, const int64_t* offsets, const double* partial,
+                             float* sigma, float* sigma_trace, int iters, int t, uint32_t* status,
+                             cudaStream_t s);
+int ida_ctas_per_image(const ImgGeom& g);
+cudaError_t launch_tidct(const float* in, float* out, int n_img, int H, int W, const float* sigma,
+                         float lambda, cudaStream_t s);
+}  // namespace abcs

@@ -1,0 +1,165 @@
+// Phase-1 pilot estimates: block boundary variation (Eq. 19) and the DCT
+// domain count n_i (Alg. 2 steps 2-4, Sec. V-B).  Both are exact integers.
+#include "abcs_common.cuh"
+
+namespace abcs {
+ABCS_TU_TABLES(pilot)
+}  // namespace abcs
+
+#include "dct_tile.cuh"
+
+namespace abcs {
+
+// ---------------------------------------------------------------------------
+// BBV_i = sum_{j < n_S} |P(1,a+1)-P(1,a)| + |P(b+1,1)-P(b,1)|
+//                     + |P(B+1,a+1)-P(B+1,a)| + |P(b+1,B+1)-P(b,B+1)|,
+// a = b = X0 + jL (1-based within block i's frame).  Row B+1 / column B+1 is
+// the first row / column of the block below / to the right; the bottom block
+// row and the right block column use their own row B / column B instead.
+// One thread per block; the per-image sum is an exact 64-bit integer.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) bbv_kernel(const uint8_t* __restrict__ img, ImgGeom g,
+                                                  int L, int X0, int nS, int32_t* __restrict__ w,
+                                                  unsigned long long* __restrict__ wsum) {
+    __shared__ unsigned long long sh[32];
+    const int k = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (i < g.n_blocks) {
+        const int B = g.B;
+        const int bi = (int)(i / g.nbw), bj = (int)(i % g.nbw);
+        const uint8_t* P = img + (int64_t)k * g.img_stride;
+        const int64_t p = g.pitch;
+        const int r0 = bi * B, c0 = bj * B;
+        const int below = (bi + 1 < g.nbh) ? r0 + B : r0 + B - 1;
+        const int right = (bj + 1 < g.nbw) ? c0 + B : c0 + B - 1;
+        int s = 0;
+        for (int j = 0; j < nS; ++j) {
+            const int a = X0 + j * L;   // 1-based; pair (a, a+1) -> 0-based (a-1, a)
+            s += abs((int)__ldg(P + r0 * p + c0 + a) - (int)__ldg(P + r0 * p + c0 + a - 1));
+            s += abs((int)__ldg(P + (r0 + a) * p + c0) - (int)__ldg(P + (r0 + a - 1) * p + c0));
+            s += abs((int)__ldg(P + below * p + c0 + a) - (int)__ldg(P + below * p + c0 + a - 1));
+            s += abs((int)__ldg(P + (r0 + a) * p + right) - (int)__ldg(P + (r0 + a - 1) * p + right));
+        }
+        w[(int64_t)k * g.n_blocks + i] = s;
+        v = (unsigned long long)s;
+    }
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0 && v) atomicAdd(wsum + k, v);
+}
+
+cudaError_t launch_bbv_pilot(const SenseArgs& a, cudaStream_t s) {
+    dim3 grid((unsigned)((a.g.n_blocks + 255) / 256), (unsigned)a.g.n_img);
+    bbv_kernel<<<grid, 256, 0, s>>>(a.img, a.g, a.L, a.X0, a.nS, a.w, a.wsum);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// DD pilot: n_i = #{ zigzag rank j < m1 : |c_j| > T }, decided on the exact
+// coefficient.  FP32 coefficients come with a rigorous error bound; any
+// coefficient within that band of T is re-evaluated: exactly in integers for
+// (u, v) in {0, B/2}^2 (those coefficients are S / B with integer S), else
+// in FP64, whose error is < 1e-11 here; an irrational coefficient within
+// 1e-9 of T is flagged ABCS_DEV_AMBIGUOUS and counted as not exceeding.
+// ---------------------------------------------------------------------------
+template <int B>
+ABCS_D int rational_sign(int u, int n) {
+    if (u == 0) return 1;
+    return (((n + 1) >> 1) & 1) ? -1 : 1;    // sign of cos(pi (2n+1) / 4)
+}
+
+template <int B>
+ABCS_D bool dd_exceeds_exact(const uint8_t* Xs, int blk, int pos, int T, uint32_t* status) {
+    const int u = pos / B, v = pos % B;
+    const int col0 = blk * B;
+    constexpr int H2 = B / 2;
+    if ((u == 0 || u == H2) && (v == 0 || v == H2)) {
+        long long S = 0;
+        for (int n = 0; n < B; ++n)
+            for (int m = 0; m < B; ++m)
+                S += rational_sign<B>(u, n) * rational_sign<B>(v, m) * (int)Xs[n * kTileCols + col0 + m];
+        return llabs(S) > (long long)T * B;
+    }
+    double c = 0.0;
+    for (int m = 0; m < B; ++m) {
+        double col = 0.0;
+        for (int n = 0; n < B; ++n) col = fma(Dd<B>(u, n), (double)Xs[n * kTileCols + col0 + m], col);
+        c = fma(col, Dd<B>(v, m), c);
+    }
+    const double d = fabs(c) - (double)T;
+    if (fabs(d) <= 1e-9) {
+        set_status(status, ABCS_DEV_AMBIGUOUS);
+        return false;
+    }
+    return d > 0.0;
+}
+
+template <int B>
+__global__ void __launch_bounds__(256) dd_pilot_kernel(SenseArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    using Tl = Tile<B>;
+    uint8_t* Xs = smem;
+    float* Ts = reinterpret_cast<float*>(smem + Tl::XS_BYTES);
+    float* Zs = Ts + Tl::TS_FLOATS;
+    __shared__ int ncount[Tl::NB];
+    __shared__ unsigned long long sh[32];
+
+    const ImgGeom& g = a.g;
+    const int k = blockIdx.z, bi = blockIdx.y, bj0 = blockIdx.x * Tl::NB;
+    const int nblk = min(Tl::NB, g.nbw - bj0);
+    const uint8_t* img = a.img + (int64_t)k * g.img_stride;
+    load_u8_tile<B>(Xs, img, g.pitch, bi * B, bj0 * B, g.W);
+    if (threadIdx.x < Tl::NB) ncount[threadIdx.x] = 0;
+    __syncthreads();
+    float x[B];
+#pragma unroll
+    for (int n = 0; n < B; ++n) x[n] = (float)Xs[n * kTileCols + threadIdx.x];
+    fwd_dct_tile_fp32<B>(x, Ts, Zs);
+
+    // rigorous FP32 band: (4B + 8) u * 255 * B bounds |c_fp32 - c| (see DESIGN)
+    const float band = (4.f * B + 8.f) * 5.9604645e-8f * 255.f * B;
+    const float T = (float)a.T;
+    const int m1 = a.m1;
+    for (int e = threadIdx.x; e < nblk * m1; e += blockDim.x) {
+        const int b = e / m1, r = e % m1;
+        const float c = fabsf(Zs[b * B * B + r]);
+        bool hit;
+        if (c > T + band) hit = true;
+        else if (c < T - band) hit = false;
+        else hit = dd_exceeds_exact<B>(Xs, b, zz_pos<B>(r), a.T, a.status);
+        if (hit) atomicAdd(&ncount[b], 1);
+    }
+    __syncthreads();
+    unsigned long long v = 0;
+    if (threadIdx.x < nblk) {
+        const int n = ncount[threadIdx.x];
+        a.w[(int64_t)k * g.n_blocks + (int64_t)bi * g.nbw + bj0 + threadIdx.x] = n;
+        v = (unsigned long long)n;
+    }
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0 && v) atomicAdd(a.wsum + k, v);
+}
+
+template <int B>
+static cudaError_t launch_dd_B(const SenseArgs& a, cudaStream_t s) {
+    using Tl = Tile<B>;
+    const size_t smem = Tl::XS_BYTES + (Tl::TS_FLOATS + Tl::ZS_FLOATS) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(dd_pilot_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e) return e;
+    dim3 grid((unsigned)((a.g.nbw + Tl::NB - 1) / Tl::NB), (unsigned)a.g.nbh, (unsigned)a.g.n_img);
+    dd_pilot_kernel<B><<<grid, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dd_pilot(const SenseArgs& a, cudaStream_t s) {
+    switch (a.g.B) {
+        case 4: return launch_dd_B<4>(a, s);
+        case 8: return launch_dd_B<8>(a, s);
+        case 16: return launch_dd_B<16>(a, s);
+        case 32: return launch_dd_B<32>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace abcs

@@ -26,3 +26,14 @@ def load_golden_matrix(name):
 @pytest.fixture
 def golden():
     return load_golden_matrix
+
+
+@pytest.fixture(scope="session")
+def handle():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2001_09632_gb300 import abcs
+    h = abcs.abcs_create()
+    yield h
+    abcs.abcs_destroy(h)
