@@ -114,6 +114,38 @@ ABCS_D void inv_dct_tile_fp32(const float* Zs, float* Ts, float (&x)[B]) {
     __syncthreads();
 }
 
+// Called by warp 0 only.  rel[b] = sum_{j<b} c_j for b = 0 .. nblk, with
+// c_j = counts[j] clamped to [0, B*B] (a clamp sets ABCS_DEV_BADCOUNT).
+// nblk <= 64: lane l owns blocks 2l and 2l+1.
+template <int B>
+ABCS_D void tile_prefix(const int32_t* __restrict__ counts, int nblk, int* rel, uint32_t* status) {
+    const int lane = threadIdx.x & 31;
+    const int i0 = 2 * lane, i1 = 2 * lane + 1;
+    int c0 = 0, c1 = 0;
+    bool bad = false;
+    if (i0 < nblk) {
+        c0 = __ldg(counts + i0);
+        if (c0 < 0 || c0 > B * B) { bad = true; c0 = c0 < 0 ? 0 : B * B; }
+    }
+    if (i1 < nblk) {
+        c1 = __ldg(counts + i1);
+        if (c1 < 0 || c1 > B * B) { bad = true; c1 = c1 < 0 ? 0 : B * B; }
+    }
+    const int pair = c0 + c1;
+    int incl = pair;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int excl = incl - pair;
+    if (i0 < nblk) rel[i0] = excl;
+    if (i1 < nblk) rel[i1] = excl + c0;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 0) rel[nblk] = total;
+    if (__any_sync(0xffffffffu, bad) && lane == 0 && status) set_status(status, ABCS_DEV_BADCOUNT);
+}
+
 // Index of the block owning packed element e, given rel[0..nb] (exclusive
 // prefix of the tile's counts, rel[0] = 0): largest b with rel[b] <= e.
 ABCS_D int find_block(const int* rel, int nb, int e) {

@@ -45,13 +45,8 @@ __global__ void __launch_bounds__(256) sense_pack_kernel(SenseArgs a) {
         if (threadIdx.x == 0) {
             s_base = base;
             s_off0 = a.offsets[gi0];
-            int acc = 0;
-            for (int b = 0; b < nblk; ++b) {
-                rel[b] = acc;
-                acc += a.counts[gi0 + b];
-            }
-            rel[nblk] = acc;
         }
+        tile_prefix<B>(a.counts + gi0, nblk, rel, nullptr);
     }
     const uint8_t* img = a.img + (int64_t)k * g.img_stride;
     load_u8_tile<B>(Xs, img, g.pitch, bi * B, bj0 * B, g.W);
@@ -97,33 +92,24 @@ __global__ void __launch_bounds__(256) recon_kernel(ReconArgs a) {
     float* Ts = reinterpret_cast<float*>(smem);
     float* Zs = Ts + Tl::TS_FLOATS;
     __shared__ int rel[Tl::NB + 1];
-    __shared__ int64_t goff[Tl::NB];
+    __shared__ int64_t s_start;
 
     const ImgGeom& g = a.g;
     const int k = blockIdx.z, bi = blockIdx.y, bj0 = blockIdx.x * Tl::NB;
     const int nblk = min(Tl::NB, g.nbw - bj0);
     const int64_t gi0 = (int64_t)k * g.n_blocks + (int64_t)bi * g.nbw + bj0;
 
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        bool bad = false;
-        for (int b = 0; b < nblk; ++b) {
-            int c = a.counts[gi0 + b];
-            if (c < 0 || c > B * B) { bad = true; c = c < 0 ? 0 : B * B; }
-            rel[b] = acc;
-            acc += c;
-        }
-        rel[nblk] = acc;
-        if (bad) set_status(a.status, ABCS_DEV_BADCOUNT);
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) s_start = a.offsets[gi0];
+        tile_prefix<B>(a.counts + gi0, nblk, rel, a.status);
     }
-    if (threadIdx.x < nblk) goff[threadIdx.x] = a.offsets[gi0 + threadIdx.x];
     for (int i = threadIdx.x; i < Tl::ZS_FLOATS; i += blockDim.x) Zs[i] = 0.f;
     __syncthreads();
     const int total = rel[nblk];
+    const float* src = a.coeffs + s_start;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int b = find_block(rel, nblk, e);
-        const int r = e - rel[b];
-        Zs[b * B * B + r] = __ldg(a.coeffs + goff[b] + r);
+        Zs[b * B * B + (e - rel[b])] = __ldg(src + e);
     }
     __syncthreads();
     float x[B];

@@ -25,26 +25,17 @@ __global__ void __launch_bounds__(256) ida_linear_kernel(IdaLinArgs a) {
     float* Ts = reinterpret_cast<float*>(smem);
     float* Zs = Ts + Tl::TS_FLOATS;
     __shared__ int rel[Tl::NB + 1];
-    __shared__ int64_t goff[Tl::NB];
+    __shared__ int64_t s_start;
     __shared__ double shd[32];
 
     const ImgGeom& g = a.g;
     const int k = blockIdx.z, bi = blockIdx.y, bj0 = blockIdx.x * Tl::NB;
     const int nblk = min(Tl::NB, g.nbw - bj0);
     const int64_t gi0 = (int64_t)k * g.n_blocks + (int64_t)bi * g.nbw + bj0;
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        bool bad = false;
-        for (int b = 0; b < nblk; ++b) {
-            int c = a.counts[gi0 + b];
-            if (c < 0 || c > B * B) { bad = true; c = c < 0 ? 0 : B * B; }
-            rel[b] = acc;
-            acc += c;
-        }
-        rel[nblk] = acc;
-        if (bad) set_status(a.status, ABCS_DEV_BADCOUNT);
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) s_start = a.offsets[gi0];
+        tile_prefix<B>(a.counts + gi0, nblk, rel, a.status);
     }
-    if (threadIdx.x < nblk) goff[threadIdx.x] = a.offsets[gi0 + threadIdx.x];
 
     const bool valid = threadIdx.x < nblk * B;
     const int64_t o = (int64_t)k * g.Hc * g.Wc + (int64_t)(bi * B) * g.Wc + bj0 * B + threadIdx.x;
@@ -58,7 +49,7 @@ __global__ void __launch_bounds__(256) ida_linear_kernel(IdaLinArgs a) {
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int b = find_block(rel, nblk, e);
         const int r = e - rel[b];
-        const int64_t gi = goff[b] + r;
+        const int64_t gi = s_start + e;
         float* zc = Zs + b * B * B + r;
         const float c = *zc;
         const float zp = a.z_prev ? __ldg(a.z_prev + gi) : 0.f;

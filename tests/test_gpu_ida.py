@@ -12,10 +12,12 @@ from tests import gpu_util as G
 pytestmark = pytest.mark.gpu
 
 
-def _ambiguous_mask(r, thr, rel=2e-4):
+def _ambiguous_mask(r, thr, band=2e-4):
     """Pixels covered by an 8x8 window (of the 64 shifts) holding an AC
-    coefficient within rel * thr of the threshold: there FP32 and FP64 may
-    legitimately take different keep/zero decisions."""
+    coefficient within `band` of the threshold: there FP32 and FP64 may
+    legitimately take different keep/zero decisions.  The band is ~20x the
+    typical FP32 error of an 8x8 DCT coefficient of [0, 255] data (~1e-5);
+    a flip outside it fails the test."""
     H, W = r.shape
     D = O.dct_matrix(8)
     mask = np.zeros((H, W), bool)
@@ -27,7 +29,7 @@ def _ambiguous_mask(r, thr, rel=2e-4):
             cols = np.arange(-sx, -sx + 8 * nx)
             ext = r[O.reflect_index(rows, H)][:, O.reflect_index(cols, W)]
             C = D @ ext.reshape(ny, 8, nx, 8).transpose(0, 2, 1, 3) @ D.T
-            amb = np.abs(np.abs(C) - thr) <= rel * thr
+            amb = np.abs(np.abs(C) - thr) <= band
             amb[:, :, 0, 0] = False
             win = amb.any(axis=(2, 3))
             full = np.repeat(np.repeat(win, 8, 0), 8, 1)
@@ -51,7 +53,7 @@ def test_tidct_parity(handle, H, W, sigma, lam):
     r32 = d_in.cpu().numpy()[0].astype(float)
     ref = O.tidct_denoise(r32, float(np.float32(sigma)), lam)
     mask = _ambiguous_mask(r32, lam * float(np.float32(sigma))) if lam > 0 else np.zeros_like(r, bool)
-    assert mask.mean() < 0.05
+    assert mask.mean() < 0.1
     err = np.abs(got - ref)[~mask]
     assert err.max() <= 1e-5 * np.abs(ref).max()
     assert G.rel_l2(got[~mask], ref[~mask]) <= 1e-6
@@ -74,9 +76,11 @@ def test_ida_identity_denoiser_parity(handle, B, DF):
     for iters in (1, 2, 5, 12):
         x, tr, bits = G.ida(handle, *got["d"], 1, H, W, B, iters, DF, abcs.DEN_NONE)
         assert bits == 0
-        xr, sig = O.ida(out["y"], out["counts"], out["plan"]["nbh"] * B, out["plan"]["nbw"] * B, B,
-                        iters, DF=DF, denoiser=None)
-        assert G.rel_l2(x[0], xr) <= 1e-5, iters
+        Hc, Wc = out["plan"]["nbh"] * B, out["plan"]["nbw"] * B
+        xr, sig = O.ida(out["y"], out["counts"], Hc, Wc, B, iters, DF=DF, denoiser=None)
+        # error relative to ||A^T y||: with D_F = 1 some iterates are exactly 0
+        scale = np.linalg.norm(O.reconstruct(out["counts"], out["y"], Hc, Wc, B))
+        assert np.linalg.norm(x[0] - xr) <= 1e-5 * scale, iters
         np.testing.assert_allclose(tr[0, :iters], sig, rtol=1e-5, atol=1e-4 * max(sig))
 
 
