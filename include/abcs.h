@@ -179,6 +179,25 @@ abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offse
 abcs_status abcs_denoise_tidct(abcs_handle* h, const float* in, int n_img, int H, int W,
                                const float* sigma, double lambda, float* out, void* stream);
 
+/* abcs_sense without any device allocation (the paper has no counterpart;
+ * this is a library service).  For callers that may not call cudaMalloc
+ * while running: a sensing loop whose device memory is reserved once at
+ * start-up, or a real-time loop that cannot afford cudaMalloc's implicit
+ * device synchronisation.  Same arguments and results as abcs_sense, but no
+ * handle: the scratch lives in one static device array of 4,259,840 bytes
+ * that every GPU loading the library holds until the process exits.
+ * Limits: n_img <= 4096, and n_img * n_B <= 1,048,576 blocks unless `pilot`
+ * is given (ABCS_ERR_INVALID_ARG / ABCS_ERR_CAPACITY otherwise).
+ * The first call on a device, with that device current, uploads the
+ * transform tables and looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the array: calls
+ * that overlap on the GPU (e.g. on two streams) race; serialise them.
+ * Device status bits of these calls are not reported. */
+abcs_status abcs_sense_noalloc(const uint8_t* img, int n_img, int H, int W, int64_t pitch,
+                               int64_t img_stride, int B, double subrate, int variant,
+                               int precision, int32_t* counts, int64_t* offsets, float* coeffs,
+                               int64_t coeff_capacity, int32_t* pilot, void* stream);
+
 /* Wait for `stream`, read and clear the device status word.  Returns
  * ABCS_OK if no bit was set, else ABCS_ERR_DEVICE with the bits in *bits
  * (bits may be NULL). */

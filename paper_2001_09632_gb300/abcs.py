@@ -59,6 +59,7 @@ _SIGS = {
     "abcs_ida": [_P, _P, _P, _P, _I, _I, _I, _I, _I, _D, _I, _D, _P, _P, _P, _P],
     "abcs_denoise_tidct": [_P, _P, _I, _I, _I, _P, _D, _P, _P],
     "abcs_sync_status": [_P, _P, C.POINTER(C.c_uint32)],
+    "abcs_sense_noalloc": [_P, _I, _I, _I, _L, _L, _I, _D, _I, _I, _P, _P, _P, _L, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -131,6 +132,14 @@ def abcs_ida(h, counts, offsets, y, n_img, H, W, B, iters, damping, denoiser, la
 def abcs_denoise_tidct(h, inp, n_img, H, W, sigma, lam, out, stream=None) -> None:
     _check(lib.abcs_denoise_tidct(h, _ptr(inp), n_img, H, W, _ptr(sigma), lam, _ptr(out),
                                   _stream(stream)))
+
+
+def abcs_sense_noalloc(img, n_img, H, W, pitch, img_stride, B, subrate, variant, precision,
+                       counts, offsets, coeffs, coeff_capacity, pilot=None, stream=None) -> None:
+    """abcs_sense with its scratch in a static device array (no allocation)."""
+    _check(lib.abcs_sense_noalloc(_ptr(img), n_img, H, W, pitch, img_stride, B, subrate, variant,
+                                  precision, _ptr(counts), _ptr(offsets), _ptr(coeffs),
+                                  coeff_capacity, _ptr(pilot), _stream(stream)))
 
 
 def abcs_sync_status(h, stream=None) -> int:

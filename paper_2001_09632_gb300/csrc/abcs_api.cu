@@ -147,6 +147,14 @@ T* at(abcs_handle* h, size_t off) {
 
 }  // namespace
 
+namespace abcs {
+// Lets other translation units of the library report through abcs_last_error().
+abcs_status record_error(abcs_status s, const char* msg) {
+    g_err = msg;
+    return s;
+}
+}  // namespace abcs
+
 extern "C" {
 
 const char* abcs_last_error(void) { return g_err.c_str(); }
