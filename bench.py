@@ -45,6 +45,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="abcs", choices=["abcs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp16x2", choices=["fp32", "fp16x2", "bf16x2", "bf16"],
+                    help="block-DCT arithmetic of the timed path (fp16x2 and bf16x2 meet the "
+                         "1e-5 relative-L2 bar against the FP64 oracle; bf16 does not)")
     return ap.parse_args()
 
 
@@ -196,10 +199,29 @@ def main():
     stream = torch.cuda.current_stream()
     s = stream.cuda_stream
 
-    def step():
-        abcs.abcs_sense(h, d_img, N_IMG, H, W, W, H * W, B, SUBRATE, abcs.BBV, abcs.FP32,
+    prec = abcs.PRECISIONS[a.precision]
+
+    def step(p=None):
+        p = prec if p is None else p
+        abcs.abcs_sense(h, d_img, N_IMG, H, W, W, H * W, B, SUBRATE, abcs.BBV, p,
                         counts, offsets, coeffs, cap, None, s)
-        abcs.abcs_reconstruct(h, counts, offsets, coeffs, N_IMG, H, W, B, abcs.FP32, rec, None, s)
+        abcs.abcs_reconstruct(h, counts, offsets, coeffs, N_IMG, H, W, B, p, rec, None, s)
+
+    def timed_steps(K, p):
+        """K steps of precision p, L2 flushed before each; per-call event times (ms)."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for i in range(K):
+            flush.fill_(i & 0xFF)                  # evict L2 between timed steps
+            e0, e1, e2 = ev[i]
+            e0.record(stream)
+            abcs.abcs_sense(h, d_img, N_IMG, H, W, W, H * W, B, SUBRATE, abcs.BBV, p,
+                            counts, offsets, coeffs, cap, None, s)
+            e1.record(stream)
+            abcs.abcs_reconstruct(h, counts, offsets, coeffs, N_IMG, H, W, B, p, rec, None, s)
+            e2.record(stream)
+        torch.cuda.synchronize()
+        return ([e0.elapsed_time(e1) for e0, e1, _ in ev], [e1.elapsed_time(e2) for _, e1, e2 in ev])
 
     def barrier():
         torch.cuda.synchronize()
@@ -222,27 +244,27 @@ def main():
     clk = Clocks(local)
     time.sleep(0.3)
     K = a.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     barrier()
     t_start = time.time()
-    for i in range(K):
-        flush.fill_(i & 0xFF)                      # evict L2 between timed steps
-        e0, e1, e2 = ev[i]
-        e0.record(stream)
-        abcs.abcs_sense(h, d_img, N_IMG, H, W, W, H * W, B, SUBRATE, abcs.BBV, abcs.FP32,
-                        counts, offsets, coeffs, cap, None, s)
-        e1.record(stream)
-        abcs.abcs_reconstruct(h, counts, offsets, coeffs, N_IMG, H, W, B, abcs.FP32, rec, None, s)
-        e2.record(stream)
+    sense_ms, recon_ms = timed_steps(K, prec)
     barrier()
     t_end = time.time()
-    sense_ms = [e0.elapsed_time(e1) for e0, e1, _ in ev]
-    recon_ms = [e1.elapsed_time(e2) for _, e1, e2 in ev]
     step_ms = sum(sense_ms) / K + sum(recon_ms) / K
     step_ms = max_over_ranks(step_ms)
     px = N_IMG * plan["N"]
     value = world * px / (step_ms * 1e-3) / 1e6
+
+    # ---- the other precisions of the block DCT (same workload) ------------
+    sweep = {}
+    for name, p in abcs.PRECISIONS.items():
+        for _ in range(3):
+            step(p)
+        sm, rm = timed_steps(min(K, 200), p)
+        sweep[name] = {"sense_ms": statistics.median(sm), "reconstruct_ms": statistics.median(rm),
+                       "Mpixel_per_s": world * N_IMG * plan["N"] / ((statistics.median(sm) +
+                                                                    statistics.median(rm)) * 1e-3) / 1e6}
+    step(prec)
+    torch.cuda.synchronize()
 
     # ---- IDA, plain TI-DCT denoiser --------------------------------------
     x = torch.empty((N_IMG, H, W), dtype=torch.float32, device=dev)
@@ -298,12 +320,13 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": K,
         "warmup": a.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp16x2": "f16x2 (hi+lo split, FP32 accumulate)", "bf16x2": "bf16x2 (hi+lo split, FP32 accumulate)", "bf16": "bf16 (FP32 accumulate)"}[a.precision], "data": "synthetic",
         "config": {"workload": "64 x 512x512 uint8 greyscale (seeded shapes + 1/f^2 texture), "
-                               "B=16, AL-DCT-BBV, subrate 0.3, FP32: sense + IDCT reconstruct",
+                               "B=16, AL-DCT-BBV, subrate 0.3: sense + IDCT reconstruct",
+                   "precision": a.precision,
                    "value_is": "sense+reconstruct Mpixel/s", "l2": "flushed between timed steps (512 MB write)",
                    "measurements_per_step": total_coeffs, "parallelism": f"replicas x{world}"},
-        "roofline": {"kernel": "recon_kernel<16>", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": "recon_tc_kernel" if prec != abcs.FP32 else "recon_kernel<16>", "bound": "hbm", "achieved": achieved,
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                      "peak_kind": peak_kind, "traffic": None,
                      "algorithmic_bytes_per_launch": recon_bytes},
@@ -311,13 +334,14 @@ def main():
                     "sense_GBps_algorithmic": sense_bytes / (sense_avg * 1e-3) / 1e9,
                     "sense_frac_hbm": sense_bytes / (sense_avg * 1e-3) / 1e9 / hbm_peak,
                     "sense_plus_recon_frac_hbm": (sense_bytes + recon_bytes) / (step_ms * 1e-3) / 1e9 / hbm_peak},
+        "precision_sweep": sweep,
         "ida": {"value": world * px * IDA_ITERS / (ida_ms * 1e-3) / 1e6, "unit": "Mpixel*iter/s",
                 "iters": IDA_ITERS, "denoiser": "tidct", "lambda": LAMBDA, "damping": DF,
                 "ms_per_call": ida_ms},
         "e2e": {"value": world * px / (e2e_ms * 1e-3) / 1e6, "unit": "Mpixel/s",
                 "h2d_bytes_per_step": int(h_img.numel()), "d2h_bytes_per_step": int(h_rec.numel() * 4),
                 "ms_per_step": e2e_ms},
-        "gpu_launches": 4 * K,
+        "gpu_launches": (4 if prec == abcs.FP32 else 5) * K,
         "clocks": clocks,
     }
     if world == 1 and not a.no_cpu_baseline:

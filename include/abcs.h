@@ -184,10 +184,12 @@ abcs_status abcs_denoise_tidct(abcs_handle* h, const float* in, int n_img, int H
  * while running: a sensing loop whose device memory is reserved once at
  * start-up, or a real-time loop that cannot afford cudaMalloc's implicit
  * device synchronisation.  Same arguments and results as abcs_sense, but no
- * handle: the scratch lives in one static device array of 4,259,840 bytes
+ * handle: the scratch lives in one static device array of 4,784,640 bytes
  * that every GPU loading the library holds until the process exits.
- * Limits: n_img <= 4096, and n_img * n_B <= 1,048,576 blocks unless `pilot`
- * is given (ABCS_ERR_INVALID_ARG / ABCS_ERR_CAPACITY otherwise).
+ * Limits: n_img <= 4096 (else ABCS_ERR_INVALID_ARG); n_img * n_B <=
+ * 1,048,576 blocks unless `pilot` is given, and at most 65,536 pilot partial
+ * sums (n_img * ceil(n_B / 256) for BBV, n_img * nbh * ceil(nbw * B / 256)
+ * for DD) (else ABCS_ERR_CAPACITY).
  * The first call on a device, with that device current, uploads the
  * transform tables and looks up the array's device address; make that
  * first call before any stream capture.  All calls share the array: calls

@@ -46,6 +46,7 @@ def _compile(src: str, verbose: bool, extra: list[str]) -> str:
     obj = os.path.join(BUILD, src[:-3] + ".o")
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
            "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), *extra,
+           *os.environ.get("ABCS_NVCC_EXTRA", "").split(),
            "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

@@ -13,7 +13,7 @@ using namespace abcs;
 
 struct abcs_handle {
     int device = 0;
-    uint32_t* status = nullptr;   // device status word
+    uint32_t* status = nullptr;   // device status word; word 1 is the allocation CTA counter
     void* ws = nullptr;           // workspace, grown on demand
     size_t ws_bytes = 0;
 };
@@ -171,14 +171,15 @@ abcs_status abcs_create(abcs_handle** out) {
     ABCS_CUDA(upload_tables_pilot(), "upload tables");
     ABCS_CUDA(upload_tables_dct(), "upload tables");
     ABCS_CUDA(upload_tables_ida(), "upload tables");
+    ABCS_CUDA(upload_tables_tc(), "upload tables");
     abcs_handle* h = new abcs_handle;
     h->device = dev;
-    if (cudaMalloc(&h->status, sizeof(uint32_t)) != cudaSuccess) {
+    if (cudaMalloc(&h->status, 256) != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return fail(ABCS_ERR_OOM, "status word allocation failed");
     }
-    cudaMemset(h->status, 0, sizeof(uint32_t));
+    cudaMemset(h->status, 0, 256);
     *out = h;
     return ABCS_OK;
 }
@@ -218,8 +219,12 @@ abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int
     if (pitch < W) return fail(ABCS_ERR_INVALID_ARG, "pitch %lld < W %d", (long long)pitch, W);
     if (n_img > 1 && img_stride < pitch * H)
         return fail(ABCS_ERR_INVALID_ARG, "img_stride smaller than pitch * H");
-    if (precision != ABCS_FP32)
-        return fail(ABCS_ERR_UNSUPPORTED, "precision %d is not built for sensing", precision);
+    if (precision < ABCS_FP32 || precision > ABCS_TC_BF16)
+        return fail(ABCS_ERR_INVALID_ARG, "bad precision %d", precision);
+    if (precision != ABCS_FP32 && B != 16)
+        return fail(ABCS_ERR_UNSUPPORTED, "tensor-core precisions are built for B = 16 only");
+    if ((int64_t)n_img * p.n_blocks >= (1LL << 31))
+        return fail(ABCS_ERR_INVALID_ARG, "more than 2^31 - 1 blocks in one call");
     if (coeff_capacity < (int64_t)n_img * p.M)
         return fail(ABCS_ERR_CAPACITY, "coeff_capacity %lld < n_img * M = %lld",
                     (long long)coeff_capacity, (long long)n_img * p.M);
@@ -228,17 +233,19 @@ abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     const int64_t nb_all = (int64_t)n_img * p.n_blocks;
+    SenseArgs a{};
+    a.g = make_geom(n_img, H, W, B, pitch, img_stride);
+    a.variant = variant;
+    a.pilot_cpi = pilot_ctas_per_image(a);
     Carver c;
     const size_t o_w = c.take<int32_t>(pilot ? 1 : nb_all);
-    const size_t o_wsum = c.take<unsigned long long>(n_img);
+    const size_t o_part = c.take<unsigned long long>((size_t)n_img * a.pilot_cpi);
     const size_t o_tot = c.take<int64_t>(n_img);
+    const size_t o_base = c.take<int64_t>(n_img + 1);
     st = ensure_ws(h, c.off);
     if (st) return st;
 
-    SenseArgs a{};
-    a.g = make_geom(n_img, H, W, B, pitch, img_stride);
     a.img = img;
-    a.variant = variant;
     a.precision = precision;
     a.L = p.L; a.X0 = p.X0; a.nS = p.nS; a.m1 = p.m1; a.m_zz = p.m_zz; a.T = p.T; a.cap = p.cap;
     a.R = p.R;
@@ -247,11 +254,12 @@ abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int
     a.coeffs = coeffs;
     a.capacity = coeff_capacity;
     a.w = pilot ? pilot : at<int32_t>(h, o_w);
-    a.wsum = at<unsigned long long>(h, o_wsum);
+    a.wpart = at<unsigned long long>(h, o_part);
     a.img_total = at<int64_t>(h, o_tot);
+    a.img_base = at<int64_t>(h, o_base);
+    a.done = h->status + 1;
     a.status = h->status;
 
-    ABCS_CUDA(cudaMemsetAsync(a.wsum, 0, n_img * sizeof(unsigned long long), s), "memset");
     int mode = 0;
     if (variant == ABCS_BBV && p.nS > 0) {
         ABCS_CUDA(launch_bbv_pilot(a, s), "bbv_pilot launch");
@@ -264,7 +272,10 @@ abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int
         if (pilot) ABCS_CUDA(cudaMemsetAsync(pilot, 0, nb_all * sizeof(int32_t), s), "memset");
     }
     ABCS_CUDA(launch_allocate(a, mode, s), "allocate launch");
-    ABCS_CUDA(launch_sense_pack(a, s), "sense_pack launch");
+    if (precision == ABCS_FP32)
+        ABCS_CUDA(launch_sense_pack(a, s), "sense_pack launch");
+    else
+        ABCS_CUDA(launch_sense_tc(a, s), "sense_tc launch");
     return ABCS_OK;
 }
 
@@ -277,8 +288,12 @@ abcs_status abcs_reconstruct(abcs_handle* h, const int32_t* counts, const int64_
     if (n_img < 1 || n_img > 65535) return fail(ABCS_ERR_INVALID_ARG, "n_img must be in [1, 65535]");
     if (!counts || !offsets || !coeffs || (!out && !out_u8))
         return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
-    if (precision != ABCS_FP32)
-        return fail(ABCS_ERR_UNSUPPORTED, "precision %d is not built for reconstruction", precision);
+    if (precision < ABCS_FP32 || precision > ABCS_TC_BF16)
+        return fail(ABCS_ERR_INVALID_ARG, "bad precision %d", precision);
+    if (precision != ABCS_FP32 && B != 16)
+        return fail(ABCS_ERR_UNSUPPORTED, "tensor-core precisions are built for B = 16 only");
+    if ((int64_t)n_img * (H / B) * (W / B) >= (1LL << 31))
+        return fail(ABCS_ERR_INVALID_ARG, "more than 2^31 - 1 blocks in one call");
     DeviceGuard dg(h->device);
     if (!dg.ok) return fail(ABCS_ERR_CUDA, "cannot select the handle's device");
     ReconArgs a{};
@@ -290,7 +305,10 @@ abcs_status abcs_reconstruct(abcs_handle* h, const int32_t* counts, const int64_
     a.out = out;
     a.out_u8 = out_u8;
     a.status = h->status;
-    ABCS_CUDA(launch_reconstruct(a, static_cast<cudaStream_t>(stream)), "reconstruct launch");
+    if (precision == ABCS_FP32)
+        ABCS_CUDA(launch_reconstruct(a, static_cast<cudaStream_t>(stream)), "reconstruct launch");
+    else
+        ABCS_CUDA(launch_recon_tc(a, static_cast<cudaStream_t>(stream)), "reconstruct_tc launch");
     return ABCS_OK;
 }
 

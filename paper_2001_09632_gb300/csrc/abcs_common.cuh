@@ -67,6 +67,7 @@ const HostTables& host_tables();   // computed once on the host in double
 cudaError_t upload_tables_pilot();
 cudaError_t upload_tables_dct();
 cudaError_t upload_tables_ida();
+cudaError_t upload_tables_tc();
 
 // zigzag rank of (u, v) in a B x B block, JPEG orientation: diagonal s = u+v;
 // odd s runs with u increasing, even s with u decreasing.
@@ -98,6 +99,27 @@ struct ImgGeom {
     int64_t pitch;     // bytes between rows (uint8 inputs)
     int64_t img_stride;// bytes between images (uint8 inputs)
 };
+
+// Programmatic dependent launch: a kernel launched with launch_pdl may start
+// while its predecessor in the stream drains; it must call griddep_wait()
+// before touching any global memory the predecessor may write (all inputs).
+ABCS_D void griddep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 // Device status bits are OR-ed into one word owned by the handle.
 ABCS_D void set_status(uint32_t* st, uint32_t bits) { atomicOr(st, bits); }
@@ -138,10 +160,14 @@ struct SenseArgs {
     float* coeffs;
     int64_t capacity;
     int32_t* w;          // pilot per block (BBV_i or n_i)
-    unsigned long long* wsum;   // per image sum of w
+    unsigned long long* wpart;  // per image, per pilot CTA: partial sums of w
+    int pilot_cpi;       // pilot CTAs per image (partials per image)
     int64_t* img_total;  // per image sum of counts
+    int64_t* img_base;   // exclusive prefix of img_total, n_img + 1 entries
+    unsigned* done;      // allocation CTAs finished (reset by the last one)
     uint32_t* status;
 };
+int pilot_ctas_per_image(const SenseArgs& a);
 cudaError_t launch_bbv_pilot(const SenseArgs& a, cudaStream_t s);
 cudaError_t launch_dd_pilot(const SenseArgs& a, cudaStream_t s);
 cudaError_t launch_allocate(const SenseArgs& a, int mode, cudaStream_t s);
@@ -158,6 +184,9 @@ struct ReconArgs {
     uint32_t* status;
 };
 cudaError_t launch_reconstruct(const ReconArgs& a, cudaStream_t s);
+// tensor-core paths (B = 16; a.precision selects FP16x2 / BF16x2 / BF16)
+cudaError_t launch_sense_tc(const SenseArgs& a, cudaStream_t s);
+cudaError_t launch_recon_tc(const ReconArgs& a, cudaStream_t s);
 
 struct IdaLinArgs {
     ImgGeom g;

@@ -25,11 +25,13 @@ using namespace abcs;
 // Limits of the static scratch.
 constexpr int kNoAllocMaxImages = 4096;          // images per call
 constexpr int64_t kNoAllocMaxBlocks = 1 << 20;   // blocks per call when pilot == NULL
-constexpr size_t kOffStatus = 0;
-constexpr size_t kOffWsum = 256;
-constexpr size_t kOffTotal = kOffWsum + 8 * (size_t)kNoAllocMaxImages;
-constexpr size_t kOffW = kOffTotal + 8 * (size_t)kNoAllocMaxImages;
-constexpr size_t kScratchBytes = kOffW + 4 * (size_t)kNoAllocMaxBlocks;   // 4,259,840 bytes
+constexpr int64_t kNoAllocMaxParts = 1 << 16;    // pilot partial sums per call
+constexpr size_t kOffStatus = 0;                 // status word, allocation CTA counter
+constexpr size_t kOffTotal = 256;
+constexpr size_t kOffBase = kOffTotal + 8 * (size_t)kNoAllocMaxImages;
+constexpr size_t kOffPart = (kOffBase + 8 * (size_t)(kNoAllocMaxImages + 1) + 255) / 256 * 256;
+constexpr size_t kOffW = kOffPart + 8 * (size_t)kNoAllocMaxParts;
+constexpr size_t kScratchBytes = kOffW + 4 * (size_t)kNoAllocMaxBlocks;   // 4,784,640 bytes
 
 // Held by every GPU that loads the library, until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -82,6 +84,18 @@ extern "C" abcs_status abcs_sense_noalloc(const uint8_t* img, int n_img, int H, 
         return err(ABCS_ERR_CAPACITY,
                    "abcs_sense_noalloc: %lld blocks exceed the static scratch limit of %lld "
                    "(pass a pilot buffer to lift it)", nb_all, kNoAllocMaxBlocks);
+    SenseArgs a{};
+    a.g.n_img = n_img; a.g.H = H; a.g.W = W; a.g.B = B;
+    a.g.nbh = H / B; a.g.nbw = W / B;
+    a.g.Hc = a.g.nbh * B; a.g.Wc = a.g.nbw * B;
+    a.g.n_blocks = p.n_blocks;
+    a.g.pitch = pitch; a.g.img_stride = img_stride;
+    a.variant = variant;
+    a.pilot_cpi = pilot_ctas_per_image(a);
+    if ((int64_t)n_img * a.pilot_cpi > kNoAllocMaxParts)
+        return err(ABCS_ERR_CAPACITY,
+                   "abcs_sense_noalloc: %lld pilot partial sums exceed the static scratch limit of %lld",
+                   (int64_t)n_img * a.pilot_cpi, kNoAllocMaxParts);
     if (!img || !counts || !offsets || !coeffs) return err(ABCS_ERR_INVALID_ARG, "NULL buffer");
     if (pitch < W) return err(ABCS_ERR_INVALID_ARG, "pitch %lld < W %lld", pitch, W);
     if (n_img > 1 && img_stride < pitch * H)
@@ -99,14 +113,7 @@ extern "C" abcs_status abcs_sense_noalloc(const uint8_t* img, int n_img, int H, 
     if (st) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-    SenseArgs a{};
-    a.g.n_img = n_img; a.g.H = H; a.g.W = W; a.g.B = B;
-    a.g.nbh = H / B; a.g.nbw = W / B;
-    a.g.Hc = a.g.nbh * B; a.g.Wc = a.g.nbw * B;
-    a.g.n_blocks = p.n_blocks;
-    a.g.pitch = pitch; a.g.img_stride = img_stride;
     a.img = img;
-    a.variant = variant;
     a.precision = precision;
     a.L = p.L; a.X0 = p.X0; a.nS = p.nS; a.m1 = p.m1; a.m_zz = p.m_zz; a.T = p.T; a.cap = p.cap;
     a.R = p.R;
@@ -115,14 +122,16 @@ extern "C" abcs_status abcs_sense_noalloc(const uint8_t* img, int n_img, int H, 
     a.coeffs = coeffs;
     a.capacity = coeff_capacity;
     a.status = reinterpret_cast<uint32_t*>(scratch + kOffStatus);
-    a.wsum = reinterpret_cast<unsigned long long*>(scratch + kOffWsum);
+    a.done = reinterpret_cast<unsigned*>(scratch + kOffStatus) + 1;
     a.img_total = reinterpret_cast<int64_t*>(scratch + kOffTotal);
+    a.img_base = reinterpret_cast<int64_t*>(scratch + kOffBase);
+    a.wpart = reinterpret_cast<unsigned long long*>(scratch + kOffPart);
     a.w = pilot ? pilot : reinterpret_cast<int32_t*>(scratch + kOffW);
 
-    // The array keeps the previous call's contents: the per-image sums must
-    // start at zero (pilot values and totals are fully overwritten).
-    cudaError_t e = cudaMemsetAsync(a.wsum, 0, n_img * sizeof(unsigned long long), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a.status, 0, sizeof(uint32_t), s);
+    // The array keeps the previous call's contents.  Pilot values, partial
+    // sums, totals and bases are fully overwritten by every call; the status
+    // word and the allocation CTA counter must start at zero.
+    cudaError_t e = cudaMemsetAsync(a.status, 0, 2 * sizeof(uint32_t), s);
     int mode = 0;
     if (e == cudaSuccess) {
         if (variant == ABCS_BBV && p.nS > 0) {

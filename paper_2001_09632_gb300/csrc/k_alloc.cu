@@ -46,16 +46,27 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* sh, 
 }
 
 __global__ void __launch_bounds__(kAllocThreads)
-alloc_kernel(const int32_t* __restrict__ w, const unsigned long long* __restrict__ wsum, int64_t nB,
-             AllocParams p, int32_t* __restrict__ counts, int64_t* __restrict__ offsets,
-             int64_t* __restrict__ img_total) {
+alloc_kernel(const int32_t* __restrict__ w, const unsigned long long* __restrict__ wpart, int cpi,
+             int64_t nB, AllocParams p, int32_t* __restrict__ counts, int64_t* __restrict__ offsets,
+             int64_t* __restrict__ img_total, int64_t* __restrict__ img_base, unsigned* done) {
     __shared__ int64_t sh[33];
+    __shared__ int64_t sW;
+    __shared__ bool s_last;
+    griddep_wait();
     const int k = blockIdx.x;
     const int32_t* wk = w + (int64_t)k * nB;
     int32_t* ck = counts + (int64_t)k * nB;
     int64_t* ok = offsets + (int64_t)k * nB;
     const int t = threadIdx.x, nt = blockDim.x;
-    const int64_t W = (p.mode == 1) ? (int64_t)wsum[k] : 0;
+    if (t < 32) {     // sum of the pilot CTAs' partials, fixed order
+        unsigned long long v = 0;
+        if (p.mode == 1)
+            for (int j = t; j < cpi; j += 32) v += wpart[(int64_t)k * cpi + j];
+        v = warp_sum(v);
+        if (t == 0) sW = (int64_t)v;
+    }
+    __syncthreads();
+    const int64_t W = sW;
 
     if (p.mode == 0 || W == 0) {
         const int m = p.m_add + (p.mode == 0 ? p.m_fixed : p.m_fallback);
@@ -107,7 +118,31 @@ alloc_kernel(const int32_t* __restrict__ w, const unsigned long long* __restrict
         ok[i] = run;
         run += ck[i];
     }
-    if (t == 0) img_total[k] = total;
+    // The last CTA to finish turns the per-image totals into image bases
+    // (exclusive prefix); no CTA waits for another.
+    if (t == 0) {
+        img_total[k] = total;
+        __threadfence();
+        s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int n = gridDim.x;
+    const int chunk2 = (n + nt - 1) / nt;
+    const int j0 = min(n, t * chunk2), j1 = min(n, j0 + chunk2);
+    int64_t loc = 0;
+    for (int j = j0; j < j1; ++j) loc += __ldcg(img_total + j);
+    int64_t tot2;
+    int64_t base = block_exclusive_scan(loc, sh, &tot2);
+    for (int j = j0; j < j1; ++j) {
+        img_base[j] = base;
+        base += __ldcg(img_total + j);
+    }
+    if (t == 0) {
+        img_base[n] = tot2;
+        *done = 0u;
+    }
 }
 
 }  // namespace
@@ -128,9 +163,9 @@ cudaError_t launch_allocate(const SenseArgs& a, int mode, cudaStream_t s) {
         p.m_add = a.m1;
         p.m_fallback = a.m1;
     }
-    alloc_kernel<<<a.g.n_img, kAllocThreads, 0, s>>>(a.w, a.wsum, a.g.n_blocks, p, a.counts,
-                                                     a.offsets, a.img_total);
-    return cudaGetLastError();
+    return launch_pdl(alloc_kernel, dim3(a.g.n_img), dim3(kAllocThreads), 0, s, (const int32_t*)a.w,
+                      (const unsigned long long*)a.wpart, a.pilot_cpi, (int64_t)a.g.n_blocks, p, a.counts,
+                      a.offsets, a.img_total, a.img_base, a.done);
 }
 
 }  // namespace abcs

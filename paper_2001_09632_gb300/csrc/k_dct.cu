@@ -1,5 +1,6 @@
 // Phase-2 sensing (packed zigzag measurements, Eq. 26 rows) and the
-// real-time decoder (block inverse 2D-DCT of the zero-filled measurements).
+// real-time decoder (block inverse 2D-DCT of the zero-filled measurements),
+// FP32 CUDA-core transforms for B = 4, 8, 16, 32.
 #include "abcs_common.cuh"
 
 namespace abcs {
@@ -12,132 +13,171 @@ namespace abcs {
 
 namespace {
 
-// Sum of the packed sizes of images 0 .. k-1 (warp 0 of the CTA).
-ABCS_D int64_t image_base(const int64_t* img_total, int k) {
-    int64_t s = 0;
-    for (int j = threadIdx.x; j < k; j += 32) s += img_total[j];
-    return warp_sum(s);
+// Warp 0: tile start (image base + image-local offset) and the tile's count
+// prefix.  Kept out of line: inlined, it inflates the kernel's registers.
+template <int B>
+__device__ __noinline__ void sense_prologue(const SenseArgs& a, int k, int64_t gi0, int nblk, int* rel,
+                                            int64_t* gstart) {
+    if (threadIdx.x == 0) *gstart = a.img_base[k] + a.offsets[gi0];
+    tile_prefix<B>(a.counts + gi0, nblk, rel, nullptr);
 }
 
 // ---------------------------------------------------------------------------
 // sense_pack: C = D X D^T per block; the first m_i zigzag coefficients of
-// each block are stored at coeffs[offsets[i] ...].  Offsets arrive as
-// image-local exclusive prefixes (from the allocation kernel) and leave as
-// global ones.  The CTA's output is one contiguous range: coalesced stores.
+// each block go to coeffs[offsets[i] ...].  Offsets arrive as image-local
+// exclusive prefixes (from the allocation kernel) and leave as global ones.
+// Row DCT (row mapping) -> smem -> column DCT (column mapping, registers) ->
+// measured coefficients scattered into the tile's packed range in smem ->
+// one contiguous, vectorised copy to global memory.
 // ---------------------------------------------------------------------------
 template <int B>
-__global__ void __launch_bounds__(256) sense_pack_kernel(SenseArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__global__ void __launch_bounds__(256, (B == 16 ? 3 : 4)) sense_pack_kernel(SenseArgs a) {
     using Tl = Tile<B>;
-    uint8_t* Xs = smem;
-    float* Ts = reinterpret_cast<float*>(smem + Tl::XS_BYTES);
-    float* Zs = Ts + Tl::TS_FLOATS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const TileSmem<B> sm(smem, 1);
+    float* Ts = sm.Ts;
+    float* Ps = sm.P[0];
+    uint16_t* rk = sm.rk;
     __shared__ int rel[Tl::NB + 1];
-    __shared__ int64_t s_off0, s_base;
+    __shared__ int64_t s_gstart;
 
     const ImgGeom& g = a.g;
     const int k = blockIdx.z, bi = blockIdx.y, bj0 = blockIdx.x * Tl::NB;
     const int nblk = min(Tl::NB, g.nbw - bj0);
     const int64_t gi0 = (int64_t)k * g.n_blocks + (int64_t)bi * g.nbw + bj0;
+    const int t = threadIdx.x;
 
-    if (threadIdx.x < 32) {
-        const int64_t base = image_base(a.img_total, k);
-        if (threadIdx.x == 0) {
-            s_base = base;
-            s_off0 = a.offsets[gi0];
-        }
-        tile_prefix<B>(a.counts + gi0, nblk, rel, nullptr);
-    }
-    const uint8_t* img = a.img + (int64_t)k * g.img_stride;
-    load_u8_tile<B>(Xs, img, g.pitch, bi * B, bj0 * B, g.W);
-    __syncthreads();
-    float x[B];
+    load_rank_table<B>(rk);
+    griddep_wait();
+    if (t < 32) sense_prologue<B>(a, k, gi0, nblk, rel, &s_gstart);
+    {
+        const int b = t / B, n = t % B;
+        float x[B];
+        if (b < nblk) {
+            const uint8_t* src = a.img + (int64_t)k * g.img_stride + (int64_t)(bi * B + n) * g.pitch +
+                                 (bj0 + b) * B;
+            const bool vec = ((reinterpret_cast<uintptr_t>(src) & (uintptr_t)(B >= 16 ? 15 : B - 1)) == 0);
+            load_u8_row<B>(src, vec, x);
+        } else {
 #pragma unroll
-    for (int n = 0; n < B; ++n) x[n] = (float)Xs[n * kTileCols + threadIdx.x];
-    fwd_dct_tile_fp32<B>(x, Ts, Zs);
-
-    const int64_t gstart = s_base + s_off0;
-    if (threadIdx.x < nblk) a.offsets[gi0 + threadIdx.x] = gstart + rel[threadIdx.x];
-    if (k == g.n_img - 1 && bi == g.nbh - 1 && bj0 + nblk == g.nbw && threadIdx.x == 0)
+            for (int i = 0; i < B; ++i) x[i] = 0.f;
+        }
+        fwd_rows_to_smem<B>(x, Ts);
+    }
+    __syncthreads();
+    const int64_t gstart = s_gstart;
+    const int sh = (int)(gstart & 3);
+    {
+        const int b = t / B, v = t % B;
+        const float* col = Ts + b * Tl::BLK + v;
+        float x[B], c[B];
+#pragma unroll
+        for (int n = 0; n < B; ++n) x[n] = col[n * Tl::LD];
+        fdct<B>(x, c);
+        if (b < nblk) {
+            const int r0 = rel[b], m = rel[b + 1] - r0;
+            float* dst = Ps + sh + r0;
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const int r = rk[u * B + v];
+                if (r < m) dst[r] = c[u];
+            }
+        }
+    }
+    __syncthreads();
+    if (t < nblk) a.offsets[gi0 + t] = gstart + rel[t];
+    if (k == g.n_img - 1 && bi == g.nbh - 1 && bj0 + nblk == g.nbw && t == 0)
         a.offsets[(int64_t)g.n_img * g.n_blocks] = gstart + rel[nblk];
     const int total = rel[nblk];
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int b = find_block(rel, nblk, e);
-        const int64_t dst = gstart + e;
-        if (dst < a.capacity) a.coeffs[dst] = Zs[b * B * B + (e - rel[b])];
-        else set_status(a.status, ABCS_DEV_CAPACITY);
+    if (gstart + total > a.capacity) {
+        if (t == 0) set_status(a.status, ABCS_DEV_CAPACITY);
+        return;
     }
-}
-
-template <int B>
-static cudaError_t launch_sense_B(const SenseArgs& a, cudaStream_t s) {
-    using Tl = Tile<B>;
-    const size_t smem = Tl::XS_BYTES + (Tl::TS_FLOATS + Tl::ZS_FLOATS) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(sense_pack_kernel<B>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e) return e;
-    dim3 grid((unsigned)((a.g.nbw + Tl::NB - 1) / Tl::NB), (unsigned)a.g.nbh, (unsigned)a.g.n_img);
-    sense_pack_kernel<B><<<grid, 256, smem, s>>>(a);
-    return cudaGetLastError();
+    stage_out(Ps, a.coeffs, gstart, total);
 }
 
 // ---------------------------------------------------------------------------
 // reconstruct: X = D^T C D per block with C zero outside the block's first
-// m_i zigzag positions.  Coefficients are gathered with coalesced loads.
+// m_i zigzag positions.  The tile's packed range is staged in smem with
+// cp.async; the column inverse (column mapping) reads it through the rank
+// table; the row inverse (row mapping) writes whole pixel rows.
 // ---------------------------------------------------------------------------
 template <int B>
-__global__ void __launch_bounds__(256) recon_kernel(ReconArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__global__ void __launch_bounds__(256, (B == 16 ? 3 : 4)) recon_kernel(ReconArgs a) {
     using Tl = Tile<B>;
-    float* Ts = reinterpret_cast<float*>(smem);
-    float* Zs = Ts + Tl::TS_FLOATS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const TileSmem<B> sm(smem, 1);
+    float* Ts = sm.Ts;
+    float* Ps = sm.P[0];
+    uint16_t* rk = sm.rk;
     __shared__ int rel[Tl::NB + 1];
-    __shared__ int64_t s_start;
+    __shared__ int64_t s_start, s_end;
 
     const ImgGeom& g = a.g;
     const int k = blockIdx.z, bi = blockIdx.y, bj0 = blockIdx.x * Tl::NB;
     const int nblk = min(Tl::NB, g.nbw - bj0);
     const int64_t gi0 = (int64_t)k * g.n_blocks + (int64_t)bi * g.nbw + bj0;
+    const int t = threadIdx.x;
 
-    if (threadIdx.x < 32) {
-        if (threadIdx.x == 0) s_start = a.offsets[gi0];
+    load_rank_table<B>(rk);
+    griddep_wait();
+    if (t < 32) {
+        if (t == 0) s_start = a.offsets[gi0];
+        if (t == 1) s_end = a.offsets[gi0 + nblk];
         tile_prefix<B>(a.counts + gi0, nblk, rel, a.status);
     }
-    for (int i = threadIdx.x; i < Tl::ZS_FLOATS; i += blockDim.x) Zs[i] = 0.f;
     __syncthreads();
-    const int total = rel[nblk];
-    const float* src = a.coeffs + s_start;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int b = find_block(rel, nblk, e);
-        Zs[b * B * B + (e - rel[b])] = __ldg(src + e);
+    const int64_t start = s_start;
+    int64_t n64 = s_end - start;
+    n64 = n64 < 0 ? 0 : (n64 > (int64_t)Tl::NB * B * B ? (int64_t)Tl::NB * B * B : n64);
+    stage_in_async(Ps, a.coeffs, start, (int)n64);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    const int sh = (int)(start & 3);
+    {
+        const int b = t / B, v = t % B;
+        float c[B], x[B];
+        const int r0 = rel[min(b, nblk)], m = (b < nblk) ? rel[b + 1] - r0 : 0;
+        const float* src = Ps + sh + r0;
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int r = rk[u * B + v];
+            c[u] = (r < m) ? src[r] : 0.f;
+        }
+        idct<B>(c, x);
+        float* col = Ts + b * Tl::BLK + v;
+#pragma unroll
+        for (int n = 0; n < B; ++n) col[n * Tl::LD] = x[n];
     }
     __syncthreads();
-    float x[B];
-    inv_dct_tile_fp32<B>(Zs, Ts, x);
-    if (threadIdx.x < nblk * B) {
-        const int col = bj0 * B + threadIdx.x;
-        const int64_t o = (int64_t)k * g.Hc * g.Wc + (int64_t)(bi * B) * g.Wc + col;
-#pragma unroll
-        for (int n = 0; n < B; ++n) {
-            if (a.out) a.out[o + (int64_t)n * g.Wc] = x[n];
-            if (a.out_u8) {
-                const float v = fminf(fmaxf(rintf(x[n]), 0.f), 255.f);
-                a.out_u8[o + (int64_t)n * g.Wc] = (uint8_t)v;
-            }
-        }
+    const int b = t / B, n = t % B;
+    if (b < nblk) {
+        float x[B];
+        inv_rows_from_smem<B>(Ts, x);
+        const int64_t o = (int64_t)k * g.Hc * g.Wc + (int64_t)(bi * B + n) * g.Wc + (bj0 + b) * B;
+        if (a.out) store_f32_row<B>(a.out + o, aligned16(a.out + o), x);
+        if (a.out_u8) store_u8_row<B>(a.out_u8 + o, (reinterpret_cast<uintptr_t>(a.out_u8 + o) & 3) == 0, x);
     }
 }
 
 template <int B>
-static cudaError_t launch_recon_B(const ReconArgs& a, cudaStream_t s) {
-    using Tl = Tile<B>;
-    const size_t smem = (Tl::TS_FLOATS + Tl::ZS_FLOATS) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(recon_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+cudaError_t launch_sense_B(const SenseArgs& a, cudaStream_t s) {
+    const size_t smem = Tile<B>::smem_bytes(1);
+    cudaError_t e = cudaFuncSetAttribute(sense_pack_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e) return e;
-    dim3 grid((unsigned)((a.g.nbw + Tl::NB - 1) / Tl::NB), (unsigned)a.g.nbh, (unsigned)a.g.n_img);
-    recon_kernel<B><<<grid, 256, smem, s>>>(a);
-    return cudaGetLastError();
+    dim3 grid((unsigned)((a.g.nbw + Tile<B>::NB - 1) / Tile<B>::NB), (unsigned)a.g.nbh, (unsigned)a.g.n_img);
+    return launch_pdl(sense_pack_kernel<B>, grid, dim3(256), smem, s, a);
+}
+
+template <int B>
+cudaError_t launch_recon_B(const ReconArgs& a, cudaStream_t s) {
+    const size_t smem = Tile<B>::smem_bytes(1);
+    cudaError_t e = cudaFuncSetAttribute(recon_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    dim3 grid((unsigned)((a.g.nbw + Tile<B>::NB - 1) / Tile<B>::NB), (unsigned)a.g.nbh, (unsigned)a.g.n_img);
+    return launch_pdl(recon_kernel<B>, grid, dim3(256), smem, s, a);
 }
 
 }  // namespace

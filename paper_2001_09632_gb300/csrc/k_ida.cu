@@ -19,66 +19,105 @@ namespace {
 // then r = IDCT(c) = x + A^T z, and the CTA's share of ||z||^2 in FP64.
 // ---------------------------------------------------------------------------
 template <int B>
-__global__ void __launch_bounds__(256) ida_linear_kernel(IdaLinArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__global__ void __launch_bounds__(256, (B == 16 ? 3 : 4)) ida_linear_kernel(IdaLinArgs a) {
     using Tl = Tile<B>;
-    float* Ts = reinterpret_cast<float*>(smem);
-    float* Zs = Ts + Tl::TS_FLOATS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const TileSmem<B> sm(smem, 2);
+    float* Ts = sm.Ts;
+    float* Ys = sm.P[0];       // y, overwritten in place by z
+    float* Zp = sm.P[1];       // z_prev
+    uint16_t* rk = sm.rk;
     __shared__ int rel[Tl::NB + 1];
-    __shared__ int64_t s_start;
+    __shared__ int64_t s_start, s_end;
     __shared__ double shd[32];
 
     const ImgGeom& g = a.g;
     const int k = blockIdx.z, bi = blockIdx.y, bj0 = blockIdx.x * Tl::NB;
     const int nblk = min(Tl::NB, g.nbw - bj0);
     const int64_t gi0 = (int64_t)k * g.n_blocks + (int64_t)bi * g.nbw + bj0;
-    if (threadIdx.x < 32) {
-        if (threadIdx.x == 0) s_start = a.offsets[gi0];
+    const int t = threadIdx.x;
+    load_rank_table<B>(rk);
+    griddep_wait();
+    if (t < 32) {
+        if (t == 0) s_start = a.offsets[gi0];
+        if (t == 1) s_end = a.offsets[gi0 + nblk];
         tile_prefix<B>(a.counts + gi0, nblk, rel, a.status);
     }
+    __syncthreads();
+    const int64_t start = s_start;
+    int64_t n64 = s_end - start;
+    n64 = n64 < 0 ? 0 : (n64 > (int64_t)Tl::NB * B * B ? (int64_t)Tl::NB * B * B : n64);
+    const int n_in = (int)n64;
+    stage_in_async(Ys, a.y, start, n_in);
+    if (a.z_prev) stage_in_async(Zp, a.z_prev, start, n_in);
+    cp_async_commit();
 
-    const bool valid = threadIdx.x < nblk * B;
-    const int64_t o = (int64_t)k * g.Hc * g.Wc + (int64_t)(bi * B) * g.Wc + bj0 * B + threadIdx.x;
-    float x[B];
+    const int b = t / B, n = t % B;
+    const int64_t o = (int64_t)k * g.Hc * g.Wc + (int64_t)(bi * B + n) * g.Wc + (bj0 + b) * B;
+    {
+        float x[B];
+        if (a.x && b < nblk) {
+            load_f32_row<B>(a.x + o, aligned16(a.x + o), x);
+        } else {
 #pragma unroll
-    for (int n = 0; n < B; ++n) x[n] = (a.x && valid) ? __ldg(a.x + o + (int64_t)n * g.Wc) : 0.f;
-    fwd_dct_tile_fp32<B>(x, Ts, Zs);
+            for (int i = 0; i < B; ++i) x[i] = 0.f;
+        }
+        fwd_rows_to_smem<B>(x, Ts);
+    }
+    cp_async_wait_all();
+    __syncthreads();
 
+    // column mapping: forward DCT, residual update of the measured
+    // coefficients, inverse DCT -- all in registers
     double nz = 0.0;
-    const int total = rel[nblk];
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int b = find_block(rel, nblk, e);
-        const int r = e - rel[b];
-        const int64_t gi = s_start + e;
-        float* zc = Zs + b * B * B + r;
-        const float c = *zc;
-        const float zp = a.z_prev ? __ldg(a.z_prev + gi) : 0.f;
-        const float z = (__ldg(a.y + gi) - c) + zp * a.inv_df;
-        a.z[gi] = z;
-        *zc = c + z;
-        nz += (double)z * (double)z;
+    {
+        const int v = t % B;
+        float* col = Ts + b * Tl::BLK + v;
+        float x[B], c[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) x[i] = col[i * Tl::LD];
+        fdct<B>(x, c);
+        const int sh = (int)(start & 3);
+        const int r0 = rel[min(b, nblk)], m = (b < nblk) ? rel[b + 1] - r0 : 0;
+        float* ys = Ys + sh + r0;
+        const float* zs = Zp + sh + r0;
+        const bool has_zp = a.z_prev != nullptr;
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int r = rk[u * B + v];
+            if (r < m) {
+                const float zp = has_zp ? zs[r] : 0.f;
+                const float z = (ys[r] - c[u]) + zp * a.inv_df;
+                ys[r] = z;
+                c[u] += z;
+                nz += (double)z * (double)z;
+            }
+        }
+        idct<B>(c, x);
+#pragma unroll
+        for (int i = 0; i < B; ++i) col[i * Tl::LD] = x[i];
     }
     __syncthreads();
-    inv_dct_tile_fp32<B>(Zs, Ts, x);
-    if (valid) {
-#pragma unroll
-        for (int n = 0; n < B; ++n) a.r[o + (int64_t)n * g.Wc] = x[n];
+    if (b < nblk) {
+        float x[B];
+        inv_rows_from_smem<B>(Ts, x);
+        store_f32_row<B>(a.r + o, aligned16(a.r + o), x);
     }
+    stage_out(Ys, a.z, start, n_in);
     nz = block_sum(nz, shd);
-    if (threadIdx.x == 0)
+    if (t == 0)
         a.partial[(int64_t)k * gridDim.x * gridDim.y + (int64_t)blockIdx.y * gridDim.x + blockIdx.x] = nz;
 }
 
 template <int B>
 static cudaError_t launch_lin_B(const IdaLinArgs& a, cudaStream_t s) {
     using Tl = Tile<B>;
-    const size_t smem = (Tl::TS_FLOATS + Tl::ZS_FLOATS) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(ida_linear_kernel<B>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = Tl::smem_bytes(2);
+    cudaError_t e = cudaFuncSetAttribute(ida_linear_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e) return e;
     dim3 grid((unsigned)((a.g.nbw + Tl::NB - 1) / Tl::NB), (unsigned)a.g.nbh, (unsigned)a.g.n_img);
-    ida_linear_kernel<B><<<grid, 256, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(ida_linear_kernel<B>, grid, dim3(256), smem, s, a);
 }
 
 // sigma^t = sqrt(||z^t||^2 / m) per image (Eq. 15); m = the image's
@@ -87,6 +126,7 @@ __global__ void ida_sigma_kernel(const double* __restrict__ partial, int cpi,
                                  const int64_t* __restrict__ offsets, int64_t nB,
                                  float* __restrict__ sigma, float* __restrict__ trace, int iters,
                                  int t, uint32_t* status) {
+    griddep_wait();
     const int k = blockIdx.x;
     double s = 0.0;
     for (int j = threadIdx.x; j < cpi; j += 32) s += partial[(int64_t)k * cpi + j];
@@ -132,6 +172,7 @@ __global__ void __launch_bounds__(256) tidct_kernel(const float* __restrict__ in
     extern __shared__ __align__(16) unsigned char smem[];
     float* Vs = reinterpret_cast<float*>(smem);        // [8][256]
     float* Qs = Vs + 8 * 256;                          // [kWin][kQS]
+    griddep_wait();
     const int k = blockIdx.z;
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
     const float* img = in + (int64_t)k * H * W;
@@ -154,13 +195,10 @@ __global__ void __launch_bounds__(256) tidct_kernel(const float* __restrict__ in
 
     for (int wy = y0 - 7; wy < ylast; ++wy) {
         if (has_col) {
+            float V[8];
+            fdct<8>(col, V);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                float v = 0.f;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) v = fmaf(Dc<8>(u, i), col[i], v);
-                Vs[u * 256 + t] = v;
-            }
+            for (int u = 0; u < 8; ++u) Vs[u * 256 + t] = V[u];
 #pragma unroll
             for (int i = 0; i < 7; ++i) col[i] = col[i + 1];
             if (wy + 8 < ylast + 7) col[7] = __ldg(img + (int64_t)reflect(wy + 8, H) * W + xc);
@@ -173,21 +211,14 @@ __global__ void __launch_bounds__(256) tidct_kernel(const float* __restrict__ in
                 float vr[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) vr[j] = Vs[u * 256 + t + j];
-                float c[8];
+                float c[8], qr[8];
+                fdct<8>(vr, c);
 #pragma unroll
-                for (int v = 0; v < 8; ++v) {
-                    float s = 0.f;
+                for (int v = 0; v < 8; ++v)
+                    c[v] = (fabsf(c[v]) > thr || (u == 0 && v == 0)) ? c[v] : 0.f;
+                idct<8>(c, qr);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) s = fmaf(vr[j], Dc<8>(v, j), s);
-                    c[v] = (fabsf(s) > thr || (u == 0 && v == 0)) ? s : 0.f;
-                }
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    float s = 0.f;
-#pragma unroll
-                    for (int v = 0; v < 8; ++v) s = fmaf(c[v], Dc<8>(v, j), s);
-                    q[u * 8 + j] = s;
-                }
+                for (int j = 0; j < 8; ++j) q[u * 8 + j] = qr[j];
             }
         }
         __syncthreads();
@@ -200,13 +231,10 @@ __global__ void __launch_bounds__(256) tidct_kernel(const float* __restrict__ in
                 for (int d = 0; d < 8; ++d) s += Qs[(t + d) * kQS + u * 8 + (7 - d)];
                 S[u] = s;
             }
+            float X[8];
+            idct<8>(S, X);
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                float s = acc[kk];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) s = fmaf(Dc<8>(u, kk), S[u], s);
-                acc[kk] = s;
-            }
+            for (int kk = 0; kk < 8; ++kk) acc[kk] += X[kk];
             if (wy >= y0 && x0 + t < W) dst[(int64_t)wy * W + x0 + t] = acc[0] * (1.f / 64.f);
 #pragma unroll
             for (int kk = 0; kk < 7; ++kk) acc[kk] = acc[kk + 1];
@@ -235,9 +263,8 @@ cudaError_t launch_ida_linear(const IdaLinArgs& a, cudaStream_t s) {
 cudaError_t launch_ida_sigma(const ImgGeom& g, const int64_t* offsets, const double* partial,
                              float* sigma, float* sigma_trace, int iters, int t, uint32_t* status,
                              cudaStream_t s) {
-    ida_sigma_kernel<<<g.n_img, 32, 0, s>>>(partial, ida_ctas_per_image(g), offsets, g.n_blocks,
-                                            sigma, sigma_trace, iters, t, status);
-    return cudaGetLastError();
+    return launch_pdl(ida_sigma_kernel, dim3(g.n_img), dim3(32), 0, s, partial, ida_ctas_per_image(g), offsets,
+                      (int64_t)g.n_blocks, sigma, sigma_trace, iters, t, status);
 }
 
 cudaError_t launch_tidct(const float* in, float* out, int n_img, int H, int W, const float* sigma,
@@ -247,8 +274,7 @@ cudaError_t launch_tidct(const float* in, float* out, int n_img, int H, int W, c
                                          (int)smem);
     if (e) return e;
     dim3 grid((unsigned)((W + kTW - 1) / kTW), (unsigned)((H + kTH - 1) / kTH), (unsigned)n_img);
-    tidct_kernel<<<grid, 256, smem, s>>>(in, out, H, W, sigma, lambda);
-    return cudaGetLastError();
+    return launch_pdl(tidct_kernel, grid, dim3(256), smem, s, in, out, H, W, sigma, lambda);
 }
 
 }  // namespace abcs

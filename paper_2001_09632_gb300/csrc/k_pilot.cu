@@ -20,8 +20,9 @@ namespace abcs {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) bbv_kernel(const uint8_t* __restrict__ img, ImgGeom g,
                                                   int L, int X0, int nS, int32_t* __restrict__ w,
-                                                  unsigned long long* __restrict__ wsum) {
+                                                  unsigned long long* __restrict__ wpart) {
     __shared__ unsigned long long sh[32];
+    griddep_wait();
     const int k = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long v = 0;
@@ -45,13 +46,21 @@ __global__ void __launch_bounds__(256) bbv_kernel(const uint8_t* __restrict__ im
         v = (unsigned long long)s;
     }
     v = block_sum(v, sh);
-    if (threadIdx.x == 0 && v) atomicAdd(wsum + k, v);
+    if (threadIdx.x == 0) wpart[(int64_t)k * gridDim.x + blockIdx.x] = v;
+}
+
+// Pilot CTAs per image: the number of partial sums the allocation adds up.
+int pilot_ctas_per_image(const SenseArgs& a) {
+    if (a.variant == ABCS_DD) {
+        const int NB = kTileCols / a.g.B;
+        return ((a.g.nbw + NB - 1) / NB) * a.g.nbh;
+    }
+    return (int)((a.g.n_blocks + 255) / 256);
 }
 
 cudaError_t launch_bbv_pilot(const SenseArgs& a, cudaStream_t s) {
     dim3 grid((unsigned)((a.g.n_blocks + 255) / 256), (unsigned)a.g.n_img);
-    bbv_kernel<<<grid, 256, 0, s>>>(a.img, a.g, a.L, a.X0, a.nS, a.w, a.wsum);
-    return cudaGetLastError();
+    return launch_pdl(bbv_kernel, grid, dim3(256), 0, s, a.img, a.g, a.L, a.X0, a.nS, a.w, a.wpart);
 }
 
 // ---------------------------------------------------------------------------
@@ -68,23 +77,23 @@ ABCS_D int rational_sign(int u, int n) {
     return (((n + 1) >> 1) & 1) ? -1 : 1;    // sign of cos(pi (2n+1) / 4)
 }
 
+// Exact decision |c(u,v)| > T for one block, re-reading its pixels.
 template <int B>
-ABCS_D bool dd_exceeds_exact(const uint8_t* Xs, int blk, int pos, int T, uint32_t* status) {
-    const int u = pos / B, v = pos % B;
-    const int col0 = blk * B;
+ABCS_D bool dd_exceeds_exact(const uint8_t* blk, int64_t pitch, int u, int v, int T,
+                             uint32_t* status) {
     constexpr int H2 = B / 2;
     if ((u == 0 || u == H2) && (v == 0 || v == H2)) {
         long long S = 0;
         for (int n = 0; n < B; ++n)
             for (int m = 0; m < B; ++m)
-                S += rational_sign<B>(u, n) * rational_sign<B>(v, m) * (int)Xs[n * kTileCols + col0 + m];
+                S += rational_sign<B>(u, n) * rational_sign<B>(v, m) * (int)__ldg(blk + n * pitch + m);
         return llabs(S) > (long long)T * B;
     }
     double c = 0.0;
-    for (int m = 0; m < B; ++m) {
-        double col = 0.0;
-        for (int n = 0; n < B; ++n) col = fma(Dd<B>(u, n), (double)Xs[n * kTileCols + col0 + m], col);
-        c = fma(col, Dd<B>(v, m), c);
+    for (int n = 0; n < B; ++n) {
+        double row = 0.0;
+        for (int m = 0; m < B; ++m) row = fma((double)__ldg(blk + n * pitch + m), Dd<B>(v, m), row);
+        c = fma(Dd<B>(u, n), row, c);
     }
     const double d = fabs(c) - (double)T;
     if (fabs(d) <= 1e-9) {
@@ -95,61 +104,76 @@ ABCS_D bool dd_exceeds_exact(const uint8_t* Xs, int blk, int pos, int T, uint32_
 }
 
 template <int B>
-__global__ void __launch_bounds__(256) dd_pilot_kernel(SenseArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__global__ void __launch_bounds__(256, 4) dd_pilot_kernel(SenseArgs a) {
     using Tl = Tile<B>;
-    uint8_t* Xs = smem;
-    float* Ts = reinterpret_cast<float*>(smem + Tl::XS_BYTES);
-    float* Zs = Ts + Tl::TS_FLOATS;
-    __shared__ int ncount[Tl::NB];
+    __shared__ float Ts[Tl::FLOATS];
+    __shared__ uint16_t zz[B * B];
     __shared__ unsigned long long sh[32];
 
     const ImgGeom& g = a.g;
     const int k = blockIdx.z, bi = blockIdx.y, bj0 = blockIdx.x * Tl::NB;
     const int nblk = min(Tl::NB, g.nbw - bj0);
-    const uint8_t* img = a.img + (int64_t)k * g.img_stride;
-    load_u8_tile<B>(Xs, img, g.pitch, bi * B, bj0 * B, g.W);
-    if (threadIdx.x < Tl::NB) ncount[threadIdx.x] = 0;
-    __syncthreads();
-    float x[B];
+    const int t = threadIdx.x;
+    const uint8_t* img = a.img + (int64_t)k * g.img_stride + (int64_t)(bi * B) * g.pitch;
+    load_zz_table<B>(zz);
+    griddep_wait();
+    {
+        const int b = t / B, n = t % B;
+        float x[B];
+        if (b < nblk) {
+            const uint8_t* src = img + (int64_t)n * g.pitch + (bj0 + b) * B;
+            const bool vec = ((reinterpret_cast<uintptr_t>(src) & (uintptr_t)(B >= 16 ? 15 : B - 1)) == 0);
+            load_u8_row<B>(src, vec, x);
+        } else {
 #pragma unroll
-    for (int n = 0; n < B; ++n) x[n] = (float)Xs[n * kTileCols + threadIdx.x];
-    fwd_dct_tile_fp32<B>(x, Ts, Zs);
+            for (int i = 0; i < B; ++i) x[i] = 0.f;
+        }
+        fwd_rows_to_smem<B>(x, Ts);
+    }
+    __syncthreads();
+    fwd_cols_in_smem<B>(Ts);
+    __syncthreads();
 
-    // rigorous FP32 band: (4B + 8) u * 255 * B bounds |c_fp32 - c| (see DESIGN)
+    // rigorous FP32 band: (4B + 8) u * 255 * B bounds |c_fp32 - c| for any
+    // summation order of depth <= 2B (u = 2^-24)
     const float band = (4.f * B + 8.f) * 5.9604645e-8f * 255.f * B;
     const float T = (float)a.T;
     const int m1 = a.m1;
-    for (int e = threadIdx.x; e < nblk * m1; e += blockDim.x) {
-        const int b = e / m1, r = e % m1;
-        const float c = fabsf(Zs[b * B * B + r]);
-        bool hit;
-        if (c > T + band) hit = true;
-        else if (c < T - band) hit = false;
-        else hit = dd_exceeds_exact<B>(Xs, b, zz_pos<B>(r), a.T, a.status);
-        if (hit) atomicAdd(&ncount[b], 1);
+    const int w = t >> 5, lane = t & 31;
+    unsigned long long mine = 0;
+#pragma unroll
+    for (int q = 0; q < Tl::BPW; ++q) {
+        const int b = w * Tl::BPW + q;
+        if (b >= nblk) break;
+        const float* blk = Ts + b * Tl::BLK;
+        int n = 0;
+        for (int j0 = 0; j0 < m1; j0 += 32) {
+            const int j = j0 + lane;
+            bool hit = false;
+            if (j < m1) {
+                const float c = fabsf(blk[zz[j]]);
+                if (c > T + band) hit = true;
+                else if (c >= T - band) {
+                    const int p = zz_pos<B>(j);
+                    hit = dd_exceeds_exact<B>(img + (bj0 + b) * B, g.pitch, p / B, p % B, a.T, a.status);
+                }
+            }
+            n += __popc(__ballot_sync(0xffffffffu, hit));
+        }
+        if (lane == 0) {
+            a.w[(int64_t)k * g.n_blocks + (int64_t)bi * g.nbw + bj0 + b] = n;
+            mine += (unsigned long long)n;
+        }
     }
-    __syncthreads();
-    unsigned long long v = 0;
-    if (threadIdx.x < nblk) {
-        const int n = ncount[threadIdx.x];
-        a.w[(int64_t)k * g.n_blocks + (int64_t)bi * g.nbw + bj0 + threadIdx.x] = n;
-        v = (unsigned long long)n;
-    }
-    v = block_sum(v, sh);
-    if (threadIdx.x == 0 && v) atomicAdd(a.wsum + k, v);
+    mine = block_sum(mine, sh);
+    if (t == 0) a.wpart[(int64_t)k * gridDim.x * gridDim.y + (int64_t)blockIdx.y * gridDim.x + blockIdx.x] = mine;
 }
 
 template <int B>
 static cudaError_t launch_dd_B(const SenseArgs& a, cudaStream_t s) {
     using Tl = Tile<B>;
-    const size_t smem = Tl::XS_BYTES + (Tl::TS_FLOATS + Tl::ZS_FLOATS) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(dd_pilot_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e) return e;
     dim3 grid((unsigned)((a.g.nbw + Tl::NB - 1) / Tl::NB), (unsigned)a.g.nbh, (unsigned)a.g.n_img);
-    dd_pilot_kernel<B><<<grid, 256, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(dd_pilot_kernel<B>, grid, dim3(256), 0, s, a);
 }
 
 cudaError_t launch_dd_pilot(const SenseArgs& a, cudaStream_t s) {

@@ -1,0 +1,82 @@
+"""Tensor-core block DCT (B = 16): FP16 hi+lo and BF16 hi+lo split products,
+and the single BF16 product, against the FP64 oracle.
+
+Counts never depend on the precision (the pilot decisions are exact), so
+they must be bit-exact for every precision.  Coefficients and pixels:
+FP16x2 must meet the FP32 bar (1e-5 relative L2); BF16x2 and BF16 are
+reported with the bounds their arithmetic gives (16 and 8 significant bits).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2001_09632_gb300 import abcs, synth
+from tests import gpu_util as G
+
+pytestmark = pytest.mark.gpu
+
+BOUND = {abcs.FP32: 1e-5, abcs.TC_FP16X2: 1e-5, abcs.TC_BF16X2: 1e-4, abcs.TC_BF16: 1e-2}
+NAMES = {abcs.FP32: "fp32", abcs.TC_FP16X2: "fp16x2", abcs.TC_BF16X2: "bf16x2", abcs.TC_BF16: "bf16"}
+
+
+def _oracle(imgs, B, r, variant):
+    outs = [O.sense(im, B, r, variant) for im in imgs]
+    counts = np.concatenate([o["counts"] for o in outs])
+    y = np.concatenate([o["y"] for o in outs])
+    return outs, counts, y
+
+
+@pytest.mark.parametrize("prec", [abcs.TC_FP16X2, abcs.TC_BF16X2, abcs.TC_BF16])
+@pytest.mark.parametrize("variant", [O.ZZ, O.BBV, O.DD])
+@pytest.mark.parametrize("shape", [(2, 96, 336), (1, 64, 1040), (3, 48, 48)])
+def test_tc_sense_and_reconstruct(handle, prec, variant, shape):
+    n, H, W = shape
+    B, r = 16, 0.3
+    imgs = np.stack([synth.gen_image(H, W, 300 + k) for k in range(n)])
+    outs, c_ref, y_ref = _oracle(imgs, B, r, variant)
+    got = G.sense(handle, imgs, B, r, variant, precision=prec)
+    assert got["bits"] == 0
+    assert np.array_equal(got["counts"], c_ref)
+    assert np.array_equal(got["offsets"], np.concatenate([[0], np.cumsum(c_ref)]))
+    ey = G.rel_l2(got["y"], y_ref)
+    assert ey <= BOUND[prec], ey
+    rec, _, bits = G.reconstruct(handle, *got["d"], n, H, W, B, precision=prec)
+    assert bits == 0
+    nB = outs[0]["plan"]["nB"]
+    Hc, Wc = (H // B) * B, (W // B) * B
+    for k in range(n):
+        ref = O.reconstruct(outs[k]["counts"], outs[k]["y"], Hc, Wc, B)
+        ex = G.rel_l2(rec[k], ref)
+        assert ex <= BOUND[prec], ex
+
+
+def test_precision_table(handle, capsys):
+    """Relative L2 error vs FP64 and PSNR of the reconstruction for each
+    precision on 8 images of 512x512, BBV, r = 0.3 (printed; asserted bounds)."""
+    B, r = 16, 0.3
+    imgs = synth.gen_batch(8, 512, 512, 77)
+    outs, c_ref, y_ref = _oracle(imgs, B, r, O.BBV)
+    recs_ref = [O.reconstruct(o["counts"], o["y"], 512, 512, B) for o in outs]
+    lines = []
+    for prec in (abcs.FP32, abcs.TC_FP16X2, abcs.TC_BF16X2, abcs.TC_BF16):
+        got = G.sense(handle, imgs, B, r, O.BBV, precision=prec)
+        rec, _, _ = G.reconstruct(handle, *got["d"], 8, 512, 512, B, precision=prec)
+        ey = G.rel_l2(got["y"], y_ref)
+        ex = G.rel_l2(rec, np.stack(recs_ref))
+        dpsnr = np.mean([O.psnr(rec[k], imgs[k]) - O.psnr(recs_ref[k], imgs[k]) for k in range(8)])
+        lines.append(f"{NAMES[prec]:7s} coeff relL2 {ey:.3e}  pixel relL2 {ex:.3e}  dPSNR {dpsnr:+.5f} dB")
+        assert np.array_equal(got["counts"], c_ref)
+        assert ey <= BOUND[prec] and ex <= BOUND[prec]
+    with capsys.disabled():
+        print("\n" + "\n".join(lines))
+
+
+def test_tc_rejects_other_block_sizes(handle):
+    import torch
+    d = torch.zeros(64 * 64, dtype=torch.uint8, device="cuda")
+    c = torch.zeros(64, dtype=torch.int32, device="cuda")
+    o = torch.zeros(65, dtype=torch.int64, device="cuda")
+    y = torch.zeros(4096, dtype=torch.float32, device="cuda")
+    with pytest.raises(abcs.AbcsError) as e:
+        abcs.abcs_sense(handle, d, 1, 64, 64, 64, 4096, 8, 0.3, O.ZZ, abcs.TC_FP16X2, c, o, y, 4096)
+    assert e.value.status == 2
