@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mpixel/s ABCS sense+recon and IDA/iter; learned vs plain IDA at equal PSNR"
 N_IMG, H, W, B, SUBRATE, SEED = 64, 512, 512, 16, 0.3, 1000
-IDA_ITERS, LAMBDA, DF = 10, 2.7, 2.0
+IDA_ITERS, LAMBDA, DF = 10, 2.3, 2.0
 FLUSH_BYTES = 512 << 20
 
 

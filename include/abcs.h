@@ -173,11 +173,56 @@ abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offse
                      int denoiser, double lambda, const void* cnn_weights,
                      float* x_out, float* sigma_trace, void* stream);
 
+/* The denoiser input of one IDA iteration: runs iterations 0 .. t-1 as
+ * abcs_ida does, then the linear part of iteration t, and returns
+ * r^t = x^t + A^T z^t (r_out [device] float [n_img][Hc][Wc]) and sigma^t
+ * (sigma_out [device] float [n_img]).  Used to build training pairs
+ * (r^t, clean image) for the learned denoiser. */
+abcs_status abcs_ida_capture(abcs_handle* h, const int32_t* counts, const int64_t* offsets,
+                             const float* y, int n_img, int H, int W, int B, int t, double damping,
+                             int denoiser, double lambda, const void* cnn_weights, float* r_out,
+                             float* sigma_out, void* stream);
+
 /* The plain denoiser alone: for every image k, out = TI-DCT(in, lambda * sigma[k]).
  *   in, out [device] float [n_img][H][W] (dense, H, W >= 1; in != out)
  *   sigma   [device] float [n_img] */
 abcs_status abcs_denoise_tidct(abcs_handle* h, const float* in, int n_img, int H, int W,
                                const float* sigma, double lambda, float* out, void* stream);
+
+/* Learned denoiser.  The paper plugs a pretrained 17-layer DnCNN into IDA
+ * (Sec. VI-4); this library's learned denoiser is a smaller residual CNN of
+ * the same kind, trained with the calls below:
+ *   conv3x3 2->32 + ReLU, 6 x [conv3x3 32->32 + ReLU], conv3x3 32->1,
+ *   x_hat = r - 255 * net(r / 255, sigma / 255)   (zero 'same' padding).
+ * Parameters are one FP32 vector of abcs_cnn_param_count() values, layer by
+ * layer: w_l[co][ci][3][3] then b_l[co].  Inference runs from a packed
+ * device copy (BF16 mid-layer weights) of abcs_cnn_packed_bytes() bytes. */
+int64_t abcs_cnn_param_count(void);
+size_t abcs_cnn_packed_bytes(void);
+
+/* packed [device] <- params [device] (FP32 vector above). */
+abcs_status abcs_cnn_pack(abcs_handle* h, const float* params, void* packed, void* stream);
+
+/* out = x_hat(in, sigma[k]) for every image k; in, out [device] float
+ * [n_img][H][W] (in != out), sigma [device] float [n_img]. */
+abcs_status abcs_cnn_denoise(abcs_handle* h, const void* packed, const float* in, const float* sigma,
+                             int n_img, int H, int W, float* out, void* stream);
+
+/* Loss L = mean((x_hat - clean)^2) / 255^2 over the n crops and its
+ * gradient with respect to the parameters of `packed`.
+ *   r, clean [device] float [n][H][W]; sigma [device] float [n]
+ *   grad [device] float [abcs_cnn_param_count()]; loss [device] float [1] */
+abcs_status abcs_cnn_grad(abcs_handle* h, const void* packed, const float* r, const float* clean,
+                          const float* sigma, int n, int H, int W, float* grad, float* loss,
+                          void* stream);
+
+/* One Adam step (beta = 0.9 / 0.999, eps = 1e-8, bias-corrected, `step`
+ * counted from 1) on params [device] with moments adam_m, adam_v [device]
+ * (same length, zero before step 1): packs params into `packed`, computes
+ * the gradient of the batch, updates params and the moments, re-packs. */
+abcs_status abcs_cnn_train_step(abcs_handle* h, float* params, float* adam_m, float* adam_v, int step,
+                                double lr, void* packed, const float* r, const float* clean,
+                                const float* sigma, int n, int H, int W, float* loss, void* stream);
 
 /* abcs_sense without any device allocation (the paper has no counterpart;
  * this is a library service).  For callers that may not call cudaMalloc

@@ -60,11 +60,19 @@ _SIGS = {
     "abcs_denoise_tidct": [_P, _P, _I, _I, _I, _P, _D, _P, _P],
     "abcs_sync_status": [_P, _P, C.POINTER(C.c_uint32)],
     "abcs_sense_noalloc": [_P, _I, _I, _I, _L, _L, _I, _D, _I, _I, _P, _P, _P, _L, _P, _P],
+    "abcs_ida_capture": [_P, _P, _P, _P, _I, _I, _I, _I, _I, _D, _I, _D, _P, _P, _P, _P],
+    "abcs_cnn_param_count": [],
+    "abcs_cnn_packed_bytes": [],
+    "abcs_cnn_pack": [_P, _P, _P, _P],
+    "abcs_cnn_denoise": [_P, _P, _P, _P, _I, _I, _I, _P, _P],
+    "abcs_cnn_grad": [_P, _P, _P, _P, _P, _I, _I, _I, _P, _P, _P],
+    "abcs_cnn_train_step": [_P, _P, _P, _P, _I, _D, _P, _P, _P, _P, _I, _I, _I, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
     _f.argtypes = _args
-    _f.restype = C.c_char_p if _name == "abcs_last_error" else (None if _name == "abcs_destroy" else C.c_int)
+    _f.restype = {"abcs_last_error": C.c_char_p, "abcs_destroy": None, "abcs_cnn_param_count": C.c_int64,
+                  "abcs_cnn_packed_bytes": C.c_size_t}.get(_name, C.c_int)
 
 
 def _ptr(x):
@@ -129,6 +137,13 @@ def abcs_ida(h, counts, offsets, y, n_img, H, W, B, iters, damping, denoiser, la
                         _stream(stream)))
 
 
+def abcs_ida_capture(h, counts, offsets, y, n_img, H, W, B, t, damping, denoiser, lam, cnn_weights,
+                     r_out, sigma_out, stream=None) -> None:
+    _check(lib.abcs_ida_capture(h, _ptr(counts), _ptr(offsets), _ptr(y), n_img, H, W, B, t, damping,
+                                denoiser, lam, _ptr(cnn_weights), _ptr(r_out), _ptr(sigma_out),
+                                _stream(stream)))
+
+
 def abcs_denoise_tidct(h, inp, n_img, H, W, sigma, lam, out, stream=None) -> None:
     _check(lib.abcs_denoise_tidct(h, _ptr(inp), n_img, H, W, _ptr(sigma), lam, _ptr(out),
                                   _stream(stream)))
@@ -140,6 +155,35 @@ def abcs_sense_noalloc(img, n_img, H, W, pitch, img_stride, B, subrate, variant,
     _check(lib.abcs_sense_noalloc(_ptr(img), n_img, H, W, pitch, img_stride, B, subrate, variant,
                                   precision, _ptr(counts), _ptr(offsets), _ptr(coeffs),
                                   coeff_capacity, _ptr(pilot), _stream(stream)))
+
+
+def abcs_cnn_param_count() -> int:
+    return lib.abcs_cnn_param_count()
+
+
+def abcs_cnn_packed_bytes() -> int:
+    return lib.abcs_cnn_packed_bytes()
+
+
+def abcs_cnn_pack(h, params, packed, stream=None) -> None:
+    _check(lib.abcs_cnn_pack(h, _ptr(params), _ptr(packed), _stream(stream)))
+
+
+def abcs_cnn_denoise(h, packed, inp, sigma, n_img, H, W, out, stream=None) -> None:
+    _check(lib.abcs_cnn_denoise(h, _ptr(packed), _ptr(inp), _ptr(sigma), n_img, H, W, _ptr(out),
+                                _stream(stream)))
+
+
+def abcs_cnn_grad(h, packed, r, clean, sigma, n, H, W, grad, loss, stream=None) -> None:
+    _check(lib.abcs_cnn_grad(h, _ptr(packed), _ptr(r), _ptr(clean), _ptr(sigma), n, H, W, _ptr(grad),
+                             _ptr(loss), _stream(stream)))
+
+
+def abcs_cnn_train_step(h, params, adam_m, adam_v, step, lr, packed, r, clean, sigma, n, H, W, loss,
+                        stream=None) -> None:
+    _check(lib.abcs_cnn_train_step(h, _ptr(params), _ptr(adam_m), _ptr(adam_v), step, lr, _ptr(packed),
+                                   _ptr(r), _ptr(clean), _ptr(sigma), n, H, W, _ptr(loss),
+                                   _stream(stream)))
 
 
 def abcs_sync_status(h, stream=None) -> int:

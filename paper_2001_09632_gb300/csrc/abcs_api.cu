@@ -326,25 +326,49 @@ abcs_status abcs_denoise_tidct(abcs_handle* h, const float* in, int n_img, int H
     return ABCS_OK;
 }
 
+// IDA runner: `iters` full iterations into x_out; with capture >= 0 it
+// stops after the linear part of iteration `capture` and copies r^t and
+// sigma^t to r_cap / sig_cap instead.
+static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t* offsets, const float* y,
+                           int n_img, int H, int W, int B, int iters, double damping, int denoiser,
+                           double lambda, const void* cnn_weights, float* x_out, float* sigma_trace,
+                           int capture, float* r_cap, float* sig_cap, void* stream);
+
 abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offsets, const float* y,
                      int n_img, int H, int W, int B, int iters, double damping, int denoiser,
                      double lambda, const void* cnn_weights, float* x_out, float* sigma_trace,
                      void* stream) {
+    if (!x_out) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    return ida_run(h, counts, offsets, y, n_img, H, W, B, iters, damping, denoiser, lambda, cnn_weights, x_out,
+                   sigma_trace, -1, nullptr, nullptr, stream);
+}
+
+abcs_status abcs_ida_capture(abcs_handle* h, const int32_t* counts, const int64_t* offsets, const float* y,
+                             int n_img, int H, int W, int B, int t, double damping, int denoiser, double lambda,
+                             const void* cnn_weights, float* r_out, float* sigma_out, void* stream) {
+    if (!r_out || !sigma_out) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (t < 0) return fail(ABCS_ERR_INVALID_ARG, "t must be >= 0");
+    return ida_run(h, counts, offsets, y, n_img, H, W, B, t + 1, damping, denoiser, lambda, cnn_weights, nullptr,
+                   nullptr, t, r_out, sigma_out, stream);
+}
+
+static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t* offsets, const float* y,
+                           int n_img, int H, int W, int B, int iters, double damping, int denoiser,
+                           double lambda, const void* cnn_weights, float* x_out, float* sigma_trace,
+                           int capture, float* r_cap, float* sig_cap, void* stream) {
     if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
     if (!valid_B(B)) return fail(ABCS_ERR_INVALID_ARG, "B must be 4, 8, 16 or 32");
     if (H < B || W < B) return fail(ABCS_ERR_INVALID_ARG, "image smaller than one block");
     if (n_img < 1 || n_img > 65535) return fail(ABCS_ERR_INVALID_ARG, "n_img must be in [1, 65535]");
-    if (!counts || !offsets || !y || !x_out) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (!counts || !offsets || !y) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
     if (iters < 0) return fail(ABCS_ERR_INVALID_ARG, "iters must be >= 0");
     if (!(damping > 0.0)) return fail(ABCS_ERR_INVALID_ARG, "damping must be > 0");
     if (denoiser < ABCS_DEN_NONE || denoiser > ABCS_DEN_CNN)
         return fail(ABCS_ERR_INVALID_ARG, "bad denoiser %d", denoiser);
     if (denoiser == ABCS_DEN_TIDCT && !(lambda >= 0.0))
         return fail(ABCS_ERR_INVALID_ARG, "lambda must be >= 0");
-    if (denoiser == ABCS_DEN_CNN) {
-        if (!cnn_weights) return fail(ABCS_ERR_INVALID_ARG, "CNN denoiser needs weights");
-        return fail(ABCS_ERR_UNSUPPORTED, "CNN denoiser is not built in this library");
-    }
+    if (denoiser == ABCS_DEN_CNN && !cnn_weights)
+        return fail(ABCS_ERR_INVALID_ARG, "CNN denoiser needs packed weights (abcs_cnn_pack)");
     DeviceGuard dg(h->device);
     if (!dg.ok) return fail(ABCS_ERR_CUDA, "cannot select the handle's device");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -354,6 +378,8 @@ abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offse
         ABCS_CUDA(cudaMemsetAsync(x_out, 0, npx * sizeof(float), s), "memset");
         return ABCS_OK;
     }
+    // the denoiser writes its estimate here; a capture run has no x_out
+    const bool capturing = capture >= 0;
     const int cpi = ida_ctas_per_image(g);
     Carver c;
     const size_t o_r0 = c.take<float>(npx);
@@ -362,6 +388,8 @@ abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offse
     const size_t o_z1 = c.take<float>(npx);
     const size_t o_part = c.take<double>((size_t)n_img * cpi);
     const size_t o_sig = c.take<float>(n_img);
+    const size_t o_act = c.take<uint16_t>(denoiser == ABCS_DEN_CNN ? (size_t)2 * npx * 32 : 0);
+    const size_t o_x = c.take<float>(capturing ? npx : 0);
     abcs_status st = ensure_ws(h, c.off);
     if (st) return st;
     float* rbuf[2] = {at<float>(h, o_r0), at<float>(h, o_r1)};
@@ -376,6 +404,7 @@ abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offse
     a.partial = at<double>(h, o_part);
     a.inv_df = (float)(1.0 / damping);
     a.status = h->status;
+    if (capturing) x_out = at<float>(h, o_x);
     const float* x_cur = nullptr;        // x^0 = 0
     const float* z_prev = nullptr;       // z^{-1} = 0
     for (int t = 0; t < iters; ++t) {
@@ -386,8 +415,18 @@ abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offse
         ABCS_CUDA(launch_ida_linear(a, s), "ida_linear launch");
         ABCS_CUDA(launch_ida_sigma(g, offsets, a.partial, sig, sigma_trace, iters, t, h->status, s),
                   "ida_sigma launch");
+        if (t == capture) {
+            ABCS_CUDA(cudaMemcpyAsync(r_cap, a.r, npx * sizeof(float), cudaMemcpyDeviceToDevice, s), "copy r");
+            ABCS_CUDA(cudaMemcpyAsync(sig_cap, sig, n_img * sizeof(float), cudaMemcpyDeviceToDevice, s),
+                      "copy sigma");
+            return ABCS_OK;
+        }
         if (denoiser == ABCS_DEN_TIDCT) {
             ABCS_CUDA(launch_tidct(a.r, x_out, n_img, g.Hc, g.Wc, sig, (float)lambda, s), "tidct launch");
+            x_cur = x_out;
+        } else if (denoiser == ABCS_DEN_CNN) {
+            ABCS_CUDA(cnn_forward(cnn_weights, a.r, sig, n_img, g.Hc, g.Wc, at<void>(h, o_act), 0, 0, x_out, s),
+                      "cnn launch");
             x_cur = x_out;
         } else {
             x_cur = a.r;                  // identity: x^{t+1} = r^t
@@ -397,6 +436,69 @@ abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offse
     if (x_cur != x_out)
         ABCS_CUDA(cudaMemcpyAsync(x_out, x_cur, npx * sizeof(float), cudaMemcpyDeviceToDevice, s),
                   "copy result");
+    return ABCS_OK;
+}
+
+int64_t abcs_cnn_param_count(void) { return cnn_param_count(); }
+size_t abcs_cnn_packed_bytes(void) { return cnn_packed_bytes(); }
+
+abcs_status abcs_cnn_pack(abcs_handle* h, const float* params, void* packed, void* stream) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    if (!params || !packed) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    DeviceGuard dg(h->device);
+    ABCS_CUDA(cnn_pack(params, packed, static_cast<cudaStream_t>(stream)), "cnn pack launch");
+    return ABCS_OK;
+}
+
+abcs_status abcs_cnn_denoise(abcs_handle* h, const void* packed, const float* in, const float* sigma, int n_img,
+                             int H, int W, float* out, void* stream) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    if (!packed || !in || !sigma || !out) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (in == out) return fail(ABCS_ERR_INVALID_ARG, "in and out must differ");
+    if (n_img < 1 || n_img > 65535 || H < 1 || W < 1) return fail(ABCS_ERR_INVALID_ARG, "bad size");
+    DeviceGuard dg(h->device);
+    Carver c;
+    const size_t o_act = c.take<uint16_t>((size_t)2 * n_img * H * W * 32);
+    abcs_status st = ensure_ws(h, c.off);
+    if (st) return st;
+    ABCS_CUDA(cnn_forward(packed, in, sigma, n_img, H, W, at<void>(h, o_act), 0, 0, out,
+                          static_cast<cudaStream_t>(stream)),
+              "cnn launch");
+    return ABCS_OK;
+}
+
+abcs_status abcs_cnn_grad(abcs_handle* h, const void* packed, const float* r, const float* clean, const float* sigma,
+                          int n, int H, int W, float* grad, float* loss, void* stream) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    if (!packed || !r || !clean || !sigma || !grad || !loss) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (n < 1 || n > 65535 || H < 1 || W < 1) return fail(ABCS_ERR_INVALID_ARG, "bad size");
+    DeviceGuard dg(h->device);
+    abcs_status st = ensure_ws(h, cnn_grad_ws_bytes(n, H, W));
+    if (st) return st;
+    ABCS_CUDA(cnn_grad(packed, r, clean, sigma, n, H, W, h->ws, grad, loss, static_cast<cudaStream_t>(stream)),
+              "cnn grad launch");
+    return ABCS_OK;
+}
+
+abcs_status abcs_cnn_train_step(abcs_handle* h, float* params, float* adam_m, float* adam_v, int step, double lr,
+                                void* packed, const float* r, const float* clean, const float* sigma, int n, int H,
+                                int W, float* loss, void* stream) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    if (!params || !adam_m || !adam_v || !packed || !r || !clean || !sigma || !loss)
+        return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (step < 1) return fail(ABCS_ERR_INVALID_ARG, "step counts from 1");
+    if (!(lr > 0.0)) return fail(ABCS_ERR_INVALID_ARG, "lr must be > 0");
+    if (n < 1 || n > 65535 || H < 1 || W < 1) return fail(ABCS_ERR_INVALID_ARG, "bad size");
+    DeviceGuard dg(h->device);
+    const size_t gbytes = ((size_t)cnn_param_count() * 4 + 255) & ~size_t(255);
+    abcs_status st = ensure_ws(h, cnn_grad_ws_bytes(n, H, W) + gbytes);
+    if (st) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float* grad = reinterpret_cast<float*>(static_cast<char*>(h->ws) + cnn_grad_ws_bytes(n, H, W));
+    ABCS_CUDA(cnn_pack(params, packed, s), "cnn pack launch");
+    ABCS_CUDA(cnn_grad(packed, r, clean, sigma, n, H, W, h->ws, grad, loss, s), "cnn grad launch");
+    ABCS_CUDA(cnn_adam(params, grad, adam_m, adam_v, step, (float)lr, s), "adam launch");
+    ABCS_CUDA(cnn_pack(params, packed, s), "cnn pack launch");
     return ABCS_OK;
 }
 

@@ -208,4 +208,15 @@ cudaError_t launch_ida_sigma(const ImgGeom& g, const int64_t* offsets, const dou
 int ida_ctas_per_image(const ImgGeom& g);
 cudaError_t launch_tidct(const float* in, float* out, int n_img, int H, int W, const float* sigma,
                          float lambda, cudaStream_t s);
+
+// learned denoiser (k_cnn.cu)
+int cnn_param_count();
+size_t cnn_packed_bytes();
+cudaError_t cnn_pack(const float* params, void* packed, cudaStream_t s);
+cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, int n, int H, int W,
+                        void* act_buf, int keep_all, int mode, float* out, cudaStream_t s);
+cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, const float* sigma, int n, int H,
+                     int W, void* ws, float* grad, float* loss, cudaStream_t s);
+size_t cnn_grad_ws_bytes(int n, int H, int W);
+cudaError_t cnn_adam(float* params, const float* grad, float* m, float* v, int step, float lr, cudaStream_t s);
 }  // namespace abcs

@@ -1,0 +1,656 @@
+// Learned residual denoiser for IDA (a DnCNN-style network, Sec. VI-4):
+//   conv3x3 2->32 + ReLU, 6 x [conv3x3 32->32 + ReLU], conv3x3 32->1,
+//   x_hat = r - 255 * net(r / 255, sigma / 255), zero 'same' padding.
+// Activations and mid-layer weights are BF16 (NHWC, 32 channels = 64 bytes
+// per pixel); every sum accumulates in FP32.  The 32->32 layers run as an
+// implicit GEMM on mma.sync.m16n8k16 (BF16 in, FP32 out): a CTA owns an
+// 8 x 32 output tile, stages the 10 x 34 input tile and the layer's weights
+// in shared memory and feeds the tensor cores with ldmatrix.  The thin first
+// and last layers (2 and 1 channels) run on FP32 CUDA cores.
+//
+// Training (fwd + bwd + Adam) reuses the same conv kernel for the input
+// gradient (weights transposed in (ci, co) and flipped in the tap, epilogue
+// = ReLU mask of the layer below); weight gradients are accumulated per CTA
+// in FP32 and reduced in a fixed order (deterministic).
+#include <cuda_bf16.h>
+
+#include "abcs_common.cuh"
+
+namespace abcs {
+
+// ---------------------------------------------------------------------------
+// Parameter layout (FP32, the same as the FP64 oracle's):
+//   for l in 0..7: w_l[co][ci][3][3], then b_l[co]
+// channel plan: (2->32), 6 x (32->32), (32->1).
+// ---------------------------------------------------------------------------
+constexpr int kC = 32, kMid = 6;
+constexpr int kW0 = kC * 2 * 9, kB0 = kC;
+constexpr int kWm = kC * kC * 9, kBm = kC;
+constexpr int kW7 = kC * 9, kB7 = 1;
+constexpr int kParams = kW0 + kB0 + kMid * (kWm + kBm) + kW7 + kB7;   // 56,385
+
+ABCS_HD int param_off_w(int l) {
+    return l == 0 ? 0 : (l <= kMid ? kW0 + kB0 + (l - 1) * (kWm + kBm) : kW0 + kB0 + kMid * (kWm + kBm));
+}
+ABCS_HD int param_off_b(int l) {
+    return param_off_w(l) + (l == 0 ? kW0 : (l <= kMid ? kWm : kW7));
+}
+
+// Packed device weights (one buffer, offsets in bytes).
+struct CnnPacked {
+    float w0[kC][2][9];             // first layer, FP32 [co][ci][tap]
+    float b0[kC];
+    __nv_bfloat16 wc[kMid][9][kC][kC];   // mid layers, forward [tap][co][ci]
+    __nv_bfloat16 wd[kMid][9][kC][kC];   // mid layers, input-gradient [tap'][ci][co], tap' = 8 - tap
+    float bm[kMid][kC];
+    float w7[kC][9];                // last layer, FP32 [ci][tap]
+    float b7;
+};
+
+namespace {
+
+constexpr int TH = 8, TW = 32, IH = TH + 2, IW = TW + 2, PXS = 40;   // PXS: bf16 per pixel in smem
+
+ABCS_D void ldmatrix_x4(uint32_t (&r)[4], const void* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+ABCS_D void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+ABCS_D uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+
+// ---------------------------------------------------------------------------
+// 32 -> 32 conv3x3 as an implicit GEMM (M = pixels, N = 32, K = 9 x 32).
+// EPI 0: out = ReLU(acc + bias)            (forward)
+// EPI 1: out = acc * [mask > 0]            (input gradient through a ReLU)
+// ---------------------------------------------------------------------------
+template <int EPI>
+__global__ void __launch_bounds__(256) conv32_kernel(const __nv_bfloat16* __restrict__ in, int H, int W,
+                                                     const __nv_bfloat16* __restrict__ wts,
+                                                     const float* __restrict__ bias,
+                                                     const __nv_bfloat16* __restrict__ mask,
+                                                     __nv_bfloat16* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __nv_bfloat16* tin = reinterpret_cast<__nv_bfloat16*>(smem);         // [IH*IW][PXS]
+    __nv_bfloat16* tw = tin + IH * IW * PXS;                             // [9*32][PXS]
+    griddep_wait();
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int k = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const __nv_bfloat16* img = in + (int64_t)k * H * W * kC;
+    // stage the input tile with a 1-pixel zero halo (16-byte chunks)
+    for (int c = t; c < IH * IW * 4; c += 256) {
+        const int px = c >> 2, ch = c & 3;
+        const int yy = y0 - 1 + px / IW, xx = x0 - 1 + px % IW;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+            v = __ldg(reinterpret_cast<const uint4*>(img + ((int64_t)yy * W + xx) * kC) + ch);
+        *reinterpret_cast<uint4*>(tin + px * PXS + ch * 8) = v;
+    }
+    for (int c = t; c < 9 * kC * 4; c += 256) {
+        const int row = c >> 2, ch = c & 3;
+        *reinterpret_cast<uint4*>(tw + row * PXS + ch * 8) =
+            __ldg(reinterpret_cast<const uint4*>(wts + row * kC) + ch);
+    }
+    __syncthreads();
+
+    float acc[2][4][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int n = 0; n < 4; ++n)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[h][n][e] = 0.f;
+
+    const int arow = lane & 15, acol = (lane >> 4) * 8;          // A: pixel, channel offset
+    const int bco = (lane & 7) + (lane >> 4) * 8, bci = ((lane >> 3) & 1) * 8;   // B: co, ci offset
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            uint32_t a0[4], a1[4], b01[4], b23[4];
+            const __nv_bfloat16* ap = tin + ((warp + dy) * IW + dx + arow) * PXS + ks * 16 + acol;
+            ldmatrix_x4(a0, ap);
+            ldmatrix_x4(a1, ap + 16 * PXS);
+            const __nv_bfloat16* bp = tw + (tap * kC + bco) * PXS + ks * 16 + bci;
+            ldmatrix_x4(b01, bp);
+            ldmatrix_x4(b23, bp + 16 * PXS);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t(&a)[4] = h ? a1 : a0;
+                mma_bf16(acc[h][0], a, b01[0], b01[1]);
+                mma_bf16(acc[h][1], a, b01[2], b01[3]);
+                mma_bf16(acc[h][2], a, b23[0], b23[1]);
+                mma_bf16(acc[h][3], a, b23[2], b23[3]);
+            }
+        }
+    }
+    __syncthreads();
+    // epilogue through smem: [TH*TW][PXS] output tile, then 16-byte stores
+    __nv_bfloat16* tout = tin;
+    const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            const int co = n * 8 + 2 * q;
+            const float b0 = (EPI == 0) ? __ldg(bias + co) : 0.f, b1 = (EPI == 0) ? __ldg(bias + co + 1) : 0.f;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int px = warp * TW + h * 16 + g + 8 * half;
+                float v0 = acc[h][n][2 * half] + b0, v1 = acc[h][n][2 * half + 1] + b1;
+                if (EPI == 0) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+                *reinterpret_cast<uint32_t*>(tout + px * PXS + co) = pack_bf16(v0, v1);
+            }
+        }
+    __syncthreads();
+    __nv_bfloat16* dst = out + (int64_t)k * H * W * kC;
+    const __nv_bfloat16* msk = (EPI == 1) ? mask + (int64_t)k * H * W * kC : nullptr;
+    for (int c = t; c < TH * TW * 4; c += 256) {
+        const int px = c >> 2, ch = c & 3;
+        const int yy = y0 + px / TW, xx = x0 + px % TW;
+        if (yy >= H || xx >= W) continue;
+        uint4 v = *reinterpret_cast<const uint4*>(tout + px * PXS + ch * 8);
+        const int64_t o = ((int64_t)yy * W + xx) * kC + ch * 8;
+        if (EPI == 1) {
+            const uint4 m = __ldg(reinterpret_cast<const uint4*>(msk + o));
+            const uint32_t* mw = reinterpret_cast<const uint32_t*>(&m);
+            uint32_t* vw = reinterpret_cast<uint32_t*>(&v);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                // a BF16 activation is > 0 iff its sign bit is clear and it is not +0
+                const uint32_t lo = (mw[e] & 0xFFFFu), hi = (mw[e] >> 16);
+                const uint32_t keep_lo = (lo != 0 && !(lo & 0x8000u)) ? 0xFFFFu : 0u;
+                const uint32_t keep_hi = (hi != 0 && !(hi & 0x8000u)) ? 0xFFFF0000u : 0u;
+                vw[e] &= keep_lo | keep_hi;
+            }
+        }
+        *reinterpret_cast<uint4*>(dst + o) = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// First layer: input channels (r / 255, sigma / 255), FP32 CUDA cores.
+// One thread per output pixel; 8 x 32 tile with a 1-pixel halo of r.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) cnn_first_kernel(const float* __restrict__ r, const float* __restrict__ sigma,
+                                                        int H, int W, const CnnPacked* __restrict__ P,
+                                                        __nv_bfloat16* __restrict__ out) {
+    __shared__ float tr[IH * IW];
+    __shared__ float sw[kC * 2 * 9 + kC];
+    griddep_wait();
+    const int t = threadIdx.x, k = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const float* img = r + (int64_t)k * H * W;
+    const float s255 = __ldg(sigma + k) * (1.f / 255.f);
+    for (int c = t; c < IH * IW; c += 256) {
+        const int yy = y0 - 1 + c / IW, xx = x0 - 1 + c % IW;
+        // 2 channels per input pixel: r/255 and sigma/255 (both 0 outside the image)
+        tr[c] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? __ldg(img + (int64_t)yy * W + xx) * (1.f / 255.f) : 0.f;
+    }
+    for (int c = t; c < kC * 2 * 9; c += 256) sw[c] = (&P->w0[0][0][0])[c];
+    if (t < kC) sw[kC * 2 * 9 + t] = P->b0[t];
+    __syncthreads();
+    const int py = t / TW, px = t % TW, yy = y0 + py, xx = x0 + px;
+    if (yy >= H || xx >= W) return;
+    float xin[9], sin[9];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int iy = py + tap / 3, ix = px + tap % 3;
+        xin[tap] = tr[iy * IW + ix];
+        const int gy = yy - 1 + tap / 3, gx = xx - 1 + tap % 3;
+        sin[tap] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? s255 : 0.f;
+    }
+    uint32_t o[16];
+#pragma unroll
+    for (int co = 0; co < kC; co += 2) {
+        float v[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            float a = sw[kC * 2 * 9 + co + e];
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                a = fmaf(sw[((co + e) * 2 + 0) * 9 + tap], xin[tap], a);
+                a = fmaf(sw[((co + e) * 2 + 1) * 9 + tap], sin[tap], a);
+            }
+            v[e] = fmaxf(a, 0.f);
+        }
+        o[co / 2] = pack_bf16(v[0], v[1]);
+    }
+    uint4* d = reinterpret_cast<uint4*>(out + ((int64_t)k * H * W + (int64_t)yy * W + xx) * kC);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) d[c] = make_uint4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
+}
+
+// ---------------------------------------------------------------------------
+// Last layer 32 -> 1, FP32 CUDA cores.  mode 0: out = r - 255 (acc + b)
+// (the denoised image); mode 1: out = acc + b (the network output n).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) cnn_last_kernel(const __nv_bfloat16* __restrict__ in,
+                                                       const float* __restrict__ r, int H, int W,
+                                                       const CnnPacked* __restrict__ P, int mode,
+                                                       float* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __nv_bfloat16* tin = reinterpret_cast<__nv_bfloat16*>(smem);     // [IH*IW][PXS]
+    __shared__ float sw[kC * 9];
+    griddep_wait();
+    const int t = threadIdx.x, k = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const __nv_bfloat16* img = in + (int64_t)k * H * W * kC;
+    for (int c = t; c < IH * IW * 4; c += 256) {
+        const int px = c >> 2, ch = c & 3;
+        const int yy = y0 - 1 + px / IW, xx = x0 - 1 + px % IW;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+            v = __ldg(reinterpret_cast<const uint4*>(img + ((int64_t)yy * W + xx) * kC) + ch);
+        *reinterpret_cast<uint4*>(tin + px * PXS + ch * 8) = v;
+    }
+    for (int c = t; c < kC * 9; c += 256) sw[c] = (&P->w7[0][0])[c];
+    __syncthreads();
+    const int py = t / TW, px = t % TW, yy = y0 + py, xx = x0 + px;
+    if (yy >= H || xx >= W) return;
+    float a = P->b7;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const __nv_bfloat16* p = tin + ((py + tap / 3) * IW + px + tap % 3) * PXS;
+#pragma unroll
+        for (int ci = 0; ci < kC; ci += 2) {
+            const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p + ci));
+            a = fmaf(sw[ci * 9 + tap], v.x, a);
+            a = fmaf(sw[(ci + 1) * 9 + tap], v.y, a);
+        }
+    }
+    const int64_t o = (int64_t)k * H * W + (int64_t)yy * W + xx;
+    out[o] = mode == 0 ? __ldg(r + o) - 255.f * a : a;
+}
+
+// ---------------------------------------------------------------------------
+// Packing: FP32 parameters (oracle layout) -> CnnPacked.
+// ---------------------------------------------------------------------------
+__global__ void cnn_pack_kernel(const float* __restrict__ prm, CnnPacked* __restrict__ P) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kW0) (&P->w0[0][0][0])[i] = prm[i];                        // [co][ci][tap] == [co][ci][3][3]
+    if (i < kB0) P->b0[i] = prm[kW0 + i];
+    if (i < kMid * kWm) {
+        const int l = i / kWm, j = i % kWm;                              // j over [co][ci][tap]
+        const int co = j / (kC * 9), ci = (j / 9) % kC, tap = j % 9;
+        const __nv_bfloat16 v = __float2bfloat16_rn(prm[param_off_w(l + 1) + j]);
+        P->wc[l][tap][co][ci] = v;
+        P->wd[l][8 - tap][ci][co] = v;
+    }
+    if (i < kMid * kBm) P->bm[i / kBm][i % kBm] = prm[param_off_b(i / kBm + 1) + i % kBm];
+    if (i < kW7) (&P->w7[0][0])[i] = prm[param_off_w(7) + i];              // [ci][tap] == [0][ci][3][3]
+    if (i == 0) P->b7 = prm[param_off_b(7)];
+}
+
+// ---------------------------------------------------------------------------
+// Training pieces.
+// ---------------------------------------------------------------------------
+// resid = r/255 - n - clean/255; loss += resid^2 / numel; g = -2 resid / numel
+__global__ void cnn_loss_kernel(const float* __restrict__ n, const float* __restrict__ r,
+                                const float* __restrict__ clean, int64_t numel, float* __restrict__ g,
+                                double* __restrict__ part) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < numel; i += (int64_t)gridDim.x * blockDim.x) {
+        const float res = __ldg(r + i) * (1.f / 255.f) - __ldg(n + i) - __ldg(clean + i) * (1.f / 255.f);
+        g[i] = -2.f * res / (float)numel;
+        s += (double)res * res;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s / (double)numel;
+}
+
+// input gradient of the last layer, times the ReLU mask of its input:
+// d[q][ci] = [act[q][ci] > 0] * sum_tap w7[ci][tap] g[q - off(tap)]
+__global__ void __launch_bounds__(256) cnn_last_bwd_kernel(const float* __restrict__ g, const __nv_bfloat16* __restrict__ act,
+                                                           int H, int W, const CnnPacked* __restrict__ P,
+                                                           __nv_bfloat16* __restrict__ d) {
+    __shared__ float tg[IH * IW];
+    __shared__ float sw[kC * 9];
+    const int t = threadIdx.x, k = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const float* gi = g + (int64_t)k * H * W;
+    for (int c = t; c < IH * IW; c += 256) {
+        const int yy = y0 - 1 + c / IW, xx = x0 - 1 + c % IW;
+        tg[c] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? __ldg(gi + (int64_t)yy * W + xx) : 0.f;
+    }
+    for (int c = t; c < kC * 9; c += 256) sw[c] = (&P->w7[0][0])[c];
+    __syncthreads();
+    const int py = t / TW, px = t % TW, yy = y0 + py, xx = x0 + px;
+    if (yy >= H || xx >= W) return;
+    // out[p] = sum_tap w[tap] in[p + off(tap)]  =>  d_in[q] = sum_tap w[tap] g[q - off(tap)]
+    float gv[9];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) gv[tap] = tg[(py + 2 - tap / 3) * IW + (px + 2 - tap % 3)];
+    const int64_t o = ((int64_t)k * H * W + (int64_t)yy * W + xx) * kC;
+    const __nv_bfloat162* a2 = reinterpret_cast<const __nv_bfloat162*>(act + o);
+    uint32_t res[16];
+#pragma unroll
+    for (int ci = 0; ci < kC; ci += 2) {
+        float v[2] = {0.f, 0.f};
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) v[e] = fmaf(sw[(ci + e) * 9 + tap], gv[tap], v[e]);
+        const float2 av = __bfloat1622float2(a2[ci / 2]);
+        res[ci / 2] = pack_bf16(av.x > 0.f ? v[0] : 0.f, av.y > 0.f ? v[1] : 0.f);
+    }
+    uint4* dd = reinterpret_cast<uint4*>(d + o);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dd[c] = make_uint4(res[4 * c], res[4 * c + 1], res[4 * c + 2], res[4 * c + 3]);
+}
+
+// Weight gradients of a 32 -> 32 layer: dW[co][ci][tap] = sum_p g[p][co] in[p + off(tap)][ci],
+// db[co] = sum_p g[p][co].  Persistent CTAs over 8 x 32 tiles; each CTA
+// writes its FP32 partial (kWm + kBm values) to part[blockIdx.x].
+__global__ void __launch_bounds__(256) wgrad32_kernel(const __nv_bfloat16* __restrict__ in,
+                                                      const __nv_bfloat16* __restrict__ g, int n, int H, int W,
+                                                      float* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* tin = reinterpret_cast<float*>(smem);            // [IH*IW][33]
+    float* tgg = tin + IH * IW * 33;                        // [TH*TW][33]
+    const int t = threadIdx.x;
+    // thread t owns co = t / 8 and ci in {ci0 .. ci0 + 3} (ci0 = 4 (t % 8)), all 9 taps: 36 weights
+    const int co = t >> 3, ci0 = (t & 7) * 4;
+    float acc[4][9];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 9; ++b) acc[a][b] = 0.f;
+    float accb = 0.f;
+    const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH, ntiles = tx * ty * n;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int k = tile / (tx * ty), rem = tile % (tx * ty);
+        const int y0 = (rem / tx) * TH, x0 = (rem % tx) * TW;
+        __syncthreads();
+        for (int c = t; c < IH * IW * kC / 2; c += 256) {
+            const int px = c / (kC / 2), cp = (c % (kC / 2)) * 2;
+            const int yy = y0 - 1 + px / IW, xx = x0 - 1 + px % IW;
+            float2 v = make_float2(0.f, 0.f);
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(
+                    in + (((int64_t)k * H + yy) * W + xx) * kC + cp));
+            tin[px * 33 + cp] = v.x;
+            tin[px * 33 + cp + 1] = v.y;
+        }
+        for (int c = t; c < TH * TW * kC / 2; c += 256) {
+            const int px = c / (kC / 2), cp = (c % (kC / 2)) * 2;
+            const int yy = y0 + px / TW, xx = x0 + px % TW;
+            float2 v = make_float2(0.f, 0.f);
+            if (yy < H && xx < W)
+                v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(
+                    g + (((int64_t)k * H + yy) * W + xx) * kC + cp));
+            tgg[px * 33 + cp] = v.x;
+            tgg[px * 33 + cp + 1] = v.y;
+        }
+        __syncthreads();
+        for (int p = 0; p < TH * TW; ++p) {
+            const float gv = tgg[p * 33 + co];
+            accb += gv;
+            const int py = p / TW, px = p % TW;
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const float* ip = tin + ((py + tap / 3) * IW + px + tap % 3) * 33 + ci0;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) acc[a][tap] = fmaf(gv, ip[a], acc[a][tap]);
+            }
+        }
+    }
+    float* dst = part + (int64_t)blockIdx.x * (kWm + kBm);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) dst[(co * kC + ci0 + a) * 9 + tap] = acc[a][tap];
+    if ((t & 7) == 0) dst[kWm + co] = accb;
+}
+
+// Weight gradients of the first layer (inputs r/255, sigma/255; g: 32 ch).
+__global__ void __launch_bounds__(256) wgrad_first_kernel(const float* __restrict__ r, const float* __restrict__ sigma,
+                                                          const __nv_bfloat16* __restrict__ g, int n, int H, int W,
+                                                          float* __restrict__ part) {
+    __shared__ float tr[IH * IW];
+    __shared__ float tv[IH * IW];        // 1 inside the image, 0 in the zero padding
+    __shared__ float tgg[TH * TW][33];
+    const int t = threadIdx.x;
+    // thread t: co = t / 8; threads with t % 8 < 6 own 3 of the 18 (ci, tap) weights each
+    const int co = t >> 3, sub = t & 7;
+    float acc[3] = {0.f, 0.f, 0.f};
+    float accb = 0.f;
+    const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH, ntiles = tx * ty * n;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int k = tile / (tx * ty), rem = tile % (tx * ty);
+        const int y0 = (rem / tx) * TH, x0 = (rem % tx) * TW;
+        const float s255 = __ldg(sigma + k) * (1.f / 255.f);
+        __syncthreads();
+        for (int c = t; c < IH * IW; c += 256) {
+            const int yy = y0 - 1 + c / IW, xx = x0 - 1 + c % IW;
+            const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+            tr[c] = in ? __ldg(r + ((int64_t)k * H + yy) * W + xx) * (1.f / 255.f) : 0.f;
+            tv[c] = in ? 1.f : 0.f;
+        }
+        for (int c = t; c < TH * TW * kC / 2; c += 256) {
+            const int px = c / (kC / 2), cp = (c % (kC / 2)) * 2;
+            const int yy = y0 + px / TW, xx = x0 + px % TW;
+            float2 v = make_float2(0.f, 0.f);
+            if (yy < H && xx < W)
+                v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(
+                    g + (((int64_t)k * H + yy) * W + xx) * kC + cp));
+            tgg[px][cp] = v.x;
+            tgg[px][cp + 1] = v.y;
+        }
+        __syncthreads();
+        if (sub < 6) {
+            for (int p = 0; p < TH * TW; ++p) {
+                const float gv = tgg[p][co];
+                if (sub == 0) accb += gv;
+                const int py = p / TW, px = p % TW;
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    const int idx = sub * 3 + e;            // 0..17 = ci * 9 + tap
+                    const int ci = idx / 9, tap = idx % 9;
+                    const int ti = (py + tap / 3) * IW + px + tap % 3;
+                    const float in = ci == 0 ? tr[ti] : s255 * tv[ti];
+                    acc[e] = fmaf(gv, in, acc[e]);
+                }
+            }
+        }
+    }
+    float* dst = part + (int64_t)blockIdx.x * (kW0 + kB0);
+    if (sub < 6)
+        for (int e = 0; e < 3; ++e) dst[co * 18 + sub * 3 + e] = acc[e];
+    if (sub == 0) dst[kW0 + co] = accb;
+}
+
+// Weight gradients of the last layer: dW7[ci][tap] = sum_p g[p] in[p + off(tap)][ci], db7 = sum_p g[p].
+__global__ void __launch_bounds__(256) wgrad_last_kernel(const __nv_bfloat16* __restrict__ in, const float* __restrict__ g,
+                                                         int n, int H, int W, float* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* tin = reinterpret_cast<float*>(smem);    // [IH*IW][33]
+    __shared__ float tg[TH * TW];
+    const int t = threadIdx.x;
+    // 288 weights + 1 bias over 256 threads: thread t handles (ci, tap) pairs t and t + 256
+    float acc[2] = {0.f, 0.f};
+    float accb = 0.f;
+    const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH, ntiles = tx * ty * n;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int k = tile / (tx * ty), rem = tile % (tx * ty);
+        const int y0 = (rem / tx) * TH, x0 = (rem % tx) * TW;
+        __syncthreads();
+        for (int c = t; c < IH * IW * kC / 2; c += 256) {
+            const int px = c / (kC / 2), cp = (c % (kC / 2)) * 2;
+            const int yy = y0 - 1 + px / IW, xx = x0 - 1 + px % IW;
+            float2 v = make_float2(0.f, 0.f);
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(
+                    in + (((int64_t)k * H + yy) * W + xx) * kC + cp));
+            tin[px * 33 + cp] = v.x;
+            tin[px * 33 + cp + 1] = v.y;
+        }
+        {
+            const int yy = y0 + t / TW, xx = x0 + t % TW;
+            tg[t] = (yy < H && xx < W) ? __ldg(g + ((int64_t)k * H + yy) * W + xx) : 0.f;
+        }
+        __syncthreads();
+        for (int p = 0; p < TH * TW; ++p) {
+            const float gv = tg[p];
+            if (t == 0) accb += gv;
+            const int py = p / TW, px = p % TW;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int idx = t + 256 * e;
+                if (idx < kW7) {
+                    const int ci = idx / 9, tap = idx % 9;
+                    acc[e] = fmaf(gv, tin[((py + tap / 3) * IW + px + tap % 3) * 33 + ci], acc[e]);
+                }
+            }
+        }
+    }
+    float* dst = part + (int64_t)blockIdx.x * (kW7 + kB7);
+    for (int e = 0; e < 2; ++e)
+        if (t + 256 * e < kW7) dst[t + 256 * e] = acc[e];
+    if (t == 0) dst[kW7] = accb;
+}
+
+// grad[off + j] = sum_c part[c][j], fixed order
+__global__ void reduce_parts_kernel(const float* __restrict__ part, int nparts, int len, float* __restrict__ grad) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= len) return;
+    float s = 0.f;
+    for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * len + j];
+    grad[j] = s;
+}
+
+__global__ void reduce_loss_kernel(const double* __restrict__ part, int n, float* __restrict__ loss) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) s += part[i];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) *loss = (float)s;
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+int cnn_param_count() { return kParams; }
+size_t cnn_packed_bytes() { return sizeof(CnnPacked); }
+
+cudaError_t cnn_pack(const float* params, void* packed, cudaStream_t s) {
+    cnn_pack_kernel<<<(kMid * kWm + 255) / 256, 256, 0, s>>>(params, static_cast<CnnPacked*>(packed));
+    return cudaGetLastError();
+}
+
+static size_t conv_smem() { return (size_t)(IH * IW + 9 * kC) * PXS * 2; }
+
+static cudaError_t conv32(int epi, const __nv_bfloat16* in, int n, int H, int W, const __nv_bfloat16* wts,
+                          const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out, cudaStream_t s) {
+    dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, n);
+    const size_t smem = conv_smem();
+    cudaError_t e;
+    if (epi == 0) {
+        if ((e = cudaFuncSetAttribute(conv32_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        return launch_pdl(conv32_kernel<0>, grid, dim3(256), smem, s, in, H, W, wts, bias, mask, out);
+    }
+    if ((e = cudaFuncSetAttribute(conv32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    return launch_pdl(conv32_kernel<1>, grid, dim3(256), smem, s, in, H, W, wts, bias, mask, out);
+}
+
+// Forward through layers 0..6 into act[0..6] (each n*H*W*32 bf16), then the
+// last layer into out (mode 0: denoised image, mode 1: network output n).
+cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, int n, int H, int W,
+                        void* act_buf, int keep_all, int mode, float* out, cudaStream_t s) {
+    const CnnPacked* P = static_cast<const CnnPacked*>(packed);
+    const int64_t plane = (int64_t)n * H * W * kC;
+    __nv_bfloat16* act = static_cast<__nv_bfloat16*>(act_buf);
+    auto A = [&](int l) { return act + (keep_all ? l : (l & 1)) * plane; };
+    dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, n);
+    cudaError_t e = launch_pdl(cnn_first_kernel, grid, dim3(256), 0, s, r, sigma, H, W, P, A(0));
+    for (int l = 1; l <= kMid && !e; ++l)
+        e = conv32(0, A(l - 1), n, H, W, &P->wc[l - 1][0][0][0], &P->bm[l - 1][0], nullptr, A(l), s);
+    if (e) return e;
+    const size_t smem = (size_t)IH * IW * PXS * 2;
+    if ((e = cudaFuncSetAttribute(cnn_last_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    return launch_pdl(cnn_last_kernel, grid, dim3(256), smem, s, (const __nv_bfloat16*)A(kMid), r, H, W, P, mode, out);
+}
+
+// Loss and gradients (FP32, parameter layout) of a batch of n crops.
+// Workspace: act (7 planes), gbuf (2 planes), gn (n*H*W floats), parts.
+cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, const float* sigma, int n, int H, int W,
+                     void* ws, float* grad, float* loss, cudaStream_t s) {
+    const CnnPacked* P = static_cast<const CnnPacked*>(packed);
+    const int64_t px = (int64_t)n * H * W, plane = px * kC;
+    char* w = static_cast<char*>(ws);
+    __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(w);
+    __nv_bfloat16* gb = act + 7 * plane;                         // 2 gradient planes
+    float* nout = reinterpret_cast<float*>(gb + 2 * plane);
+    float* gn = nout + px;
+    const int nparts = 304;
+    float* part = gn + px;                                       // nparts * (kWm + kBm)
+    double* lpart = reinterpret_cast<double*>(part + (size_t)nparts * (kWm + kBm));
+    cudaError_t e = cnn_forward(packed, r, sigma, n, H, W, act, 1, 1, nout, s);
+    if (e) return e;
+    cnn_loss_kernel<<<256, 256, 0, s>>>(nout, r, clean, px, gn, lpart);
+    reduce_loss_kernel<<<1, 32, 0, s>>>(lpart, 256, loss);
+    dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, n);
+    const int tiles = grid.x * grid.y * n;
+    const int np = tiles < nparts ? tiles : nparts;
+    // last layer
+    const size_t smem_l = (size_t)IH * IW * 33 * 4;
+    if ((e = cudaFuncSetAttribute(wgrad_last_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l))) return e;
+    wgrad_last_kernel<<<np, 256, smem_l, s>>>(act + kMid * plane, gn, n, H, W, part);
+    reduce_parts_kernel<<<(kW7 + kB7 + 255) / 256, 256, 0, s>>>(part, np, kW7 + kB7, grad + param_off_w(7));
+    cnn_last_bwd_kernel<<<grid, 256, 0, s>>>(gn, act + kMid * plane, H, W, P, gb);
+    // mid layers, l = 6 .. 1: g_l (pre-activation grad) in gb[cur]
+    const size_t smem_w = (size_t)(IH * IW + TH * TW) * 33 * 4;
+    if ((e = cudaFuncSetAttribute(wgrad32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w))) return e;
+    int cur = 0;
+    for (int l = kMid; l >= 1; --l) {
+        __nv_bfloat16* g = gb + cur * plane;
+        wgrad32_kernel<<<np, 256, smem_w, s>>>(act + (l - 1) * plane, g, n, H, W, part);
+        reduce_parts_kernel<<<(kWm + kBm + 255) / 256, 256, 0, s>>>(part, np, kWm + kBm, grad + param_off_w(l));
+        // input gradient, masked by the ReLU of layer l-1's output
+        e = conv32(1, g, n, H, W, &P->wd[l - 1][0][0][0], nullptr, act + (l - 1) * plane, gb + (1 - cur) * plane, s);
+        if (e) return e;
+        cur = 1 - cur;
+    }
+    wgrad_first_kernel<<<np, 256, 0, s>>>(r, sigma, gb + cur * plane, n, H, W, part);
+    reduce_parts_kernel<<<(kW0 + kB0 + 255) / 256, 256, 0, s>>>(part, np, kW0 + kB0, grad);
+    return cudaGetLastError();
+}
+
+size_t cnn_grad_ws_bytes(int n, int H, int W) {
+    const int64_t px = (int64_t)n * H * W, plane = px * kC;
+    return (size_t)(9 * plane) * 2 + (size_t)(2 * px) * 4 + (size_t)304 * (kWm + kBm) * 4 + 256 * 8 + 1024;
+}
+
+cudaError_t cnn_adam(float* params, const float* grad, float* m, float* v, int step, float lr, cudaStream_t s) {
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    adam_kernel<<<(kParams + 255) / 256, 256, 0, s>>>(params, grad, m, v, kParams, lr, b1, b2, 1e-8f, c1, c2);
+    return cudaGetLastError();
+}
+
+}  // namespace abcs

@@ -1,0 +1,246 @@
+"""Training and evaluation driver of the learned IDA denoiser.
+
+Everything numeric runs in libabcs.so through the C ABI; this module only
+moves tensors (torch is used for device memory, random crop indices and the
+PSNR bookkeeping of the evaluation).
+
+  python -m paper_2001_09632_gb300.train tune-lambda   # plain TI-DCT threshold factor
+  python -m paper_2001_09632_gb300.train train --out weights.f32
+  python -m paper_2001_09632_gb300.train eval --weights weights.f32
+
+Training pairs follow the method itself: synthetic images are sensed
+(AL-DCT-BBV or AL-DCT-DD, subrate drawn from {0.1, ..., 0.5}), plain IDA
+runs on them, and the denoiser input r^t of iteration t (with its sigma^t)
+is captured for several t; random 64x64 crops of (r^t, clean image) form the
+training set.  Seeds of training, tuning and evaluation images are disjoint.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import abcs, synth
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "cnn_ida_b16.f32")
+DEFAULT_LAMBDA = 2.3   # tuned: tune_lambda() over 2.0..3.5 on held-out synthetic images
+TRAIN_SEED, TUNE_SEED, EVAL_SEED = 10_000_000, 20_000_000, 30_000_000
+
+
+def load_weights(path: str = WEIGHTS) -> np.ndarray:
+    w = np.fromfile(path, dtype="<f4")
+    if w.size != abcs.abcs_cnn_param_count():
+        raise ValueError(f"{path}: {w.size} values, expected {abcs.abcs_cnn_param_count()}")
+    return w
+
+
+def init_params(seed: int) -> np.ndarray:
+    """He-normal weights (last layer x 0.1), zero biases, in the ABI's layout."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    chans = [2] + [32] * 7 + [1]
+    out = []
+    for l in range(8):
+        ci, co = chans[l], chans[l + 1]
+        w = rng.standard_normal((co, ci, 3, 3)) * math.sqrt(2.0 / (9 * ci))
+        if l == 7:
+            w *= 0.1
+        out += [w.reshape(-1), np.zeros(co)]
+    return np.concatenate(out).astype(np.float32)
+
+
+class Sensed:
+    """One batch of equally sized images sensed on the device."""
+
+    def __init__(self, h, imgs: np.ndarray, B: int, subrate: float, variant: int):
+        n, H, W = imgs.shape
+        plan = abcs.abcs_plan(H, W, B, subrate, variant)
+        nB = plan["n_blocks"]
+        self.n, self.H, self.W, self.B = n, H, W, B
+        self.Hc, self.Wc = plan["nbh"] * B, plan["nbw"] * B
+        self.d_img = torch.from_numpy(imgs).cuda()
+        self.clean = self.d_img[:, : self.Hc, : self.Wc].float()
+        self.counts = torch.empty(n * nB, dtype=torch.int32, device="cuda")
+        self.offsets = torch.empty(n * nB + 1, dtype=torch.int64, device="cuda")
+        cap = n * plan["M"]
+        self.y = torch.empty(cap, dtype=torch.float32, device="cuda")
+        abcs.abcs_sense(h, self.d_img, n, H, W, W, H * W, B, subrate, variant, abcs.FP32,
+                        self.counts, self.offsets, self.y, cap)
+
+    def ida(self, h, iters, denoiser, lam=DEFAULT_LAMBDA, packed=None, x=None):
+        x = torch.empty((self.n, self.Hc, self.Wc), dtype=torch.float32, device="cuda") if x is None else x
+        abcs.abcs_ida(h, self.counts, self.offsets, self.y, self.n, self.H, self.W, self.B, iters, 2.0,
+                      denoiser, lam, packed, x)
+        return x
+
+    def capture(self, h, t, lam=DEFAULT_LAMBDA):
+        r = torch.empty((self.n, self.Hc, self.Wc), dtype=torch.float32, device="cuda")
+        s = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        abcs.abcs_ida_capture(h, self.counts, self.offsets, self.y, self.n, self.H, self.W, self.B, t, 2.0,
+                              abcs.DEN_TIDCT, lam, None, r, s)
+        return r, s
+
+
+def psnr(x: torch.Tensor, ref: torch.Tensor) -> torch.Tensor:
+    """Per image 10 log10(255^2 / MSE) of x clipped to [0, 255]."""
+    d = x.clamp(0, 255) - ref
+    mse = (d * d).flatten(1).mean(1)
+    return 10.0 * torch.log10(255.0 ** 2 / mse)
+
+
+def make_pairs(h, n_images=512, H=512, W=512, captures=(0, 1, 2, 4, 8, 16, 29), crops=56, crop=64,
+               batch=32, seed=TRAIN_SEED, lam=DEFAULT_LAMBDA, log=print):
+    subrates = (0.1, 0.2, 0.3, 0.4, 0.5)
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    R, C, S = [], [], []
+    t0 = time.time()
+    for i0 in range(0, n_images, batch):
+        j = i0 // batch
+        imgs = synth.gen_batch(min(batch, n_images - i0), H, W, seed + i0)
+        variant = abcs.BBV if j % 2 == 0 else abcs.DD
+        sd = Sensed(h, imgs, 16, subrates[j % len(subrates)], variant)
+        for t in captures:
+            r, s = sd.capture(h, t, lam)
+            n = r.shape[0]
+            ys = torch.randint(0, sd.Hc - crop + 1, (n, crops), device="cuda", generator=gen)
+            xs = torch.randint(0, sd.Wc - crop + 1, (n, crops), device="cuda", generator=gen)
+            ar = torch.arange(crop, device="cuda")
+            rows = (ys[..., None] + ar)[..., :, None]          # n, crops, crop, 1
+            cols = (xs[..., None] + ar)[..., None, :]          # n, crops, 1, crop
+            kk = torch.arange(n, device="cuda")[:, None, None, None]
+            R.append(r[kk, rows, cols].reshape(-1, crop, crop))
+            C.append(sd.clean[kk, rows, cols].reshape(-1, crop, crop))
+            S.append(s[:, None].expand(n, crops).reshape(-1))
+        if j % 8 == 0:
+            log(f"pairs: {i0 + batch}/{n_images} images, {sum(x.shape[0] for x in R)} crops, {time.time() - t0:.1f}s")
+    assert abcs.abcs_sync_status(h) == 0
+    return torch.cat(R), torch.cat(C), torch.cat(S)
+
+
+def train(h, R, C, S, steps=4000, batch=128, lr=1e-3, seed=1, params=None, log=print):
+    n, crop = R.shape[0], R.shape[1]
+    p = torch.tensor(init_params(seed) if params is None else params, device="cuda")
+    m, v = torch.zeros_like(p), torch.zeros_like(p)
+    packed = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    hist = []
+    t0 = time.time()
+    for step in range(1, steps + 1):
+        idx = torch.randint(0, n, (batch,), device="cuda", generator=gen)
+        rb, cb, sb = R[idx].contiguous(), C[idx].contiguous(), S[idx].contiguous()
+        lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * (step - 1) / steps))     # cosine decay
+        abcs.abcs_cnn_train_step(h, p, m, v, step, lr_t, packed, rb, cb, sb, batch, crop, crop, loss)
+        if step % 200 == 0 or step == 1:
+            l = loss.item()
+            hist.append((step, l))
+            log(f"step {step:5d}  loss {l:.6f}  (rmse {255 * math.sqrt(l):.2f})  {time.time() - t0:.1f}s")
+    torch.cuda.synchronize()
+    assert abcs.abcs_sync_status(h) == 0
+    return p.cpu().numpy(), hist, time.time() - t0
+
+
+def tune_lambda(h, n=16, H=512, W=512, iters=30, grid=None, log=print):
+    grid = grid or [round(2.0 + 0.1 * i, 1) for i in range(16)]
+    imgs = synth.gen_batch(n, H, W, TUNE_SEED)
+    res = {}
+    for r in (0.1, 0.3, 0.5):
+        sd = Sensed(h, imgs, 16, r, abcs.BBV)
+        for lam in grid:
+            x = sd.ida(h, iters, abcs.DEN_TIDCT, lam)
+            res.setdefault(lam, []).append(float(psnr(x, sd.clean).mean()))
+    mean = {lam: float(np.mean(v)) for lam, v in res.items()}
+    best = max(mean, key=mean.get)
+    log(json.dumps({"lambda_psnr": mean, "best": best}))
+    return best, mean
+
+
+def timed_ida(h, sd: Sensed, iters, denoiser, lam, packed, reps=3):
+    x = sd.ida(h, iters, denoiser, lam, packed)
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sd.ida(h, iters, denoiser, lam, packed, x)
+        e1.record()
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    return x, ms
+
+
+def evaluate(h, weights, n=128, H=512, W=512, subrates=(0.1, 0.2, 0.3, 0.4, 0.5), variant=abcs.BBV,
+             plain_iters=30, learned_iters=10, lam=DEFAULT_LAMBDA, batch=32, seed=EVAL_SEED, log=print):
+    """Plain IDA (TI-DCT, plain_iters) vs learned IDA (CNN, learned_iters):
+    mean PSNR over the held-out images and Mpixel/s of each."""
+    p = torch.tensor(weights, device="cuda")
+    packed = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
+    abcs.abcs_cnn_pack(h, p, packed)
+    out = {}
+    for r in subrates:
+        acc = {"idct": [], "plain": [], "learned": [], "plain_ms": 0.0, "learned_ms": 0.0, "px": 0}
+        for i0 in range(0, n, batch):
+            imgs = synth.gen_batch(min(batch, n - i0), H, W, seed + i0)
+            sd = Sensed(h, imgs, 16, r, variant)
+            x0 = sd.ida(h, 1, abcs.DEN_NONE)      # one identity iteration = A^T y, the IDCT image
+            xp, tp = timed_ida(h, sd, plain_iters, abcs.DEN_TIDCT, lam, None)
+            xl, tl = timed_ida(h, sd, learned_iters, abcs.DEN_CNN, lam, packed)
+            acc["idct"] += psnr(x0, sd.clean).tolist()
+            acc["plain"] += psnr(xp, sd.clean).tolist()
+            acc["learned"] += psnr(xl, sd.clean).tolist()
+            acc["plain_ms"] += tp
+            acc["learned_ms"] += tl
+            acc["px"] += sd.n * sd.Hc * sd.Wc
+        res = {"psnr_idct": float(np.mean(acc["idct"])), "psnr_plain": float(np.mean(acc["plain"])),
+               "psnr_learned": float(np.mean(acc["learned"])),
+               "plain_Mpx_per_s": acc["px"] / (acc["plain_ms"] * 1e-3) / 1e6,
+               "learned_Mpx_per_s": acc["px"] / (acc["learned_ms"] * 1e-3) / 1e6}
+        res["speedup"] = res["learned_Mpx_per_s"] / res["plain_Mpx_per_s"]
+        res["dpsnr"] = res["psnr_learned"] - res["psnr_plain"]
+        out[str(r)] = res
+        log(f"r={r}: " + json.dumps({k: round(v, 3) for k, v in res.items()}))
+    assert abcs.abcs_sync_status(h) == 0
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("cmd", choices=["tune-lambda", "train", "eval", "all"])
+    ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--weights", default=WEIGHTS)
+    ap.add_argument("--images", type=int, default=512)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--lam", type=float, default=DEFAULT_LAMBDA)
+    ap.add_argument("--eval-images", type=int, default=128)
+    ap.add_argument("--report", default=None, help="write a JSON report here")
+    a = ap.parse_args()
+    h = abcs.abcs_create()
+    report = {}
+    if a.cmd in ("tune-lambda", "all"):
+        best, mean = tune_lambda(h)
+        report["tune_lambda"] = {"best": best, "mean_psnr": mean}
+    if a.cmd in ("train", "all"):
+        R, C, S = make_pairs(h, n_images=a.images, lam=a.lam)
+        print(f"{R.shape[0]} training crops")
+        w, hist, secs = train(h, R, C, S, steps=a.steps)
+        os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+        w.astype("<f4").tofile(a.out)
+        report["train"] = {"crops": int(R.shape[0]), "steps": a.steps, "seconds": secs, "loss": hist}
+        del R, C, S
+        torch.cuda.empty_cache()
+    if a.cmd in ("eval", "all"):
+        w = load_weights(a.out if a.cmd == "all" else a.weights)
+        report["eval"] = evaluate(h, w, n=a.eval_images, lam=a.lam)
+    if a.report:
+        with open(a.report, "w") as f:
+            json.dump(report, f, indent=1)
+    abcs.abcs_destroy(h)
+
+
+if __name__ == "__main__":
+    main()

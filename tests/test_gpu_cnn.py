@@ -1,0 +1,155 @@
+"""GPU parity of the learned denoiser (BF16 weights / activations, FP32
+accumulation) against the FP64 oracle run with the same BF16-rounded
+mid-layer weights.
+
+Tolerances follow from BF16's unit roundoff 2^-9 ~ 2e-3 per rounded
+activation and 7 rounded layers: relative L2 of the network output within
+2e-2; gradients (which also pass through BF16-stored activations and
+BF16-stored upstream gradients) within 6e-2 per layer."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2001_09632_gb300 import abcs, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _params(seed=0, scale_last=1.0):
+    p = O.cnn_init(c_in=2, width=32, depth=8, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    out = []
+    for l, (w, b) in enumerate(p):
+        b = rng.standard_normal(b.shape) * 0.05
+        if l == 7:
+            w = w * scale_last
+        out.append((w, b))
+    return out
+
+
+def _bf16_mid(params):
+    """The oracle copy with mid-layer weights rounded to BF16 as the GPU packs them."""
+    out = []
+    for l, (w, b) in enumerate(params):
+        if 1 <= l <= 6:
+            w = torch.tensor(w).to(torch.bfloat16).to(torch.float64).numpy()
+        out.append((w, b))
+    return out
+
+
+def _flat(params):
+    return np.concatenate([np.concatenate([w.reshape(-1), b.reshape(-1)]) for w, b in params])
+
+
+def _unflat(vec, params):
+    out, i = [], 0
+    for w, b in params:
+        gw = vec[i:i + w.size].reshape(w.shape); i += w.size
+        gb = vec[i:i + b.size]; i += b.size
+        out.append((gw, gb))
+    return out
+
+
+def _pack(h, params):
+    assert len(_flat(params)) == abcs.abcs_cnn_param_count()
+    d_p = torch.tensor(_flat(params), dtype=torch.float32, device="cuda")
+    packed = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
+    abcs.abcs_cnn_pack(h, d_p, packed)
+    return d_p, packed
+
+
+def _noisy(n, H, W, seed, sigma):
+    rng = np.random.default_rng(seed)
+    clean = np.stack([synth.gen_image(max(H, 16), max(W, 16), seed + k)[:H, :W] for k in range(n)]).astype(float)
+    return clean, clean + rng.standard_normal(clean.shape) * sigma
+
+
+@pytest.mark.parametrize("n,H,W", [(1, 24, 40), (2, 37, 70), (1, 8, 33)])
+def test_cnn_forward_parity(handle, n, H, W):
+    params = _params(3)
+    ref_p = _bf16_mid(params)
+    _, packed = _pack(handle, params)
+    clean, r = _noisy(n, H, W, 10, 12.0)
+    sig = np.array([12.0, 20.0][:n])
+    d_in = torch.tensor(r, dtype=torch.float32, device="cuda")
+    d_out = torch.full_like(d_in, float("nan"))
+    d_sig = torch.tensor(sig, dtype=torch.float32, device="cuda")
+    abcs.abcs_cnn_denoise(handle, packed, d_in, d_sig, n, H, W, d_out)
+    assert abcs.abcs_sync_status(handle) == 0
+    got = d_out.cpu().numpy()
+    r32 = d_in.cpu().numpy().astype(float)
+    for k in range(n):
+        ref = O.cnn_denoise(ref_p, r32[k], float(np.float32(sig[k])))
+        n_ref = (r32[k] - ref) / 255.0
+        n_got = (r32[k] - got[k]) / 255.0
+        err = np.linalg.norm(n_got - n_ref) / np.linalg.norm(n_ref)
+        assert err <= 2e-2, err
+
+
+def test_cnn_gradient_parity(handle):
+    params = _params(5)
+    ref_p = _bf16_mid(params)
+    _, packed = _pack(handle, params)
+    n, H, W = 2, 24, 40
+    clean, r = _noisy(n, H, W, 20, 15.0)
+    sig = np.array([15.0, 15.0])
+    d = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    d_r, d_c, d_s = d(r), d(clean), d(sig)
+    grad = torch.zeros(abcs.abcs_cnn_param_count(), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    abcs.abcs_cnn_grad(handle, packed, d_r, d_c, d_s, n, H, W, grad, loss)
+    assert abcs.abcs_sync_status(handle) == 0
+    r32, c32 = d_r.cpu().numpy().astype(float), d_c.cpu().numpy().astype(float)
+    ref_loss, ref_grads = 0.0, None
+    for k in range(n):
+        lk, gk = O.cnn_loss_and_grads(ref_p, r32[k], float(np.float32(sig[k])), c32[k])
+        ref_loss += lk / n
+        gk = [(gw / n, gb / n) for gw, gb in gk]
+        ref_grads = gk if ref_grads is None else [(a + c, b + e) for (a, b), (c, e) in zip(ref_grads, gk)]
+    assert abs(loss.item() - ref_loss) <= 1e-2 * ref_loss
+    got = _unflat(grad.cpu().numpy().astype(float), params)
+    for l, ((gw, gb), (rw, rb)) in enumerate(zip(got, ref_grads)):
+        ew = np.linalg.norm(gw - rw) / np.linalg.norm(rw)
+        eb = np.linalg.norm(gb - rb) / max(np.linalg.norm(rb), 1e-12)
+        assert ew <= 6e-2 and eb <= 6e-2, (l, ew, eb)
+
+
+def test_cnn_training_reduces_loss(handle):
+    params = _params(7, scale_last=0.1)
+    d_p, packed = _pack(handle, params)
+    m = torch.zeros_like(d_p)
+    v = torch.zeros_like(d_p)
+    n, H, W = 8, 32, 32
+    clean, r = _noisy(n, H, W, 30, 20.0)
+    d = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    d_r, d_c, d_s = d(r), d(clean), d(np.full(n, 20.0))
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    losses = []
+    for step in range(1, 61):
+        abcs.abcs_cnn_train_step(handle, d_p, m, v, step, 2e-3, packed, d_r, d_c, d_s, n, H, W, loss)
+        losses.append(loss.item())
+    assert abcs.abcs_sync_status(handle) == 0
+    assert losses[-1] < 0.75 * losses[0], losses[::10]
+    assert all(b <= a * 1.05 for a, b in zip(losses[::10], losses[10::10])), losses[::10]
+
+
+def test_ida_with_cnn_runs_and_matches_oracle_first_iterations(handle):
+    params = _params(9, scale_last=0.3)
+    ref_p = _bf16_mid(params)
+    _, packed = _pack(handle, params)
+    H, W, B = 48, 64, 16
+    img = synth.gen_image(H, W, 4)
+    out = O.sense(img, B, 0.3, O.BBV)
+    plan = abcs.abcs_plan(H, W, B, 0.3, abcs.BBV)
+    from tests import gpu_util as G
+    got = G.sense(handle, img[None], B, 0.3, O.BBV)
+    x = torch.empty((1, H, W), dtype=torch.float32, device="cuda")
+    tr = torch.zeros((1, 2), dtype=torch.float32, device="cuda")
+    abcs.abcs_ida(handle, *got["d"], 1, H, W, B, 2, 2.0, abcs.DEN_CNN, 0.0, packed, x, tr)
+    assert abcs.abcs_sync_status(handle) == 0
+    xr, sig = O.ida(out["y"], out["counts"], H, W, B, 2, DF=2.0,
+                    denoiser=lambda rr, s: O.cnn_denoise(ref_p, rr, s))
+    assert abs(tr.cpu().numpy()[0, 0] - sig[0]) <= 1e-5 * sig[0]
+    err = np.linalg.norm(x.cpu().numpy()[0] - xr) / np.linalg.norm(xr)
+    assert err <= 2e-2, err

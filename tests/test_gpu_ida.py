@@ -113,3 +113,18 @@ def test_ida_batch_matches_single(handle):
         g1 = G.sense(handle, imgs[k:k + 1], B, 0.2, O.DD)
         x1, tr1, _ = G.ida(handle, *g1["d"], 1, H, W, B, 4, 2.0, abcs.DEN_TIDCT, 2.7)
         assert np.array_equal(x1[0], xb[k]) and np.array_equal(tr1[0], trb[k])
+
+
+def test_ida_capture_matches_oracle_trace(handle):
+    """r^t and sigma^t of iteration t (the learned denoiser's training input)."""
+    H, W, B = 64, 96, 16
+    img, out = _setup(H, W, B, 0.3, O.BBV, 8)
+    got = G.sense(handle, img[None], B, 0.3, O.BBV)
+    _, sig, rs, _ = O.ida(out["y"], out["counts"], H, W, B, 3, DF=2.0, denoiser=None, trace=True)
+    for t in (0, 2):
+        r_out = torch.empty((1, H, W), dtype=torch.float32, device="cuda")
+        s_out = torch.empty(1, dtype=torch.float32, device="cuda")
+        abcs.abcs_ida_capture(handle, *got["d"], 1, H, W, B, t, 2.0, abcs.DEN_NONE, 0.0, None, r_out, s_out)
+        assert abcs.abcs_sync_status(handle) == 0
+        assert G.rel_l2(r_out.cpu().numpy()[0], rs[t]) <= 1e-5
+        assert abs(s_out.item() - sig[t]) <= 1e-5 * sig[t]
