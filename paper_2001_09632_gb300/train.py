@@ -77,11 +77,12 @@ class Sensed:
                       denoiser, lam, packed, x)
         return x
 
-    def capture(self, h, t, lam=DEFAULT_LAMBDA):
+    def capture(self, h, t, lam=DEFAULT_LAMBDA, packed=None):
         r = torch.empty((self.n, self.Hc, self.Wc), dtype=torch.float32, device="cuda")
         s = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        den = abcs.DEN_TIDCT if packed is None else abcs.DEN_CNN
         abcs.abcs_ida_capture(h, self.counts, self.offsets, self.y, self.n, self.H, self.W, self.B, t, 2.0,
-                              abcs.DEN_TIDCT, lam, None, r, s)
+                              den, lam, packed, r, s)
         return r, s
 
 
@@ -93,7 +94,9 @@ def psnr(x: torch.Tensor, ref: torch.Tensor) -> torch.Tensor:
 
 
 def make_pairs(h, n_images=512, H=512, W=512, captures=(0, 1, 2, 4, 8, 16, 29), crops=56, crop=64,
-               batch=32, seed=TRAIN_SEED, lam=DEFAULT_LAMBDA, log=print):
+               batch=32, seed=TRAIN_SEED, lam=DEFAULT_LAMBDA, packed=None, log=print):
+    """(r^t, clean, sigma^t) crops; r^t from plain IDA, or from learned IDA
+    when `packed` weights are given (its own trajectories)."""
     subrates = (0.1, 0.2, 0.3, 0.4, 0.5)
     gen = torch.Generator(device="cuda").manual_seed(seed)
     R, C, S = [], [], []
@@ -104,7 +107,7 @@ def make_pairs(h, n_images=512, H=512, W=512, captures=(0, 1, 2, 4, 8, 16, 29), 
         variant = abcs.BBV if j % 2 == 0 else abcs.DD
         sd = Sensed(h, imgs, 16, subrates[j % len(subrates)], variant)
         for t in captures:
-            r, s = sd.capture(h, t, lam)
+            r, s = sd.capture(h, t, lam, packed)
             n = r.shape[0]
             ys = torch.randint(0, sd.Hc - crop + 1, (n, crops), device="cuda", generator=gen)
             xs = torch.randint(0, sd.Wc - crop + 1, (n, crops), device="cuda", generator=gen)
@@ -175,35 +178,51 @@ def timed_ida(h, sd: Sensed, iters, denoiser, lam, packed, reps=3):
 
 
 def evaluate(h, weights, n=128, H=512, W=512, subrates=(0.1, 0.2, 0.3, 0.4, 0.5), variant=abcs.BBV,
-             plain_iters=30, learned_iters=10, lam=DEFAULT_LAMBDA, batch=32, seed=EVAL_SEED, log=print):
-    """Plain IDA (TI-DCT, plain_iters) vs learned IDA (CNN, learned_iters):
-    mean PSNR over the held-out images and Mpixel/s of each."""
+             plain_iters=(1, 3, 5, 10, 20, 30), learned_iters=(1, 2, 3, 4, 6, 10), lam=DEFAULT_LAMBDA,
+             batch=32, seed=EVAL_SEED, log=print):
+    """Plain IDA (TI-DCT) and learned IDA (CNN) on held-out images: mean PSNR
+    after each iteration count, and Mpixel/s of a full reconstruction with
+    that many iterations.  `equal` compares the fewest learned iterations
+    whose PSNR reaches the plain reference (its last iteration count) minus
+    0.1 dB with that reference."""
     p = torch.tensor(weights, device="cuda")
     packed = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
     abcs.abcs_cnn_pack(h, p, packed)
     out = {}
     for r in subrates:
-        acc = {"idct": [], "plain": [], "learned": [], "plain_ms": 0.0, "learned_ms": 0.0, "px": 0}
+        ps = {("idct", 0): []}
+        ms = {}
+        px = 0
         for i0 in range(0, n, batch):
             imgs = synth.gen_batch(min(batch, n - i0), H, W, seed + i0)
             sd = Sensed(h, imgs, 16, r, variant)
             x0 = sd.ida(h, 1, abcs.DEN_NONE)      # one identity iteration = A^T y, the IDCT image
-            xp, tp = timed_ida(h, sd, plain_iters, abcs.DEN_TIDCT, lam, None)
-            xl, tl = timed_ida(h, sd, learned_iters, abcs.DEN_CNN, lam, packed)
-            acc["idct"] += psnr(x0, sd.clean).tolist()
-            acc["plain"] += psnr(xp, sd.clean).tolist()
-            acc["learned"] += psnr(xl, sd.clean).tolist()
-            acc["plain_ms"] += tp
-            acc["learned_ms"] += tl
-            acc["px"] += sd.n * sd.Hc * sd.Wc
-        res = {"psnr_idct": float(np.mean(acc["idct"])), "psnr_plain": float(np.mean(acc["plain"])),
-               "psnr_learned": float(np.mean(acc["learned"])),
-               "plain_Mpx_per_s": acc["px"] / (acc["plain_ms"] * 1e-3) / 1e6,
-               "learned_Mpx_per_s": acc["px"] / (acc["learned_ms"] * 1e-3) / 1e6}
-        res["speedup"] = res["learned_Mpx_per_s"] / res["plain_Mpx_per_s"]
-        res["dpsnr"] = res["psnr_learned"] - res["psnr_plain"]
+            ps[("idct", 0)] += psnr(x0, sd.clean).tolist()
+            for kind, its, den, pk in (("plain", plain_iters, abcs.DEN_TIDCT, None),
+                                       ("learned", learned_iters, abcs.DEN_CNN, packed)):
+                for it in its:
+                    x, t_ms = timed_ida(h, sd, it, den, lam, pk, reps=2)
+                    ps.setdefault((kind, it), []).extend(psnr(x, sd.clean).tolist())
+                    ms[(kind, it)] = ms.get((kind, it), 0.0) + t_ms
+            px += sd.n * sd.Hc * sd.Wc
+        res = {"psnr_idct": float(np.mean(ps[("idct", 0)]))}
+        for kind, its in (("plain", plain_iters), ("learned", learned_iters)):
+            res[kind] = {str(it): {"psnr": float(np.mean(ps[(kind, it)])),
+                                   "Mpx_per_s": px / (ms[(kind, it)] * 1e-3) / 1e6} for it in its}
+        ref_it = str(plain_iters[-1])
+        ref = res["plain"][ref_it]
+        eq = None
+        for it in learned_iters:
+            e = res["learned"][str(it)]
+            if e["psnr"] >= ref["psnr"] - 0.1:
+                eq = {"learned_iters": it, "plain_iters": plain_iters[-1], "psnr_learned": e["psnr"],
+                      "psnr_plain": ref["psnr"], "speedup": e["Mpx_per_s"] / ref["Mpx_per_s"]}
+                break
+        res["equal"] = eq
         out[str(r)] = res
-        log(f"r={r}: " + json.dumps({k: round(v, 3) for k, v in res.items()}))
+        log(f"r={r}: idct {res['psnr_idct']:.2f}  plain " +
+            " ".join(f"{k}:{v['psnr']:.2f}" for k, v in res["plain"].items()) + "  learned " +
+            " ".join(f"{k}:{v['psnr']:.2f}" for k, v in res["learned"].items()) + f"  equal {eq}")
     assert abcs.abcs_sync_status(h) == 0
     return out
 
@@ -214,7 +233,7 @@ def main():
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--images", type=int, default=512)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=12000)
     ap.add_argument("--lam", type=float, default=DEFAULT_LAMBDA)
     ap.add_argument("--eval-images", type=int, default=128)
     ap.add_argument("--report", default=None, help="write a JSON report here")
@@ -225,17 +244,29 @@ def main():
         best, mean = tune_lambda(h)
         report["tune_lambda"] = {"best": best, "mean_psnr": mean}
     if a.cmd in ("train", "all"):
-        R, C, S = make_pairs(h, n_images=a.images, lam=a.lam)
-        print(f"{R.shape[0]} training crops")
-        w, hist, secs = train(h, R, C, S, steps=a.steps)
+        # phase A: denoiser inputs along plain-IDA trajectories
+        R, C, S = make_pairs(h, n_images=a.images, lam=a.lam, captures=(0, 1, 2, 3, 5, 8, 15, 29), crops=48)
+        print(f"phase A: {R.shape[0]} training crops")
+        w, hist_a, secs_a = train(h, R, C, S, steps=a.steps)
+        # phase B: add inputs along the network's own IDA trajectories, fine-tune
+        pk = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
+        abcs.abcs_cnn_pack(h, torch.tensor(w, device="cuda"), pk)
+        R2, C2, S2 = make_pairs(h, n_images=a.images // 2, lam=a.lam, captures=(1, 2, 3, 5), crops=96,
+                                seed=TRAIN_SEED + 5_000_000, packed=pk)
+        R, C, S = torch.cat([R, R2]), torch.cat([C, C2]), torch.cat([S, S2])
+        del R2, C2, S2
+        print(f"phase B: {R.shape[0]} training crops")
+        w, hist_b, secs_b = train(h, R, C, S, steps=a.steps, lr=3e-4, params=w, seed=2)
         os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
         w.astype("<f4").tofile(a.out)
-        report["train"] = {"crops": int(R.shape[0]), "steps": a.steps, "seconds": secs, "loss": hist}
+        report["train"] = {"crops": int(R.shape[0]), "steps": [a.steps, a.steps], "seconds": secs_a + secs_b,
+                           "loss": {"A": hist_a, "B": hist_b}}
         del R, C, S
         torch.cuda.empty_cache()
     if a.cmd in ("eval", "all"):
         w = load_weights(a.out if a.cmd == "all" else a.weights)
         report["eval"] = evaluate(h, w, n=a.eval_images, lam=a.lam)
+        report["lambda"] = a.lam
     if a.report:
         with open(a.report, "w") as f:
             json.dump(report, f, indent=1)
