@@ -173,6 +173,36 @@ abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offse
                      int denoiser, double lambda, const void* cnn_weights,
                      float* x_out, float* sigma_trace, void* stream);
 
+/* One image of an uneven batch (abcs_ida_batch). */
+typedef struct abcs_image_desc {
+    int32_t H, W, B;         /* image size in pixels, block size (4, 8, 16 or 32) */
+    int32_t reserved;        /* 0 */
+    int64_t block_offset;    /* index of the image's first block in counts / offsets */
+    int64_t coeff_base;      /* added to the image's offsets to index y */
+    int64_t pixel_offset;    /* index of the image's first pixel in x_out (dense Hc x Wc) */
+} abcs_image_desc;
+
+/* IDA (same iteration as abcs_ida) over a batch of images of different
+ * sizes and block sizes, all iterations in ONE persistent cooperative
+ * launch whose phases are separated by grid barriers (each wait bounded:
+ * on expiry ABCS_DEV_TIMEOUT is set and the launch ends).  The launch is
+ * captured once into a CUDA graph cached in the handle (keyed by all
+ * arguments) and replayed; the denoiser tile height and CTAs per SM are
+ * chosen the first time a batch shape is seen by timing each candidate on
+ * the caller's data (autotuner; the choice is kept in the handle).
+ *   desc        [host] n_img descriptors
+ *   counts, offsets [device] blocks of image k at desc[k].block_offset ...;
+ *               image k's coefficients at y[desc[k].coeff_base + offsets[.]]
+ *   y           [device] float [y_len]
+ *   x_out       [device] float, image k at x_out + desc[k].pixel_offset
+ *   sigma_trace [device] float [n_img][iters] or NULL
+ * denoiser: ABCS_DEN_NONE or ABCS_DEN_TIDCT (the learned denoiser runs
+ * through abcs_ida). */
+abcs_status abcs_ida_batch(abcs_handle* h, const abcs_image_desc* desc, int n_img, const int32_t* counts,
+                           const int64_t* offsets, const float* y, int64_t y_len, int iters,
+                           double damping, int denoiser, double lambda, float* x_out,
+                           float* sigma_trace, void* stream);
+
 /* The denoiser input of one IDA iteration: runs iterations 0 .. t-1 as
  * abcs_ida does, then the linear part of iteration t, and returns
  * r^t = x^t + A^T z^t (r_out [device] float [n_img][Hc][Wc]) and sigma^t

@@ -32,6 +32,11 @@ class AbcsError(RuntimeError):
         self.status = status
 
 
+class abcs_image_desc(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("B", C.c_int32), ("reserved", C.c_int32),
+                ("block_offset", C.c_int64), ("coeff_base", C.c_int64), ("pixel_offset", C.c_int64)]
+
+
 class abcs_plan_info(C.Structure):
     _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("B", C.c_int32), ("variant", C.c_int32),
                 ("nbh", C.c_int32), ("nbw", C.c_int32), ("n_blocks", C.c_int64), ("N", C.c_int64),
@@ -60,6 +65,7 @@ _SIGS = {
     "abcs_denoise_tidct": [_P, _P, _I, _I, _I, _P, _D, _P, _P],
     "abcs_sync_status": [_P, _P, C.POINTER(C.c_uint32)],
     "abcs_sense_noalloc": [_P, _I, _I, _I, _L, _L, _I, _D, _I, _I, _P, _P, _P, _L, _P, _P],
+    "abcs_ida_batch": [_P, _P, _I, _P, _P, _P, _L, _I, _D, _I, _D, _P, _P, _P],
     "abcs_ida_capture": [_P, _P, _P, _P, _I, _I, _I, _I, _I, _D, _I, _D, _P, _P, _P, _P],
     "abcs_cnn_param_count": [],
     "abcs_cnn_packed_bytes": [],
@@ -135,6 +141,15 @@ def abcs_ida(h, counts, offsets, y, n_img, H, W, B, iters, damping, denoiser, la
     _check(lib.abcs_ida(h, _ptr(counts), _ptr(offsets), _ptr(y), n_img, H, W, B, iters, damping,
                         denoiser, lam, _ptr(cnn_weights), _ptr(x_out), _ptr(sigma_trace),
                         _stream(stream)))
+
+
+def abcs_ida_batch(h, descs, counts, offsets, y, y_len, iters, damping, denoiser, lam, x_out,
+                   sigma_trace=None, stream=None) -> None:
+    """descs: list of (H, W, B, block_offset, coeff_base, pixel_offset)."""
+    arr = (abcs_image_desc * len(descs))(*[abcs_image_desc(H, W, B, 0, bo, cb, po)
+                                           for (H, W, B, bo, cb, po) in descs])
+    _check(lib.abcs_ida_batch(h, arr, len(descs), _ptr(counts), _ptr(offsets), _ptr(y), y_len, iters,
+                              damping, denoiser, lam, _ptr(x_out), _ptr(sigma_trace), _stream(stream)))
 
 
 def abcs_ida_capture(h, counts, offsets, y, n_img, H, W, B, t, damping, denoiser, lam, cnn_weights,

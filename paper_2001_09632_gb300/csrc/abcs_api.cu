@@ -3,9 +3,12 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "abcs_common.cuh"
 
@@ -16,6 +19,12 @@ struct abcs_handle {
     uint32_t* status = nullptr;   // device status word; word 1 is the allocation CTA counter
     void* ws = nullptr;           // workspace, grown on demand
     size_t ws_bytes = 0;
+    // uneven IDA batches: autotuned configurations and captured graphs
+    struct Tuned { int th, ctas_per_sm; float ms; };
+    std::map<std::string, Tuned> tuned;
+    std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;
+    cudaStream_t capture_stream = nullptr;
+    bool graphs_ok = true;
 };
 
 namespace {
@@ -188,6 +197,8 @@ void abcs_destroy(abcs_handle* h) {
     if (!h) return;
     DeviceGuard dg(h->device);
     cudaDeviceSynchronize();
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->ws) cudaFree(h->ws);
     if (h->status) cudaFree(h->status);
     delete h;
@@ -436,6 +447,180 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
     if (x_cur != x_out)
         ABCS_CUDA(cudaMemcpyAsync(x_out, x_cur, npx * sizeof(float), cudaMemcpyDeviceToDevice, s),
                   "copy result");
+    return ABCS_OK;
+}
+
+abcs_status abcs_ida_batch(abcs_handle* h, const abcs_image_desc* desc, int n_img, const int32_t* counts,
+                           const int64_t* offsets, const float* y, int64_t y_len, int iters, double damping,
+                           int denoiser, double lambda, float* x_out, float* sigma_trace, void* stream) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    if (!desc || !counts || !offsets || !y || !x_out) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (n_img < 1) return fail(ABCS_ERR_INVALID_ARG, "n_img must be >= 1");
+    if (iters < 1) return fail(ABCS_ERR_INVALID_ARG, "iters must be >= 1");
+    if (!(damping > 0.0)) return fail(ABCS_ERR_INVALID_ARG, "damping must be > 0");
+    if (denoiser != ABCS_DEN_NONE && denoiser != ABCS_DEN_TIDCT)
+        return fail(ABCS_ERR_UNSUPPORTED, "abcs_ida_batch runs the identity or the TI-DCT denoiser");
+    if (denoiser == ABCS_DEN_TIDCT && !(lambda >= 0.0)) return fail(ABCS_ERR_INVALID_ARG, "lambda must be >= 0");
+    if (y_len < 1) return fail(ABCS_ERR_INVALID_ARG, "y_len must be >= 1");
+    unsigned bmask = 0;
+    int64_t npx_end = 0;
+    std::string key;
+    for (int k = 0; k < n_img; ++k) {
+        const abcs_image_desc& d = desc[k];
+        if (!valid_B(d.B) || d.H < d.B || d.W < d.B)
+            return fail(ABCS_ERR_INVALID_ARG, "descriptor %d: bad size or block size", k);
+        if (d.block_offset < 0 || d.coeff_base < 0 || d.pixel_offset < 0)
+            return fail(ABCS_ERR_INVALID_ARG, "descriptor %d: negative offset", k);
+        bmask |= (unsigned)d.B;
+        const int64_t end = d.pixel_offset + (int64_t)(d.H / d.B) * d.B * (d.W / d.B) * d.B;
+        npx_end = end > npx_end ? end : npx_end;
+        char buf[96];
+        snprintf(buf, sizeof buf, "%d,%d,%d;", d.H, d.W, d.B);
+        key += buf;
+    }
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(ABCS_ERR_CUDA, "cannot select the handle's device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t smem = ida_batch_smem(bmask);
+    const int TW = ida_batch_tile_w();
+
+    // per-image tables for both denoiser tile heights
+    std::vector<BatchImg> tab[2];
+    int n_lin = 0, n_den[2] = {0, 0};
+    const int ths[2] = {32, 64};
+    for (int v = 0; v < 2; ++v) {
+        tab[v].resize(n_img);
+        int lin = 0, den = 0;
+        for (int k = 0; k < n_img; ++k) {
+            const abcs_image_desc& d = desc[k];
+            BatchImg& b = tab[v][k];
+            b.B = d.B; b.nbh = d.H / d.B; b.nbw = d.W / d.B;
+            b.Hc = b.nbh * d.B; b.Wc = b.nbw * d.B;
+            b.blk0 = d.block_offset; b.coeff_base = d.coeff_base; b.pix0 = d.pixel_offset;
+            b.lin0 = lin;
+            b.den0 = den;
+            const int NB = kTileCols / d.B;
+            lin += b.nbh * ((b.nbw + NB - 1) / NB);
+            den += ((b.Wc + TW - 1) / TW) * ((b.Hc + ths[v] - 1) / ths[v]);
+        }
+        n_lin = lin;
+        n_den[v] = den;
+    }
+    Carver c;
+    const size_t o_tab = c.take<BatchImg>(n_img);
+    const size_t o_r0 = c.take<float>(npx_end), o_r1 = c.take<float>(npx_end);
+    const size_t o_z0 = c.take<float>(y_len), o_z1 = c.take<float>(y_len);
+    const size_t o_part = c.take<double>(n_lin);
+    const size_t o_sig = c.take<float>(n_img);
+    const size_t o_bar = c.take<unsigned>(4);
+    abcs_status st = ensure_ws(h, c.off);
+    if (st) return st;
+
+    BatchArgs a{};
+    a.imgs = at<BatchImg>(h, o_tab);
+    a.n_img = n_img; a.n_lin = n_lin; a.iters = iters; a.denoiser = denoiser;
+    a.counts = counts; a.offsets = offsets; a.y = y; a.x = x_out;
+    a.r0 = at<float>(h, o_r0); a.r1 = at<float>(h, o_r1);
+    a.z0 = at<float>(h, o_z0); a.z1 = at<float>(h, o_z1);
+    a.partial = at<double>(h, o_part);
+    a.sigma = at<float>(h, o_sig);
+    a.trace = sigma_trace;
+    a.inv_df = (float)(1.0 / damping);
+    a.lambda = (float)lambda;
+    a.status = h->status;
+    a.bar = at<unsigned>(h, o_bar);
+    a.timeout = 4000000000LL;          // ~2 s at the GB300 SM clock
+    // Failure-detection test hook: ABCS_FAULT_SKIP_ARRIVE=k makes CTA k skip
+    // its first barrier arrival, so the other CTAs' bounded waits expire and
+    // the launch ends with ABCS_DEV_TIMEOUT (nothing faults or hangs).
+    a.skip_cta = -1;
+    if (const char* f = getenv("ABCS_FAULT_SKIP_ARRIVE")) a.skip_cta = atoi(f);
+    float* last_r = ((iters - 1) & 1) ? a.r1 : a.r0;
+
+    auto enqueue = [&](int v, int cps, cudaStream_t q) -> cudaError_t {
+        BatchArgs b = a;
+        b.n_den = n_den[v];
+        cudaError_t e = cudaMemsetAsync(b.bar, 0, 4 * sizeof(unsigned), q);
+        if (!e) e = launch_ida_batch(b, ths[v], cps, smem, q, nullptr);
+        if (!e && denoiser == ABCS_DEN_NONE)
+            e = cudaMemcpyAsync(x_out, last_r, npx_end * sizeof(float), cudaMemcpyDeviceToDevice, q);
+        return e;
+    };
+    auto upload = [&](int v) {
+        return cudaMemcpyAsync(const_cast<BatchImg*>(a.imgs), tab[v].data(), n_img * sizeof(BatchImg),
+                               cudaMemcpyHostToDevice, s);
+    };
+
+    // autotune: denoiser tile height x CTAs per SM, timed on this data
+    const std::string tkey = key + (denoiser == ABCS_DEN_TIDCT ? "T" : "N");
+    auto it = h->tuned.find(tkey);
+    if (it == h->tuned.end()) {
+        abcs_handle::Tuned best{64, 1, 1e30f};
+        cudaEvent_t e0, e1;
+        ABCS_CUDA(cudaEventCreate(&e0), "event");
+        ABCS_CUDA(cudaEventCreate(&e1), "event");
+        for (int v = 0; v < 2; ++v) {
+            if (denoiser != ABCS_DEN_TIDCT && v == 0) continue;     // tile height only matters for TI-DCT
+            ABCS_CUDA(upload(v), "upload batch table");
+            for (int cps = 1; cps <= 2; ++cps) {
+                ABCS_CUDA(cudaEventRecord(e0, s), "event");
+                ABCS_CUDA(enqueue(v, cps, s), "ida_batch launch");
+                ABCS_CUDA(cudaEventRecord(e1, s), "event");
+                ABCS_CUDA(cudaEventSynchronize(e1), "event");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best.ms) best = {ths[v], cps, ms};
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        it = h->tuned.emplace(tkey, best).first;
+    }
+    const int v = it->second.th == 32 ? 0 : 1;
+    const int cps = it->second.ctas_per_sm;
+    ABCS_CUDA(upload(v), "upload batch table");
+
+    // replay the captured graph of this exact call, or capture it now
+    char gk[512];
+    snprintf(gk, sizeof gk, "|%d,%d|%p%p%p%p%p%p%p|%lld|%d|%d|%a|%a|%d|", v, cps, (const void*)counts,
+             (const void*)offsets, (const void*)y, (void*)x_out, (void*)sigma_trace, h->ws, (void*)h->status,
+             (long long)y_len, iters, denoiser, damping, lambda, a.skip_cta);
+    const std::string gkey = tkey + gk;
+    if (h->graphs_ok) {
+        for (auto& g : h->graphs)
+            if (g.first == gkey) {
+                ABCS_CUDA(cudaGraphLaunch(g.second, s), "graph launch");
+                return ABCS_OK;
+            }
+        if (!h->capture_stream && cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking)) {
+            cudaGetLastError();
+            h->graphs_ok = false;
+        }
+        if (h->graphs_ok) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+            if (!e) {
+                const cudaError_t e2 = enqueue(v, cps, h->capture_stream);
+                e = cudaStreamEndCapture(h->capture_stream, &graph);
+                if (!e) e = e2;
+            }
+            if (!e) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (!e) {
+                if (h->graphs.size() >= 16) {
+                    cudaGraphExecDestroy(h->graphs.front().second);
+                    h->graphs.erase(h->graphs.begin());
+                }
+                h->graphs.emplace_back(gkey, exec);
+                ABCS_CUDA(cudaGraphLaunch(exec, s), "graph launch");
+                return ABCS_OK;
+            }
+            cudaGetLastError();            // capture unsupported here: launch directly from now on
+            h->graphs_ok = false;
+        }
+    }
+    ABCS_CUDA(enqueue(v, cps, s), "ida_batch launch");
     return ABCS_OK;
 }
 

@@ -209,6 +209,40 @@ int ida_ctas_per_image(const ImgGeom& g);
 cudaError_t launch_tidct(const float* in, float* out, int n_img, int H, int W, const float* sigma,
                          float lambda, cudaStream_t s);
 
+// Uneven IDA batch (k_ida.cu): per-image geometry and the persistent kernel's arguments.
+struct BatchImg {
+    int Hc, Wc, B, nbw, nbh;
+    int lin0, den0;            // first linear / denoiser tile of the image
+    int64_t blk0;              // first block in counts / offsets
+    int64_t pix0;              // first pixel in x / r
+    int64_t coeff_base;        // added to offsets
+};
+
+struct BatchArgs {
+    const BatchImg* imgs;
+    int n_img, n_lin, n_den, iters, denoiser;
+    const int32_t* counts;
+    const int64_t* offsets;
+    const float* y;
+    float* x;
+    float* r0;
+    float* r1;
+    float* z0;
+    float* z1;
+    double* partial;           // one per linear tile
+    float* sigma;              // one per image
+    float* trace;              // [n_img][iters] or NULL
+    float inv_df, lambda;
+    uint32_t* status;
+    unsigned* bar;             // arrival count, generation, abort flag
+    long long timeout;
+    int skip_cta;              // failure-detection test: this CTA skips its first arrival (-1: none)
+};
+
+size_t ida_batch_smem(unsigned used_b_mask);
+int ida_batch_tile_w();
+cudaError_t launch_ida_batch(const BatchArgs& a, int th, int ctas_per_sm, size_t smem, cudaStream_t s, int* grid);
+
 // learned denoiser (k_cnn.cu)
 int cnn_param_count();
 size_t cnn_packed_bytes();

@@ -18,46 +18,53 @@ namespace {
 //   c <- c + z                          (adds A^T z in the DCT domain)
 // then r = IDCT(c) = x + A^T z, and the CTA's share of ||z||^2 in FP64.
 // ---------------------------------------------------------------------------
+// One tile: NB = 256 / B blocks of one block row.  All pointers address the
+// tile's first block / pixel; coefficient indices are coeff_base +
+// offsets[.].  Returns the tile's ||z||^2 (valid in thread 0).
+struct LinTile {
+    const int32_t* counts;
+    const int64_t* offsets;
+    int64_t coeff_base;
+    const float* y;
+    const float* x;        // NULL: x = 0
+    const float* z_prev;   // NULL: z_prev = 0
+    float* z;
+    float* r;
+    int64_t pix;           // pixel index of the tile's top-left pixel in x / r
+    int Wc;                // row stride of x / r
+    int nblk;
+    float inv_df;
+    uint32_t* status;
+};
+
 template <int B>
-__global__ void __launch_bounds__(256, (B == 16 ? 3 : 4)) ida_linear_kernel(IdaLinArgs a) {
+ABCS_D double linear_tile(const LinTile& L, unsigned char* smem, int* rel, int64_t* s_start, double* shd) {
     using Tl = Tile<B>;
-    extern __shared__ __align__(16) unsigned char smem[];
     const TileSmem<B> sm(smem, 2);
     float* Ts = sm.Ts;
     float* Ys = sm.P[0];       // y, overwritten in place by z
     float* Zp = sm.P[1];       // z_prev
     uint16_t* rk = sm.rk;
-    __shared__ int rel[Tl::NB + 1];
-    __shared__ int64_t s_start, s_end;
-    __shared__ double shd[32];
-
-    const ImgGeom& g = a.g;
-    const int k = blockIdx.z, bi = blockIdx.y, bj0 = blockIdx.x * Tl::NB;
-    const int nblk = min(Tl::NB, g.nbw - bj0);
-    const int64_t gi0 = (int64_t)k * g.n_blocks + (int64_t)bi * g.nbw + bj0;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, nblk = L.nblk;
+    __syncthreads();           // smem of a previous tile is free
     load_rank_table<B>(rk);
-    griddep_wait();
     if (t < 32) {
-        if (t == 0) s_start = a.offsets[gi0];
-        if (t == 1) s_end = a.offsets[gi0 + nblk];
-        tile_prefix<B>(a.counts + gi0, nblk, rel, a.status);
+        if (t == 0) *s_start = L.coeff_base + L.offsets[0];
+        tile_prefix<B>(L.counts, nblk, rel, L.status);
     }
     __syncthreads();
-    const int64_t start = s_start;
-    int64_t n64 = s_end - start;
-    n64 = n64 < 0 ? 0 : (n64 > (int64_t)Tl::NB * B * B ? (int64_t)Tl::NB * B * B : n64);
-    const int n_in = (int)n64;
-    stage_in_async(Ys, a.y, start, n_in);
-    if (a.z_prev) stage_in_async(Zp, a.z_prev, start, n_in);
+    const int64_t start = *s_start;
+    const int n_in = rel[nblk];
+    stage_in_async(Ys, L.y, start, n_in);
+    if (L.z_prev) stage_in_async(Zp, L.z_prev, start, n_in);
     cp_async_commit();
 
     const int b = t / B, n = t % B;
-    const int64_t o = (int64_t)k * g.Hc * g.Wc + (int64_t)(bi * B + n) * g.Wc + (bj0 + b) * B;
+    const int64_t o = L.pix + (int64_t)n * L.Wc + b * B;
     {
         float x[B];
-        if (a.x && b < nblk) {
-            load_f32_row<B>(a.x + o, aligned16(a.x + o), x);
+        if (L.x && b < nblk) {
+            load_f32_row<B>(L.x + o, aligned16(L.x + o), x);
         } else {
 #pragma unroll
             for (int i = 0; i < B; ++i) x[i] = 0.f;
@@ -81,13 +88,13 @@ __global__ void __launch_bounds__(256, (B == 16 ? 3 : 4)) ida_linear_kernel(IdaL
         const int r0 = rel[min(b, nblk)], m = (b < nblk) ? rel[b + 1] - r0 : 0;
         float* ys = Ys + sh + r0;
         const float* zs = Zp + sh + r0;
-        const bool has_zp = a.z_prev != nullptr;
+        const bool has_zp = L.z_prev != nullptr;
 #pragma unroll
         for (int u = 0; u < B; ++u) {
             const int r = rk[u * B + v];
             if (r < m) {
                 const float zp = has_zp ? zs[r] : 0.f;
-                const float z = (ys[r] - c[u]) + zp * a.inv_df;
+                const float z = (ys[r] - c[u]) + zp * L.inv_df;
                 ys[r] = z;
                 c[u] += z;
                 nz += (double)z * (double)z;
@@ -101,11 +108,35 @@ __global__ void __launch_bounds__(256, (B == 16 ? 3 : 4)) ida_linear_kernel(IdaL
     if (b < nblk) {
         float x[B];
         inv_rows_from_smem<B>(Ts, x);
-        store_f32_row<B>(a.r + o, aligned16(a.r + o), x);
+        store_f32_row<B>(L.r + o, aligned16(L.r + o), x);
     }
-    stage_out(Ys, a.z, start, n_in);
-    nz = block_sum(nz, shd);
-    if (t == 0)
+    stage_out(Ys, L.z, start, n_in);
+    return block_sum(nz, shd);
+}
+
+template <int B>
+__global__ void __launch_bounds__(256, (B == 16 ? 3 : 4)) ida_linear_kernel(IdaLinArgs a) {
+    using Tl = Tile<B>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int rel[Tl::NB + 1];
+    __shared__ int64_t s_start;
+    __shared__ double shd[32];
+    const ImgGeom& g = a.g;
+    const int k = blockIdx.z, bi = blockIdx.y, bj0 = blockIdx.x * Tl::NB;
+    const int64_t gi0 = (int64_t)k * g.n_blocks + (int64_t)bi * g.nbw + bj0;
+    LinTile L;
+    L.counts = a.counts + gi0;
+    L.offsets = a.offsets + gi0;
+    L.coeff_base = 0;
+    L.y = a.y; L.x = a.x; L.z_prev = a.z_prev; L.z = a.z; L.r = a.r;
+    L.pix = (int64_t)k * g.Hc * g.Wc + (int64_t)(bi * B) * g.Wc + bj0 * B;
+    L.Wc = g.Wc;
+    L.nblk = min(Tl::NB, g.nbw - bj0);
+    L.inv_df = a.inv_df;
+    L.status = a.status;
+    griddep_wait();
+    const double nz = linear_tile<B>(L, smem, rel, &s_start, shd);
+    if (threadIdx.x == 0)
         a.partial[(int64_t)k * gridDim.x * gridDim.y + (int64_t)blockIdx.y * gridDim.x + blockIdx.x] = nz;
 }
 
@@ -157,7 +188,8 @@ __global__ void ida_sigma_kernel(const double* __restrict__ partial, int cpi,
 //       row is complete and written out.
 // Every output accumulates in a fixed order (deterministic).
 // ---------------------------------------------------------------------------
-constexpr int kTW = 240, kTH = 64, kWin = kTW + 7, kCols = kTW + 14, kQS = 65;
+constexpr int kTW = 240, kWin = kTW + 7, kCols = kTW + 14, kQS = 65;
+constexpr size_t kTidctSmem = (8 * 256 + kWin * kQS) * sizeof(float);
 
 ABCS_D int reflect(int i, int n) {
     const int p = 2 * n;
@@ -166,19 +198,14 @@ ABCS_D int reflect(int i, int n) {
     return i < n ? i : p - 1 - i;
 }
 
-__global__ void __launch_bounds__(256) tidct_kernel(const float* __restrict__ in,
-                                                   float* __restrict__ out, int H, int W,
-                                                   const float* __restrict__ sigma, float lambda) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// One 240 x TH output tile of the plain denoiser (img, dst: one image).
+template <int TH>
+ABCS_D void tidct_tile(const float* __restrict__ img, float* __restrict__ dst, int H, int W, int x0, int y0,
+                       float thr, unsigned char* smem) {
     float* Vs = reinterpret_cast<float*>(smem);        // [8][256]
     float* Qs = Vs + 8 * 256;                          // [kWin][kQS]
-    griddep_wait();
-    const int k = blockIdx.z;
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
-    const float* img = in + (int64_t)k * H * W;
-    float* dst = out + (int64_t)k * H * W;
-    const float thr = lambda * __ldg(sigma + k);
     const int t = threadIdx.x;
+    __syncthreads();                                   // smem of a previous tile is free
 
     // (a) state: this thread's input column and its 8-row window
     const bool has_col = t < kCols;
@@ -191,7 +218,7 @@ __global__ void __launch_bounds__(256) tidct_kernel(const float* __restrict__ in
     float acc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i] = 0.f;
-    const int ylast = min(y0 + kTH, H);
+    const int ylast = min(y0 + TH, H);
 
     for (int wy = y0 - 7; wy < ylast; ++wy) {
         if (has_col) {
@@ -243,6 +270,141 @@ __global__ void __launch_bounds__(256) tidct_kernel(const float* __restrict__ in
     }
 }
 
+template <int TH>
+__global__ void __launch_bounds__(256) tidct_kernel(const float* __restrict__ in, float* __restrict__ out, int H,
+                                                   int W, const float* __restrict__ sigma, float lambda) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    griddep_wait();
+    const int k = blockIdx.z;
+    tidct_tile<TH>(in + (int64_t)k * H * W, out + (int64_t)k * H * W, H, W, blockIdx.x * kTW, blockIdx.y * TH,
+                   lambda * __ldg(sigma + k), smem);
+}
+
+// ---------------------------------------------------------------------------
+// Uneven batch: every iteration of IDA for images of different sizes and
+// block sizes in ONE persistent cooperative launch.  Phases (linear step,
+// per-image sigma, denoiser) are separated by grid barriers whose waits are
+// bounded: a wait that exceeds `timeout` clock cycles sets
+// ABCS_DEV_TIMEOUT, raises the abort flag and every CTA leaves the kernel.
+// ---------------------------------------------------------------------------
+ABCS_D bool grid_sync(unsigned* bar, long long timeout, uint32_t* status, int* s_ok, bool skip_arrival = false) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = bar + 1;
+        volatile unsigned* vabort = bar + 2;
+        int ok = *vabort ? 0 : 1;
+        if (ok) {
+            const unsigned g = *vgen;
+            __threadfence();
+            if (!skip_arrival && atomicAdd(bar, 1u) == gridDim.x - 1) {
+                bar[0] = 0u;
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+            } else {
+                const long long t0 = clock64();
+                while (*vgen == g) {
+                    if (*vabort) { ok = 0; break; }
+                    if (clock64() - t0 > timeout) {
+                        atomicExch(bar + 2, 1u);
+                        set_status(status, ABCS_DEV_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// image owning tile `tile` (first-tile indices ascending)
+ABCS_D int find_image(const BatchImg* imgs, int n, int tile, bool linear) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int f = linear ? __ldg(&imgs[mid].lin0) : __ldg(&imgs[mid].den0);
+        if (f <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int TH>
+__global__ void __launch_bounds__(256) ida_batch_kernel(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int rel[kTileCols / 4 + 1];
+    __shared__ int64_t s_start;
+    __shared__ double shd[32];
+    __shared__ int s_ok;
+    const int G = gridDim.x;
+    for (int t = 0; t < a.iters; ++t) {
+        const float* xcur = t == 0 ? nullptr : (a.denoiser == ABCS_DEN_NONE ? ((t - 1) & 1 ? a.r1 : a.r0) : a.x);
+        const float* zp = t == 0 ? nullptr : ((t - 1) & 1 ? a.z1 : a.z0);
+        float* zc = (t & 1) ? a.z1 : a.z0;
+        float* rc = (t & 1) ? a.r1 : a.r0;
+        // linear step (Eqs. 25, 28) over every block row tile of every image
+        for (int tile = blockIdx.x; tile < a.n_lin; tile += G) {
+            const int k = find_image(a.imgs, a.n_img, tile, true);
+            const BatchImg im = a.imgs[k];
+            const int NB = kTileCols / im.B, tpr = (im.nbw + NB - 1) / NB;
+            const int local = tile - im.lin0, bi = local / tpr, bj0 = (local - bi * tpr) * NB;
+            const int64_t gi0 = im.blk0 + (int64_t)bi * im.nbw + bj0;
+            LinTile L;
+            L.counts = a.counts + gi0;
+            L.offsets = a.offsets + gi0;
+            L.coeff_base = im.coeff_base;
+            L.y = a.y; L.x = xcur; L.z_prev = zp; L.z = zc; L.r = rc;
+            L.pix = im.pix0 + (int64_t)(bi * im.B) * im.Wc + bj0 * im.B;
+            L.Wc = im.Wc;
+            L.nblk = min(NB, im.nbw - bj0);
+            L.inv_df = a.inv_df;
+            L.status = a.status;
+            double nz = 0.0;
+            switch (im.B) {
+                case 4: nz = linear_tile<4>(L, smem, rel, &s_start, shd); break;
+                case 8: nz = linear_tile<8>(L, smem, rel, &s_start, shd); break;
+                case 16: nz = linear_tile<16>(L, smem, rel, &s_start, shd); break;
+                default: nz = linear_tile<32>(L, smem, rel, &s_start, shd); break;
+            }
+            if (threadIdx.x == 0) a.partial[tile] = nz;
+        }
+        if (!grid_sync(a.bar, a.timeout, a.status, &s_ok, t == 0 && (int)blockIdx.x == a.skip_cta)) return;
+        // sigma^t per image (Eq. 15), partials in a fixed order
+        for (int k = blockIdx.x; k < a.n_img; k += G) {
+            if (threadIdx.x < 32) {
+                const BatchImg im = a.imgs[k];
+                const int l1 = k + 1 < a.n_img ? a.imgs[k + 1].lin0 : a.n_lin;
+                double s = 0.0;
+                for (int j = im.lin0 + threadIdx.x; j < l1; j += 32) s += a.partial[j];
+                s = warp_sum(s);
+                if (threadIdx.x == 0) {
+                    const int64_t last = im.blk0 + (int64_t)im.nbh * im.nbw - 1;
+                    const int64_t m = a.offsets[last] + a.counts[last] - a.offsets[im.blk0];
+                    const double v = m > 0 ? sqrt(s / (double)m) : 0.0;
+                    if (!isfinite(v)) set_status(a.status, ABCS_DEV_NONFINITE);
+                    a.sigma[k] = (float)v;
+                    if (a.trace) a.trace[(int64_t)k * a.iters + t] = (float)v;
+                }
+            }
+        }
+        if (!grid_sync(a.bar, a.timeout, a.status, &s_ok)) return;
+        if (a.denoiser == ABCS_DEN_TIDCT) {
+            for (int tile = blockIdx.x; tile < a.n_den; tile += G) {
+                const int k = find_image(a.imgs, a.n_img, tile, false);
+                const BatchImg im = a.imgs[k];
+                const int tx = (im.Wc + kTW - 1) / kTW;
+                const int local = tile - im.den0;
+                tidct_tile<TH>(rc + im.pix0, a.x + im.pix0, im.Hc, im.Wc, (local % tx) * kTW, (local / tx) * TH,
+                               a.lambda * a.sigma[k], smem);
+            }
+            if (!grid_sync(a.bar, a.timeout, a.status, &s_ok)) return;
+        }
+    }
+}
+
 }  // namespace
 
 int ida_ctas_per_image(const ImgGeom& g) {
@@ -267,14 +429,59 @@ cudaError_t launch_ida_sigma(const ImgGeom& g, const int64_t* offsets, const dou
                       (int64_t)g.n_blocks, sigma, sigma_trace, iters, t, status);
 }
 
+size_t ida_batch_smem(unsigned used_b_mask) {
+    size_t s = kTidctSmem;
+    if (used_b_mask & 4) s = s > Tile<4>::smem_bytes(2) ? s : Tile<4>::smem_bytes(2);
+    if (used_b_mask & 8) s = s > Tile<8>::smem_bytes(2) ? s : Tile<8>::smem_bytes(2);
+    if (used_b_mask & 16) s = s > Tile<16>::smem_bytes(2) ? s : Tile<16>::smem_bytes(2);
+    if (used_b_mask & 32) s = s > Tile<32>::smem_bytes(2) ? s : Tile<32>::smem_bytes(2);
+    return s;
+}
+
+int ida_batch_tile_w() { return kTW; }
+
+template <int TH>
+static cudaError_t launch_batch_th(const BatchArgs& a, int ctas_per_sm, size_t smem, cudaStream_t s, int* grid_out) {
+    cudaError_t e = cudaFuncSetAttribute(ida_batch_kernel<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    int dev, sms, per_sm;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ida_batch_kernel<TH>, 256, smem))) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int use = ctas_per_sm < per_sm ? ctas_per_sm : per_sm;
+    int grid = sms * use;
+    const int work = a.n_lin > a.n_den ? a.n_lin : a.n_den;
+    if (grid > work) grid = work > 0 ? work : 1;
+    if (grid_out) *grid_out = grid;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ida_batch_kernel<TH>, a);
+}
+
+// th: denoiser tile height (32 or 64); ctas_per_sm: requested residency
+cudaError_t launch_ida_batch(const BatchArgs& a, int th, int ctas_per_sm, size_t smem, cudaStream_t s, int* grid) {
+    if (th == 32) return launch_batch_th<32>(a, ctas_per_sm, smem, s, grid);
+    return launch_batch_th<64>(a, ctas_per_sm, smem, s, grid);
+}
+
 cudaError_t launch_tidct(const float* in, float* out, int n_img, int H, int W, const float* sigma,
                          float lambda, cudaStream_t s) {
-    const size_t smem = (8 * 256 + kWin * kQS) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(tidct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    constexpr int TH = 64;
+    const size_t smem = kTidctSmem;
+    cudaError_t e = cudaFuncSetAttribute(tidct_kernel<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e) return e;
-    dim3 grid((unsigned)((W + kTW - 1) / kTW), (unsigned)((H + kTH - 1) / kTH), (unsigned)n_img);
-    return launch_pdl(tidct_kernel, grid, dim3(256), smem, s, in, out, H, W, sigma, lambda);
+    dim3 grid((unsigned)((W + kTW - 1) / kTW), (unsigned)((H + TH - 1) / TH), (unsigned)n_img);
+    return launch_pdl(tidct_kernel<TH>, grid, dim3(256), smem, s, in, out, H, W, sigma, lambda);
 }
 
 }  // namespace abcs
