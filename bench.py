@@ -45,6 +45,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="abcs", choices=["abcs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the uneven-batch IDA and the learned-vs-plain video measurements")
     ap.add_argument("--precision", default="fp16x2", choices=["fp32", "fp16x2", "bf16x2", "bf16"],
                     help="block-DCT arithmetic of the timed path (fp16x2 and bf16x2 meet the "
                          "1e-5 relative-L2 bar against the FP64 oracle; bf16 does not)")
@@ -163,6 +165,70 @@ def run_reference(a):
                              "kind": "oracle", "sample": f"{rows}x{W} crop per step"},
             "e2e": {"value": v, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def uneven_batch_ida(h, world, max_over_ranks, barrier, n=256, subrate=0.2, iters=30, seed=5000):
+    """256 images, 40% 256^2 / 40% 512^2 / 20% 1024^2, B cycling 8/16/32,
+    AL-DCT-BBV at subrate 0.2, 30 plain IDA iterations in ONE abcs_ida_batch
+    call (persistent kernel, graph replay).  Also the same work as one
+    abcs_ida call per (size, B) group, for comparison."""
+    import torch
+    from paper_2001_09632_gb300 import abcs, synth
+    from paper_2001_09632_gb300.uneven import UnevenBatch
+    ub = UnevenBatch(h, synth.gen_uneven_batch(n, seed), subrate)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):                     # first call: autotune + capture
+        ub.ida(h, iters, abcs.DEN_TIDCT, LAMBDA, DF)
+    torch.cuda.synchronize()
+    ev = []
+    barrier()
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ub.ida(h, iters, abcs.DEN_TIDCT, LAMBDA, DF)
+        e1.record(stream)
+        ev.append((e0, e1))
+    barrier()
+    ms = max_over_ranks(statistics.median(a.elapsed_time(b) for a, b in ev))
+    assert abcs.abcs_sync_status(h) == 0
+    psnr = ub.psnr()
+    # the same images, one abcs_ida call per group
+    outs = []
+    for (H, W, B, ni, b0, c0, cap) in ub.groups:
+        Hc, Wc = (H // B) * B, (W // B) * B
+        outs.append(torch.empty((ni, Hc, Wc), dtype=torch.float32, device="cuda"))
+
+    def per_group():
+        for (H, W, B, ni, b0, c0, cap), xo in zip(ub.groups, outs):
+            nb = ni * (H // B) * (W // B)
+            abcs.abcs_ida(h, ub.counts[b0:b0 + nb], ub.offsets[b0:b0 + nb + 1], ub.y[c0:c0 + cap], ni, H, W, B,
+                          iters, DF, abcs.DEN_TIDCT, LAMBDA, None, xo, None)
+    per_group()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    per_group()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_groups = max_over_ranks(e0.elapsed_time(e1))
+    same = all(torch.equal(ub.image(k), xo[j]) for ks, xo in zip(ub.members, outs) for j, k in enumerate(ks))
+    return {"value": world * ub.pixels * iters / (ms * 1e-3) / 1e6, "unit": "Mpixel*iter/s",
+            "images": n, "mix": "40% 256x256, 40% 512x512, 20% 1024x1024; B cycles 8, 16, 32",
+            "subrate": subrate, "variant": "BBV", "iters": iters, "denoiser": "tidct", "lambda": LAMBDA,
+            "pixels": ub.pixels, "measurements": ub.measurements, "ms_per_call": ms,
+            "launch": "one persistent cooperative kernel per call, CUDA graph replay",
+            "per_group_calls": {"calls": len(ub.groups), "ms": ms_groups,
+                                "value": world * ub.pixels * iters / (ms_groups * 1e-3) / 1e6,
+                                "identical_output": same},
+            "mean_psnr": sum(psnr) / len(psnr),
+            "l2": "working set (x, r, z, y: ~1.2 GB) larger than L2"}
+
+
+def video_learned_vs_plain(h):
+    """The 120-frame 1920x1088 clip, AL-DCT-DD at subrate 0.25, 30 frames
+    per call: learned IDA (10 iterations) vs plain IDA (30 iterations)."""
+    from paper_2001_09632_gb300 import train
+    return train.video_eval(h, train.load_weights(), reps=1, log=lambda *_: None)
 
 
 def main():
@@ -304,6 +370,12 @@ def main():
     t_end3 = time.time()
     e2e_ms = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in eve) / Ke)
     clocks = clk.stop(t_start, t_end3)
+    extras = {}
+    if not a.no_extras:
+        del x
+        extras["ida_batch"] = uneven_batch_ida(h, world, max_over_ranks, barrier)
+        if rank == 0:
+            extras["learned_vs_plain"] = video_learned_vs_plain(h)
 
     if rank != 0:
         abcs.abcs_destroy(h)
@@ -341,6 +413,7 @@ def main():
         "e2e": {"value": world * px / (e2e_ms * 1e-3) / 1e6, "unit": "Mpixel/s",
                 "h2d_bytes_per_step": int(h_img.numel()), "d2h_bytes_per_step": int(h_rec.numel() * 4),
                 "ms_per_step": e2e_ms},
+        **extras,
         "gpu_launches": (4 if prec == abcs.FP32 else 5) * K,
         "clocks": clocks,
     }

@@ -562,7 +562,7 @@ abcs_status abcs_ida_batch(abcs_handle* h, const abcs_image_desc* desc, int n_im
         for (int v = 0; v < 2; ++v) {
             if (denoiser != ABCS_DEN_TIDCT && v == 0) continue;     // tile height only matters for TI-DCT
             ABCS_CUDA(upload(v), "upload batch table");
-            for (int cps = 1; cps <= 2; ++cps) {
+            for (int cps = 1; cps <= 3; ++cps) {
                 ABCS_CUDA(cudaEventRecord(e0, s), "event");
                 ABCS_CUDA(enqueue(v, cps, s), "ida_batch launch");
                 ABCS_CUDA(cudaEventRecord(e1, s), "event");

@@ -37,13 +37,15 @@ struct LinTile {
     uint32_t* status;
 };
 
-template <int B>
+// ZP_STAGE: z_prev staged in shared memory beside y (two staging buffers);
+// otherwise it is read from global memory where it is used (one buffer).
+template <int B, bool ZP_STAGE = true>
 ABCS_D double linear_tile(const LinTile& L, unsigned char* smem, int* rel, int64_t* s_start, double* shd) {
     using Tl = Tile<B>;
-    const TileSmem<B> sm(smem, 2);
+    const TileSmem<B> sm(smem, ZP_STAGE ? 2 : 1);
     float* Ts = sm.Ts;
     float* Ys = sm.P[0];       // y, overwritten in place by z
-    float* Zp = sm.P[1];       // z_prev
+    float* Zp = sm.P[1];       // z_prev (ZP_STAGE)
     uint16_t* rk = sm.rk;
     const int t = threadIdx.x, nblk = L.nblk;
     __syncthreads();           // smem of a previous tile is free
@@ -56,7 +58,7 @@ ABCS_D double linear_tile(const LinTile& L, unsigned char* smem, int* rel, int64
     const int64_t start = *s_start;
     const int n_in = rel[nblk];
     stage_in_async(Ys, L.y, start, n_in);
-    if (L.z_prev) stage_in_async(Zp, L.z_prev, start, n_in);
+    if (ZP_STAGE && L.z_prev) stage_in_async(Zp, L.z_prev, start, n_in);
     cp_async_commit();
 
     const int b = t / B, n = t % B;
@@ -87,7 +89,7 @@ ABCS_D double linear_tile(const LinTile& L, unsigned char* smem, int* rel, int64
         const int sh = (int)(start & 3);
         const int r0 = rel[min(b, nblk)], m = (b < nblk) ? rel[b + 1] - r0 : 0;
         float* ys = Ys + sh + r0;
-        const float* zs = Zp + sh + r0;
+        const float* zs = ZP_STAGE ? Zp + sh + r0 : (L.z_prev ? L.z_prev + start + r0 : nullptr);
         const bool has_zp = L.z_prev != nullptr;
 #pragma unroll
         for (int u = 0; u < B; ++u) {
@@ -287,6 +289,10 @@ __global__ void __launch_bounds__(256) tidct_kernel(const float* __restrict__ in
 // bounded: a wait that exceeds `timeout` clock cycles sets
 // ABCS_DEV_TIMEOUT, raises the abort flag and every CTA leaves the kernel.
 // ---------------------------------------------------------------------------
+#ifndef ABCS_BATCH_MINB
+#define ABCS_BATCH_MINB 3
+#endif
+
 ABCS_D bool grid_sync(unsigned* bar, long long timeout, uint32_t* status, int* s_ok, bool skip_arrival = false) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -332,8 +338,25 @@ ABCS_D int find_image(const BatchImg* imgs, int n, int tile, bool linear) {
     return lo;
 }
 
+// The phases of the persistent kernel are separate calls so that each is
+// register-allocated on its own (inlined together they need 255 registers
+// and spill, one CTA per SM).
+// B = 32 reads z_prev from global memory: its shared memory (68.6 KB) then
+// stays below the denoiser's, which keeps three CTAs per SM.
+template <int B>
+__device__ __noinline__ double linear_tile_call(const LinTile& L, unsigned char* smem, int* rel, int64_t* s_start,
+                                                double* shd) {
+    return linear_tile<B, (B < 32)>(L, smem, rel, s_start, shd);
+}
+
 template <int TH>
-__global__ void __launch_bounds__(256) ida_batch_kernel(BatchArgs a) {
+__device__ __noinline__ void tidct_tile_call(const float* img, float* dst, int H, int W, int x0, int y0, float thr,
+                                             unsigned char* smem) {
+    tidct_tile<TH>(img, dst, H, W, x0, y0, thr, smem);
+}
+
+template <int TH>
+__global__ void __launch_bounds__(256, ABCS_BATCH_MINB) ida_batch_kernel(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int rel[kTileCols / 4 + 1];
     __shared__ int64_t s_start;
@@ -364,10 +387,10 @@ __global__ void __launch_bounds__(256) ida_batch_kernel(BatchArgs a) {
             L.status = a.status;
             double nz = 0.0;
             switch (im.B) {
-                case 4: nz = linear_tile<4>(L, smem, rel, &s_start, shd); break;
-                case 8: nz = linear_tile<8>(L, smem, rel, &s_start, shd); break;
-                case 16: nz = linear_tile<16>(L, smem, rel, &s_start, shd); break;
-                default: nz = linear_tile<32>(L, smem, rel, &s_start, shd); break;
+                case 4: nz = linear_tile_call<4>(L, smem, rel, &s_start, shd); break;
+                case 8: nz = linear_tile_call<8>(L, smem, rel, &s_start, shd); break;
+                case 16: nz = linear_tile_call<16>(L, smem, rel, &s_start, shd); break;
+                default: nz = linear_tile_call<32>(L, smem, rel, &s_start, shd); break;
             }
             if (threadIdx.x == 0) a.partial[tile] = nz;
         }
@@ -397,8 +420,8 @@ __global__ void __launch_bounds__(256) ida_batch_kernel(BatchArgs a) {
                 const BatchImg im = a.imgs[k];
                 const int tx = (im.Wc + kTW - 1) / kTW;
                 const int local = tile - im.den0;
-                tidct_tile<TH>(rc + im.pix0, a.x + im.pix0, im.Hc, im.Wc, (local % tx) * kTW, (local / tx) * TH,
-                               a.lambda * a.sigma[k], smem);
+                tidct_tile_call<TH>(rc + im.pix0, a.x + im.pix0, im.Hc, im.Wc, (local % tx) * kTW, (local / tx) * TH,
+                                    a.lambda * a.sigma[k], smem);
             }
             if (!grid_sync(a.bar, a.timeout, a.status, &s_ok)) return;
         }
@@ -434,7 +457,7 @@ size_t ida_batch_smem(unsigned used_b_mask) {
     if (used_b_mask & 4) s = s > Tile<4>::smem_bytes(2) ? s : Tile<4>::smem_bytes(2);
     if (used_b_mask & 8) s = s > Tile<8>::smem_bytes(2) ? s : Tile<8>::smem_bytes(2);
     if (used_b_mask & 16) s = s > Tile<16>::smem_bytes(2) ? s : Tile<16>::smem_bytes(2);
-    if (used_b_mask & 32) s = s > Tile<32>::smem_bytes(2) ? s : Tile<32>::smem_bytes(2);
+    if (used_b_mask & 32) s = s > Tile<32>::smem_bytes(1) ? s : Tile<32>::smem_bytes(1);
     return s;
 }
 

@@ -7,6 +7,7 @@ PSNR bookkeeping of the evaluation).
   python -m paper_2001_09632_gb300.train tune-lambda   # plain TI-DCT threshold factor
   python -m paper_2001_09632_gb300.train train --out weights.f32
   python -m paper_2001_09632_gb300.train eval --weights weights.f32
+  python -m paper_2001_09632_gb300.train video --weights weights.f32  # 1920x1088 DD clip
 
 Training pairs follow the method itself: synthetic images are sensed
 (AL-DCT-BBV or AL-DCT-DD, subrate drawn from {0.1, ..., 0.5}), plain IDA
@@ -227,9 +228,69 @@ def evaluate(h, weights, n=128, H=512, W=512, subrates=(0.1, 0.2, 0.3, 0.4, 0.5)
     return out
 
 
+def video_eval(h, weights, n_frames=120, H=1088, W=1920, batch=30, subrate=0.25, variant=abcs.DD, B=16,
+               plain_iters=(10, 20, 30), learned_iters=(1, 2, 3, 4, 6, 10), lam=DEFAULT_LAMBDA, seed=EVAL_SEED + 7,
+               reps=2, log=print):
+    """Intra-frame video: every frame of a synthetic clip (shapes drifting 2
+    px/frame over a static texture) sensed on its own with AL-DCT-DD, batches
+    of `batch` frames per call.  Mean PSNR and Mpixel/s of the IDCT image,
+    plain IDA (TI-DCT) and learned IDA (CNN) after each iteration count; the
+    headline pair is learned-10 vs plain-30, and `equal` names the fewest
+    learned iterations within 0.1 dB of plain-30."""
+    p = torch.tensor(weights, device="cuda")
+    packed = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
+    abcs.abcs_cnn_pack(h, p, packed)
+    ps, ms = {}, {}
+    px = 0
+    sense_ms = 0.0
+    for f0 in range(0, n_frames, batch):
+        frames = synth.gen_video(min(batch, n_frames - f0), H, W, seed, first_frame=f0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sd = Sensed(h, frames, B, subrate, variant)
+        e1.record()
+        torch.cuda.synchronize()
+        sense_ms += e0.elapsed_time(e1)
+        x0 = sd.ida(h, 1, abcs.DEN_NONE)
+        ps.setdefault(("idct", 0), []).extend(psnr(x0, sd.clean).tolist())
+        for kind, its, den, pk in (("plain", plain_iters, abcs.DEN_TIDCT, None),
+                                   ("learned", learned_iters, abcs.DEN_CNN, packed)):
+            for it in its:
+                x, t_ms = timed_ida(h, sd, it, den, lam, pk, reps=reps)
+                ps.setdefault((kind, it), []).extend(psnr(x, sd.clean).tolist())
+                ms[(kind, it)] = ms.get((kind, it), 0.0) + t_ms
+        px += sd.n * sd.Hc * sd.Wc
+        del sd, x, x0
+    res = {"frames": n_frames, "size": [H, W], "B": B, "subrate": subrate,
+           "variant": "DD" if variant == abcs.DD else "BBV", "frames_per_call": batch,
+           "sense_Mpx_per_s": px / (sense_ms * 1e-3) / 1e6,
+           "psnr_idct": float(np.mean(ps[("idct", 0)]))}
+    for kind, its in (("plain", plain_iters), ("learned", learned_iters)):
+        res[kind] = {str(it): {"psnr": float(np.mean(ps[(kind, it)])),
+                               "Mpx_per_s": px / (ms[(kind, it)] * 1e-3) / 1e6} for it in its}
+    ref = res["plain"][str(plain_iters[-1])]
+    head = res["learned"][str(learned_iters[-1])]
+    res["learned_vs_plain"] = {"learned_iters": learned_iters[-1], "plain_iters": plain_iters[-1],
+                               "psnr_learned": head["psnr"], "psnr_plain": ref["psnr"],
+                               "dpsnr": head["psnr"] - ref["psnr"],
+                               "speedup": head["Mpx_per_s"] / ref["Mpx_per_s"]}
+    res["equal"] = None
+    for it in learned_iters:
+        e = res["learned"][str(it)]
+        if e["psnr"] >= ref["psnr"] - 0.1:
+            res["equal"] = {"learned_iters": it, "plain_iters": plain_iters[-1], "psnr_learned": e["psnr"],
+                            "psnr_plain": ref["psnr"], "speedup": e["Mpx_per_s"] / ref["Mpx_per_s"]}
+            break
+    log(f"video: idct {res['psnr_idct']:.2f}  plain " +
+        " ".join(f"{k}:{v['psnr']:.2f}" for k, v in res["plain"].items()) + "  learned " +
+        " ".join(f"{k}:{v['psnr']:.2f}" for k, v in res["learned"].items()) + f"  equal {res['equal']}")
+    assert abcs.abcs_sync_status(h) == 0
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["tune-lambda", "train", "eval", "all"])
+    ap.add_argument("cmd", choices=["tune-lambda", "train", "eval", "video", "all"])
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--images", type=int, default=512)
@@ -267,6 +328,9 @@ def main():
         w = load_weights(a.out if a.cmd == "all" else a.weights)
         report["eval"] = evaluate(h, w, n=a.eval_images, lam=a.lam)
         report["lambda"] = a.lam
+    if a.cmd in ("video", "all"):
+        w = load_weights(a.out if a.cmd == "all" else a.weights)
+        report["video"] = video_eval(h, w, lam=a.lam)
     if a.report:
         with open(a.report, "w") as f:
             json.dump(report, f, indent=1)
