@@ -17,6 +17,7 @@ using namespace abcs;
 struct abcs_handle {
     int device = 0;
     uint32_t* status = nullptr;   // device status word; word 1 is the allocation CTA counter
+    unsigned* img_done = nullptr; // per image pilot-CTA counters of the fused allocation (65536, zero at rest)
     void* ws = nullptr;           // workspace, grown on demand
     size_t ws_bytes = 0;
     // uneven IDA batches: autotuned configurations and captured graphs
@@ -181,6 +182,7 @@ abcs_status abcs_create(abcs_handle** out) {
     ABCS_CUDA(upload_tables_dct(), "upload tables");
     ABCS_CUDA(upload_tables_ida(), "upload tables");
     ABCS_CUDA(upload_tables_tc(), "upload tables");
+    ABCS_CUDA(setup_tc_fragments(), "tensor-core fragment setup");
     abcs_handle* h = new abcs_handle;
     h->device = dev;
     if (cudaMalloc(&h->status, 256) != cudaSuccess) {
@@ -189,6 +191,13 @@ abcs_status abcs_create(abcs_handle** out) {
         return fail(ABCS_ERR_OOM, "status word allocation failed");
     }
     cudaMemset(h->status, 0, 256);
+    if (cudaMalloc(&h->img_done, 65536 * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->status);
+        delete h;
+        return fail(ABCS_ERR_OOM, "counter allocation failed");
+    }
+    cudaMemset(h->img_done, 0, 65536 * sizeof(unsigned));
     *out = h;
     return ABCS_OK;
 }
@@ -201,6 +210,7 @@ void abcs_destroy(abcs_handle* h) {
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->ws) cudaFree(h->ws);
     if (h->status) cudaFree(h->status);
+    if (h->img_done) cudaFree(h->img_done);
     delete h;
 }
 
@@ -269,20 +279,19 @@ abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int
     a.img_total = at<int64_t>(h, o_tot);
     a.img_base = at<int64_t>(h, o_base);
     a.done = h->status + 1;
+    a.img_done = h->img_done;
     a.status = h->status;
 
-    int mode = 0;
+    // pilot kernels allocate in their fused tail; without a pilot the
+    // stand-alone allocation kernel runs
     if (variant == ABCS_BBV && p.nS > 0) {
-        ABCS_CUDA(launch_bbv_pilot(a, s), "bbv_pilot launch");
-        mode = 1;
+        ABCS_CUDA(launch_bbv_alloc(a, s), "bbv pilot + allocation launch");
     } else if (variant == ABCS_DD) {
-        ABCS_CUDA(launch_dd_pilot(a, s), "dd_pilot launch");
-        mode = 2;
+        ABCS_CUDA(launch_dd_alloc(a, s), "dd pilot + allocation launch");
     } else {
-        mode = (variant == ABCS_BBV) ? 3 : 0;
         if (pilot) ABCS_CUDA(cudaMemsetAsync(pilot, 0, nb_all * sizeof(int32_t), s), "memset");
+        ABCS_CUDA(launch_allocate(a, variant == ABCS_BBV ? 3 : 0, s), "allocate launch");
     }
-    ABCS_CUDA(launch_allocate(a, mode, s), "allocate launch");
     if (precision == ABCS_FP32)
         ABCS_CUDA(launch_sense_pack(a, s), "sense_pack launch");
     else

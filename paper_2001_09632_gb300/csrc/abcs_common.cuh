@@ -68,6 +68,7 @@ cudaError_t upload_tables_pilot();
 cudaError_t upload_tables_dct();
 cudaError_t upload_tables_ida();
 cudaError_t upload_tables_tc();
+cudaError_t setup_tc_fragments();   // after upload_tables_tc(), per device
 
 // zigzag rank of (u, v) in a B x B block, JPEG orientation: diagonal s = u+v;
 // odd s runs with u increasing, even s with u decreasing.
@@ -165,12 +166,16 @@ struct SenseArgs {
     int64_t* img_total;  // per image sum of counts
     int64_t* img_base;   // exclusive prefix of img_total, n_img + 1 entries
     unsigned* done;      // allocation CTAs finished (reset by the last one)
+    unsigned* img_done;  // per image: pilot CTAs finished (fused allocation; reset after use), or NULL
     uint32_t* status;
 };
 int pilot_ctas_per_image(const SenseArgs& a);
 cudaError_t launch_bbv_pilot(const SenseArgs& a, cudaStream_t s);
 cudaError_t launch_dd_pilot(const SenseArgs& a, cudaStream_t s);
 cudaError_t launch_allocate(const SenseArgs& a, int mode, cudaStream_t s);
+// pilot + allocation in one launch (needs a.img_done, zero on entry)
+cudaError_t launch_bbv_alloc(const SenseArgs& a, cudaStream_t s);
+cudaError_t launch_dd_alloc(const SenseArgs& a, cudaStream_t s);
 cudaError_t launch_sense_pack(const SenseArgs& a, cudaStream_t s);
 
 struct ReconArgs {

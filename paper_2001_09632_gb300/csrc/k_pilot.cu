@@ -6,6 +6,7 @@ namespace abcs {
 ABCS_TU_TABLES(pilot)
 }  // namespace abcs
 
+#include "alloc_dev.cuh"
 #include "dct_tile.cuh"
 
 namespace abcs {
@@ -18,35 +19,163 @@ namespace abcs {
 // row and the right block column use their own row B / column B instead.
 // One thread per block; the per-image sum is an exact 64-bit integer.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) bbv_kernel(const uint8_t* __restrict__ img, ImgGeom g,
-                                                  int L, int X0, int nS, int32_t* __restrict__ w,
-                                                  unsigned long long* __restrict__ wpart) {
+// The loop over the n_S sample positions is unrolled four-fold so that its
+// byte loads are in flight together.  With `fuse`, the last CTA of an image
+// allocates it (Eqs. 22-23) and the last image allocated writes the bases.
+__global__ void __launch_bounds__(256) bbv_kernel(SenseArgs a, int fuse) {
     __shared__ unsigned long long sh[32];
+    __shared__ int64_t sh2[33];
+    __shared__ int64_t sW;
+    __shared__ bool s_last;
     griddep_wait();
+    const ImgGeom& g = a.g;
     const int k = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long v = 0;
     if (i < g.n_blocks) {
-        const int B = g.B;
-        const int bi = (int)(i / g.nbw), bj = (int)(i % g.nbw);
-        const uint8_t* P = img + (int64_t)k * g.img_stride;
+        const int B = g.B, L = a.L, X0 = a.X0, nS = a.nS;
+        const int bi = (int)(i / g.nbw), bj = (int)(i - (int64_t)bi * g.nbw);
+        const uint8_t* P = a.img + (int64_t)k * g.img_stride;
         const int64_t p = g.pitch;
         const int r0 = bi * B, c0 = bj * B;
         const int below = (bi + 1 < g.nbh) ? r0 + B : r0 + B - 1;
         const int right = (bj + 1 < g.nbw) ? c0 + B : c0 + B - 1;
+        const uint8_t* top = P + r0 * p + c0;
+        const uint8_t* bot = P + below * p + c0;
+        const uint8_t* lft = P + r0 * p + c0;
+        const uint8_t* rgt = P + r0 * p + right;
         int s = 0;
+#pragma unroll 4
         for (int j = 0; j < nS; ++j) {
-            const int a = X0 + j * L;   // 1-based; pair (a, a+1) -> 0-based (a-1, a)
-            s += abs((int)__ldg(P + r0 * p + c0 + a) - (int)__ldg(P + r0 * p + c0 + a - 1));
-            s += abs((int)__ldg(P + (r0 + a) * p + c0) - (int)__ldg(P + (r0 + a - 1) * p + c0));
-            s += abs((int)__ldg(P + below * p + c0 + a) - (int)__ldg(P + below * p + c0 + a - 1));
-            s += abs((int)__ldg(P + (r0 + a) * p + right) - (int)__ldg(P + (r0 + a - 1) * p + right));
+            const int a1 = X0 + j * L;   // 1-based; pair (a, a+1) -> 0-based (a-1, a)
+            s += abs((int)__ldg(top + a1) - (int)__ldg(top + a1 - 1));
+            s += abs((int)__ldg(lft + a1 * p) - (int)__ldg(lft + (a1 - 1) * p));
+            s += abs((int)__ldg(bot + a1) - (int)__ldg(bot + a1 - 1));
+            s += abs((int)__ldg(rgt + a1 * p) - (int)__ldg(rgt + (a1 - 1) * p));
         }
-        w[(int64_t)k * g.n_blocks + i] = s;
+        a.w[(int64_t)k * g.n_blocks + i] = s;
         v = (unsigned long long)s;
     }
     v = block_sum(v, sh);
-    if (threadIdx.x == 0) wpart[(int64_t)k * gridDim.x + blockIdx.x] = v;
+    if (threadIdx.x == 0) a.wpart[(int64_t)k * gridDim.x + blockIdx.x] = v;
+    if (fuse) pilot_alloc_tail(a, 1, k, gridDim.x, sh2, &sW, &s_last);
+}
+
+// ---------------------------------------------------------------------------
+// BBV pilot and allocation of one image in one CTA (1024 threads): thread t
+// takes the CH or fewer consecutive blocks [t ch, t ch + ch), keeps their
+// BBV_i in registers, and the CTA runs Eq. 22 (cap and redistribution of
+// Sec. V-A included) and the exclusive prefix without leaving the chip.
+// The last image's CTA writes the image bases.
+// ---------------------------------------------------------------------------
+ABCS_D int bbv_block(const SenseArgs& a, int k, int64_t i) {
+    const ImgGeom& g = a.g;
+    const int B = g.B, L = a.L, X0 = a.X0, nS = a.nS;
+    const int ii = (int)i;                     // < n_B < 2^31
+    const int bi = ii / g.nbw, bj = ii - bi * g.nbw;
+    const int64_t p = g.pitch;
+    const uint8_t* P = a.img + (int64_t)k * g.img_stride;
+    const int r0 = bi * B, c0 = bj * B;
+    const int below = (bi + 1 < g.nbh) ? r0 + B : r0 + B - 1;
+    const int right = (bj + 1 < g.nbw) ? c0 + B : c0 + B - 1;
+    const uint8_t* top = P + r0 * p + c0;
+    const uint8_t* bot = P + below * p + c0;
+    const uint8_t* rgt = P + r0 * p + right;
+    // samples in predicated chunks of 8 so that all their loads are in flight together
+    int s = 0;
+    for (int j0 = 0; j0 < nS; j0 += 8) {
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+            if (j0 + jj < nS) {
+                const int a1 = X0 + (j0 + jj) * L;
+                s += abs((int)__ldg(top + a1) - (int)__ldg(top + a1 - 1));
+                s += abs((int)__ldg(top + a1 * p) - (int)__ldg(top + (a1 - 1) * p));
+                s += abs((int)__ldg(bot + a1) - (int)__ldg(bot + a1 - 1));
+                s += abs((int)__ldg(rgt + a1 * p) - (int)__ldg(rgt + (a1 - 1) * p));
+            }
+        }
+    }
+    return s;
+}
+
+template <int CH>
+__global__ void __launch_bounds__(1024) bbv_image_kernel(SenseArgs a) {
+    __shared__ int64_t sh[33];
+    __shared__ bool s_last;
+    griddep_wait();
+    const int k = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
+    const int64_t nB = a.g.n_blocks;
+    const int64_t ch = (nB + nt - 1) / nt;                 // <= CH (host)
+    const int64_t i0 = min(nB, (int64_t)t * ch), i1 = min(nB, i0 + ch);
+    int w[CH], m[CH];
+    int64_t wsum = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const int64_t i = i0 + c;
+        w[c] = (i < i1) ? bbv_block(a, k, i) : 0;
+        wsum += w[c];
+    }
+    const int64_t W = block_sum(wsum, sh);
+    const int cap = a.cap;
+    if (W == 0) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) m[c] = a.m_zz;               // L-DCT-ZZ fallback
+    } else {
+        // Eq. 22: m_i = floor(R BBV_i / sum BBV), capped at B^2 - 2 n_S
+        int64_t E = 0;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            int64_t v = a.R * (int64_t)w[c] / W;
+            if (v > cap) { E += v - cap; v = cap; }
+            m[c] = (int)v;
+        }
+        E = block_sum(E, sh);
+        // Sec. V-A: the excess goes to the blocks that are not fully measured,
+        // in proportion to BBV_i, until nothing is left or nothing moves
+        for (int64_t round = 0; E > 0 && round <= nB + 1; ++round) {
+            int64_t wu = 0;
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                if (m[c] < cap && w[c] > 0) wu += w[c];
+            const int64_t WU = block_sum(wu, sh);
+            if (WU == 0) break;
+            int64_t added = 0, e2 = 0;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                if (m[c] < cap && w[c] > 0) {
+                    const int64_t add = E * (int64_t)w[c] / WU;
+                    int64_t v = m[c] + add;
+                    added += add;
+                    if (v > cap) { e2 += v - cap; v = cap; }
+                    m[c] = (int)v;
+                }
+            }
+            added = block_sum(added, sh);
+            e2 = block_sum(e2, sh);
+            if (added == 0) break;
+            E = e2;
+        }
+    }
+    int64_t local = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+        if (i0 + c < i1) local += m[c];
+    int64_t total;
+    int64_t run = block_exclusive_scan(local, sh, &total);
+    int32_t* wk = a.w + (int64_t)k * nB;
+    int32_t* ck = a.counts + (int64_t)k * nB;
+    int64_t* ok = a.offsets + (int64_t)k * nB;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        if (i0 + c < i1) {
+            wk[i0 + c] = w[c];
+            ck[i0 + c] = m[c];
+            ok[i0 + c] = run;
+            run += m[c];
+        }
+    }
+    if (t == 0) a.img_total[k] = total;
+    alloc_finish(a.g.n_img, a.img_total, a.img_base, a.done, sh, &s_last);
 }
 
 // Pilot CTAs per image: the number of partial sums the allocation adds up.
@@ -60,7 +189,21 @@ int pilot_ctas_per_image(const SenseArgs& a) {
 
 cudaError_t launch_bbv_pilot(const SenseArgs& a, cudaStream_t s) {
     dim3 grid((unsigned)((a.g.n_blocks + 255) / 256), (unsigned)a.g.n_img);
-    return launch_pdl(bbv_kernel, grid, dim3(256), 0, s, a.img, a.g, a.L, a.X0, a.nS, a.w, a.wpart);
+    return launch_pdl(bbv_kernel, grid, dim3(256), 0, s, a, 0);
+}
+
+// One CTA per image when its blocks fit 16 per thread (n_B <= 16384), else
+// the block-parallel pilot whose last CTA per image allocates it.
+cudaError_t launch_bbv_alloc(const SenseArgs& a, cudaStream_t s) {
+    const int64_t ch = (a.g.n_blocks + 1023) / 1024;
+    const dim3 grid1((unsigned)a.g.n_img);
+    if (ch <= 1) return launch_pdl(bbv_image_kernel<1>, grid1, dim3(1024), 0, s, a);
+    if (ch <= 2) return launch_pdl(bbv_image_kernel<2>, grid1, dim3(1024), 0, s, a);
+    if (ch <= 4) return launch_pdl(bbv_image_kernel<4>, grid1, dim3(1024), 0, s, a);
+    if (ch <= 8) return launch_pdl(bbv_image_kernel<8>, grid1, dim3(1024), 0, s, a);
+    if (ch <= 16) return launch_pdl(bbv_image_kernel<16>, grid1, dim3(1024), 0, s, a);
+    dim3 grid((unsigned)((a.g.n_blocks + 255) / 256), (unsigned)a.g.n_img);
+    return launch_pdl(bbv_kernel, grid, dim3(256), 0, s, a, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -104,11 +247,14 @@ ABCS_D bool dd_exceeds_exact(const uint8_t* blk, int64_t pitch, int u, int v, in
 }
 
 template <int B>
-__global__ void __launch_bounds__(256, 4) dd_pilot_kernel(SenseArgs a) {
+__global__ void __launch_bounds__(256, 4) dd_pilot_kernel(SenseArgs a, int fuse) {
     using Tl = Tile<B>;
     __shared__ float Ts[Tl::FLOATS];
     __shared__ uint16_t zz[B * B];
     __shared__ unsigned long long sh[32];
+    __shared__ int64_t sh2[33];
+    __shared__ int64_t sW;
+    __shared__ bool s_last;
 
     const ImgGeom& g = a.g;
     const int k = blockIdx.z, bi = blockIdx.y, bj0 = blockIdx.x * Tl::NB;
@@ -167,23 +313,27 @@ __global__ void __launch_bounds__(256, 4) dd_pilot_kernel(SenseArgs a) {
     }
     mine = block_sum(mine, sh);
     if (t == 0) a.wpart[(int64_t)k * gridDim.x * gridDim.y + (int64_t)blockIdx.y * gridDim.x + blockIdx.x] = mine;
+    if (fuse) pilot_alloc_tail(a, 2, k, gridDim.x * gridDim.y, sh2, &sW, &s_last);
 }
 
 template <int B>
-static cudaError_t launch_dd_B(const SenseArgs& a, cudaStream_t s) {
+static cudaError_t launch_dd_B(const SenseArgs& a, int fuse, cudaStream_t s) {
     using Tl = Tile<B>;
     dim3 grid((unsigned)((a.g.nbw + Tl::NB - 1) / Tl::NB), (unsigned)a.g.nbh, (unsigned)a.g.n_img);
-    return launch_pdl(dd_pilot_kernel<B>, grid, dim3(256), 0, s, a);
+    return launch_pdl(dd_pilot_kernel<B>, grid, dim3(256), 0, s, a, fuse);
 }
 
-cudaError_t launch_dd_pilot(const SenseArgs& a, cudaStream_t s) {
+static cudaError_t launch_dd(const SenseArgs& a, int fuse, cudaStream_t s) {
     switch (a.g.B) {
-        case 4: return launch_dd_B<4>(a, s);
-        case 8: return launch_dd_B<8>(a, s);
-        case 16: return launch_dd_B<16>(a, s);
-        case 32: return launch_dd_B<32>(a, s);
+        case 4: return launch_dd_B<4>(a, fuse, s);
+        case 8: return launch_dd_B<8>(a, fuse, s);
+        case 16: return launch_dd_B<16>(a, fuse, s);
+        case 32: return launch_dd_B<32>(a, fuse, s);
     }
     return cudaErrorInvalidValue;
 }
+
+cudaError_t launch_dd_pilot(const SenseArgs& a, cudaStream_t s) { return launch_dd(a, 0, s); }
+cudaError_t launch_dd_alloc(const SenseArgs& a, cudaStream_t s) { return launch_dd(a, 1, s); }
 
 }  // namespace abcs

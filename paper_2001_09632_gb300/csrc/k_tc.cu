@@ -72,28 +72,44 @@ ABCS_D void split2d(double a, double b, uint32_t& hi, uint32_t& lo) {
     lo = pk<P>((float)(a - ha), (float)(b - hb));
 }
 
+// d += a * b on the tensor cores (m16n8k16, FP32 accumulate)
 template <int P>
 ABCS_D void mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     if constexpr (P == kP16) {
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
             "{%0,%1,%2,%3};\n"
             : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
             : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
     } else {
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
             "{%0,%1,%2,%3};\n"
             : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
             : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
     }
 }
 
-// d += A * B with both operands split (3 products) or single (1 product)
+// d = a * b (zero accumulator)
+template <int P>
+ABCS_D void mma0(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    const float z = 0.f;
+    if constexpr (P == kP16) {
+        asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%10,%10,%10,%10};\n"
+            : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(z));
+    } else {
+        asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%10,%10,%10,%10};\n"
+            : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(z));
+    }
+}
+
+// d = A * B with both operands split (3 products) or single (1 product)
 template <int P>
 ABCS_D void mma_split(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4], uint32_t bh0,
                       uint32_t bh1, uint32_t bl0, uint32_t bl1) {
-    mma<P>(d, ah, bh0, bh1);
+    mma0<P>(d, ah, bh0, bh1);
     if constexpr (P != kPB1) {
         mma<P>(d, al, bh0, bh1);
         mma<P>(d, ah, bl0, bl1);
@@ -134,19 +150,201 @@ ABCS_D void load_b_const(bool transpose, uint32_t (&h)[2][2], uint32_t (&l)[2][2
     }
 }
 
+// Operand fragments of the constant factors D and D^T (hi and lo words), per
+// precision, fragment set and lane.  They are split from the FP64 table once
+// per device by tc_frag_setup_kernel: doing it in every CTA's prologue kept
+// the narrow FP64 pipe of this GPU busy for a large part of each launch.
+enum { kSetSenseA = 0, kSetSenseB = 1, kSetReconA = 2, kSetReconB = 3 };
+__device__ uint32_t g_tc_frag[3][4][8][32];
+
+template <int P>
+__host__ __device__ constexpr int pidx() { return P == kP16 ? 0 : (P == kPB16 ? 1 : 2); }
+
+// A fragment of the sensing row transform: A[m][k] = D[m][pi(k)] with
+// pi(2q + e) = 4q + e, pi(2q + 8 + e) = 4q + 2 + e (e = 0, 1).
+template <int P>
+ABCS_D void load_a_perm(uint32_t (&h)[4], uint32_t (&l)[4]) {
+    const Frag f;
+    split2d<P>(Dd<16>(f.g, 4 * f.q), Dd<16>(f.g, 4 * f.q + 1), h[0], l[0]);
+    split2d<P>(Dd<16>(f.g + 8, 4 * f.q), Dd<16>(f.g + 8, 4 * f.q + 1), h[1], l[1]);
+    split2d<P>(Dd<16>(f.g, 4 * f.q + 2), Dd<16>(f.g, 4 * f.q + 3), h[2], l[2]);
+    split2d<P>(Dd<16>(f.g + 8, 4 * f.q + 2), Dd<16>(f.g + 8, 4 * f.q + 3), h[3], l[3]);
+}
+
+template <int P>
+ABCS_D void frag_setup_p() {
+    const int lane = threadIdx.x & 31;
+    uint32_t (*t)[8][32] = g_tc_frag[pidx<P>()];
+    uint32_t h[4], l[4], bh[2][2], bl[2][2];
+    auto put_a = [&](int set) {
+        for (int i = 0; i < 4; ++i) {
+            t[set][i][lane] = h[i];
+            t[set][4 + i][lane] = l[i];
+        }
+    };
+    auto put_b = [&](int set) {
+        for (int i = 0; i < 4; ++i) {
+            t[set][i][lane] = bh[i >> 1][i & 1];
+            t[set][4 + i][lane] = bl[i >> 1][i & 1];
+        }
+    };
+    load_a_perm<P>(h, l);
+    put_a(kSetSenseA);
+    load_b_const<P>(true, bh, bl);
+    put_b(kSetSenseB);
+    load_a_const<P>(true, h, l);
+    put_a(kSetReconA);
+    load_b_const<P>(false, bh, bl);
+    put_b(kSetReconB);
+}
+
+__global__ void tc_frag_setup_kernel() {
+    frag_setup_p<kP16>();
+    frag_setup_p<kPB16>();
+    frag_setup_p<kPB1>();
+}
+
+template <int P>
+ABCS_D void frag_a(int set, uint32_t (&h)[4], uint32_t (&l)[4]) {
+    const uint32_t* t = &g_tc_frag[pidx<P>()][set][0][threadIdx.x & 31];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        h[i] = t[32 * i];
+        l[i] = t[32 * (4 + i)];
+    }
+}
+
+template <int P>
+ABCS_D void frag_b(int set, uint32_t (&h)[2][2], uint32_t (&l)[2][2]) {
+    const uint32_t* t = &g_tc_frag[pidx<P>()][set][0][threadIdx.x & 31];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        h[i >> 1][i & 1] = t[32 * i];
+        l[i >> 1][i & 1] = t[32 * (4 + i)];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Segments.  A CTA works on SEG = 32 consecutive blocks of one block row (a
+// 16 x 512 pixel strip).  Their packed coefficients form one contiguous
+// range, moved between global and shared memory with coalesced 16-byte
+// copies.  CTAs are persistent and walk the segments grid-stride; the next
+// segment's input is copied (cp.async) while the current one is
+// transformed, and each warp transforms four blocks of the segment.
+// ---------------------------------------------------------------------------
+constexpr int SEG = 32;
+constexpr int kSegFloats = SEG * 256 + 4;      // packed range of a segment + alignment shift
+
+struct SegGeom {
+    int64_t b0;        // first block of the segment (index over the batch)
+    int k, bi, bj0, nblk;
+};
+
+ABCS_D SegGeom seg_geom(const ImgGeom& g, int s) {
+    const int spr = (g.nbw + SEG - 1) / SEG;
+    const int per_img = g.nbh * spr;
+    SegGeom r;
+    r.k = s / per_img;
+    const int rem = s - r.k * per_img;
+    r.bi = rem / spr;
+    r.bj0 = (rem - r.bi * spr) * SEG;
+    r.nblk = min(SEG, g.nbw - r.bj0);
+    r.b0 = (int64_t)r.k * g.n_blocks + (int64_t)r.bi * g.nbw + r.bj0;
+    return r;
+}
+
+ABCS_HD int seg_count(const ImgGeom& g) { return g.n_img * g.nbh * ((g.nbw + SEG - 1) / SEG); }
+
+struct SegMeta {
+    int64_t start;     // index of the segment's first coefficient in the packed vector
+    int n;             // coefficients of the segment
+    int sh;            // start & 3: stage position of coefficient `start`
+    int rel[SEG];      // block offsets relative to start
+    int cnt[SEG];      // block counts
+    SegGeom sg;
+};
+
+ABCS_D int warp_max(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Metadata of a segment as loaded by warp 0 (lane = block of the segment).
+// Loads are issued two segments ahead and written to shared memory one
+// segment ahead, so their latency is hidden behind a segment's transforms.
+struct MetaRaw {
+    int64_t off;       // the block's offset (recon: global; sense: image-local)
+    int64_t base;      // sense: image base of the segment's image
+    int m;             // the block's count
+};
+
+ABCS_D MetaRaw recon_meta_load(const ReconArgs& a, int s) {
+    const int lane = threadIdx.x & 31;
+    const SegGeom sg = seg_geom(a.g, s);
+    MetaRaw r;
+    r.off = 0;
+    r.base = 0;
+    r.m = 0;
+    if (lane < sg.nblk) {
+        r.off = __ldg(a.offsets + sg.b0 + lane);
+        r.m = __ldg(a.counts + sg.b0 + lane);
+    }
+    return r;
+}
+
+// Inconsistent counts or offsets are flagged and the block is treated as
+// unmeasured, so every stage access stays inside the segment's buffer.
+ABCS_D void recon_meta_store(const ReconArgs& a, int s, const MetaRaw& r, SegMeta& M) {
+    const int lane = threadIdx.x & 31;
+    const SegGeom sg = seg_geom(a.g, s);
+    int64_t off = r.off;
+    int m = r.m;
+    int64_t start = __shfl_sync(0xffffffffu, off, 0);
+    bool bad = false;
+    if (start < 0) {
+        bad = true;
+        start = 0;
+        off = 0;
+        m = 0;
+    }
+    int64_t rel = off - start;
+    if (lane < sg.nblk) {
+        if (m < 0 || m > 256) { bad = true; m = m < 0 ? 0 : 256; }
+        if (rel < 0 || rel + m > SEG * 256) { bad = true; rel = 0; m = 0; }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(a.status, ABCS_DEV_BADCOUNT);
+    const int end = warp_max(lane < sg.nblk ? (int)(rel + m) : 0);
+    if (lane < SEG) {
+        M.rel[lane] = (int)rel;
+        M.cnt[lane] = m;
+    }
+    if (lane == 0) {
+        M.start = start;
+        M.n = end;
+        M.sh = (int)(start & 3);
+        M.sg = sg;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // reconstruct: X = D^T C D.  Stage 1 Y = D^T C (A = D^T constant, B = C
-// gathered from the block's zigzag-packed coefficients); stage 2 X = Y D
-// (A = Y straight from stage 1's accumulators, B = D constant).
+// gathered by zigzag rank from the staged segment); stage 2 X = Y D (A = Y
+// straight from stage 1's accumulators, B = D constant).
 // ---------------------------------------------------------------------------
+constexpr size_t kReconSmem = 2 * kSegFloats * sizeof(float) + 3 * sizeof(SegMeta);
+constexpr size_t kSenseSmem = 2 * 16 * SEG * 16 + kSegFloats * sizeof(float) + 3 * sizeof(SegMeta);
+
 template <int P>
-__global__ void __launch_bounds__(256) recon_tc_kernel(ReconArgs a, int64_t total) {
-    __shared__ __align__(16) float stage[8][2][256];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256, 3) recon_tc_kernel(ReconArgs a, int nseg) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float (*stage)[kSegFloats] = reinterpret_cast<float (*)[kSegFloats]>(smem);
+    SegMeta* meta = reinterpret_cast<SegMeta*>(smem + 2 * kSegFloats * sizeof(float));
+    const int warp = threadIdx.x >> 5;
     const Frag f;
     uint32_t ATh[4], ATl[4], DBh[2][2], DBl[2][2];
-    load_a_const<P>(true, ATh, ATl);
-    load_b_const<P>(false, DBh, DBl);
+    frag_a<P>(kSetReconA, ATh, ATl);
+    frag_b<P>(kSetReconB, DBh, DBl);
     // ranks of the 8 coefficients this lane feeds into B = C: (2q + e, g + 8 nt), e in {0,1,8,9}
     int rk[2][4];
 #pragma unroll
@@ -156,213 +354,306 @@ __global__ void __launch_bounds__(256) recon_tc_kernel(ReconArgs a, int64_t tota
 
     griddep_wait();
     const ImgGeom& g = a.g;
-    const int W = gridDim.x * 8;
-    const int ntot = (int)total;
-    int blk = blockIdx.x * 8 + warp;
-    if (blk >= ntot) return;
-    const unsigned nB = (unsigned)g.n_blocks, nbw = (unsigned)g.nbw;
-    auto meta = [&](int b, int64_t& off, int& m) {
-        off = __ldg(a.offsets + b);
-        m = __ldg(a.counts + b);
-        m = m < 0 ? 0 : (m > 256 ? 256 : m);
-    };
-    auto issue = [&](int64_t off, int m, float* dst) {
-        const float* src = a.coeffs + off;
-        for (int k = lane; k < m; k += 32) cp_async4(dst + k, src + k);
-    };
-    int64_t off0, off1 = 0;
-    int m0, m1 = 0;
-    meta(blk, off0, m0);
-    if (blk + W < ntot) meta(blk + W, off1, m1);
-    issue(off0, m0, stage[warp][0]);
+    const int G = gridDim.x;
+    int s = blockIdx.x;
+    if (s >= nseg) return;
+    const int lo = f.g * g.Wc + 2 * f.q;       // lane's first output pixel within a block
+    const int64_t img_px = (int64_t)g.Hc * g.Wc;
+    MetaRaw raw;
+    if (warp == 0) {
+        recon_meta_store(a, s, recon_meta_load(a, s), meta[0]);
+        if (s + G < nseg) raw = recon_meta_load(a, s + G);
+    }
+    __syncthreads();
+    stage_in_async(stage[0], a.coeffs, meta[0].start, meta[0].n);
     cp_async_commit();
-    for (int j = 0; blk < ntot; ++j, blk += W) {
-        int64_t off2 = 0;
-        int m2 = 0;
-        if (blk + 2 * W < ntot) meta(blk + 2 * W, off2, m2);
-        if (blk + W < ntot) issue(off1, m1, stage[warp][(j + 1) & 1]);
+    int mi = 0;                                 // meta slot of segment j (j mod 3)
+    for (int j = 0; s < nseg; ++j, s += G) {
+        const int mn = mi == 2 ? 0 : mi + 1;
+        const int s1 = s + G;
+        if (s1 < nseg && warp == 0) {
+            recon_meta_store(a, s1, raw, meta[mn]);
+            if (s1 + G < nseg) raw = recon_meta_load(a, s1 + G);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (s1 < nseg) stage_in_async(stage[(j + 1) & 1], a.coeffs, meta[mn].start, meta[mn].n);
         cp_async_commit();
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        __syncwarp();
 
-        const float* st = stage[warp][j & 1];
-        uint32_t bh[2][2], bl[2][2];
+        const SegMeta& M = meta[mi];
+        const SegGeom sg = M.sg;
+        const float* st = stage[j & 1] + M.sh;
+        const int64_t seg_px = (int64_t)sg.k * img_px + (int64_t)(sg.bi * 16) * g.Wc + sg.bj0 * 16 + lo;
+#pragma unroll 2
+        for (int c = warp; c < sg.nblk; c += 8) {
+            const int m = M.cnt[c];
+            const float* sb = st + M.rel[c];
+            uint32_t bh[2][2], bl[2][2];
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            float cv[4];
+            for (int nt = 0; nt < 2; ++nt) {
+                float cv[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) cv[i] = (rk[nt][i] < m0) ? st[rk[nt][i]] : 0.f;
-            split2<P>(cv[0], cv[1], bh[nt][0], bl[nt][0]);
-            split2<P>(cv[2], cv[3], bh[nt][1], bl[nt][1]);
-        }
-        float Y[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+                for (int i = 0; i < 4; ++i) cv[i] = (rk[nt][i] < m) ? sb[rk[nt][i]] : 0.f;
+                split2<P>(cv[0], cv[1], bh[nt][0], bl[nt][0]);
+                split2<P>(cv[2], cv[3], bh[nt][1], bl[nt][1]);
+            }
+            float Y[2][4];
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt) mma_split<P>(Y[nt], ATh, ATl, bh[nt][0], bh[nt][1], bl[nt][0], bl[nt][1]);
-        uint32_t Ah[4], Al[4];
-        split2<P>(Y[0][0], Y[0][1], Ah[0], Al[0]);
-        split2<P>(Y[0][2], Y[0][3], Ah[1], Al[1]);
-        split2<P>(Y[1][0], Y[1][1], Ah[2], Al[2]);
-        split2<P>(Y[1][2], Y[1][3], Ah[3], Al[3]);
-        float X[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+            for (int nt = 0; nt < 2; ++nt)
+                mma_split<P>(Y[nt], ATh, ATl, bh[nt][0], bh[nt][1], bl[nt][0], bl[nt][1]);
+            uint32_t Ah[4], Al[4];
+            split2<P>(Y[0][0], Y[0][1], Ah[0], Al[0]);
+            split2<P>(Y[0][2], Y[0][3], Ah[1], Al[1]);
+            split2<P>(Y[1][0], Y[1][1], Ah[2], Al[2]);
+            split2<P>(Y[1][2], Y[1][3], Ah[3], Al[3]);
+            float X[2][4];
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt) mma_split<P>(X[nt], Ah, Al, DBh[nt][0], DBh[nt][1], DBl[nt][0], DBl[nt][1]);
+            for (int nt = 0; nt < 2; ++nt)
+                mma_split<P>(X[nt], Ah, Al, DBh[nt][0], DBh[nt][1], DBl[nt][0], DBl[nt][1]);
 
-        const unsigned k = (unsigned)blk / nB;
-        const unsigned i = (unsigned)blk - k * nB;
-        const unsigned bi = i / nbw, bj = i - bi * nbw;
-        const int64_t o = (int64_t)k * g.Hc * g.Wc + ((int64_t)(bi * 16 + f.g) * g.Wc + bj * 16 + 2 * f.q);
-        const int64_t o8 = o + 8 * (int64_t)g.Wc;
-        if (a.out) {
-            *reinterpret_cast<float2*>(a.out + o) = make_float2(X[0][0], X[0][1]);
-            *reinterpret_cast<float2*>(a.out + o + 8) = make_float2(X[1][0], X[1][1]);
-            *reinterpret_cast<float2*>(a.out + o8) = make_float2(X[0][2], X[0][3]);
-            *reinterpret_cast<float2*>(a.out + o8 + 8) = make_float2(X[1][2], X[1][3]);
+            const int64_t o = seg_px + c * 16;
+            const int64_t o8 = o + 8 * (int64_t)g.Wc;
+            if (a.out) {
+                *reinterpret_cast<float2*>(a.out + o) = make_float2(X[0][0], X[0][1]);
+                *reinterpret_cast<float2*>(a.out + o + 8) = make_float2(X[1][0], X[1][1]);
+                *reinterpret_cast<float2*>(a.out + o8) = make_float2(X[0][2], X[0][3]);
+                *reinterpret_cast<float2*>(a.out + o8 + 8) = make_float2(X[1][2], X[1][3]);
+            }
+            if (a.out_u8) {
+                auto u8 = [](float v) { return (uint32_t)fminf(fmaxf(rintf(v), 0.f), 255.f); };
+                *reinterpret_cast<uint16_t*>(a.out_u8 + o) = (uint16_t)(u8(X[0][0]) | (u8(X[0][1]) << 8));
+                *reinterpret_cast<uint16_t*>(a.out_u8 + o + 8) = (uint16_t)(u8(X[1][0]) | (u8(X[1][1]) << 8));
+                *reinterpret_cast<uint16_t*>(a.out_u8 + o8) = (uint16_t)(u8(X[0][2]) | (u8(X[0][3]) << 8));
+                *reinterpret_cast<uint16_t*>(a.out_u8 + o8 + 8) = (uint16_t)(u8(X[1][2]) | (u8(X[1][3]) << 8));
+            }
         }
-        if (a.out_u8) {
-            auto u8 = [](float v) { return (uint32_t)fminf(fmaxf(rintf(v), 0.f), 255.f); };
-            *reinterpret_cast<uint16_t*>(a.out_u8 + o) = (uint16_t)(u8(X[0][0]) | (u8(X[0][1]) << 8));
-            *reinterpret_cast<uint16_t*>(a.out_u8 + o + 8) = (uint16_t)(u8(X[1][0]) | (u8(X[1][1]) << 8));
-            *reinterpret_cast<uint16_t*>(a.out_u8 + o8) = (uint16_t)(u8(X[0][2]) | (u8(X[0][3]) << 8));
-            *reinterpret_cast<uint16_t*>(a.out_u8 + o8 + 8) = (uint16_t)(u8(X[1][2]) | (u8(X[1][3]) << 8));
-        }
-        __syncwarp();
-        off0 = off1; m0 = m1; off1 = off2; m1 = m2;
+        mi = mn;
     }
     cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------------------
-// sense: C = D X D^T.  Stage 1 T = D X (A = D constant, B = pixels from the
-// warp's staged block); stage 2 C = T D^T (A = T from the accumulators,
-// B = D^T constant).  The block's first m_i zigzag coefficients are
-// scattered into a per-warp staging row and copied out contiguously.
+// sense: C = D X D^T, computed transposed.  Stage 1 V = D X^T (A = D with
+// its columns permuted, B = X^T read from the staged pixels) is the row
+// transform of every pixel row; stage 2 R = V D^T (A = V from the
+// accumulators, B = D^T constant) gives R[v][u] = C[u][v].
+// K-permutation of stage 1: MMA k = 2q + e, 2q + 8 + e (e = 0, 1) stands for
+// pixel column 4q + e, 4q + 2 + e, so each lane's B fragment of one pixel
+// row is 4 consecutive bytes (one 32-bit shared load).  Pixels sit in shared
+// memory as a 16 x 512 strip whose 16-byte chunks are XOR-swizzled by
+// (row & 7), which makes those loads bank-conflict free.  The block's first
+// m_i zigzag coefficients are scattered into the segment's packed staging
+// buffer and the whole segment range is written out with 16-byte stores.
 // ---------------------------------------------------------------------------
+
+// two pixels (bytes `hi2` * 2 and * 2 + 1 of w) as an operand pair; exact
 template <int P>
-__global__ void __launch_bounds__(256) sense_tc_kernel(SenseArgs a, int64_t total) {
-    __shared__ __align__(16) uint8_t pix[8][2][256];
-    __shared__ __align__(16) float ost[8][256];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+ABCS_D uint32_t px_pair(uint32_t w, int hi2) {
+    if constexpr (P == kP16) {
+        // 0x64XX as FP16 is 1024 + XX exactly; subtract 1024
+        const uint32_t v = __byte_perm(w, 0x64646464u, hi2 ? 0x4342 : 0x4140);
+        __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&v), __halves2half2(__ushort_as_half(0x6400),
+                                                                                 __ushort_as_half(0x6400)));
+        return *reinterpret_cast<uint32_t*>(&h);
+    } else {
+        const int b0 = (w >> (16 * hi2)) & 0xFF, b1 = (w >> (16 * hi2 + 8)) & 0xFF;
+        return pk<P>((float)b0, (float)b1);
+    }
+}
+
+ABCS_D MetaRaw sense_meta_load(const SenseArgs& a, int s) {
+    const int lane = threadIdx.x & 31;
+    const SegGeom sg = seg_geom(a.g, s);
+    MetaRaw r;
+    r.off = 0;
+    r.m = 0;
+    r.base = __ldg(a.img_base + sg.k);
+    if (lane < sg.nblk) {
+        r.off = __ldg(a.offsets + sg.b0 + lane);
+        r.m = __ldg(a.counts + sg.b0 + lane);
+    }
+    return r;
+}
+
+// counts and image-local offsets from the allocation, image bases from its last CTA
+ABCS_D void sense_meta_store(const SenseArgs& a, int s, const MetaRaw& r, SegMeta& M) {
+    const int lane = threadIdx.x & 31;
+    const SegGeom sg = seg_geom(a.g, s);
+    const int64_t loc0 = __shfl_sync(0xffffffffu, r.off, 0);
+    const int rel = (int)(r.off - loc0);
+    const int end = warp_max(lane < sg.nblk ? rel + r.m : 0);
+    if (lane < SEG) {
+        M.rel[lane] = rel;
+        M.cnt[lane] = r.m;
+    }
+    if (lane == 0) {
+        M.start = r.base + loc0;
+        M.n = end;
+        M.sh = (int)(M.start & 3);
+        M.sg = sg;
+    }
+}
+
+// all threads: copy the 16 x (16 nblk) pixel strip of segment sg; chunk
+// (row r, block c) of 16 bytes goes to r * 512 + 16 (c ^ (r & 7))
+ABCS_D void sense_pixels(const SenseArgs& a, const SegGeom& sg, uint8_t* dst, bool vec) {
+    const uint8_t* base = a.img + (int64_t)sg.k * a.g.img_stride + (int64_t)(sg.bi * 16) * a.g.pitch + sg.bj0 * 16;
+#pragma unroll
+    for (int h = 0; h < SEG * 16 / 256; ++h) {
+        const int id = threadIdx.x + 256 * h, r = id / SEG, c = id % SEG;
+        if (c >= sg.nblk) continue;
+        const uint8_t* src = base + (int64_t)r * a.g.pitch + c * 16;
+        uint8_t* d = dst + r * (SEG * 16) + ((c ^ (r & 7)) << 4);
+        if (vec) {
+            const unsigned sd = (unsigned)__cvta_generic_to_shared(d);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sd), "l"(src) : "memory");
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) d[i] = __ldg(src + i);
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int nseg) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint8_t (*pix)[16 * SEG * 16] = reinterpret_cast<uint8_t (*)[16 * SEG * 16]>(smem);
+    float* ost = reinterpret_cast<float*>(smem + 2 * 16 * SEG * 16);
+    SegMeta* meta = reinterpret_cast<SegMeta*>(smem + 2 * 16 * SEG * 16 + kSegFloats * sizeof(float));
+    const int warp = threadIdx.x >> 5;
     const Frag f;
     uint32_t DAh[4], DAl[4], DTh[2][2], DTl[2][2];
-    load_a_const<P>(false, DAh, DAl);
-    load_b_const<P>(true, DTh, DTl);
-    int rk[2][4];   // ranks of this lane's accumulator positions (g + 8 (i>>1), 2q + (i&1) + 8 nt)
+    frag_a<P>(kSetSenseA, DAh, DAl);
+    frag_b<P>(kSetSenseB, DTh, DTl);
+    int rk[2][4];   // ranks of R[g + 8 (i>>1)][2q + (i&1) + 8 nt] = C[u = 2q + (i&1) + 8 nt][v = g + 8 (i>>1)]
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) rk[nt][i] = zz_rank(f.g + 8 * (i >> 1), 2 * f.q + (i & 1) + 8 * nt, 16);
+        for (int i = 0; i < 4; ++i) rk[nt][i] = zz_rank(2 * f.q + (i & 1) + 8 * nt, f.g + 8 * (i >> 1), 16);
 
-    griddep_wait();
-    const int64_t* img_base = a.img_base;
     const ImgGeom& g = a.g;
-    const int W = gridDim.x * 8;
-    const int ntot = (int)total;
-    int blk = blockIdx.x * 8 + warp;
-    if (blk >= ntot) return;
-    const unsigned nB = (unsigned)g.n_blocks, nbw = (unsigned)g.nbw;
-    auto issue = [&](int b, uint8_t* dst) {
-        if (lane < 16) {
-            const unsigned k = (unsigned)b / nB;
-            const unsigned i = (unsigned)b - k * nB;
-            const unsigned bi = i / nbw, bj = i - bi * nbw;
-            const uint8_t* src = a.img + (int64_t)k * g.img_stride + (int64_t)(bi * 16 + lane) * g.pitch + bj * 16;
-            if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-                const unsigned d = (unsigned)__cvta_generic_to_shared(dst + lane * 16);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-            } else {
-                for (int c = 0; c < 16; ++c) dst[lane * 16 + c] = __ldg(src + c);
-            }
-        }
-    };
-    issue(blk, pix[warp][0]);
+    const bool vec = ((reinterpret_cast<uintptr_t>(a.img) | (uintptr_t)g.pitch |
+                       (uintptr_t)(g.n_img > 1 ? g.img_stride : 0)) & 15) == 0;
+    const int G = gridDim.x;
+    int s = blockIdx.x;
+    if (s >= nseg) return;
+    sense_pixels(a, seg_geom(g, s), pix[0], vec);     // pixels do not depend on the previous kernels
     cp_async_commit();
-    for (int j = 0; blk < ntot; ++j, blk += W) {
-        // output metadata of this block (latency hidden by the transform)
-        const unsigned k = (unsigned)blk / nB;
-        const int m = __ldg(a.counts + blk);
-        const int64_t gstart = __ldg(img_base + k) + __ldg(a.offsets + blk);
-        if (blk + W < ntot) issue(blk + W, pix[warp][(j + 1) & 1]);
+    griddep_wait();
+    MetaRaw raw;
+    if (warp == 0) {
+        sense_meta_store(a, s, sense_meta_load(a, s), meta[0]);
+        if (s + G < nseg) raw = sense_meta_load(a, s + G);
+    }
+    const int64_t ntot = (int64_t)g.n_img * g.n_blocks;
+    int mi = 0;
+    for (int j = 0; s < nseg; ++j, s += G) {
+        const int mn = mi == 2 ? 0 : mi + 1;
+        const int s1 = s + G;
+        if (s1 < nseg && warp == 0) {
+            sense_meta_store(a, s1, raw, meta[mn]);
+            if (s1 + G < nseg) raw = sense_meta_load(a, s1 + G);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (s1 < nseg) sense_pixels(a, meta[mn].sg, pix[(j + 1) & 1], vec);
         cp_async_commit();
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        __syncwarp();
 
-        const uint8_t* px = pix[warp][j & 1];
-        uint32_t xb[2][2];
+        const SegMeta& M = meta[mi];
+        const int nblk = M.sg.nblk;
+        const uint8_t* px = pix[j & 1];
+        float* os = ost + M.sh;
+#pragma unroll 2
+        for (int c = warp; c < nblk; c += 8) {
+            uint32_t xb[2][2];
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            const int col = f.g + 8 * nt;
-            xb[nt][0] = pk<P>((float)px[(2 * f.q) * 16 + col], (float)px[(2 * f.q + 1) * 16 + col]);
-            xb[nt][1] = pk<P>((float)px[(2 * f.q + 8) * 16 + col], (float)px[(2 * f.q + 9) * 16 + col]);
+            for (int nt = 0; nt < 2; ++nt) {
+                const int y = f.g + 8 * nt;    // y & 7 == g
+                const uint32_t w =
+                    *reinterpret_cast<const uint32_t*>(px + y * (SEG * 16) + ((c ^ f.g) << 4) + 4 * f.q);
+                xb[nt][0] = px_pair<P>(w, 0);
+                xb[nt][1] = px_pair<P>(w, 1);
+            }
+            float V[2][4];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                mma0<P>(V[nt], DAh, xb[nt][0], xb[nt][1]);
+                if constexpr (P != kPB1) mma<P>(V[nt], DAl, xb[nt][0], xb[nt][1]);
+            }
+            uint32_t Ah[4], Al[4];
+            split2<P>(V[0][0], V[0][1], Ah[0], Al[0]);
+            split2<P>(V[0][2], V[0][3], Ah[1], Al[1]);
+            split2<P>(V[1][0], V[1][1], Ah[2], Al[2]);
+            split2<P>(V[1][2], V[1][3], Ah[3], Al[3]);
+            float R[2][4];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+                mma_split<P>(R[nt], Ah, Al, DTh[nt][0], DTh[nt][1], DTl[nt][0], DTl[nt][1]);
+            const int m = M.cnt[c];
+            float* ob = os + M.rel[c];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (rk[nt][i] < m) ob[rk[nt][i]] = R[nt][i];
         }
-        float T[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            mma<P>(T[nt], DAh, xb[nt][0], xb[nt][1]);
-            if constexpr (P != kPB1) mma<P>(T[nt], DAl, xb[nt][0], xb[nt][1]);
+        __syncthreads();
+        // copy-out of the segment's packed range and its global offsets
+        const int64_t start = M.start;
+        int n = M.n;
+        if (start + n > a.capacity) {
+            if (threadIdx.x == 0) set_status(a.status, ABCS_DEV_CAPACITY);
+            n = start < a.capacity ? (int)(a.capacity - start) : 0;
         }
-        uint32_t Ah[4], Al[4];
-        split2<P>(T[0][0], T[0][1], Ah[0], Al[0]);
-        split2<P>(T[0][2], T[0][3], Ah[1], Al[1]);
-        split2<P>(T[1][0], T[1][1], Ah[2], Al[2]);
-        split2<P>(T[1][2], T[1][3], Ah[3], Al[3]);
-        float C[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) mma_split<P>(C[nt], Ah, Al, DTh[nt][0], DTh[nt][1], DTl[nt][0], DTl[nt][1]);
-
-        float* os = ost[warp];
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (rk[nt][i] < m) os[rk[nt][i]] = C[nt][i];
-        __syncwarp();
-        if (gstart + m <= a.capacity) {
-            float* dst = a.coeffs + gstart;
-            for (int c = lane; c < m; c += 32) dst[c] = os[c];
-        } else if (lane == 0) {
-            set_status(a.status, ABCS_DEV_CAPACITY);
+        stage_out(ost, a.coeffs, start, n);
+        if (threadIdx.x < nblk) {
+            const int64_t b = M.sg.b0 + threadIdx.x;
+            a.offsets[b] = start + M.rel[threadIdx.x];
+            if (b == ntot - 1) a.offsets[ntot] = start + M.n;
         }
-        if (lane == 0) {
-            a.offsets[blk] = gstart;
-            if (blk == ntot - 1) a.offsets[ntot] = gstart + m;
-        }
-        __syncwarp();
+        mi = mn;
     }
     cp_async_wait_all();
 }
 
 template <typename K>
-cudaError_t grid_for(K kernel, int64_t total_blocks, int* grid) {
+cudaError_t grid_segs(K kernel, int nseg, size_t smem, int* grid) {
     int dev, sms, per_sm;
-    cudaError_t e = cudaGetDevice(&dev);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!e) e = cudaGetDevice(&dev);
     if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem);
     if (e) return e;
-    const int64_t need = (total_blocks + 7) / 8;
-    const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-    *grid = (int)(need < cap ? need : cap);
+    const int cap = sms * (per_sm > 0 ? per_sm : 1);
+    *grid = nseg < cap ? nseg : cap;
     return cudaSuccess;
 }
 
 template <int P>
 cudaError_t launch_recon_tc_p(const ReconArgs& a, cudaStream_t s) {
-    const int64_t total = (int64_t)a.g.n_img * a.g.n_blocks;
+    const int nseg = seg_count(a.g);
     int grid = 0;
-    cudaError_t e = grid_for(recon_tc_kernel<P>, total, &grid);
+    cudaError_t e = grid_segs(recon_tc_kernel<P>, nseg, kReconSmem, &grid);
     if (e) return e;
-    return launch_pdl(recon_tc_kernel<P>, dim3(grid), dim3(256), 0, s, a, total);
+    return launch_pdl(recon_tc_kernel<P>, dim3(grid), dim3(256), kReconSmem, s, a, nseg);
 }
 
 template <int P>
 cudaError_t launch_sense_tc_p(const SenseArgs& a, cudaStream_t s) {
-    const int64_t total = (int64_t)a.g.n_img * a.g.n_blocks;
+    const int nseg = seg_count(a.g);
     int grid = 0;
-    cudaError_t e = grid_for(sense_tc_kernel<P>, total, &grid);
+    cudaError_t e = grid_segs(sense_tc_kernel<P>, nseg, kSenseSmem, &grid);
     if (e) return e;
-    return launch_pdl(sense_tc_kernel<P>, dim3(grid), dim3(256), 0, s, a, total);
+    return launch_pdl(sense_tc_kernel<P>, dim3(grid), dim3(256), kSenseSmem, s, a, nseg);
 }
-
 }  // namespace
+
+cudaError_t setup_tc_fragments() {
+    tc_frag_setup_kernel<<<1, 32>>>();
+    cudaError_t e = cudaGetLastError();
+    if (!e) e = cudaDeviceSynchronize();
+    return e;
+}
 
 cudaError_t launch_recon_tc(const ReconArgs& a, cudaStream_t s) {
     if (a.g.B != 16) return cudaErrorInvalidValue;
