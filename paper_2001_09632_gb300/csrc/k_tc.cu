@@ -225,42 +225,50 @@ ABCS_D void frag_b(int set, uint32_t (&h)[2][2], uint32_t (&l)[2][2]) {
 }
 
 // ---------------------------------------------------------------------------
-// Segments.  A CTA works on SEG = 32 consecutive blocks of one block row (a
-// 16 x 512 pixel strip).  Their packed coefficients form one contiguous
-// range, moved between global and shared memory with coalesced 16-byte
-// copies.  CTAs are persistent and walk the segments grid-stride; the next
-// segment's input is copied (cp.async) while the current one is
-// transformed, and each warp transforms four blocks of the segment.
+// Segments.  The batch's blocks (raster order within an image, images
+// consecutive) are split into one contiguous range per CTA, equal to within
+// one block, so every CTA has the same work.  A CTA walks its range in
+// segments of SEG = RSEG = 32 blocks (a segment may cross block rows and
+// images):
+// their packed coefficients form one contiguous range, moved between global
+// and shared memory with coalesced 16-byte copies; the next segment's input
+// is copied (cp.async) while the current one is transformed, and each warp
+// transforms four blocks of the segment.
 // ---------------------------------------------------------------------------
-constexpr int SEG = 32;
-constexpr int kSegFloats = SEG * 256 + 4;      // packed range of a segment + alignment shift
+constexpr int SEG = 32;                        // sensing segment (blocks)
+constexpr int RSEG = 32;                       // reconstruction segment (blocks)
+template <int S>
+constexpr int seg_floats() { return S * 256 + 4; }   // packed range of a segment + alignment shift
+constexpr int kSegFloats = seg_floats<SEG>();
+constexpr int kRSegFloats = seg_floats<RSEG>();
 
 struct SegGeom {
     int64_t b0;        // first block of the segment (index over the batch)
-    int k, bi, bj0, nblk;
+    int nblk;
 };
 
-ABCS_D SegGeom seg_geom(const ImgGeom& g, int s) {
-    const int spr = (g.nbw + SEG - 1) / SEG;
-    const int per_img = g.nbh * spr;
+// the CTA's block range [r0, r1) and its segment j
+ABCS_D void cta_range(int64_t ntot, int64_t* r0, int64_t* r1) {
+    *r0 = ntot * blockIdx.x / gridDim.x;
+    *r1 = ntot * (blockIdx.x + 1) / gridDim.x;
+}
+
+template <int S>
+ABCS_D SegGeom seg_geom(int64_t r0, int64_t r1, int j) {
     SegGeom r;
-    r.k = s / per_img;
-    const int rem = s - r.k * per_img;
-    r.bi = rem / spr;
-    r.bj0 = (rem - r.bi * spr) * SEG;
-    r.nblk = min(SEG, g.nbw - r.bj0);
-    r.b0 = (int64_t)r.k * g.n_blocks + (int64_t)r.bi * g.nbw + r.bj0;
+    r.b0 = r0 + (int64_t)j * S;
+    r.nblk = (int)min((int64_t)S, r1 - r.b0);
     return r;
 }
 
-ABCS_HD int seg_count(const ImgGeom& g) { return g.n_img * g.nbh * ((g.nbw + SEG - 1) / SEG); }
-
+template <int SEG>
 struct SegMeta {
     int64_t start;     // index of the segment's first coefficient in the packed vector
     int n;             // coefficients of the segment
     int sh;            // start & 3: stage position of coefficient `start`
     int rel[SEG];      // block offsets relative to start
     int cnt[SEG];      // block counts
+    int64_t pos[SEG];  // block's top-left pixel: recon, in the output; sense, byte offset in the input
     SegGeom sg;
 };
 
@@ -270,34 +278,45 @@ ABCS_D int warp_max(int v) {
     return v;
 }
 
+// block b of the batch -> image k, block row bi, block column bj (b < 2^31)
+ABCS_D void block_coords(const ImgGeom& g, int64_t b, int& k, int& bi, int& bj) {
+    const int bb = (int)b, nB = (int)g.n_blocks;
+    k = bb / nB;
+    const int i = bb - k * nB;
+    bi = i / g.nbw;
+    bj = i - bi * g.nbw;
+}
+
 // Metadata of a segment as loaded by warp 0 (lane = block of the segment).
 // Loads are issued two segments ahead and written to shared memory one
 // segment ahead, so their latency is hidden behind a segment's transforms.
 struct MetaRaw {
-    int64_t off;       // the block's offset (recon: global; sense: image-local)
-    int64_t base;      // sense: image base of the segment's image
+    int64_t off;       // the block's offset (recon: global; sense: image-local + image base)
+    int64_t pos;       // the block's pixel position
     int m;             // the block's count
 };
 
-ABCS_D MetaRaw recon_meta_load(const ReconArgs& a, int s) {
+ABCS_D MetaRaw recon_meta_load(const ReconArgs& a, const SegGeom& sg) {
     const int lane = threadIdx.x & 31;
-    const SegGeom sg = seg_geom(a.g, s);
     MetaRaw r;
     r.off = 0;
-    r.base = 0;
+    r.pos = 0;
     r.m = 0;
     if (lane < sg.nblk) {
-        r.off = __ldg(a.offsets + sg.b0 + lane);
-        r.m = __ldg(a.counts + sg.b0 + lane);
+        const int64_t b = sg.b0 + lane;
+        r.off = __ldg(a.offsets + b);
+        r.m = __ldg(a.counts + b);
+        int k, bi, bj;
+        block_coords(a.g, b, k, bi, bj);
+        r.pos = (int64_t)k * a.g.Hc * a.g.Wc + (int64_t)(bi * 16) * a.g.Wc + bj * 16;
     }
     return r;
 }
 
 // Inconsistent counts or offsets are flagged and the block is treated as
 // unmeasured, so every stage access stays inside the segment's buffer.
-ABCS_D void recon_meta_store(const ReconArgs& a, int s, const MetaRaw& r, SegMeta& M) {
+ABCS_D void recon_meta_store(const ReconArgs& a, const SegGeom& sg, const MetaRaw& r, SegMeta<RSEG>& M) {
     const int lane = threadIdx.x & 31;
-    const SegGeom sg = seg_geom(a.g, s);
     int64_t off = r.off;
     int m = r.m;
     int64_t start = __shfl_sync(0xffffffffu, off, 0);
@@ -311,13 +330,14 @@ ABCS_D void recon_meta_store(const ReconArgs& a, int s, const MetaRaw& r, SegMet
     int64_t rel = off - start;
     if (lane < sg.nblk) {
         if (m < 0 || m > 256) { bad = true; m = m < 0 ? 0 : 256; }
-        if (rel < 0 || rel + m > SEG * 256) { bad = true; rel = 0; m = 0; }
+        if (rel < 0 || rel + m > RSEG * 256) { bad = true; rel = 0; m = 0; }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(a.status, ABCS_DEV_BADCOUNT);
     const int end = warp_max(lane < sg.nblk ? (int)(rel + m) : 0);
-    if (lane < SEG) {
+    if (lane < RSEG) {
         M.rel[lane] = (int)rel;
         M.cnt[lane] = m;
+        M.pos[lane] = r.pos;
     }
     if (lane == 0) {
         M.start = start;
@@ -332,14 +352,14 @@ ABCS_D void recon_meta_store(const ReconArgs& a, int s, const MetaRaw& r, SegMet
 // gathered by zigzag rank from the staged segment); stage 2 X = Y D (A = Y
 // straight from stage 1's accumulators, B = D constant).
 // ---------------------------------------------------------------------------
-constexpr size_t kReconSmem = 2 * kSegFloats * sizeof(float) + 3 * sizeof(SegMeta);
-constexpr size_t kSenseSmem = 2 * 16 * SEG * 16 + kSegFloats * sizeof(float) + 3 * sizeof(SegMeta);
+constexpr size_t kReconSmem = 2 * kRSegFloats * sizeof(float) + 3 * sizeof(SegMeta<RSEG>);
+constexpr size_t kSenseSmem = 2 * 16 * SEG * 16 + kSegFloats * sizeof(float) + 3 * sizeof(SegMeta<SEG>);
 
 template <int P>
-__global__ void __launch_bounds__(256, 3) recon_tc_kernel(ReconArgs a, int nseg) {
+__global__ void __launch_bounds__(256, 3) recon_tc_kernel(ReconArgs a, int64_t ntot) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float (*stage)[kSegFloats] = reinterpret_cast<float (*)[kSegFloats]>(smem);
-    SegMeta* meta = reinterpret_cast<SegMeta*>(smem + 2 * kSegFloats * sizeof(float));
+    float (*stage)[kRSegFloats] = reinterpret_cast<float (*)[kRSegFloats]>(smem);
+    SegMeta<RSEG>* meta = reinterpret_cast<SegMeta<RSEG>*>(smem + 2 * kRSegFloats * sizeof(float));
     const int warp = threadIdx.x >> 5;
     const Frag f;
     uint32_t ATh[4], ATl[4], DBh[2][2], DBl[2][2];
@@ -354,37 +374,35 @@ __global__ void __launch_bounds__(256, 3) recon_tc_kernel(ReconArgs a, int nseg)
 
     griddep_wait();
     const ImgGeom& g = a.g;
-    const int G = gridDim.x;
-    int s = blockIdx.x;
-    if (s >= nseg) return;
-    const int lo = f.g * g.Wc + 2 * f.q;       // lane's first output pixel within a block
-    const int64_t img_px = (int64_t)g.Hc * g.Wc;
+    int64_t r0, r1;
+    cta_range(ntot, &r0, &r1);
+    const int nseg = (int)((r1 - r0 + RSEG - 1) / RSEG);
+    if (nseg <= 0) return;
+    const int lo = f.g * g.Wc + 2 * f.q;
     MetaRaw raw;
     if (warp == 0) {
-        recon_meta_store(a, s, recon_meta_load(a, s), meta[0]);
-        if (s + G < nseg) raw = recon_meta_load(a, s + G);
+        recon_meta_store(a, seg_geom<RSEG>(r0, r1, 0), recon_meta_load(a, seg_geom<RSEG>(r0, r1, 0)), meta[0]);
+        if (1 < nseg) raw = recon_meta_load(a, seg_geom<RSEG>(r0, r1, 1));
     }
     __syncthreads();
     stage_in_async(stage[0], a.coeffs, meta[0].start, meta[0].n);
     cp_async_commit();
     int mi = 0;                                 // meta slot of segment j (j mod 3)
-    for (int j = 0; s < nseg; ++j, s += G) {
+    for (int j = 0; j < nseg; ++j) {
         const int mn = mi == 2 ? 0 : mi + 1;
-        const int s1 = s + G;
-        if (s1 < nseg && warp == 0) {
-            recon_meta_store(a, s1, raw, meta[mn]);
-            if (s1 + G < nseg) raw = recon_meta_load(a, s1 + G);
+        if (j + 1 < nseg && warp == 0) {
+            recon_meta_store(a, seg_geom<RSEG>(r0, r1, j + 1), raw, meta[mn]);
+            if (j + 2 < nseg) raw = recon_meta_load(a, seg_geom<RSEG>(r0, r1, j + 2));
         }
         cp_async_wait_all();
         __syncthreads();
-        if (s1 < nseg) stage_in_async(stage[(j + 1) & 1], a.coeffs, meta[mn].start, meta[mn].n);
+        if (j + 1 < nseg) stage_in_async(stage[(j + 1) & 1], a.coeffs, meta[mn].start, meta[mn].n);
         cp_async_commit();
 
-        const SegMeta& M = meta[mi];
+        const SegMeta<RSEG>& M = meta[mi];
         const SegGeom sg = M.sg;
         const float* st = stage[j & 1] + M.sh;
-        const int64_t seg_px = (int64_t)sg.k * img_px + (int64_t)(sg.bi * 16) * g.Wc + sg.bj0 * 16 + lo;
-#pragma unroll 2
+#pragma unroll
         for (int c = warp; c < sg.nblk; c += 8) {
             const int m = M.cnt[c];
             const float* sb = st + M.rel[c];
@@ -411,7 +429,7 @@ __global__ void __launch_bounds__(256, 3) recon_tc_kernel(ReconArgs a, int nseg)
             for (int nt = 0; nt < 2; ++nt)
                 mma_split<P>(X[nt], Ah, Al, DBh[nt][0], DBh[nt][1], DBl[nt][0], DBl[nt][1]);
 
-            const int64_t o = seg_px + c * 16;
+            const int64_t o = M.pos[c] + lo;
             const int64_t o8 = o + 8 * (int64_t)g.Wc;
             if (a.out) {
                 *reinterpret_cast<float2*>(a.out + o) = make_float2(X[0][0], X[0][1]);
@@ -440,8 +458,8 @@ __global__ void __launch_bounds__(256, 3) recon_tc_kernel(ReconArgs a, int nseg)
 // K-permutation of stage 1: MMA k = 2q + e, 2q + 8 + e (e = 0, 1) stands for
 // pixel column 4q + e, 4q + 2 + e, so each lane's B fragment of one pixel
 // row is 4 consecutive bytes (one 32-bit shared load).  Pixels sit in shared
-// memory as a 16 x 512 strip whose 16-byte chunks are XOR-swizzled by
-// (row & 7), which makes those loads bank-conflict free.  The block's first
+// memory block after block, 16 bytes per row, which makes those loads
+// bank-conflict free.  The block's first
 // m_i zigzag coefficients are scattered into the segment's packed staging
 // buffer and the whole segment range is written out with 16-byte stores.
 // ---------------------------------------------------------------------------
@@ -461,49 +479,50 @@ ABCS_D uint32_t px_pair(uint32_t w, int hi2) {
     }
 }
 
-ABCS_D MetaRaw sense_meta_load(const SenseArgs& a, int s) {
+// counts and image-local offsets from the allocation, image bases from its
+// last CTA; pos = byte offset of the block's top-left pixel in the input
+ABCS_D MetaRaw sense_meta_load(const SenseArgs& a, const SegGeom& sg) {
     const int lane = threadIdx.x & 31;
-    const SegGeom sg = seg_geom(a.g, s);
     MetaRaw r;
     r.off = 0;
+    r.pos = 0;
     r.m = 0;
-    r.base = __ldg(a.img_base + sg.k);
     if (lane < sg.nblk) {
-        r.off = __ldg(a.offsets + sg.b0 + lane);
-        r.m = __ldg(a.counts + sg.b0 + lane);
+        const int64_t b = sg.b0 + lane;
+        int k, bi, bj;
+        block_coords(a.g, b, k, bi, bj);
+        r.off = __ldg(a.offsets + b) + __ldg(a.img_base + k);
+        r.m = __ldg(a.counts + b);
+        r.pos = (int64_t)k * a.g.img_stride + (int64_t)(bi * 16) * a.g.pitch + bj * 16;
     }
     return r;
 }
 
-// counts and image-local offsets from the allocation, image bases from its last CTA
-ABCS_D void sense_meta_store(const SenseArgs& a, int s, const MetaRaw& r, SegMeta& M) {
+ABCS_D void sense_meta_store(const SegGeom& sg, const MetaRaw& r, SegMeta<SEG>& M) {
     const int lane = threadIdx.x & 31;
-    const SegGeom sg = seg_geom(a.g, s);
-    const int64_t loc0 = __shfl_sync(0xffffffffu, r.off, 0);
-    const int rel = (int)(r.off - loc0);
+    const int64_t start = __shfl_sync(0xffffffffu, r.off, 0);
+    const int rel = (int)(r.off - start);
     const int end = warp_max(lane < sg.nblk ? rel + r.m : 0);
-    if (lane < SEG) {
-        M.rel[lane] = rel;
-        M.cnt[lane] = r.m;
-    }
+    M.rel[lane] = rel;
+    M.cnt[lane] = r.m;
+    M.pos[lane] = r.pos;
     if (lane == 0) {
-        M.start = r.base + loc0;
+        M.start = start;
         M.n = end;
-        M.sh = (int)(M.start & 3);
+        M.sh = (int)(start & 3);
         M.sg = sg;
     }
 }
 
-// all threads: copy the 16 x (16 nblk) pixel strip of segment sg; chunk
-// (row r, block c) of 16 bytes goes to r * 512 + 16 (c ^ (r & 7))
-ABCS_D void sense_pixels(const SenseArgs& a, const SegGeom& sg, uint8_t* dst, bool vec) {
-    const uint8_t* base = a.img + (int64_t)sg.k * a.g.img_stride + (int64_t)(sg.bi * 16) * a.g.pitch + sg.bj0 * 16;
+// all threads: copy the pixels of the segment's blocks, block c's row r
+// (16 bytes) to 256 c + 16 r
+ABCS_D void sense_pixels(const SenseArgs& a, const SegMeta<SEG>& M, uint8_t* dst, bool vec) {
 #pragma unroll
     for (int h = 0; h < SEG * 16 / 256; ++h) {
-        const int id = threadIdx.x + 256 * h, r = id / SEG, c = id % SEG;
-        if (c >= sg.nblk) continue;
-        const uint8_t* src = base + (int64_t)r * a.g.pitch + c * 16;
-        uint8_t* d = dst + r * (SEG * 16) + ((c ^ (r & 7)) << 4);
+        const int id = threadIdx.x + 256 * h, c = id >> 4, r = id & 15;
+        if (c >= M.sg.nblk) continue;
+        const uint8_t* src = a.img + M.pos[c] + (int64_t)r * a.g.pitch;
+        uint8_t* d = dst + 256 * c + 16 * r;
         if (vec) {
             const unsigned sd = (unsigned)__cvta_generic_to_shared(d);
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sd), "l"(src) : "memory");
@@ -515,11 +534,11 @@ ABCS_D void sense_pixels(const SenseArgs& a, const SegGeom& sg, uint8_t* dst, bo
 }
 
 template <int P>
-__global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int nseg) {
+__global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int64_t ntot) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint8_t (*pix)[16 * SEG * 16] = reinterpret_cast<uint8_t (*)[16 * SEG * 16]>(smem);
     float* ost = reinterpret_cast<float*>(smem + 2 * 16 * SEG * 16);
-    SegMeta* meta = reinterpret_cast<SegMeta*>(smem + 2 * 16 * SEG * 16 + kSegFloats * sizeof(float));
+    SegMeta<SEG>* meta = reinterpret_cast<SegMeta<SEG>*>(smem + 2 * 16 * SEG * 16 + kSegFloats * sizeof(float));
     const int warp = threadIdx.x >> 5;
     const Frag f;
     uint32_t DAh[4], DAl[4], DTh[2][2], DTl[2][2];
@@ -534,32 +553,32 @@ __global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int nseg)
     const ImgGeom& g = a.g;
     const bool vec = ((reinterpret_cast<uintptr_t>(a.img) | (uintptr_t)g.pitch |
                        (uintptr_t)(g.n_img > 1 ? g.img_stride : 0)) & 15) == 0;
-    const int G = gridDim.x;
-    int s = blockIdx.x;
-    if (s >= nseg) return;
-    sense_pixels(a, seg_geom(g, s), pix[0], vec);     // pixels do not depend on the previous kernels
-    cp_async_commit();
+    int64_t r0, r1;
+    cta_range(ntot, &r0, &r1);
+    const int nseg = (int)((r1 - r0 + SEG - 1) / SEG);
+    if (nseg <= 0) return;
     griddep_wait();
     MetaRaw raw;
     if (warp == 0) {
-        sense_meta_store(a, s, sense_meta_load(a, s), meta[0]);
-        if (s + G < nseg) raw = sense_meta_load(a, s + G);
+        sense_meta_store(seg_geom<SEG>(r0, r1, 0), sense_meta_load(a, seg_geom<SEG>(r0, r1, 0)), meta[0]);
+        if (1 < nseg) raw = sense_meta_load(a, seg_geom<SEG>(r0, r1, 1));
     }
-    const int64_t ntot = (int64_t)g.n_img * g.n_blocks;
+    __syncthreads();
+    sense_pixels(a, meta[0], pix[0], vec);
+    cp_async_commit();
     int mi = 0;
-    for (int j = 0; s < nseg; ++j, s += G) {
+    for (int j = 0; j < nseg; ++j) {
         const int mn = mi == 2 ? 0 : mi + 1;
-        const int s1 = s + G;
-        if (s1 < nseg && warp == 0) {
-            sense_meta_store(a, s1, raw, meta[mn]);
-            if (s1 + G < nseg) raw = sense_meta_load(a, s1 + G);
+        if (j + 1 < nseg && warp == 0) {
+            sense_meta_store(seg_geom<SEG>(r0, r1, j + 1), raw, meta[mn]);
+            if (j + 2 < nseg) raw = sense_meta_load(a, seg_geom<SEG>(r0, r1, j + 2));
         }
         cp_async_wait_all();
         __syncthreads();
-        if (s1 < nseg) sense_pixels(a, meta[mn].sg, pix[(j + 1) & 1], vec);
+        if (j + 1 < nseg) sense_pixels(a, meta[mn], pix[(j + 1) & 1], vec);
         cp_async_commit();
 
-        const SegMeta& M = meta[mi];
+        const SegMeta<SEG>& M = meta[mi];
         const int nblk = M.sg.nblk;
         const uint8_t* px = pix[j & 1];
         float* os = ost + M.sh;
@@ -568,9 +587,8 @@ __global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int nseg)
             uint32_t xb[2][2];
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
-                const int y = f.g + 8 * nt;    // y & 7 == g
-                const uint32_t w =
-                    *reinterpret_cast<const uint32_t*>(px + y * (SEG * 16) + ((c ^ f.g) << 4) + 4 * f.q);
+                const int y = f.g + 8 * nt;    // bank 4 g + q: conflict free
+                const uint32_t w = *reinterpret_cast<const uint32_t*>(px + 256 * c + 16 * y + 4 * f.q);
                 xb[nt][0] = px_pair<P>(w, 0);
                 xb[nt][1] = px_pair<P>(w, 1);
             }
@@ -616,35 +634,37 @@ __global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int nseg)
     cp_async_wait_all();
 }
 
+// one CTA per segment at most, and no more CTAs than fit on the GPU at once
 template <typename K>
-cudaError_t grid_segs(K kernel, int nseg, size_t smem, int* grid) {
+cudaError_t grid_segs(K kernel, int64_t ntot, int seg, size_t smem, int* grid) {
+    const int64_t nseg = (ntot + seg - 1) / seg;
     int dev, sms, per_sm;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (!e) e = cudaGetDevice(&dev);
     if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem);
     if (e) return e;
-    const int cap = sms * (per_sm > 0 ? per_sm : 1);
-    *grid = nseg < cap ? nseg : cap;
+    const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    *grid = (int)(nseg < cap ? nseg : cap);
     return cudaSuccess;
 }
 
 template <int P>
 cudaError_t launch_recon_tc_p(const ReconArgs& a, cudaStream_t s) {
-    const int nseg = seg_count(a.g);
+    const int64_t ntot = (int64_t)a.g.n_img * a.g.n_blocks;
     int grid = 0;
-    cudaError_t e = grid_segs(recon_tc_kernel<P>, nseg, kReconSmem, &grid);
+    cudaError_t e = grid_segs(recon_tc_kernel<P>, ntot, RSEG, kReconSmem, &grid);
     if (e) return e;
-    return launch_pdl(recon_tc_kernel<P>, dim3(grid), dim3(256), kReconSmem, s, a, nseg);
+    return launch_pdl(recon_tc_kernel<P>, dim3(grid), dim3(256), kReconSmem, s, a, ntot);
 }
 
 template <int P>
 cudaError_t launch_sense_tc_p(const SenseArgs& a, cudaStream_t s) {
-    const int nseg = seg_count(a.g);
+    const int64_t ntot = (int64_t)a.g.n_img * a.g.n_blocks;
     int grid = 0;
-    cudaError_t e = grid_segs(sense_tc_kernel<P>, nseg, kSenseSmem, &grid);
+    cudaError_t e = grid_segs(sense_tc_kernel<P>, ntot, SEG, kSenseSmem, &grid);
     if (e) return e;
-    return launch_pdl(sense_tc_kernel<P>, dim3(grid), dim3(256), kSenseSmem, s, a, nseg);
+    return launch_pdl(sense_tc_kernel<P>, dim3(grid), dim3(256), kSenseSmem, s, a, ntot);
 }
 }  // namespace
 
