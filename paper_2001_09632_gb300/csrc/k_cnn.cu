@@ -2,17 +2,19 @@
 //   conv3x3 2->32 + ReLU, 6 x [conv3x3 32->32 + ReLU], conv3x3 32->1,
 //   x_hat = r - 255 * net(r / 255, sigma / 255), zero 'same' padding.
 // Activations and mid-layer weights are BF16 (NHWC, 32 channels = 64 bytes
-// per pixel); every sum accumulates in FP32.  The 32->32 layers run as an
-// implicit GEMM on mma.sync.m16n8k16 (BF16 in, FP32 out): a CTA owns an
-// 8 x 32 output tile, stages the 10 x 34 input tile and the layer's weights
-// in shared memory and feeds the tensor cores with ldmatrix.  The thin first
-// and last layers (2 and 1 channels) run on FP32 CUDA cores.
+// per pixel); every sum accumulates in FP32.  All layers are implicit GEMMs
+// on mma.sync.m16n8k16 with FP32 accumulation: the 32->32 layers in BF16
+// (persistent CTAs, 8 x 32 output tiles, weights resident in shared memory,
+// input tiles double-buffered and fed to the tensor cores with ldmatrix),
+// the first layer (2 channels: r / 255 and sigma / 255) in FP16, the last
+// (32 -> 1) in BF16 with the weights split hi + lo.
 //
 // Training (fwd + bwd + Adam) reuses the same conv kernel for the input
 // gradient (weights transposed in (ci, co) and flipped in the tap, epilogue
 // = ReLU mask of the layer below); weight gradients are accumulated per CTA
 // in FP32 and reduced in a fixed order (deterministic).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "abcs_common.cuh"
 
@@ -76,177 +78,264 @@ ABCS_D uint32_t pack_bf16(float a, float b) {
 // 32 -> 32 conv3x3 as an implicit GEMM (M = pixels, N = 32, K = 9 x 32).
 // EPI 0: out = ReLU(acc + bias)            (forward)
 // EPI 1: out = acc * [mask > 0]            (input gradient through a ReLU)
+// Persistent CTAs: the layer's weights are loaded once, the input tiles
+// (8 x 32 outputs, 10 x 34 inputs with a zero halo) are double-buffered with
+// cp.async (zero fill outside the image), so the next tile streams in while
+// the tensor cores work on the current one.  A pixel's 32 channels take 64
+// bytes of shared memory; the 16-byte chunks are XOR-swizzled by
+// (pixel >> 1) & 3, which keeps every ldmatrix conflict-free.
 // ---------------------------------------------------------------------------
+ABCS_D int swz(int p, int c) { return p * 32 + ((c ^ ((p >> 1) & 3)) << 3); }   // bf16 index
+
+ABCS_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+ABCS_D void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+ABCS_D void cp_async16_zfill(void* sdst, const void* gsrc, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    const int nbytes = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(nbytes) : "memory");
+}
+
+constexpr int kTileElems = IH * IW * kC;          // bf16 of one staged input tile
+constexpr int kWElems = 9 * kC * kC;              // bf16 of one layer's weights
+constexpr size_t kConvSmem = (size_t)(2 * kTileElems + kWElems) * 2;
+
 template <int EPI>
-__global__ void __launch_bounds__(256) conv32_kernel(const __nv_bfloat16* __restrict__ in, int H, int W,
-                                                     const __nv_bfloat16* __restrict__ wts,
-                                                     const float* __restrict__ bias,
-                                                     const __nv_bfloat16* __restrict__ mask,
-                                                     __nv_bfloat16* __restrict__ out) {
+__global__ void __launch_bounds__(256, 3) conv32_kernel(const __nv_bfloat16* __restrict__ in, int n, int H,
+                                                        int W, const __nv_bfloat16* __restrict__ wts,
+                                                        const float* __restrict__ bias,
+                                                        const __nv_bfloat16* __restrict__ mask,
+                                                        __nv_bfloat16* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __nv_bfloat16* tin = reinterpret_cast<__nv_bfloat16*>(smem);         // [IH*IW][PXS]
-    __nv_bfloat16* tw = tin + IH * IW * PXS;                             // [9*32][PXS]
-    griddep_wait();
+    __nv_bfloat16* tw = reinterpret_cast<__nv_bfloat16*>(smem);        // [9 * 32 rows (tap, co)][32 ci]
+    __nv_bfloat16* tb0 = tw + kWElems;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int k = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
-    const __nv_bfloat16* img = in + (int64_t)k * H * W * kC;
-    // stage the input tile with a 1-pixel zero halo (16-byte chunks)
-    for (int c = t; c < IH * IW * 4; c += 256) {
-        const int px = c >> 2, ch = c & 3;
-        const int yy = y0 - 1 + px / IW, xx = x0 - 1 + px % IW;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-            v = __ldg(reinterpret_cast<const uint4*>(img + ((int64_t)yy * W + xx) * kC) + ch);
-        *reinterpret_cast<uint4*>(tin + px * PXS + ch * 8) = v;
+    const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH, per_img = tx * ty;
+    const int ntiles = per_img * n;
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    for (int c = t; c < 9 * kC * 4; c += 256)        // weights do not depend on the previous kernel
+        cp_async16_zfill(tw + swz(c >> 2, c & 3), wts + (c >> 2) * kC + (c & 3) * 8, true);
+    griddep_wait();
+    auto origin = [&](int tl, int& k, int& x0, int& y0) {
+        k = tl / per_img;
+        const int rem = tl - k * per_img, by = rem / tx;
+        x0 = (rem - by * tx) * TW;
+        y0 = by * TH;
+    };
+    auto stage = [&](int tl, __nv_bfloat16* dst) {
+        int k, x0, y0;
+        origin(tl, k, x0, y0);
+        const __nv_bfloat16* img = in + (int64_t)k * H * W * kC;
+        for (int c = t; c < IH * IW * 4; c += 256) {
+            const int px = c >> 2, ch = c & 3;
+            const int yy = y0 - 1 + px / IW, xx = x0 - 1 + px % IW;
+            const bool v = yy >= 0 && yy < H && xx >= 0 && xx < W;
+            cp_async16_zfill(dst + swz(px, ch), v ? img + ((int64_t)yy * W + xx) * kC + ch * 8 : img, v);
+        }
+    };
+    stage(tile, tb0);
+    cp_async_commit();
+    const int G = gridDim.x;
+    const int arow = lane & 15, achk = lane >> 4;                                // A: pixel row, chunk
+    const int brow = (lane & 7) + (lane >> 4) * 8, bchk = (lane >> 3) & 1;      // B: co row, chunk
+    const int g = lane >> 2, q = lane & 3;
+    for (int i = 0; tile < ntiles; ++i, tile += G) {
+        __nv_bfloat16* cur = tb0 + (i & 1) * kTileElems;
+        if (tile + G < ntiles) stage(tile + G, tb0 + ((i + 1) & 1) * kTileElems);
+        cp_async_commit();
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        __syncthreads();
+
+        float acc[2][4][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int nn = 0; nn < 4; ++nn)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[h][nn][e] = 0.f;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3;
+            const int p0 = (warp + dy) * IW + dx + arow;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                uint32_t a0[4], a1[4], b01[4], b23[4];
+                ldmatrix_x4(a0, cur + swz(p0, 2 * ks + achk));
+                ldmatrix_x4(a1, cur + swz(p0 + 16, 2 * ks + achk));
+                ldmatrix_x4(b01, tw + swz(tap * kC + brow, 2 * ks + bchk));
+                ldmatrix_x4(b23, tw + swz(tap * kC + brow + 16, 2 * ks + bchk));
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t(&a)[4] = h ? a1 : a0;
+                    mma_bf16(acc[h][0], a, b01[0], b01[1]);
+                    mma_bf16(acc[h][1], a, b01[2], b01[3]);
+                    mma_bf16(acc[h][2], a, b23[0], b23[1]);
+                    mma_bf16(acc[h][3], a, b23[2], b23[3]);
+                }
+            }
+        }
+        __syncthreads();                     // every warp is done reading `cur`
+        // epilogue through `cur`: [TH * TW pixels][32 channels], then 16-byte stores
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int nn = 0; nn < 4; ++nn) {
+                const int co = nn * 8 + 2 * q;
+                const float b0 = (EPI == 0) ? __ldg(bias + co) : 0.f, b1 = (EPI == 0) ? __ldg(bias + co + 1) : 0.f;
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const int px = warp * TW + h * 16 + g + 8 * half;
+                    float v0 = acc[h][nn][2 * half] + b0, v1 = acc[h][nn][2 * half + 1] + b1;
+                    if (EPI == 0) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+                    *reinterpret_cast<uint32_t*>(cur + swz(px, nn) + 2 * q) = pack_bf16(v0, v1);
+                }
+            }
+        __syncthreads();
+        int k, x0, y0;
+        origin(tile, k, x0, y0);
+        __nv_bfloat16* dst = out + (int64_t)k * H * W * kC;
+        const __nv_bfloat16* msk = (EPI == 1) ? mask + (int64_t)k * H * W * kC : nullptr;
+        for (int c = t; c < TH * TW * 4; c += 256) {
+            const int px = c >> 2, ch = c & 3;
+            const int yy = y0 + px / TW, xx = x0 + px % TW;
+            if (yy >= H || xx >= W) continue;
+            uint4 v = *reinterpret_cast<const uint4*>(cur + swz(px, ch));
+            const int64_t o = ((int64_t)yy * W + xx) * kC + ch * 8;
+            if (EPI == 1) {
+                const uint4 m = __ldg(reinterpret_cast<const uint4*>(msk + o));
+                const uint32_t* mw = reinterpret_cast<const uint32_t*>(&m);
+                uint32_t* vw = reinterpret_cast<uint32_t*>(&v);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    // a BF16 activation is > 0 iff its sign bit is clear and it is not +0
+                    const uint32_t lo = (mw[e] & 0xFFFFu), hi = (mw[e] >> 16);
+                    const uint32_t keep_lo = (lo != 0 && !(lo & 0x8000u)) ? 0xFFFFu : 0u;
+                    const uint32_t keep_hi = (hi != 0 && !(hi & 0x8000u)) ? 0xFFFF0000u : 0u;
+                    vw[e] &= keep_lo | keep_hi;
+                }
+            }
+            *reinterpret_cast<uint4*>(dst + o) = v;
+        }
+        __syncthreads();                     // `cur` is staged into again two tiles later
     }
-    for (int c = t; c < 9 * kC * 4; c += 256) {
-        const int row = c >> 2, ch = c & 3;
-        *reinterpret_cast<uint4*>(tw + row * PXS + ch * 8) =
-            __ldg(reinterpret_cast<const uint4*>(wts + row * kC) + ch);
+    cp_async_wait_all();
+}
+
+// ---------------------------------------------------------------------------
+// First layer on the tensor cores: an implicit GEMM with K = (tap, channel),
+// k = 2 tap + ci (18 values, zero-padded to 32), FP16 operands, FP32
+// accumulation.  Each shared pixel holds the pair (r / 255, sigma / 255) as
+// FP16x2 (sigma is zero outside the image: zero padding of that channel),
+// so one 32-bit shared load is one A-fragment register (pixel, tap).
+// ---------------------------------------------------------------------------
+ABCS_D void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+ABCS_D uint32_t pack_f16(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__global__ void __launch_bounds__(256) cnn_first_tc_kernel(const float* __restrict__ r,
+                                                           const float* __restrict__ sigma, int H, int W,
+                                                           const CnnPacked* __restrict__ P,
+                                                           __nv_bfloat16* __restrict__ out) {
+    __shared__ uint32_t tin[IH * IW];                     // (r/255, sigma/255) FP16x2
+    __shared__ __align__(16) __nv_bfloat16 tout[TH * TW * PXS];
+    griddep_wait();
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = lane >> 2, q = lane & 3;
+    const int k = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const float* img = r + (int64_t)k * H * W;
+    const float s255 = __ldg(sigma + k) * (1.f / 255.f);
+    for (int c = t; c < IH * IW; c += 256) {
+        const int yy = y0 - 1 + c / IW, xx = x0 - 1 + c % IW;
+        const bool in_img = yy >= 0 && yy < H && xx >= 0 && xx < W;
+        tin[c] = in_img ? pack_f16(__ldg(img + (int64_t)yy * W + xx) * (1.f / 255.f), s255) : 0u;
+    }
+    // B fragments: B[k][co] = w0[co][ci][tap], k = 2 tap + ci; ks 0: taps 0..7, ks 1: tap 8
+    uint32_t b[2][4][2];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+        const int co = 8 * nt + g;
+        b[0][nt][0] = pack_f16(__ldg(&P->w0[co][0][q]), __ldg(&P->w0[co][1][q]));
+        b[0][nt][1] = pack_f16(__ldg(&P->w0[co][0][q + 4]), __ldg(&P->w0[co][1][q + 4]));
+        b[1][nt][0] = q == 0 ? pack_f16(__ldg(&P->w0[co][0][8]), __ldg(&P->w0[co][1][8])) : 0u;
+        b[1][nt][1] = 0u;
     }
     __syncthreads();
-
     float acc[2][4][4];
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int n = 0; n < 4; ++n)
+        for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[h][n][e] = 0.f;
-
-    const int arow = lane & 15, acol = (lane >> 4) * 8;          // A: pixel, channel offset
-    const int bco = (lane & 7) + (lane >> 4) * 8, bci = ((lane >> 3) & 1) * 8;   // B: co, ci offset
+            for (int e = 0; e < 4; ++e) acc[h][nt][e] = 0.f;
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;
+    for (int h = 0; h < 2; ++h) {
+        // pixel (warp, 16 h + g) and (warp, 16 h + g + 8); tap (dy, dx) reads (warp + dy, col + dx)
+        auto at = [&](int row8, int tap) {
+            return tin[(warp + tap / 3) * IW + 16 * h + g + 8 * row8 + tap % 3];
+        };
+        uint32_t a0[4], a1[4];
+        a0[0] = at(0, q);
+        a0[1] = at(1, q);
+        a0[2] = at(0, q + 4);
+        a0[3] = at(1, q + 4);
+        a1[0] = q == 0 ? at(0, 8) : 0u;
+        a1[1] = q == 0 ? at(1, 8) : 0u;
+        a1[2] = 0u;
+        a1[3] = 0u;
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-            uint32_t a0[4], a1[4], b01[4], b23[4];
-            const __nv_bfloat16* ap = tin + ((warp + dy) * IW + dx + arow) * PXS + ks * 16 + acol;
-            ldmatrix_x4(a0, ap);
-            ldmatrix_x4(a1, ap + 16 * PXS);
-            const __nv_bfloat16* bp = tw + (tap * kC + bco) * PXS + ks * 16 + bci;
-            ldmatrix_x4(b01, bp);
-            ldmatrix_x4(b23, bp + 16 * PXS);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t(&a)[4] = h ? a1 : a0;
-                mma_bf16(acc[h][0], a, b01[0], b01[1]);
-                mma_bf16(acc[h][1], a, b01[2], b01[3]);
-                mma_bf16(acc[h][2], a, b23[0], b23[1]);
-                mma_bf16(acc[h][3], a, b23[2], b23[3]);
-            }
+        for (int nt = 0; nt < 4; ++nt) {
+            mma_f16(acc[h][nt], a0, b[0][nt][0], b[0][nt][1]);
+            mma_f16(acc[h][nt], a1, b[1][nt][0], b[1][nt][1]);
         }
     }
-    __syncthreads();
-    // epilogue through smem: [TH*TW][PXS] output tile, then 16-byte stores
-    __nv_bfloat16* tout = tin;
-    const int g = lane >> 2, q = lane & 3;
+    // epilogue through shared memory: bias, ReLU, BF16, 16-byte stores
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int n = 0; n < 4; ++n) {
-            const int co = n * 8 + 2 * q;
-            const float b0 = (EPI == 0) ? __ldg(bias + co) : 0.f, b1 = (EPI == 0) ? __ldg(bias + co + 1) : 0.f;
+        for (int nt = 0; nt < 4; ++nt) {
+            const int co = nt * 8 + 2 * q;
+            const float b0 = __ldg(&P->b0[co]), b1 = __ldg(&P->b0[co + 1]);
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 const int px = warp * TW + h * 16 + g + 8 * half;
-                float v0 = acc[h][n][2 * half] + b0, v1 = acc[h][n][2 * half + 1] + b1;
-                if (EPI == 0) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+                const float v0 = fmaxf(acc[h][nt][2 * half] + b0, 0.f), v1 = fmaxf(acc[h][nt][2 * half + 1] + b1, 0.f);
                 *reinterpret_cast<uint32_t*>(tout + px * PXS + co) = pack_bf16(v0, v1);
             }
         }
     __syncthreads();
     __nv_bfloat16* dst = out + (int64_t)k * H * W * kC;
-    const __nv_bfloat16* msk = (EPI == 1) ? mask + (int64_t)k * H * W * kC : nullptr;
     for (int c = t; c < TH * TW * 4; c += 256) {
         const int px = c >> 2, ch = c & 3;
         const int yy = y0 + px / TW, xx = x0 + px % TW;
         if (yy >= H || xx >= W) continue;
-        uint4 v = *reinterpret_cast<const uint4*>(tout + px * PXS + ch * 8);
-        const int64_t o = ((int64_t)yy * W + xx) * kC + ch * 8;
-        if (EPI == 1) {
-            const uint4 m = __ldg(reinterpret_cast<const uint4*>(msk + o));
-            const uint32_t* mw = reinterpret_cast<const uint32_t*>(&m);
-            uint32_t* vw = reinterpret_cast<uint32_t*>(&v);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                // a BF16 activation is > 0 iff its sign bit is clear and it is not +0
-                const uint32_t lo = (mw[e] & 0xFFFFu), hi = (mw[e] >> 16);
-                const uint32_t keep_lo = (lo != 0 && !(lo & 0x8000u)) ? 0xFFFFu : 0u;
-                const uint32_t keep_hi = (hi != 0 && !(hi & 0x8000u)) ? 0xFFFF0000u : 0u;
-                vw[e] &= keep_lo | keep_hi;
-            }
-        }
-        *reinterpret_cast<uint4*>(dst + o) = v;
+        *reinterpret_cast<uint4*>(dst + ((int64_t)yy * W + xx) * kC + ch * 8) =
+            *reinterpret_cast<const uint4*>(tout + px * PXS + ch * 8);
     }
 }
 
 // ---------------------------------------------------------------------------
-// First layer: input channels (r / 255, sigma / 255), FP32 CUDA cores.
-// One thread per output pixel; 8 x 32 tile with a 1-pixel halo of r.
+// Last layer 32 -> 1 on the tensor cores: the 32 -> 32 implicit GEMM with
+// one useful output column; the FP32 weights enter as BF16 hi + lo (two
+// products), the activations are BF16 already, so the sum is FP32-accurate.
+// mode 0: out = r - 255 (acc + b) (the denoised image); mode 1: out = acc + b.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) cnn_first_kernel(const float* __restrict__ r, const float* __restrict__ sigma,
-                                                        int H, int W, const CnnPacked* __restrict__ P,
-                                                        __nv_bfloat16* __restrict__ out) {
-    __shared__ float tr[IH * IW];
-    __shared__ float sw[kC * 2 * 9 + kC];
-    griddep_wait();
-    const int t = threadIdx.x, k = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
-    const float* img = r + (int64_t)k * H * W;
-    const float s255 = __ldg(sigma + k) * (1.f / 255.f);
-    for (int c = t; c < IH * IW; c += 256) {
-        const int yy = y0 - 1 + c / IW, xx = x0 - 1 + c % IW;
-        // 2 channels per input pixel: r/255 and sigma/255 (both 0 outside the image)
-        tr[c] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? __ldg(img + (int64_t)yy * W + xx) * (1.f / 255.f) : 0.f;
-    }
-    for (int c = t; c < kC * 2 * 9; c += 256) sw[c] = (&P->w0[0][0][0])[c];
-    if (t < kC) sw[kC * 2 * 9 + t] = P->b0[t];
-    __syncthreads();
-    const int py = t / TW, px = t % TW, yy = y0 + py, xx = x0 + px;
-    if (yy >= H || xx >= W) return;
-    float xin[9], sin[9];
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int iy = py + tap / 3, ix = px + tap % 3;
-        xin[tap] = tr[iy * IW + ix];
-        const int gy = yy - 1 + tap / 3, gx = xx - 1 + tap % 3;
-        sin[tap] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? s255 : 0.f;
-    }
-    uint32_t o[16];
-#pragma unroll
-    for (int co = 0; co < kC; co += 2) {
-        float v[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            float a = sw[kC * 2 * 9 + co + e];
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                a = fmaf(sw[((co + e) * 2 + 0) * 9 + tap], xin[tap], a);
-                a = fmaf(sw[((co + e) * 2 + 1) * 9 + tap], sin[tap], a);
-            }
-            v[e] = fmaxf(a, 0.f);
-        }
-        o[co / 2] = pack_bf16(v[0], v[1]);
-    }
-    uint4* d = reinterpret_cast<uint4*>(out + ((int64_t)k * H * W + (int64_t)yy * W + xx) * kC);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) d[c] = make_uint4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
-}
-
-// ---------------------------------------------------------------------------
-// Last layer 32 -> 1, FP32 CUDA cores.  mode 0: out = r - 255 (acc + b)
-// (the denoised image); mode 1: out = acc + b (the network output n).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) cnn_last_kernel(const __nv_bfloat16* __restrict__ in,
-                                                       const float* __restrict__ r, int H, int W,
-                                                       const CnnPacked* __restrict__ P, int mode,
-                                                       float* __restrict__ out) {
+__global__ void __launch_bounds__(256) cnn_last_tc_kernel(const __nv_bfloat16* __restrict__ in,
+                                                          const float* __restrict__ r, int H, int W,
+                                                          const CnnPacked* __restrict__ P, int mode,
+                                                          float* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem[];
     __nv_bfloat16* tin = reinterpret_cast<__nv_bfloat16*>(smem);     // [IH*IW][PXS]
-    __shared__ float sw[kC * 9];
     griddep_wait();
-    const int t = threadIdx.x, k = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = lane >> 2, q = lane & 3;
+    const int k = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
     const __nv_bfloat16* img = in + (int64_t)k * H * W * kC;
     for (int c = t; c < IH * IW * 4; c += 256) {
         const int px = c >> 2, ch = c & 3;
@@ -256,23 +345,55 @@ __global__ void __launch_bounds__(256) cnn_last_kernel(const __nv_bfloat16* __re
             v = __ldg(reinterpret_cast<const uint4*>(img + ((int64_t)yy * W + xx) * kC) + ch);
         *reinterpret_cast<uint4*>(tin + px * PXS + ch * 8) = v;
     }
-    for (int c = t; c < kC * 9; c += 256) sw[c] = (&P->w7[0][0])[c];
+    // B column 0: w7[ci][tap] split into BF16 hi + lo; lanes with g != 0 hold zeros
+    uint32_t bh[9][2][2], bl[9][2][2];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int ci = 16 * ks + 2 * q + 8 * j;
+                const float w0 = g == 0 ? __ldg(&P->w7[ci][tap]) : 0.f, w1 = g == 0 ? __ldg(&P->w7[ci + 1][tap]) : 0.f;
+                const __nv_bfloat162 hi = __floats2bfloat162_rn(w0, w1);
+                const float2 hf = __bfloat1622float2(hi);
+                bh[tap][ks][j] = *reinterpret_cast<const uint32_t*>(&hi);
+                bl[tap][ks][j] = pack_bf16(w0 - hf.x, w1 - hf.y);
+            }
     __syncthreads();
-    const int py = t / TW, px = t % TW, yy = y0 + py, xx = x0 + px;
-    if (yy >= H || xx >= W) return;
-    float a = P->b7;
+    float acc[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[h][e] = 0.f;
+    const int arow = lane & 15, acol = (lane >> 4) * 8;
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
-        const __nv_bfloat16* p = tin + ((py + tap / 3) * IW + px + tap % 3) * PXS;
+        const int dy = tap / 3, dx = tap % 3;
 #pragma unroll
-        for (int ci = 0; ci < kC; ci += 2) {
-            const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p + ci));
-            a = fmaf(sw[ci * 9 + tap], v.x, a);
-            a = fmaf(sw[(ci + 1) * 9 + tap], v.y, a);
+        for (int ks = 0; ks < 2; ++ks) {
+            uint32_t a0[4], a1[4];
+            const __nv_bfloat16* ap = tin + ((warp + dy) * IW + dx + arow) * PXS + ks * 16 + acol;
+            ldmatrix_x4(a0, ap);
+            ldmatrix_x4(a1, ap + 16 * PXS);
+            mma_bf16(acc[0], a0, bh[tap][ks][0], bh[tap][ks][1]);
+            mma_bf16(acc[0], a0, bl[tap][ks][0], bl[tap][ks][1]);
+            mma_bf16(acc[1], a1, bh[tap][ks][0], bh[tap][ks][1]);
+            mma_bf16(acc[1], a1, bl[tap][ks][0], bl[tap][ks][1]);
         }
     }
-    const int64_t o = (int64_t)k * H * W + (int64_t)yy * W + xx;
-    out[o] = mode == 0 ? __ldg(r + o) - 255.f * a : a;
+    if (q != 0) return;                                  // column 0 lives in lanes q = 0 (c0, c2)
+    const float b7 = __ldg(&P->b7);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int yy = y0 + warp, xx = x0 + 16 * h + g + 8 * half;
+            if (yy >= H || xx >= W) continue;
+            const float a = acc[h][2 * half] + b7;
+            const int64_t o = (int64_t)k * H * W + (int64_t)yy * W + xx;
+            out[o] = mode == 0 ? __ldg(r + o) - 255.f * a : a;
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -563,19 +684,26 @@ cudaError_t cnn_pack(const float* params, void* packed, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-static size_t conv_smem() { return (size_t)(IH * IW + 9 * kC) * PXS * 2; }
+template <int EPI>
+static cudaError_t conv32_launch(const __nv_bfloat16* in, int n, int H, int W, const __nv_bfloat16* wts,
+                                 const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(conv32_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kConvSmem);
+    int dev, sms, per_sm;
+    if (!e) e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv32_kernel<EPI>, 256, kConvSmem);
+    if (e) return e;
+    const int64_t tiles = (int64_t)((W + TW - 1) / TW) * ((H + TH - 1) / TH) * n;
+    const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const int grid = (int)(tiles < cap ? tiles : cap);
+    return launch_pdl(conv32_kernel<EPI>, dim3(grid), dim3(256), kConvSmem, s, in, n, H, W, wts, bias, mask, out);
+}
 
 static cudaError_t conv32(int epi, const __nv_bfloat16* in, int n, int H, int W, const __nv_bfloat16* wts,
                           const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out, cudaStream_t s) {
-    dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, n);
-    const size_t smem = conv_smem();
-    cudaError_t e;
-    if (epi == 0) {
-        if ((e = cudaFuncSetAttribute(conv32_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-        return launch_pdl(conv32_kernel<0>, grid, dim3(256), smem, s, in, H, W, wts, bias, mask, out);
-    }
-    if ((e = cudaFuncSetAttribute(conv32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-    return launch_pdl(conv32_kernel<1>, grid, dim3(256), smem, s, in, H, W, wts, bias, mask, out);
+    return epi == 0 ? conv32_launch<0>(in, n, H, W, wts, bias, mask, out, s)
+                    : conv32_launch<1>(in, n, H, W, wts, bias, mask, out, s);
 }
 
 // Forward through layers 0..6 into act[0..6] (each n*H*W*32 bf16), then the
@@ -587,13 +715,15 @@ cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, 
     __nv_bfloat16* act = static_cast<__nv_bfloat16*>(act_buf);
     auto A = [&](int l) { return act + (keep_all ? l : (l & 1)) * plane; };
     dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, n);
-    cudaError_t e = launch_pdl(cnn_first_kernel, grid, dim3(256), 0, s, r, sigma, H, W, P, A(0));
+    cudaError_t e = launch_pdl(cnn_first_tc_kernel, grid, dim3(256), 0, s, r, sigma, H, W, P, A(0));
     for (int l = 1; l <= kMid && !e; ++l)
         e = conv32(0, A(l - 1), n, H, W, &P->wc[l - 1][0][0][0], &P->bm[l - 1][0], nullptr, A(l), s);
     if (e) return e;
     const size_t smem = (size_t)IH * IW * PXS * 2;
-    if ((e = cudaFuncSetAttribute(cnn_last_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-    return launch_pdl(cnn_last_kernel, grid, dim3(256), smem, s, (const __nv_bfloat16*)A(kMid), r, H, W, P, mode, out);
+    if ((e = cudaFuncSetAttribute(cnn_last_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    return launch_pdl(cnn_last_tc_kernel, grid, dim3(256), smem, s, (const __nv_bfloat16*)A(kMid), r, H, W, P, mode,
+                      out);
 }
 
 // Loss and gradients (FP32, parameter layout) of a batch of n crops.
