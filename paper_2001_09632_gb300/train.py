@@ -95,11 +95,12 @@ def psnr(x: torch.Tensor, ref: torch.Tensor) -> torch.Tensor:
 
 
 def make_pairs(h, n_images=512, H=512, W=512, captures=(0, 1, 2, 4, 8, 16, 29), crops=56, crop=64,
-               batch=32, seed=TRAIN_SEED, lam=DEFAULT_LAMBDA, packed=None, large_every=0, log=print):
+               batch=32, seed=TRAIN_SEED, lam=DEFAULT_LAMBDA, packed=None, large_every=0,
+               large_size=(1024, 1024), log=print):
     """(r^t, clean, sigma^t) crops; r^t from plain IDA, or from learned IDA
     when `packed` weights are given (its own trajectories).  A capture index
     listed twice contributes twice the crops.  With large_every = n, every
-    n-th batch uses 1024 x 1024 images (8 per batch) instead."""
+    n-th batch uses 8 images of large_size instead."""
     subrates = (0.1, 0.2, 0.3, 0.4, 0.5)
     gen = torch.Generator(device="cuda").manual_seed(seed)
     R, C, S = [], [], []
@@ -107,7 +108,7 @@ def make_pairs(h, n_images=512, H=512, W=512, captures=(0, 1, 2, 4, 8, 16, 29), 
     for i0 in range(0, n_images, batch):
         j = i0 // batch
         if large_every and j % large_every == large_every - 1:
-            imgs = synth.gen_batch(8, 1024, 1024, seed + i0)
+            imgs = synth.gen_batch(8, large_size[0], large_size[1], seed + i0)
         else:
             imgs = synth.gen_batch(min(batch, n_images - i0), H, W, seed + i0)
         variant = abcs.BBV if j % 2 == 0 else abcs.DD
@@ -308,7 +309,8 @@ def main():
     ap.add_argument("--captures-b", default="1,2,3,5",
                     help="iterations captured along the network's own trajectories (phase B)")
     ap.add_argument("--large-every", type=int, default=0,
-                    help="every n-th training batch of 1024x1024 images (0: none)")
+                    help="every n-th training batch of large images (0: none)")
+    ap.add_argument("--large-size", default="1024,1024", help="H,W of the large training images")
     a = ap.parse_args()
     h = abcs.abcs_create()
     report = {}
@@ -319,15 +321,17 @@ def main():
         # phase A: denoiser inputs along plain-IDA trajectories
         caps_a = tuple(int(x) for x in a.captures_a.split(","))
         caps_b = tuple(int(x) for x in a.captures_b.split(","))
+        large = tuple(int(x) for x in a.large_size.split(","))
         R, C, S = make_pairs(h, n_images=a.images, lam=a.lam, captures=caps_a, crops=48,
-                             large_every=a.large_every)
+                             large_every=a.large_every, large_size=large)
         print(f"phase A: {R.shape[0]} training crops")
         w, hist_a, secs_a = train(h, R, C, S, steps=a.steps)
         # phase B: add inputs along the network's own IDA trajectories, fine-tune
         pk = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
         abcs.abcs_cnn_pack(h, torch.tensor(w, device="cuda"), pk)
         R2, C2, S2 = make_pairs(h, n_images=a.images // 2, lam=a.lam, captures=caps_b, crops=96,
-                                seed=TRAIN_SEED + 5_000_000, packed=pk, large_every=a.large_every)
+                                seed=TRAIN_SEED + 5_000_000, packed=pk, large_every=a.large_every,
+                                large_size=large)
         R, C, S = torch.cat([R, R2]), torch.cat([C, C2]), torch.cat([S, S2])
         del R2, C2, S2
         print(f"phase B: {R.shape[0]} training crops")
