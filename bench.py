@@ -36,6 +36,10 @@ METRIC = "Mpixel/s ABCS sense+recon and IDA/iter; learned vs plain IDA at equal 
 N_IMG, H, W, B, SUBRATE, SEED = 64, 512, 512, 16, 0.3, 1000
 IDA_ITERS, LAMBDA, DF = 10, 2.3, 2.0
 FLUSH_BYTES = 512 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one reconstruct launch on
+# this workload, from an ncu capture of the current kernel (None where none
+# was taken); must be re-measured whenever the kernel changes
+RECON_TRAFFIC = {"fp16x2": 28773120}
 
 
 def _args():
@@ -418,7 +422,10 @@ def main():
                    "measurements_per_step": total_coeffs, "parallelism": f"replicas x{world}"},
         "roofline": {"kernel": "recon_tc_kernel" if prec != abcs.FP32 else "recon_kernel<16>", "bound": "hbm", "achieved": achieved,
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                     "peak_kind": peak_kind, "traffic": None,
+                     "peak_kind": peak_kind, "traffic": RECON_TRAFFIC.get(a.precision),
+                     "traffic_source": "DRAM read + write bytes of one launch of this kernel on this "
+                                       "workload in an ncu capture (most of the FP32 output is still "
+                                       "in L2 when the kernel ends)",
                      "algorithmic_bytes_per_launch": recon_bytes},
         "kernels": {"sense_ms": sense_avg, "reconstruct_ms": recon_avg,
                     "sense_GBps_algorithmic": sense_bytes / (sense_avg * 1e-3) / 1e9,

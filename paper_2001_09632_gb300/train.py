@@ -8,6 +8,7 @@ PSNR bookkeeping of the evaluation).
   python -m paper_2001_09632_gb300.train train --out weights.f32
   python -m paper_2001_09632_gb300.train eval --weights weights.f32
   python -m paper_2001_09632_gb300.train video --weights weights.f32  # 1920x1088 DD clip
+  python -m paper_2001_09632_gb300.train time --iters 2               # learned IDA throughput
 
 Training pairs follow the method itself: synthetic images are sensed
 (AL-DCT-BBV or AL-DCT-DD, subrate drawn from {0.1, ..., 0.5}), plain IDA
@@ -294,9 +295,30 @@ def video_eval(h, weights, n_frames=120, H=1088, W=1920, batch=30, subrate=0.25,
     return res
 
 
+def time_learned(h, weights, iters=2, n=16, H=512, W=512, subrate=0.3, seed=77, log=print):
+    """Learned IDA on n seeded images: one warm-up call, one timed call.
+    Returns Gpixel * iteration / s."""
+    p = torch.tensor(weights, device="cuda")
+    packed = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
+    abcs.abcs_cnn_pack(h, p, packed)
+    sd = Sensed(h, synth.gen_batch(n, H, W, seed), 16, subrate, abcs.BBV)
+    x = sd.ida(h, iters, abcs.DEN_CNN, DEFAULT_LAMBDA, packed)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sd.ida(h, iters, abcs.DEN_CNN, DEFAULT_LAMBDA, packed, x)
+    e1.record()
+    torch.cuda.synchronize()
+    assert abcs.abcs_sync_status(h) == 0
+    ms = e0.elapsed_time(e1)
+    v = n * sd.Hc * sd.Wc * iters / (ms * 1e-3) / 1e9
+    log(json.dumps({"learned_ida_iters": iters, "images": n, "ms": ms, "Gpx_iter_per_s": v}))
+    return v
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["tune-lambda", "train", "eval", "video", "all"])
+    ap.add_argument("cmd", choices=["tune-lambda", "train", "eval", "video", "time", "all"])
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--images", type=int, default=512)
@@ -311,6 +333,7 @@ def main():
     ap.add_argument("--large-every", type=int, default=0,
                     help="every n-th training batch of large images (0: none)")
     ap.add_argument("--large-size", default="1024,1024", help="H,W of the large training images")
+    ap.add_argument("--iters", type=int, default=2, help="time: learned IDA iterations")
     a = ap.parse_args()
     h = abcs.abcs_create()
     report = {}
@@ -346,6 +369,8 @@ def main():
         w = load_weights(a.out if a.cmd == "all" else a.weights)
         report["eval"] = evaluate(h, w, n=a.eval_images, lam=a.lam)
         report["lambda"] = a.lam
+    if a.cmd == "time":
+        time_learned(h, load_weights(a.weights), iters=a.iters)
     if a.cmd in ("video", "all"):
         w = load_weights(a.out if a.cmd == "all" else a.weights)
         report["video"] = video_eval(h, w, lam=a.lam)
