@@ -24,7 +24,7 @@ Functions and the passages they follow:
   A, At ........................... Eq. 26 (block-diagonal sensing matrix and its transpose)
   ida ............................. Eqs. 13, 15, 25 with the Onsager term of Eq. 28
   tidct_denoise ................... the plain denoiser D_sigma (stand-in; see docstring)
-  cnn_* / adam_step ............... the learned residual denoiser (DnCNN-style, Sec. VI-4)
+  cnn_*, density_map, adam_step ... the learned residual denoiser (DnCNN-style, Sec. VI-4)
   psnr, ssim ...................... quality measures (Sec. I, ref. [18])
 """
 from __future__ import annotations
@@ -462,7 +462,7 @@ def ida(y: np.ndarray, counts: np.ndarray, Hc: int, Wc: int, B: int, iters: int,
 # --------------------------------------------------------------------------
 # Learned denoiser: a DnCNN-style residual CNN (Sec. VI-4, ref. [21]).
 # --------------------------------------------------------------------------
-def cnn_init(c_in: int = 2, width: int = 32, depth: int = 8, seed: int = 0):
+def cnn_init(c_in: int = 3, width: int = 32, depth: int = 8, seed: int = 0):
     """He-normal weights, zero biases.  Layers: conv3x3 c_in->width + ReLU,
     (depth - 2) x [conv3x3 width->width + ReLU], conv3x3 width->1.
     Weight layout w[c_out, c_in, 3, 3]."""
@@ -491,12 +491,25 @@ def conv3x3(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
     return out
 
 
-def cnn_input(r: np.ndarray, sigma: float) -> np.ndarray:
-    """Network input: channel 0 = r / 255, channel 1 = sigma / 255 everywhere.
-    Reading: the noise level enters as a constant map so one network serves
-    every sigma of the IDA schedule."""
+def density_map(counts, H: int, W: int, B: int) -> np.ndarray:
+    """Per-pixel measured fraction m_i / B^2 of the pixel's block, over the
+    cropped image (block i in raster order).  Side information the decoder
+    has (Alg. 1/2 output: the counts)."""
+    nbh, nbw = H // B, W // B
+    m = np.asarray(counts, dtype=np.float64).reshape(nbh, nbw) / float(B * B)
+    return np.kron(m, np.ones((B, B)))
+
+
+def cnn_input(r: np.ndarray, sigma: float, density=None) -> np.ndarray:
+    """Network input: channel 0 = r / 255, channel 1 = sigma / 255
+    everywhere, channel 2 = the measured fraction of the pixel's block
+    (zero when not given).  Readings: the noise level enters as a constant
+    map so one network serves every sigma of the IDA schedule; the density
+    tells it where coefficients are missing (the error of the first
+    iterate A^T y is the energy of the unmeasured coefficients)."""
+    d = np.zeros(np.shape(r)) if density is None else np.asarray(density, dtype=np.float64)
     return np.stack([np.asarray(r, dtype=np.float64) / 255.0,
-                     np.full(np.shape(r), sigma / 255.0)])
+                     np.full(np.shape(r), sigma / 255.0), d])
 
 
 def cnn_forward(params, x_in: np.ndarray):
@@ -511,9 +524,9 @@ def cnn_forward(params, x_in: np.ndarray):
     return h[0], acts
 
 
-def cnn_denoise(params, r: np.ndarray, sigma: float) -> np.ndarray:
-    """x_hat = r - 255 * net(r/255, sigma/255): residual learning (DnCNN)."""
-    n, _ = cnn_forward(params, cnn_input(r, sigma))
+def cnn_denoise(params, r: np.ndarray, sigma: float, density=None) -> np.ndarray:
+    """x_hat = r - 255 * net(r/255, sigma/255, density): residual learning (DnCNN)."""
+    n, _ = cnn_forward(params, cnn_input(r, sigma, density))
     return np.asarray(r, dtype=np.float64) - 255.0 * n
 
 
@@ -532,9 +545,9 @@ def conv3x3_backward(x: np.ndarray, w: np.ndarray, g: np.ndarray):
     return gxp[:, 1:-1, 1:-1], gw, gb
 
 
-def cnn_loss_and_grads(params, r: np.ndarray, sigma: float, clean: np.ndarray):
+def cnn_loss_and_grads(params, r: np.ndarray, sigma: float, clean: np.ndarray, density=None):
     """L = mean((x_hat - clean)^2) / 255^2 for one image, and dL/dparams."""
-    x_in = cnn_input(r, sigma)
+    x_in = cnn_input(r, sigma, density)
     n, acts = cnn_forward(params, x_in)
     resid = (np.asarray(r, dtype=np.float64) - 255.0 * n - clean) / 255.0
     numel = resid.size

@@ -70,9 +70,10 @@ _SIGS = {
     "abcs_cnn_param_count": [],
     "abcs_cnn_packed_bytes": [],
     "abcs_cnn_pack": [_P, _P, _P, _P],
-    "abcs_cnn_denoise": [_P, _P, _P, _P, _I, _I, _I, _P, _P],
-    "abcs_cnn_grad": [_P, _P, _P, _P, _P, _I, _I, _I, _P, _P, _P],
-    "abcs_cnn_train_step": [_P, _P, _P, _P, _I, _D, _P, _P, _P, _P, _I, _I, _I, _P, _P],
+    "abcs_cnn_denoise": [_P, _P, _P, _P, _P, _I, _I, _I, _P, _P],
+    "abcs_cnn_grad": [_P, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P, _P],
+    "abcs_cnn_train_step": [_P, _P, _P, _P, _I, _D, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P],
+    "abcs_density_map": [_P, _P, _I, _I, _I, _I, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -184,21 +185,27 @@ def abcs_cnn_pack(h, params, packed, stream=None) -> None:
     _check(lib.abcs_cnn_pack(h, _ptr(params), _ptr(packed), _stream(stream)))
 
 
-def abcs_cnn_denoise(h, packed, inp, sigma, n_img, H, W, out, stream=None) -> None:
-    _check(lib.abcs_cnn_denoise(h, _ptr(packed), _ptr(inp), _ptr(sigma), n_img, H, W, _ptr(out),
+def abcs_cnn_denoise(h, packed, inp, sigma, density, n_img, H, W, out, stream=None) -> None:
+    """density: per-pixel measured fraction (abcs_density_map) or None."""
+    _check(lib.abcs_cnn_denoise(h, _ptr(packed), _ptr(inp), _ptr(sigma), _ptr(density), n_img, H, W, _ptr(out),
                                 _stream(stream)))
 
 
-def abcs_cnn_grad(h, packed, r, clean, sigma, n, H, W, grad, loss, stream=None) -> None:
-    _check(lib.abcs_cnn_grad(h, _ptr(packed), _ptr(r), _ptr(clean), _ptr(sigma), n, H, W, _ptr(grad),
-                             _ptr(loss), _stream(stream)))
+def abcs_cnn_grad(h, packed, r, clean, sigma, density, n, H, W, grad, loss, stream=None) -> None:
+    _check(lib.abcs_cnn_grad(h, _ptr(packed), _ptr(r), _ptr(clean), _ptr(sigma), _ptr(density), n, H, W,
+                             _ptr(grad), _ptr(loss), _stream(stream)))
 
 
-def abcs_cnn_train_step(h, params, adam_m, adam_v, step, lr, packed, r, clean, sigma, n, H, W, loss,
+def abcs_cnn_train_step(h, params, adam_m, adam_v, step, lr, packed, r, clean, sigma, density, n, H, W, loss,
                         stream=None) -> None:
     _check(lib.abcs_cnn_train_step(h, _ptr(params), _ptr(adam_m), _ptr(adam_v), step, lr, _ptr(packed),
-                                   _ptr(r), _ptr(clean), _ptr(sigma), n, H, W, _ptr(loss),
+                                   _ptr(r), _ptr(clean), _ptr(sigma), _ptr(density), n, H, W, _ptr(loss),
                                    _stream(stream)))
+
+
+def abcs_density_map(h, counts, n_img, H, W, B, out, stream=None) -> None:
+    """out[k][y][x] = m_i / B^2 of the block holding pixel (y, x)."""
+    _check(lib.abcs_density_map(h, _ptr(counts), n_img, H, W, B, _ptr(out), _stream(stream)))
 
 
 def abcs_sync_status(h, stream=None) -> int:

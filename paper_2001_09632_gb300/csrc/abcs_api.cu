@@ -409,6 +409,7 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
     const size_t o_part = c.take<double>((size_t)n_img * cpi);
     const size_t o_sig = c.take<float>(n_img);
     const size_t o_act = c.take<uint16_t>(denoiser == ABCS_DEN_CNN ? (size_t)2 * npx * 32 : 0);
+    const size_t o_den = c.take<float>(denoiser == ABCS_DEN_CNN ? npx : 0);
     const size_t o_x = c.take<float>(capturing ? npx : 0);
     abcs_status st = ensure_ws(h, c.off);
     if (st) return st;
@@ -425,6 +426,8 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
     a.inv_df = (float)(1.0 / damping);
     a.status = h->status;
     if (capturing) x_out = at<float>(h, o_x);
+    float* dens = at<float>(h, o_den);
+    if (denoiser == ABCS_DEN_CNN) ABCS_CUDA(launch_density(g, counts, dens, s), "density launch");
     const float* x_cur = nullptr;        // x^0 = 0
     const float* z_prev = nullptr;       // z^{-1} = 0
     for (int t = 0; t < iters; ++t) {
@@ -445,7 +448,8 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
             ABCS_CUDA(launch_tidct(a.r, x_out, n_img, g.Hc, g.Wc, sig, (float)lambda, s), "tidct launch");
             x_cur = x_out;
         } else if (denoiser == ABCS_DEN_CNN) {
-            ABCS_CUDA(cnn_forward(cnn_weights, a.r, sig, n_img, g.Hc, g.Wc, at<void>(h, o_act), 0, 0, x_out, s),
+            ABCS_CUDA(cnn_forward(cnn_weights, a.r, sig, dens, n_img, g.Hc, g.Wc, at<void>(h, o_act), 0, 0, x_out,
+                                  s),
                       "cnn launch");
             x_cur = x_out;
         } else {
@@ -633,6 +637,20 @@ abcs_status abcs_ida_batch(abcs_handle* h, const abcs_image_desc* desc, int n_im
     return ABCS_OK;
 }
 
+abcs_status abcs_density_map(abcs_handle* h, const int32_t* counts, int n_img, int H, int W, int B, float* out,
+                             void* stream) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    if (!counts || !out) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (!valid_B(B)) return fail(ABCS_ERR_INVALID_ARG, "B must be 4, 8, 16 or 32");
+    if (H < B || W < B) return fail(ABCS_ERR_INVALID_ARG, "image smaller than one block");
+    if (n_img < 1 || n_img > 65535) return fail(ABCS_ERR_INVALID_ARG, "n_img must be in [1, 65535]");
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(ABCS_ERR_CUDA, "cannot select the handle's device");
+    ABCS_CUDA(launch_density(make_geom(n_img, H, W, B, W, 0), counts, out, static_cast<cudaStream_t>(stream)),
+              "density launch");
+    return ABCS_OK;
+}
+
 int64_t abcs_cnn_param_count(void) { return cnn_param_count(); }
 size_t abcs_cnn_packed_bytes(void) { return cnn_packed_bytes(); }
 
@@ -644,8 +662,8 @@ abcs_status abcs_cnn_pack(abcs_handle* h, const float* params, void* packed, voi
     return ABCS_OK;
 }
 
-abcs_status abcs_cnn_denoise(abcs_handle* h, const void* packed, const float* in, const float* sigma, int n_img,
-                             int H, int W, float* out, void* stream) {
+abcs_status abcs_cnn_denoise(abcs_handle* h, const void* packed, const float* in, const float* sigma,
+                             const float* density, int n_img, int H, int W, float* out, void* stream) {
     if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
     if (!packed || !in || !sigma || !out) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
     if (in == out) return fail(ABCS_ERR_INVALID_ARG, "in and out must differ");
@@ -655,28 +673,29 @@ abcs_status abcs_cnn_denoise(abcs_handle* h, const void* packed, const float* in
     const size_t o_act = c.take<uint16_t>((size_t)2 * n_img * H * W * 32);
     abcs_status st = ensure_ws(h, c.off);
     if (st) return st;
-    ABCS_CUDA(cnn_forward(packed, in, sigma, n_img, H, W, at<void>(h, o_act), 0, 0, out,
+    ABCS_CUDA(cnn_forward(packed, in, sigma, density, n_img, H, W, at<void>(h, o_act), 0, 0, out,
                           static_cast<cudaStream_t>(stream)),
               "cnn launch");
     return ABCS_OK;
 }
 
 abcs_status abcs_cnn_grad(abcs_handle* h, const void* packed, const float* r, const float* clean, const float* sigma,
-                          int n, int H, int W, float* grad, float* loss, void* stream) {
+                          const float* density, int n, int H, int W, float* grad, float* loss, void* stream) {
     if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
     if (!packed || !r || !clean || !sigma || !grad || !loss) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
     if (n < 1 || n > 65535 || H < 1 || W < 1) return fail(ABCS_ERR_INVALID_ARG, "bad size");
     DeviceGuard dg(h->device);
     abcs_status st = ensure_ws(h, cnn_grad_ws_bytes(n, H, W));
     if (st) return st;
-    ABCS_CUDA(cnn_grad(packed, r, clean, sigma, n, H, W, h->ws, grad, loss, static_cast<cudaStream_t>(stream)),
+    ABCS_CUDA(cnn_grad(packed, r, clean, sigma, density, n, H, W, h->ws, grad, loss,
+                       static_cast<cudaStream_t>(stream)),
               "cnn grad launch");
     return ABCS_OK;
 }
 
 abcs_status abcs_cnn_train_step(abcs_handle* h, float* params, float* adam_m, float* adam_v, int step, double lr,
-                                void* packed, const float* r, const float* clean, const float* sigma, int n, int H,
-                                int W, float* loss, void* stream) {
+                                void* packed, const float* r, const float* clean, const float* sigma,
+                                const float* density, int n, int H, int W, float* loss, void* stream) {
     if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
     if (!params || !adam_m || !adam_v || !packed || !r || !clean || !sigma || !loss)
         return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
@@ -690,7 +709,7 @@ abcs_status abcs_cnn_train_step(abcs_handle* h, float* params, float* adam_m, fl
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     float* grad = reinterpret_cast<float*>(static_cast<char*>(h->ws) + cnn_grad_ws_bytes(n, H, W));
     ABCS_CUDA(cnn_pack(params, packed, s), "cnn pack launch");
-    ABCS_CUDA(cnn_grad(packed, r, clean, sigma, n, H, W, h->ws, grad, loss, s), "cnn grad launch");
+    ABCS_CUDA(cnn_grad(packed, r, clean, sigma, density, n, H, W, h->ws, grad, loss, s), "cnn grad launch");
     ABCS_CUDA(cnn_adam(params, grad, adam_m, adam_v, step, (float)lr, s), "adam launch");
     ABCS_CUDA(cnn_pack(params, packed, s), "cnn pack launch");
     return ABCS_OK;

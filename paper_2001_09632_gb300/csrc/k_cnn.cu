@@ -1,12 +1,13 @@
 // Learned residual denoiser for IDA (a DnCNN-style network, Sec. VI-4):
-//   conv3x3 2->32 + ReLU, 6 x [conv3x3 32->32 + ReLU], conv3x3 32->1,
-//   x_hat = r - 255 * net(r / 255, sigma / 255), zero 'same' padding.
+//   conv3x3 3->32 + ReLU, 6 x [conv3x3 32->32 + ReLU], conv3x3 32->1,
+//   x_hat = r - 255 * net(r / 255, sigma / 255, d), zero 'same' padding,
+//   d = the measured fraction m_i / B^2 of the pixel's block (or 0).
 // Activations and mid-layer weights are BF16 (NHWC, 32 channels = 64 bytes
 // per pixel); every sum accumulates in FP32.  All layers are implicit GEMMs
 // on mma.sync.m16n8k16 with FP32 accumulation: the 32->32 layers in BF16
 // (persistent CTAs, 8 x 32 output tiles, weights resident in shared memory,
 // input tiles double-buffered and fed to the tensor cores with ldmatrix),
-// the first layer (2 channels: r / 255 and sigma / 255) in FP16, the last
+// the first layer (3 channels: r / 255, sigma / 255, d) in FP16, the last
 // (32 -> 1) in BF16 with the weights split hi + lo.
 //
 // Training (fwd + bwd + Adam) reuses the same conv kernel for the input
@@ -23,13 +24,13 @@ namespace abcs {
 // ---------------------------------------------------------------------------
 // Parameter layout (FP32, the same as the FP64 oracle's):
 //   for l in 0..7: w_l[co][ci][3][3], then b_l[co]
-// channel plan: (2->32), 6 x (32->32), (32->1).
+// channel plan: (3->32), 6 x (32->32), (32->1).
 // ---------------------------------------------------------------------------
-constexpr int kC = 32, kMid = 6;
-constexpr int kW0 = kC * 2 * 9, kB0 = kC;
+constexpr int kC = 32, kMid = 6, kIn = 3;
+constexpr int kW0 = kC * kIn * 9, kB0 = kC;
 constexpr int kWm = kC * kC * 9, kBm = kC;
 constexpr int kW7 = kC * 9, kB7 = 1;
-constexpr int kParams = kW0 + kB0 + kMid * (kWm + kBm) + kW7 + kB7;   // 56,385
+constexpr int kParams = kW0 + kB0 + kMid * (kWm + kBm) + kW7 + kB7;   // 56,673
 
 ABCS_HD int param_off_w(int l) {
     return l == 0 ? 0 : (l <= kMid ? kW0 + kB0 + (l - 1) * (kWm + kBm) : kW0 + kB0 + kMid * (kWm + kBm));
@@ -40,7 +41,7 @@ ABCS_HD int param_off_b(int l) {
 
 // Packed device weights (one buffer, offsets in bytes).
 struct CnnPacked {
-    float w0[kC][2][9];             // first layer, FP32 [co][ci][tap]
+    float w0[kC][kIn][9];           // first layer, FP32 [co][ci][tap]
     float b0[kC];
     __nv_bfloat16 wc[kMid][9][kC][kC];   // mid layers, forward [tap][co][ci]
     __nv_bfloat16 wd[kMid][9][kC][kC];   // mid layers, input-gradient [tap'][ci][co], tap' = 8 - tap
@@ -224,10 +225,11 @@ __global__ void __launch_bounds__(256, 3) conv32_kernel(const __nv_bfloat16* __r
 
 // ---------------------------------------------------------------------------
 // First layer on the tensor cores: an implicit GEMM with K = (tap, channel),
-// k = 2 tap + ci (18 values, zero-padded to 32), FP16 operands, FP32
-// accumulation.  Each shared pixel holds the pair (r / 255, sigma / 255) as
-// FP16x2 (sigma is zero outside the image: zero padding of that channel),
-// so one 32-bit shared load is one A-fragment register (pixel, tap).
+// k = 4 tap + ci over the channels (r / 255, sigma / 255, d, 0), 36 values
+// zero-padded to 48, FP16 operands, FP32 accumulation.  Each shared pixel
+// holds the two pairs (r / 255, sigma / 255) and (d, 0) as FP16x2 words
+// (zero outside the image: the zero padding of every channel), so one
+// 32-bit shared load is one A-fragment register.
 // ---------------------------------------------------------------------------
 ABCS_D void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -241,32 +243,43 @@ ABCS_D uint32_t pack_f16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// weight pair p = 2 tap + half of output channel co: (w[r], w[sigma]) or (w[d], 0)
+ABCS_D uint32_t w0_pair(const CnnPacked* P, int co, int p) {
+    if (p >= 18) return 0u;
+    const int tap = p >> 1;
+    return (p & 1) ? pack_f16(__ldg(&P->w0[co][2][tap]), 0.f)
+                   : pack_f16(__ldg(&P->w0[co][0][tap]), __ldg(&P->w0[co][1][tap]));
+}
+
 __global__ void __launch_bounds__(256) cnn_first_tc_kernel(const float* __restrict__ r,
-                                                           const float* __restrict__ sigma, int H, int W,
+                                                           const float* __restrict__ sigma,
+                                                           const float* __restrict__ dens, int H, int W,
                                                            const CnnPacked* __restrict__ P,
                                                            __nv_bfloat16* __restrict__ out) {
-    __shared__ uint32_t tin[IH * IW];                     // (r/255, sigma/255) FP16x2
+    __shared__ uint32_t tin[IH * IW * 2];                 // per pixel: (r, sigma), (d, 0) as FP16x2
     __shared__ __align__(16) __nv_bfloat16 tout[TH * TW * PXS];
     griddep_wait();
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = lane >> 2, q = lane & 3;
     const int k = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
     const float* img = r + (int64_t)k * H * W;
+    const float* dk = dens ? dens + (int64_t)k * H * W : nullptr;
     const float s255 = __ldg(sigma + k) * (1.f / 255.f);
     for (int c = t; c < IH * IW; c += 256) {
         const int yy = y0 - 1 + c / IW, xx = x0 - 1 + c % IW;
         const bool in_img = yy >= 0 && yy < H && xx >= 0 && xx < W;
-        tin[c] = in_img ? pack_f16(__ldg(img + (int64_t)yy * W + xx) * (1.f / 255.f), s255) : 0u;
+        const int64_t o = (int64_t)yy * W + xx;
+        tin[2 * c] = in_img ? pack_f16(__ldg(img + o) * (1.f / 255.f), s255) : 0u;
+        tin[2 * c + 1] = (in_img && dk) ? pack_f16(__ldg(dk + o), 0.f) : 0u;
     }
-    // B fragments: B[k][co] = w0[co][ci][tap], k = 2 tap + ci; ks 0: taps 0..7, ks 1: tap 8
-    uint32_t b[2][4][2];
+    // B fragments: ks covers pairs 8 ks .. 8 ks + 7; b0 = pair 8 ks + q, b1 = pair 8 ks + q + 4
+    uint32_t b[3][4][2];
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        const int co = 8 * nt + g;
-        b[0][nt][0] = pack_f16(__ldg(&P->w0[co][0][q]), __ldg(&P->w0[co][1][q]));
-        b[0][nt][1] = pack_f16(__ldg(&P->w0[co][0][q + 4]), __ldg(&P->w0[co][1][q + 4]));
-        b[1][nt][0] = q == 0 ? pack_f16(__ldg(&P->w0[co][0][8]), __ldg(&P->w0[co][1][8])) : 0u;
-        b[1][nt][1] = 0u;
-    }
+    for (int ks = 0; ks < 3; ++ks)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            b[ks][nt][0] = w0_pair(P, 8 * nt + g, 8 * ks + q);
+            b[ks][nt][1] = w0_pair(P, 8 * nt + g, 8 * ks + q + 4);
+        }
     __syncthreads();
     float acc[2][4][4];
 #pragma unroll
@@ -277,23 +290,21 @@ __global__ void __launch_bounds__(256) cnn_first_tc_kernel(const float* __restri
             for (int e = 0; e < 4; ++e) acc[h][nt][e] = 0.f;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        // pixel (warp, 16 h + g) and (warp, 16 h + g + 8); tap (dy, dx) reads (warp + dy, col + dx)
-        auto at = [&](int row8, int tap) {
-            return tin[(warp + tap / 3) * IW + 16 * h + g + 8 * row8 + tap % 3];
+        // pixel (warp, 16 h + g + 8 row8); pair p = 2 tap + half reads input (warp + dy, col + dx)
+        auto at = [&](int row8, int p) -> uint32_t {
+            if (p >= 18) return 0u;
+            const int tap = p >> 1;
+            return tin[2 * ((warp + tap / 3) * IW + 16 * h + g + 8 * row8 + tap % 3) + (p & 1)];
         };
-        uint32_t a0[4], a1[4];
-        a0[0] = at(0, q);
-        a0[1] = at(1, q);
-        a0[2] = at(0, q + 4);
-        a0[3] = at(1, q + 4);
-        a1[0] = q == 0 ? at(0, 8) : 0u;
-        a1[1] = q == 0 ? at(1, 8) : 0u;
-        a1[2] = 0u;
-        a1[3] = 0u;
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            mma_f16(acc[h][nt], a0, b[0][nt][0], b[0][nt][1]);
-            mma_f16(acc[h][nt], a1, b[1][nt][0], b[1][nt][1]);
+        for (int ks = 0; ks < 3; ++ks) {
+            uint32_t a[4];
+            a[0] = at(0, 8 * ks + q);
+            a[1] = at(1, 8 * ks + q);
+            a[2] = at(0, 8 * ks + q + 4);
+            a[3] = at(1, 8 * ks + q + 4);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) mma_f16(acc[h][nt], a, b[ks][nt][0], b[ks][nt][1]);
         }
     }
     // epilogue through shared memory: bias, ReLU, BF16, 16-byte stores
@@ -536,17 +547,19 @@ __global__ void __launch_bounds__(256) wgrad32_kernel(const __nv_bfloat16* __res
     if ((t & 7) == 0) dst[kWm + co] = accb;
 }
 
-// Weight gradients of the first layer (inputs r/255, sigma/255; g: 32 ch).
+// Weight gradients of the first layer (inputs r/255, sigma/255, d; g: 32 ch).
 __global__ void __launch_bounds__(256) wgrad_first_kernel(const float* __restrict__ r, const float* __restrict__ sigma,
+                                                          const float* __restrict__ dens,
                                                           const __nv_bfloat16* __restrict__ g, int n, int H, int W,
                                                           float* __restrict__ part) {
     __shared__ float tr[IH * IW];
     __shared__ float tv[IH * IW];        // 1 inside the image, 0 in the zero padding
+    __shared__ float td[IH * IW];        // density, 0 in the padding
     __shared__ float tgg[TH * TW][33];
     const int t = threadIdx.x;
-    // thread t: co = t / 8; threads with t % 8 < 6 own 3 of the 18 (ci, tap) weights each
+    // thread t: co = t / 8; threads with t % 8 < 7 own 4 of the 27 (ci, tap) weights each
     const int co = t >> 3, sub = t & 7;
-    float acc[3] = {0.f, 0.f, 0.f};
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
     float accb = 0.f;
     const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH, ntiles = tx * ty * n;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -557,8 +570,10 @@ __global__ void __launch_bounds__(256) wgrad_first_kernel(const float* __restric
         for (int c = t; c < IH * IW; c += 256) {
             const int yy = y0 - 1 + c / IW, xx = x0 - 1 + c % IW;
             const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
-            tr[c] = in ? __ldg(r + ((int64_t)k * H + yy) * W + xx) * (1.f / 255.f) : 0.f;
+            const int64_t o = ((int64_t)k * H + yy) * W + xx;
+            tr[c] = in ? __ldg(r + o) * (1.f / 255.f) : 0.f;
             tv[c] = in ? 1.f : 0.f;
+            td[c] = (in && dens) ? __ldg(dens + o) : 0.f;
         }
         for (int c = t; c < TH * TW * kC / 2; c += 256) {
             const int px = c / (kC / 2), cp = (c % (kC / 2)) * 2;
@@ -571,25 +586,28 @@ __global__ void __launch_bounds__(256) wgrad_first_kernel(const float* __restric
             tgg[px][cp + 1] = v.y;
         }
         __syncthreads();
-        if (sub < 6) {
+        if (sub < 7) {
             for (int p = 0; p < TH * TW; ++p) {
                 const float gv = tgg[p][co];
                 if (sub == 0) accb += gv;
                 const int py = p / TW, px = p % TW;
 #pragma unroll
-                for (int e = 0; e < 3; ++e) {
-                    const int idx = sub * 3 + e;            // 0..17 = ci * 9 + tap
-                    const int ci = idx / 9, tap = idx % 9;
-                    const int ti = (py + tap / 3) * IW + px + tap % 3;
-                    const float in = ci == 0 ? tr[ti] : s255 * tv[ti];
-                    acc[e] = fmaf(gv, in, acc[e]);
+                for (int e = 0; e < 4; ++e) {
+                    const int idx = sub * 4 + e;            // 0..26 = ci * 9 + tap
+                    if (idx < kIn * 9) {
+                        const int ci = idx / 9, tap = idx % 9;
+                        const int ti = (py + tap / 3) * IW + px + tap % 3;
+                        const float in = ci == 0 ? tr[ti] : (ci == 1 ? s255 * tv[ti] : td[ti]);
+                        acc[e] = fmaf(gv, in, acc[e]);
+                    }
                 }
             }
         }
     }
     float* dst = part + (int64_t)blockIdx.x * (kW0 + kB0);
-    if (sub < 6)
-        for (int e = 0; e < 3; ++e) dst[co * 18 + sub * 3 + e] = acc[e];
+    if (sub < 7)
+        for (int e = 0; e < 4; ++e)
+            if (sub * 4 + e < kIn * 9) dst[co * kIn * 9 + sub * 4 + e] = acc[e];
     if (sub == 0) dst[kW0 + co] = accb;
 }
 
@@ -708,14 +726,14 @@ static cudaError_t conv32(int epi, const __nv_bfloat16* in, int n, int H, int W,
 
 // Forward through layers 0..6 into act[0..6] (each n*H*W*32 bf16), then the
 // last layer into out (mode 0: denoised image, mode 1: network output n).
-cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, int n, int H, int W,
-                        void* act_buf, int keep_all, int mode, float* out, cudaStream_t s) {
+cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, const float* dens, int n, int H,
+                        int W, void* act_buf, int keep_all, int mode, float* out, cudaStream_t s) {
     const CnnPacked* P = static_cast<const CnnPacked*>(packed);
     const int64_t plane = (int64_t)n * H * W * kC;
     __nv_bfloat16* act = static_cast<__nv_bfloat16*>(act_buf);
     auto A = [&](int l) { return act + (keep_all ? l : (l & 1)) * plane; };
     dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, n);
-    cudaError_t e = launch_pdl(cnn_first_tc_kernel, grid, dim3(256), 0, s, r, sigma, H, W, P, A(0));
+    cudaError_t e = launch_pdl(cnn_first_tc_kernel, grid, dim3(256), 0, s, r, sigma, dens, H, W, P, A(0));
     for (int l = 1; l <= kMid && !e; ++l)
         e = conv32(0, A(l - 1), n, H, W, &P->wc[l - 1][0][0][0], &P->bm[l - 1][0], nullptr, A(l), s);
     if (e) return e;
@@ -728,8 +746,8 @@ cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, 
 
 // Loss and gradients (FP32, parameter layout) of a batch of n crops.
 // Workspace: act (7 planes), gbuf (2 planes), gn (n*H*W floats), parts.
-cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, const float* sigma, int n, int H, int W,
-                     void* ws, float* grad, float* loss, cudaStream_t s) {
+cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, const float* sigma, const float* dens,
+                     int n, int H, int W, void* ws, float* grad, float* loss, cudaStream_t s) {
     const CnnPacked* P = static_cast<const CnnPacked*>(packed);
     const int64_t px = (int64_t)n * H * W, plane = px * kC;
     char* w = static_cast<char*>(ws);
@@ -740,7 +758,7 @@ cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, con
     const int nparts = 304;
     float* part = gn + px;                                       // nparts * (kWm + kBm)
     double* lpart = reinterpret_cast<double*>(part + (size_t)nparts * (kWm + kBm));
-    cudaError_t e = cnn_forward(packed, r, sigma, n, H, W, act, 1, 1, nout, s);
+    cudaError_t e = cnn_forward(packed, r, sigma, dens, n, H, W, act, 1, 1, nout, s);
     if (e) return e;
     cnn_loss_kernel<<<256, 256, 0, s>>>(nout, r, clean, px, gn, lpart);
     reduce_loss_kernel<<<1, 32, 0, s>>>(lpart, 256, loss);
@@ -766,7 +784,7 @@ cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, con
         if (e) return e;
         cur = 1 - cur;
     }
-    wgrad_first_kernel<<<np, 256, 0, s>>>(r, sigma, gb + cur * plane, n, H, W, part);
+    wgrad_first_kernel<<<np, 256, 0, s>>>(r, sigma, dens, gb + cur * plane, n, H, W, part);
     reduce_parts_kernel<<<(kW0 + kB0 + 255) / 256, 256, 0, s>>>(part, np, kW0 + kB0, grad);
     return cudaGetLastError();
 }

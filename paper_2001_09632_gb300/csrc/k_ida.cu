@@ -428,7 +428,27 @@ __global__ void __launch_bounds__(256, ABCS_BATCH_MINB) ida_batch_kernel(BatchAr
     }
 }
 
+// d[k][y][x] = m_i / B^2 of the block holding pixel (y, x) of image k
+__global__ void __launch_bounds__(256) density_kernel(ImgGeom g, const int32_t* __restrict__ counts,
+                                                      float* __restrict__ out) {
+    griddep_wait();
+    const int64_t npx = (int64_t)g.n_img * g.Hc * g.Wc;
+    const float inv = 1.f / (float)(g.B * g.B);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = p / ((int64_t)g.Hc * g.Wc);
+        const int rem = (int)(p - k * g.Hc * g.Wc), y = rem / g.Wc, x = rem - y * g.Wc;
+        out[p] = (float)__ldg(counts + k * g.n_blocks + (int64_t)(y / g.B) * g.nbw + x / g.B) * inv;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_density(const ImgGeom& g, const int32_t* counts, float* out, cudaStream_t s) {
+    const int64_t npx = (int64_t)g.n_img * g.Hc * g.Wc;
+    const int64_t want = (npx + 255) / 256;
+    const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+    return launch_pdl(density_kernel, dim3(grid > 0 ? grid : 1), dim3(256), 0, s, g, counts, out);
+}
 
 int ida_ctas_per_image(const ImgGeom& g) {
     const int NB = kTileCols / g.B;

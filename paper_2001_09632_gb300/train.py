@@ -44,7 +44,7 @@ def load_weights(path: str = WEIGHTS) -> np.ndarray:
 def init_params(seed: int) -> np.ndarray:
     """He-normal weights (last layer x 0.1), zero biases, in the ABI's layout."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    chans = [2] + [32] * 7 + [1]
+    chans = [3] + [32] * 7 + [1]
     out = []
     for l in range(8):
         ci, co = chans[l], chans[l + 1]
@@ -72,6 +72,9 @@ class Sensed:
         self.y = torch.empty(cap, dtype=torch.float32, device="cuda")
         abcs.abcs_sense(h, self.d_img, n, H, W, W, H * W, B, subrate, variant, abcs.FP32,
                         self.counts, self.offsets, self.y, cap)
+        # the learned denoiser's third input: measured fraction of each pixel's block
+        self.density = torch.empty((n, self.Hc, self.Wc), dtype=torch.float32, device="cuda")
+        abcs.abcs_density_map(h, self.counts, n, H, W, B, self.density)
 
     def ida(self, h, iters, denoiser, lam=DEFAULT_LAMBDA, packed=None, x=None):
         x = torch.empty((self.n, self.Hc, self.Wc), dtype=torch.float32, device="cuda") if x is None else x
@@ -104,7 +107,7 @@ def make_pairs(h, n_images=512, H=512, W=512, captures=(0, 1, 2, 4, 8, 16, 29), 
     n-th batch uses 8 images of large_size instead."""
     subrates = (0.1, 0.2, 0.3, 0.4, 0.5)
     gen = torch.Generator(device="cuda").manual_seed(seed)
-    R, C, S = [], [], []
+    R, C, S, D = [], [], [], []
     t0 = time.time()
     for i0 in range(0, n_images, batch):
         j = i0 // batch
@@ -125,14 +128,15 @@ def make_pairs(h, n_images=512, H=512, W=512, captures=(0, 1, 2, 4, 8, 16, 29), 
             kk = torch.arange(n, device="cuda")[:, None, None, None]
             R.append(r[kk, rows, cols].reshape(-1, crop, crop))
             C.append(sd.clean[kk, rows, cols].reshape(-1, crop, crop))
+            D.append(sd.density[kk, rows, cols].reshape(-1, crop, crop))
             S.append(s[:, None].expand(n, crops).reshape(-1))
         if j % 8 == 0:
             log(f"pairs: {i0 + batch}/{n_images} images, {sum(x.shape[0] for x in R)} crops, {time.time() - t0:.1f}s")
     assert abcs.abcs_sync_status(h) == 0
-    return torch.cat(R), torch.cat(C), torch.cat(S)
+    return torch.cat(R), torch.cat(C), torch.cat(S), torch.cat(D)
 
 
-def train(h, R, C, S, steps=4000, batch=128, lr=1e-3, seed=1, params=None, log=print):
+def train(h, R, C, S, D, steps=4000, batch=128, lr=1e-3, seed=1, params=None, log=print):
     n, crop = R.shape[0], R.shape[1]
     p = torch.tensor(init_params(seed) if params is None else params, device="cuda")
     m, v = torch.zeros_like(p), torch.zeros_like(p)
@@ -143,9 +147,9 @@ def train(h, R, C, S, steps=4000, batch=128, lr=1e-3, seed=1, params=None, log=p
     t0 = time.time()
     for step in range(1, steps + 1):
         idx = torch.randint(0, n, (batch,), device="cuda", generator=gen)
-        rb, cb, sb = R[idx].contiguous(), C[idx].contiguous(), S[idx].contiguous()
+        rb, cb, sb, db = R[idx].contiguous(), C[idx].contiguous(), S[idx].contiguous(), D[idx].contiguous()
         lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * (step - 1) / steps))     # cosine decay
-        abcs.abcs_cnn_train_step(h, p, m, v, step, lr_t, packed, rb, cb, sb, batch, crop, crop, loss)
+        abcs.abcs_cnn_train_step(h, p, m, v, step, lr_t, packed, rb, cb, sb, db, batch, crop, crop, loss)
         if step % 200 == 0 or step == 1:
             l = loss.item()
             hist.append((step, l))
@@ -326,13 +330,13 @@ def main():
     ap.add_argument("--lam", type=float, default=DEFAULT_LAMBDA)
     ap.add_argument("--eval-images", type=int, default=128)
     ap.add_argument("--report", default=None, help="write a JSON report here")
-    ap.add_argument("--captures-a", default="0,1,2,3,5,8,15,29",
+    ap.add_argument("--captures-a", default="0,0,0,1,2,3,5,8,15,29",
                     help="IDA iterations whose denoiser inputs form the phase-A crops (repeat to weight)")
-    ap.add_argument("--captures-b", default="1,2,3,5",
+    ap.add_argument("--captures-b", default="0,0,1,2,3,5",
                     help="iterations captured along the network's own trajectories (phase B)")
-    ap.add_argument("--large-every", type=int, default=0,
+    ap.add_argument("--large-every", type=int, default=3,
                     help="every n-th training batch of large images (0: none)")
-    ap.add_argument("--large-size", default="1024,1024", help="H,W of the large training images")
+    ap.add_argument("--large-size", default="1088,1920", help="H,W of the large training images")
     ap.add_argument("--iters", type=int, default=2, help="time: learned IDA iterations")
     a = ap.parse_args()
     h = abcs.abcs_create()
@@ -345,25 +349,25 @@ def main():
         caps_a = tuple(int(x) for x in a.captures_a.split(","))
         caps_b = tuple(int(x) for x in a.captures_b.split(","))
         large = tuple(int(x) for x in a.large_size.split(","))
-        R, C, S = make_pairs(h, n_images=a.images, lam=a.lam, captures=caps_a, crops=48,
-                             large_every=a.large_every, large_size=large)
+        R, C, S, D = make_pairs(h, n_images=a.images, lam=a.lam, captures=caps_a, crops=48,
+                                large_every=a.large_every, large_size=large)
         print(f"phase A: {R.shape[0]} training crops")
-        w, hist_a, secs_a = train(h, R, C, S, steps=a.steps)
+        w, hist_a, secs_a = train(h, R, C, S, D, steps=a.steps)
         # phase B: add inputs along the network's own IDA trajectories, fine-tune
         pk = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
         abcs.abcs_cnn_pack(h, torch.tensor(w, device="cuda"), pk)
-        R2, C2, S2 = make_pairs(h, n_images=a.images // 2, lam=a.lam, captures=caps_b, crops=96,
-                                seed=TRAIN_SEED + 5_000_000, packed=pk, large_every=a.large_every,
-                                large_size=large)
-        R, C, S = torch.cat([R, R2]), torch.cat([C, C2]), torch.cat([S, S2])
-        del R2, C2, S2
+        R2, C2, S2, D2 = make_pairs(h, n_images=a.images // 2, lam=a.lam, captures=caps_b, crops=96,
+                                    seed=TRAIN_SEED + 5_000_000, packed=pk, large_every=a.large_every,
+                                    large_size=large)
+        R, C, S, D = torch.cat([R, R2]), torch.cat([C, C2]), torch.cat([S, S2]), torch.cat([D, D2])
+        del R2, C2, S2, D2
         print(f"phase B: {R.shape[0]} training crops")
-        w, hist_b, secs_b = train(h, R, C, S, steps=a.steps, lr=3e-4, params=w, seed=2)
+        w, hist_b, secs_b = train(h, R, C, S, D, steps=a.steps, lr=3e-4, params=w, seed=2)
         os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
         w.astype("<f4").tofile(a.out)
         report["train"] = {"crops": int(R.shape[0]), "steps": [a.steps, a.steps], "seconds": secs_a + secs_b,
                            "loss": {"A": hist_a, "B": hist_b}}
-        del R, C, S
+        del R, C, S, D
         torch.cuda.empty_cache()
     if a.cmd in ("eval", "all"):
         w = load_weights(a.out if a.cmd == "all" else a.weights)

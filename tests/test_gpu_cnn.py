@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _params(seed=0, scale_last=1.0):
-    p = O.cnn_init(c_in=2, width=32, depth=8, seed=seed)
+    p = O.cnn_init(c_in=3, width=32, depth=8, seed=seed)
     rng = np.random.default_rng(seed + 1)
     out = []
     for l, (w, b) in enumerate(p):
@@ -65,22 +65,43 @@ def _noisy(n, H, W, seed, sigma):
     return clean, clean + rng.standard_normal(clean.shape) * sigma
 
 
+def _density(n, H, W, seed):
+    """A per-pixel measured-fraction plane: random counts over 8 x 8 blocks."""
+    rng = np.random.default_rng(seed)
+    nbh, nbw = -(-H // 8), -(-W // 8)
+    d = np.stack([np.kron(rng.integers(0, 65, (nbh, nbw)) / 64.0, np.ones((8, 8)))[:H, :W] for _ in range(n)])
+    return d.astype(np.float32)
+
+
+def test_density_map_matches_oracle(handle):
+    for (H, W, B) in ((48, 80, 16), (40, 24, 8), (64, 96, 32)):
+        img = synth.gen_image(H, W, 3)
+        from tests import gpu_util as G
+        got = G.sense(handle, img[None], B, 0.3, O.BBV)
+        out = torch.full((1, (H // B) * B, (W // B) * B), float("nan"), dtype=torch.float32, device="cuda")
+        abcs.abcs_density_map(handle, got["d"][0], 1, H, W, B, out)
+        assert abcs.abcs_sync_status(handle) == 0
+        assert np.array_equal(out.cpu().numpy()[0], O.density_map(got["counts"], H, W, B).astype(np.float32))
+
+
 @pytest.mark.parametrize("n,H,W", [(1, 24, 40), (2, 37, 70), (1, 8, 33)])
 def test_cnn_forward_parity(handle, n, H, W):
     params = _params(3)
     ref_p = _bf16_mid(params)
     _, packed = _pack(handle, params)
     clean, r = _noisy(n, H, W, 10, 12.0)
+    dens = _density(n, H, W, 11)
     sig = np.array([12.0, 20.0][:n])
     d_in = torch.tensor(r, dtype=torch.float32, device="cuda")
     d_out = torch.full_like(d_in, float("nan"))
     d_sig = torch.tensor(sig, dtype=torch.float32, device="cuda")
-    abcs.abcs_cnn_denoise(handle, packed, d_in, d_sig, n, H, W, d_out)
+    d_den = torch.tensor(dens, device="cuda")
+    abcs.abcs_cnn_denoise(handle, packed, d_in, d_sig, d_den, n, H, W, d_out)
     assert abcs.abcs_sync_status(handle) == 0
     got = d_out.cpu().numpy()
     r32 = d_in.cpu().numpy().astype(float)
     for k in range(n):
-        ref = O.cnn_denoise(ref_p, r32[k], float(np.float32(sig[k])))
+        ref = O.cnn_denoise(ref_p, r32[k], float(np.float32(sig[k])), dens[k].astype(float))
         n_ref = (r32[k] - ref) / 255.0
         n_got = (r32[k] - got[k]) / 255.0
         err = np.linalg.norm(n_got - n_ref) / np.linalg.norm(n_ref)
@@ -94,16 +115,17 @@ def test_cnn_gradient_parity(handle):
     n, H, W = 2, 24, 40
     clean, r = _noisy(n, H, W, 20, 15.0)
     sig = np.array([15.0, 15.0])
+    dens = _density(n, H, W, 21)
     d = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
-    d_r, d_c, d_s = d(r), d(clean), d(sig)
+    d_r, d_c, d_s, d_d = d(r), d(clean), d(sig), d(dens)
     grad = torch.zeros(abcs.abcs_cnn_param_count(), dtype=torch.float32, device="cuda")
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
-    abcs.abcs_cnn_grad(handle, packed, d_r, d_c, d_s, n, H, W, grad, loss)
+    abcs.abcs_cnn_grad(handle, packed, d_r, d_c, d_s, d_d, n, H, W, grad, loss)
     assert abcs.abcs_sync_status(handle) == 0
     r32, c32 = d_r.cpu().numpy().astype(float), d_c.cpu().numpy().astype(float)
     ref_loss, ref_grads = 0.0, None
     for k in range(n):
-        lk, gk = O.cnn_loss_and_grads(ref_p, r32[k], float(np.float32(sig[k])), c32[k])
+        lk, gk = O.cnn_loss_and_grads(ref_p, r32[k], float(np.float32(sig[k])), c32[k], dens[k].astype(float))
         ref_loss += lk / n
         gk = [(gw / n, gb / n) for gw, gb in gk]
         ref_grads = gk if ref_grads is None else [(a + c, b + e) for (a, b), (c, e) in zip(ref_grads, gk)]
@@ -126,8 +148,8 @@ def test_cnn_training_reduces_loss(handle):
     d_r, d_c, d_s = d(r), d(clean), d(np.full(n, 20.0))
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     losses = []
-    for step in range(1, 61):
-        abcs.abcs_cnn_train_step(handle, d_p, m, v, step, 2e-3, packed, d_r, d_c, d_s, n, H, W, loss)
+    for step in range(1, 61):   # no density plane (NULL: d = 0); the gradient test covers the density path
+        abcs.abcs_cnn_train_step(handle, d_p, m, v, step, 2e-3, packed, d_r, d_c, d_s, None, n, H, W, loss)
         losses.append(loss.item())
     assert abcs.abcs_sync_status(handle) == 0
     assert losses[-1] < 0.75 * losses[0], losses[::10]
@@ -148,8 +170,9 @@ def test_ida_with_cnn_runs_and_matches_oracle_first_iterations(handle):
     tr = torch.zeros((1, 2), dtype=torch.float32, device="cuda")
     abcs.abcs_ida(handle, *got["d"], 1, H, W, B, 2, 2.0, abcs.DEN_CNN, 0.0, packed, x, tr)
     assert abcs.abcs_sync_status(handle) == 0
+    dmap = O.density_map(out["counts"], H, W, B)
     xr, sig = O.ida(out["y"], out["counts"], H, W, B, 2, DF=2.0,
-                    denoiser=lambda rr, s: O.cnn_denoise(ref_p, rr, s))
+                    denoiser=lambda rr, s: O.cnn_denoise(ref_p, rr, s, dmap))
     assert abs(tr.cpu().numpy()[0, 0] - sig[0]) <= 1e-5 * sig[0]
     err = np.linalg.norm(x.cpu().numpy()[0] - xr) / np.linalg.norm(xr)
     assert err <= 2e-2, err

@@ -21,22 +21,44 @@ def test_conv3x3_matches_library_correlation():
 
 
 def test_zero_last_layer_is_identity():
-    params = O.cnn_init(c_in=2, width=8, depth=4, seed=1)
+    params = O.cnn_init(c_in=3, width=8, depth=4, seed=1)
     w, b = params[-1]
     params[-1] = (np.zeros_like(w), np.zeros_like(b))
     r = np.random.default_rng(2).standard_normal((12, 10)) * 50 + 100
     assert np.max(np.abs(O.cnn_denoise(params, r, 7.0) - r)) < 1e-12
 
 
+def test_density_map_blocks():
+    """Each pixel carries m_i / B^2 of its own block (raster order, cropped)."""
+    d = O.density_map([0, 4, 16, 8, 2, 1], 8, 12, 4)
+    assert d.shape == (8, 12)
+    assert d[0, 0] == 0.0 and d[3, 5] == 4 / 16 and d[0, 11] == 1.0
+    assert d[4, 0] == 0.5 and d[7, 7] == 2 / 16 and d[5, 9] == 1 / 16
+
+
+def test_density_channel_enters_the_first_layer():
+    """Only the first layer's channel-2 weights see the density map."""
+    params = O.cnn_init(c_in=3, width=4, depth=3, seed=9)
+    r = np.random.default_rng(5).standard_normal((6, 7)) * 30 + 100
+    d = np.random.default_rng(6).random((6, 7))
+    assert np.max(np.abs(O.cnn_denoise(params, r, 5.0, d) - O.cnn_denoise(params, r, 5.0))) > 0
+    w0, b0 = params[0]
+    w0 = w0.copy()
+    w0[:, 2] = 0.0
+    p2 = [(w0, b0)] + params[1:]
+    assert np.max(np.abs(O.cnn_denoise(p2, r, 5.0, d) - O.cnn_denoise(p2, r, 5.0))) < 1e-12
+
+
 def test_cnn_gradients_central_differences():
     rng = np.random.default_rng(3)
-    params = O.cnn_init(c_in=2, width=4, depth=3, seed=4)
+    params = O.cnn_init(c_in=3, width=4, depth=3, seed=4)
     params = [(w + 0.05 * rng.standard_normal(w.shape), b + 0.05 * rng.standard_normal(b.shape))
               for w, b in params]
     r = rng.standard_normal((8, 8)) * 40 + 120
     clean = r + rng.standard_normal((8, 8)) * 5
+    dens = rng.random((8, 8))
     sigma = 11.0
-    loss, grads = O.cnn_loss_and_grads(params, r, sigma, clean)
+    loss, grads = O.cnn_loss_and_grads(params, r, sigma, clean, dens)
     h = 1e-6
     for l, (w, b) in enumerate(params):
         for arr, g in ((w, grads[l][0]), (b, grads[l][1])):
@@ -44,9 +66,9 @@ def test_cnn_gradients_central_differences():
             for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
                 old = flat[idx]
                 flat[idx] = old + h
-                lp, _ = O.cnn_loss_and_grads(params, r, sigma, clean)
+                lp, _ = O.cnn_loss_and_grads(params, r, sigma, clean, dens)
                 flat[idx] = old - h
-                lm, _ = O.cnn_loss_and_grads(params, r, sigma, clean)
+                lm, _ = O.cnn_loss_and_grads(params, r, sigma, clean, dens)
                 flat[idx] = old
                 fd = (lp - lm) / (2 * h)
                 assert abs(fd - g.reshape(-1)[idx]) < 1e-6 * max(1.0, abs(fd)) + 1e-9, (l, idx)
