@@ -61,6 +61,13 @@ ABCS_D void ldmatrix_x4(uint32_t (&r)[4], const void* p) {
                  : "r"(a));
 }
 
+// the same from a shared-window address
+ABCS_D void ldmatrix_x4s(uint32_t (&r)[4], uint32_t a) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
 ABCS_D void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -97,7 +104,12 @@ ABCS_D void cp_async16_zfill(void* sdst, const void* gsrc, bool valid) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(nbytes) : "memory");
 }
 
-constexpr int kTileElems = IH * IW * kC;          // bf16 of one staged input tile
+// The staged input tile keeps a row stride of IWP = 40 pixels (34 used):
+// since IWP / 2 is a multiple of 4, moving by whole rows (and by 16 pixels)
+// leaves the swizzle term unchanged, so every ldmatrix address of the inner
+// loop is one of eight per-lane bases plus a compile-time offset.
+constexpr int IWP = 40;
+constexpr int kTileElems = IH * IWP * kC;         // bf16 of one staged input tile
 constexpr int kWElems = 9 * kC * kC;              // bf16 of one layer's weights
 constexpr size_t kConvSmem = (size_t)(2 * kTileElems + kWElems) * 2;
 
@@ -130,9 +142,10 @@ __global__ void __launch_bounds__(256, 3) conv32_kernel(const __nv_bfloat16* __r
         const __nv_bfloat16* img = in + (int64_t)k * H * W * kC;
         for (int c = t; c < IH * IW * 4; c += 256) {
             const int px = c >> 2, ch = c & 3;
-            const int yy = y0 - 1 + px / IW, xx = x0 - 1 + px % IW;
+            const int py = px / IW, pxx = px - py * IW;
+            const int yy = y0 - 1 + py, xx = x0 - 1 + pxx;
             const bool v = yy >= 0 && yy < H && xx >= 0 && xx < W;
-            cp_async16_zfill(dst + swz(px, ch), v ? img + ((int64_t)yy * W + xx) * kC + ch * 8 : img, v);
+            cp_async16_zfill(dst + swz(py * IWP + pxx, ch), v ? img + ((int64_t)yy * W + xx) * kC + ch * 8 : img, v);
         }
     };
     stage(tile, tb0);
@@ -141,6 +154,15 @@ __global__ void __launch_bounds__(256, 3) conv32_kernel(const __nv_bfloat16* __r
     const int arow = lane & 15, achk = lane >> 4;                                // A: pixel row, chunk
     const int brow = (lane & 7) + (lane >> 4) * 8, bchk = (lane >> 3) & 1;      // B: co row, chunk
     const int g = lane >> 2, q = lane & 3;
+    // per-lane byte offsets: A for tap column dx and k-step ks (row warp, dy = 0), B for ks (tap 0)
+    uint32_t aoff[3][2], boff[2];
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) aoff[dx][ks] = 2u * (uint32_t)swz(warp * IWP + dx + arow, 2 * ks + achk);
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) boff[ks] = 2u * (uint32_t)swz(brow, 2 * ks + bchk);
+    const uint32_t tw_s = (uint32_t)__cvta_generic_to_shared(tw);
     for (int i = 0; tile < ntiles; ++i, tile += G) {
         __nv_bfloat16* cur = tb0 + (i & 1) * kTileElems;
         if (tile + G < ntiles) stage(tile + G, tb0 + ((i + 1) & 1) * kTileElems);
@@ -155,17 +177,19 @@ __global__ void __launch_bounds__(256, 3) conv32_kernel(const __nv_bfloat16* __r
             for (int nn = 0; nn < 4; ++nn)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc[h][nn][e] = 0.f;
+        const uint32_t cur_s = (uint32_t)__cvta_generic_to_shared(cur);
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
             const int dy = tap / 3, dx = tap % 3;
-            const int p0 = (warp + dy) * IW + dx + arow;
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
                 uint32_t a0[4], a1[4], b01[4], b23[4];
-                ldmatrix_x4(a0, cur + swz(p0, 2 * ks + achk));
-                ldmatrix_x4(a1, cur + swz(p0 + 16, 2 * ks + achk));
-                ldmatrix_x4(b01, tw + swz(tap * kC + brow, 2 * ks + bchk));
-                ldmatrix_x4(b23, tw + swz(tap * kC + brow + 16, 2 * ks + bchk));
+                const uint32_t aa = cur_s + aoff[dx][ks] + 2u * (uint32_t)(dy * IWP * kC);
+                const uint32_t bb = tw_s + boff[ks] + 2u * (uint32_t)(tap * kC * kC);
+                ldmatrix_x4s(a0, aa);
+                ldmatrix_x4s(a1, aa + 2u * 16 * kC);
+                ldmatrix_x4s(b01, bb);
+                ldmatrix_x4s(b23, bb + 2u * 16 * kC);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const uint32_t(&a)[4] = h ? a1 : a0;
