@@ -449,7 +449,7 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
             x_cur = x_out;
         } else if (denoiser == ABCS_DEN_CNN) {
             ABCS_CUDA(cnn_forward(cnn_weights, a.r, sig, dens, n_img, g.Hc, g.Wc, at<void>(h, o_act), 0, 0, x_out,
-                                  s),
+                                  h->status, s),
                       "cnn launch");
             x_cur = x_out;
         } else {
@@ -673,7 +673,7 @@ abcs_status abcs_cnn_denoise(abcs_handle* h, const void* packed, const float* in
     const size_t o_act = c.take<uint16_t>((size_t)2 * n_img * H * W * 32);
     abcs_status st = ensure_ws(h, c.off);
     if (st) return st;
-    ABCS_CUDA(cnn_forward(packed, in, sigma, density, n_img, H, W, at<void>(h, o_act), 0, 0, out,
+    ABCS_CUDA(cnn_forward(packed, in, sigma, density, n_img, H, W, at<void>(h, o_act), 0, 0, out, h->status,
                           static_cast<cudaStream_t>(stream)),
               "cnn launch");
     return ABCS_OK;
@@ -687,7 +687,7 @@ abcs_status abcs_cnn_grad(abcs_handle* h, const void* packed, const float* r, co
     DeviceGuard dg(h->device);
     abcs_status st = ensure_ws(h, cnn_grad_ws_bytes(n, H, W));
     if (st) return st;
-    ABCS_CUDA(cnn_grad(packed, r, clean, sigma, density, n, H, W, h->ws, grad, loss,
+    ABCS_CUDA(cnn_grad(packed, r, clean, sigma, density, n, H, W, h->ws, grad, loss, h->status,
                        static_cast<cudaStream_t>(stream)),
               "cnn grad launch");
     return ABCS_OK;
@@ -709,7 +709,8 @@ abcs_status abcs_cnn_train_step(abcs_handle* h, float* params, float* adam_m, fl
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     float* grad = reinterpret_cast<float*>(static_cast<char*>(h->ws) + cnn_grad_ws_bytes(n, H, W));
     ABCS_CUDA(cnn_pack(params, packed, s), "cnn pack launch");
-    ABCS_CUDA(cnn_grad(packed, r, clean, sigma, density, n, H, W, h->ws, grad, loss, s), "cnn grad launch");
+    ABCS_CUDA(cnn_grad(packed, r, clean, sigma, density, n, H, W, h->ws, grad, loss, h->status, s),
+              "cnn grad launch");
     ABCS_CUDA(cnn_adam(params, grad, adam_m, adam_v, step, (float)lr, s), "adam launch");
     ABCS_CUDA(cnn_pack(params, packed, s), "cnn pack launch");
     return ABCS_OK;

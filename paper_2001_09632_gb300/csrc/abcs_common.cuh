@@ -253,9 +253,9 @@ int cnn_param_count();
 size_t cnn_packed_bytes();
 cudaError_t cnn_pack(const float* params, void* packed, cudaStream_t s);
 cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, const float* dens, int n, int H,
-                        int W, void* act_buf, int keep_all, int mode, float* out, cudaStream_t s);
+                        int W, void* act_buf, int keep_all, int mode, float* out, uint32_t* status, cudaStream_t s);
 cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, const float* sigma, const float* dens,
-                     int n, int H, int W, void* ws, float* grad, float* loss, cudaStream_t s);
+                     int n, int H, int W, void* ws, float* grad, float* loss, uint32_t* status, cudaStream_t s);
 // per-pixel measured fraction m_i / B^2 of the pixel's block (k_ida.cu)
 cudaError_t launch_density(const ImgGeom& g, const int32_t* counts, float* out, cudaStream_t s);
 size_t cnn_grad_ws_bytes(int n, int H, int W);

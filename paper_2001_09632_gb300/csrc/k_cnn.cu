@@ -4,16 +4,19 @@
 //   d = the measured fraction m_i / B^2 of the pixel's block (or 0).
 // Activations and mid-layer weights are BF16 (NHWC, 32 channels = 64 bytes
 // per pixel); every sum accumulates in FP32.  All layers are implicit GEMMs
-// on mma.sync.m16n8k16 with FP32 accumulation: the 32->32 layers in BF16
-// (persistent CTAs, 8 x 32 output tiles, weights resident in shared memory,
-// input tiles double-buffered and fed to the tensor cores with ldmatrix),
-// the first layer (3 channels: r / 255, sigma / 255, d) in FP16, the last
-// (32 -> 1) in BF16 with the weights split hi + lo.
+// on the tensor cores: the forward 32->32 layers on tcgen05 (TMEM
+// accumulators, 128-pixel rows, operands read from shared memory by
+// descriptor), the input-gradient 32->32 layers on mma.sync (persistent
+// CTAs, weights resident, double-buffered tiles fed with ldmatrix), the
+// first layer (3 channels: r / 255, sigma / 255, d) in FP16 mma.sync, the
+// last (32 -> 1) in BF16 mma.sync with the weights split hi + lo.
 //
 // Training (fwd + bwd + Adam) reuses the same conv kernel for the input
 // gradient (weights transposed in (ci, co) and flipped in the tap, epilogue
 // = ReLU mask of the layer below); weight gradients are accumulated per CTA
 // in FP32 and reduced in a fixed order (deterministic).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -726,6 +729,296 @@ cudaError_t cnn_pack(const float* params, void* packed, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// 32 -> 32 forward layer on the 5th-generation tensor cores (tcgen05, TMEM
+// accumulators, TMA).  Per output row of 128 pixels and per tap (dy, dx)
+// one row-level implicit GEMM:
+//   D[128 px][32 co] += A[128 px][32 ci] B[32 ci][32 co]
+// as two MMAs of K = 16 (M = 128, N = 32), FP32 accumulation in tensor memory.
+// A is read straight from the staged input tile: the tile is kept
+// k-chunk-major (four planes of 8 channels, 16 bytes per pixel, pixels
+// contiguous), which is exactly what a TMA box of 8 channels x 130 pixels x
+// 6 rows of the NHWC activations lands as, so the A matrix of tap (dy, dx)
+// is the same no-swizzle K-major layout starting (dy * 130 + dx) pixels on.
+//   tile: 4 output rows x 128 pixels; input 6 x 130 pixels (TMA zero-fills
+//   the halo outside the image)
+//   warp 0: TMA producer (3 input buffers, full/empty mbarriers)
+//   warp 1: tensor-memory allocation and the MMA issuer (2 accumulator
+//           buffers of 4 rows x 32 columns)
+//   warps 2-9: epilogue; warp w reads TMEM lanes 32 (w % 4) of rows
+//           (w - 2) / 4 and (w - 2) / 4 + 2 (tcgen05.ld), adds the bias,
+//           applies the ReLU, converts to BF16, 64-byte stores
+// Every mbarrier wait is bounded; a wait that expires sets ABCS_DEV_TIMEOUT
+// and an abort flag that ends every role, and the CTA frees its tensor
+// memory before it leaves.
+// ---------------------------------------------------------------------------
+constexpr int T5_TH = 4, T5_TW = 128, T5_IH = T5_TH + 2, T5_IW = T5_TW + 2;
+constexpr int T5_EPI_WARPS = 8, T5_THREADS = 32 * (2 + T5_EPI_WARPS);
+constexpr uint32_t T5_BOX = T5_IH * T5_IW * 16;            // bytes of one TMA box (8 channels)
+constexpr uint32_t T5_PLANE = (T5_BOX + 127) / 128 * 128;  // plane stride: TMA destinations 128-byte aligned
+constexpr uint32_t T5_TILE = 4 * T5_PLANE;
+constexpr uint32_t T5_TX = 4 * T5_BOX;                     // bytes the 4 loads of a tile deliver
+constexpr int T5_NBUF = 3;
+constexpr uint32_t T5_WOFF = T5_NBUF * T5_TILE;            // weights after the tiles
+constexpr uint32_t T5_WTAP = kC * kC * 2;                  // bytes of one tap's weights
+constexpr uint32_t T5_MISC = T5_WOFF + 9 * T5_WTAP;        // mbarriers, tensor-memory address, abort flag
+constexpr size_t T5_SMEM = T5_MISC + 128;
+constexpr uint32_t T5_TMEM_COLS = 2 * T5_TH * 32;          // 2 buffers x 4 rows x 32 channels
+static_assert(T5_SMEM <= 232448, "tcgen05 conv shared layout");
+// mbarriers in the misc area: full[3], empty[3], acc_full[2], acc_empty[2]
+constexpr uint32_t T5_FULL = 0, T5_EMPTY = 24, T5_AFULL = 48, T5_AEMPTY = 64, T5_SLOT = 80, T5_ABORT = 84;
+
+ABCS_D uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: K-major, no swizzle; lbo = byte distance
+// of adjacent 16-byte K chunks, sbo = byte distance of adjacent 8-row groups
+ABCS_D uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;                                // descriptor version of tcgen05
+    return d;                                              // base offset 0, no swizzle
+}
+
+// instruction descriptor, kind::f16: D F32, A and B BF16, both K-major, N = 32, M = 128
+constexpr uint32_t T5_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+ABCS_D void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(T5_IDESC), "r"(accum));
+}
+
+ABCS_D void umma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
+}
+
+ABCS_D void tc5_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+ABCS_D void tc5_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+ABCS_D void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+          "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+          "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+ABCS_D bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the phase of `parity`; false (and the abort flag set) on
+// expiry or when another role has aborted
+ABCS_D bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if (*abort_flag) return false;
+    }
+    *abort_flag = 1;
+    set_status(status, ABCS_DEV_TIMEOUT);
+    return false;
+}
+
+__global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __grid_constant__ CUtensorMap tin,
+                                                                   int n, int H, int W,
+                                                                   const __nv_bfloat16* __restrict__ wts,
+                                                                   const float* __restrict__ bias,
+                                                                   __nv_bfloat16* __restrict__ out,
+                                                                   uint32_t* status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t sb = smem_u32(smem), mb = sb + T5_MISC;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + T5_MISC + T5_SLOT);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + T5_MISC + T5_ABORT);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int tx = (W + T5_TW - 1) / T5_TW, ty = (H + T5_TH - 1) / T5_TH, per_img = tx * ty;
+    const int ntiles = per_img * n;
+    const int G = gridDim.x;
+    if ((int)blockIdx.x >= ntiles) return;
+    const int my_n = (ntiles - (int)blockIdx.x + G - 1) / G;
+    auto origin = [&](int j, int& k, int& y0, int& x0) {
+        const int tile = (int)blockIdx.x + j * G;
+        k = tile / per_img;
+        const int rem = tile - k * per_img, by = rem / tx;
+        y0 = by * T5_TH;
+        x0 = (rem - by * tx) * T5_TW;
+    };
+
+    // the layer's weights (tap, 16-byte chunk c = ci 8c .. 8c+7, row co), barriers, tensor memory
+    for (int i = t; i < 9 * kC * 4; i += T5_THREADS) {
+        const int tap = i >> 7, co = (i >> 2) & 31, c = i & 3;
+        cp_async16_zfill(smem + T5_WOFF + tap * T5_WTAP + c * 512 + co * 16, wts + (tap * kC + co) * kC + c * 8,
+                         true);
+    }
+    cp_async_commit();
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "r"(T5_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (t == 0) {
+        for (int b = 0; b < T5_NBUF; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb + T5_FULL + 8 * b) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb + T5_EMPTY + 8 * b) : "memory");
+        }
+        for (int a = 0; a < 2; ++a) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb + T5_AFULL + 8 * a) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mb + T5_AEMPTY + 8 * a),
+                         "r"(T5_EPI_WARPS)
+                         : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        *abort_flag = 0;
+    }
+    cp_async_wait_all();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    tc5_fence_before();
+    __syncthreads();
+    tc5_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    griddep_wait();
+
+    if (warp == 0) {
+        // ---- TMA producer
+        if (lane == 0) {
+            const uint64_t tmap = reinterpret_cast<uint64_t>(&tin);
+            for (int j = 0; j < my_n; ++j) {
+                const int b = j % T5_NBUF;
+                if (!mbar_wait(mb + T5_EMPTY + 8 * b, ((j / T5_NBUF) & 1) ^ 1, abort_flag, status)) break;
+                int k, y0, x0;
+                origin(j, k, y0, x0);
+                const uint32_t full = mb + T5_FULL + 8 * b;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full), "r"(T5_TX)
+                             : "memory");
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    asm volatile(
+                        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(sb + b * T5_TILE + c * T5_PLANE),
+                        "l"(tmap), "r"(8 * c), "r"(x0 - 1), "r"(y0 - 1), "r"(k), "r"(full)
+                        : "memory");
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            const uint64_t bdesc0 = umma_desc(sb + T5_WOFF, 512, 128);
+            for (int j = 0; j < my_n; ++j) {
+                const int b = j % T5_NBUF, a = j & 1;
+                if (!mbar_wait(mb + T5_FULL + 8 * b, (j / T5_NBUF) & 1, abort_flag, status)) break;
+                if (!mbar_wait(mb + T5_AEMPTY + 8 * a, ((j >> 1) & 1) ^ 1, abort_flag, status)) break;
+                tc5_fence_after();
+                const uint64_t adesc0 = umma_desc(sb + b * T5_TILE, T5_PLANE, 128);
+#pragma unroll
+                for (int r = 0; r < T5_TH; ++r) {
+                    const uint32_t d = tmem + (uint32_t)(a * (T5_TH * 32) + r * 32);
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const uint64_t ad = adesc0 + (uint64_t)((((r + dy) * T5_IW + dx) * 16 + 2 * h * T5_PLANE) >> 4);
+                            const uint64_t bd = bdesc0 + (uint64_t)((tap * T5_WTAP + 2 * h * 512) >> 4);
+                            umma_bf16(d, ad, bd, (tap | h) != 0);
+                        }
+                    }
+                }
+                umma_commit(mb + T5_EMPTY + 8 * b);        // the input buffer is free once these complete
+                umma_commit(mb + T5_AFULL + 8 * a);        // the accumulators are ready
+            }
+        }
+    } else {
+        // ---- epilogue
+        const int e = warp - 2, lg = warp & 3, r0 = e >> 2;
+        float bz[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) bz[c] = __ldg(bias + c);
+        for (int j = 0; j < my_n; ++j) {
+            const int a = j & 1;
+            if (!mbar_wait(mb + T5_AFULL + 8 * a, (j >> 1) & 1, abort_flag, status)) break;
+            tc5_fence_after();
+            int k, y0, x0;
+            origin(j, k, y0, x0);
+            const int x = x0 + 32 * lg + lane;
+#pragma unroll
+            for (int r = r0; r < T5_TH; r += 2) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(a * (T5_TH * 32) + r * 32), v);
+                const int y = y0 + r;
+                if (x < W && y < H) {
+                    uint32_t o[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        o[c] = pack_bf16(fmaxf(__uint_as_float(v[2 * c]) + bz[2 * c], 0.f),
+                                         fmaxf(__uint_as_float(v[2 * c + 1]) + bz[2 * c + 1], 0.f));
+                    uint4* dst = reinterpret_cast<uint4*>(out + (((int64_t)k * H + y) * W + x) * kC);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) dst[c] = make_uint4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
+                }
+            }
+            tc5_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mb + T5_AEMPTY + 8 * a) : "memory");
+        }
+    }
+    tc5_fence_before();
+    __syncthreads();
+    tc5_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(T5_TMEM_COLS)
+                     : "memory");
+}
+
+// TMA descriptor of an NHWC BF16 activation plane set: dims (32 channels, W, H, n),
+// box (8 channels, 130 pixels, 6 rows, 1 image), zero fill outside
+static cudaError_t make_act_tmap(const __nv_bfloat16* act, int n, int H, int W, CUtensorMap* map) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e || q != cudaDriverEntryPointSuccess || !fn) return e ? e : cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)kC, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
+    const cuuint64_t strides[3] = {(cuuint64_t)kC * 2, (cuuint64_t)W * kC * 2, (cuuint64_t)H * W * kC * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)T5_IW, (cuuint32_t)T5_IH, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(act), dims,
+                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+static cudaError_t conv32_tc5_launch(const __nv_bfloat16* in, int n, int H, int W, const __nv_bfloat16* wts,
+                                     const float* bias, __nv_bfloat16* out, uint32_t* status, cudaStream_t s) {
+    CUtensorMap map;
+    cudaError_t e = make_act_tmap(in, n, H, W, &map);
+    if (!e) e = cudaFuncSetAttribute(conv32_tc5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T5_SMEM);
+    int dev, sms;
+    if (!e) e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e) return e;
+    const int64_t tiles = (int64_t)((W + T5_TW - 1) / T5_TW) * ((H + T5_TH - 1) / T5_TH) * n;
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    return launch_pdl(conv32_tc5_kernel, dim3(grid), dim3(T5_THREADS), T5_SMEM, s, map, n, H, W, wts, bias, out,
+                      status);
+}
+
 template <int EPI>
 static cudaError_t conv32_launch(const __nv_bfloat16* in, int n, int H, int W, const __nv_bfloat16* wts,
                                  const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out, cudaStream_t s) {
@@ -751,7 +1044,7 @@ static cudaError_t conv32(int epi, const __nv_bfloat16* in, int n, int H, int W,
 // Forward through layers 0..6 into act[0..6] (each n*H*W*32 bf16), then the
 // last layer into out (mode 0: denoised image, mode 1: network output n).
 cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, const float* dens, int n, int H,
-                        int W, void* act_buf, int keep_all, int mode, float* out, cudaStream_t s) {
+                        int W, void* act_buf, int keep_all, int mode, float* out, uint32_t* status, cudaStream_t s) {
     const CnnPacked* P = static_cast<const CnnPacked*>(packed);
     const int64_t plane = (int64_t)n * H * W * kC;
     __nv_bfloat16* act = static_cast<__nv_bfloat16*>(act_buf);
@@ -759,7 +1052,7 @@ cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, 
     dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, n);
     cudaError_t e = launch_pdl(cnn_first_tc_kernel, grid, dim3(256), 0, s, r, sigma, dens, H, W, P, A(0));
     for (int l = 1; l <= kMid && !e; ++l)
-        e = conv32(0, A(l - 1), n, H, W, &P->wc[l - 1][0][0][0], &P->bm[l - 1][0], nullptr, A(l), s);
+        e = conv32_tc5_launch(A(l - 1), n, H, W, &P->wc[l - 1][0][0][0], &P->bm[l - 1][0], A(l), status, s);
     if (e) return e;
     const size_t smem = (size_t)IH * IW * PXS * 2;
     if ((e = cudaFuncSetAttribute(cnn_last_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
@@ -771,7 +1064,7 @@ cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, 
 // Loss and gradients (FP32, parameter layout) of a batch of n crops.
 // Workspace: act (7 planes), gbuf (2 planes), gn (n*H*W floats), parts.
 cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, const float* sigma, const float* dens,
-                     int n, int H, int W, void* ws, float* grad, float* loss, cudaStream_t s) {
+                     int n, int H, int W, void* ws, float* grad, float* loss, uint32_t* status, cudaStream_t s) {
     const CnnPacked* P = static_cast<const CnnPacked*>(packed);
     const int64_t px = (int64_t)n * H * W, plane = px * kC;
     char* w = static_cast<char*>(ws);
@@ -782,7 +1075,7 @@ cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, con
     const int nparts = 304;
     float* part = gn + px;                                       // nparts * (kWm + kBm)
     double* lpart = reinterpret_cast<double*>(part + (size_t)nparts * (kWm + kBm));
-    cudaError_t e = cnn_forward(packed, r, sigma, dens, n, H, W, act, 1, 1, nout, s);
+    cudaError_t e = cnn_forward(packed, r, sigma, dens, n, H, W, act, 1, 1, nout, status, s);
     if (e) return e;
     cnn_loss_kernel<<<256, 256, 0, s>>>(nout, r, clean, px, gn, lpart);
     reduce_loss_kernel<<<1, 32, 0, s>>>(lpart, 256, loss);
