@@ -2,14 +2,14 @@
 //   conv3x3 3->32 + ReLU, 6 x [conv3x3 32->32 + ReLU], conv3x3 32->1,
 //   x_hat = r - 255 * net(r / 255, sigma / 255, d), zero 'same' padding,
 //   d = the measured fraction m_i / B^2 of the pixel's block (or 0).
-// Activations and mid-layer weights are BF16 (NHWC, 32 channels = 64 bytes
-// per pixel); every sum accumulates in FP32.  All layers are implicit GEMMs
-// on the tensor cores: the forward 32->32 layers on tcgen05 (TMEM
-// accumulators, 128-pixel rows, operands read from shared memory by
+// Activations and mid-layer weights are BF16 (activations chunk-planar:
+// four planes of 8 channels per image); every sum accumulates in FP32.  All
+// layers are implicit GEMMs on the tensor cores: the forward 32->32 layers
+// and the last (32 -> 1, weights split BF16 hi + lo) on tcgen05 (TMA-fed,
+// TMEM accumulators, 128-pixel rows, operands read from shared memory by
 // descriptor), the input-gradient 32->32 layers on mma.sync (persistent
 // CTAs, weights resident, double-buffered tiles fed with ldmatrix), the
-// first layer (3 channels: r / 255, sigma / 255, d) in FP16 mma.sync, the
-// last (32 -> 1) in BF16 mma.sync with the weights split hi + lo.
+// first layer (3 channels: r / 255, sigma / 255, d) in FP16 mma.sync.
 //
 // Training (fwd + bwd + Adam) reuses the same conv kernel for the input
 // gradient (weights transposed in (ci, co) and flipped in the tap, epilogue
@@ -51,20 +51,22 @@ struct CnnPacked {
     float bm[kMid][kC];
     float w7[kC][9];                // last layer, FP32 [ci][tap]
     float b7;
+    alignas(16) __nv_bfloat16 w7t[9][16][kC];   // last layer for the tensor cores: [tap][col][ci], col 0 = BF16 hi, 1 = lo
 };
 
 namespace {
 
 constexpr int TH = 8, TW = 32, IH = TH + 2, IW = TW + 2, PXS = 40;   // PXS: bf16 per pixel in smem
 
-ABCS_D void ldmatrix_x4(uint32_t (&r)[4], const void* p) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(a));
+// Activations and their gradients are stored chunk-planar, [n][4][H][W][8]:
+// image k, 16-byte chunk c / 8 (channels 8 (c / 8) .. 8 (c / 8) + 7), row y,
+// pixel x, channel c % 8.  A row of one chunk is contiguous, so tile loads
+// and stores move whole lines.
+ABCS_D int64_t act_off(int k, int y, int x, int c, int H, int W) {
+    return ((((int64_t)k * 4 + (c >> 3)) * H + y) * W + x) * 8 + (c & 7);
 }
 
-// the same from a shared-window address
+// four 8 x 8 BF16 matrices from a shared-window address
 ABCS_D void ldmatrix_x4s(uint32_t (&r)[4], uint32_t a) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
@@ -142,13 +144,12 @@ __global__ void __launch_bounds__(256, 3) conv32_kernel(const __nv_bfloat16* __r
     auto stage = [&](int tl, __nv_bfloat16* dst) {
         int k, x0, y0;
         origin(tl, k, x0, y0);
-        const __nv_bfloat16* img = in + (int64_t)k * H * W * kC;
         for (int c = t; c < IH * IW * 4; c += 256) {
-            const int px = c >> 2, ch = c & 3;
+            const int ch = c / (IH * IW), px = c - ch * (IH * IW);
             const int py = px / IW, pxx = px - py * IW;
             const int yy = y0 - 1 + py, xx = x0 - 1 + pxx;
             const bool v = yy >= 0 && yy < H && xx >= 0 && xx < W;
-            cp_async16_zfill(dst + swz(py * IWP + pxx, ch), v ? img + ((int64_t)yy * W + xx) * kC + ch * 8 : img, v);
+            cp_async16_zfill(dst + swz(py * IWP + pxx, ch), v ? in + act_off(k, yy, xx, 8 * ch, H, W) : in, v);
         }
     };
     stage(tile, tb0);
@@ -222,16 +223,14 @@ __global__ void __launch_bounds__(256, 3) conv32_kernel(const __nv_bfloat16* __r
         __syncthreads();
         int k, x0, y0;
         origin(tile, k, x0, y0);
-        __nv_bfloat16* dst = out + (int64_t)k * H * W * kC;
-        const __nv_bfloat16* msk = (EPI == 1) ? mask + (int64_t)k * H * W * kC : nullptr;
         for (int c = t; c < TH * TW * 4; c += 256) {
-            const int px = c >> 2, ch = c & 3;
+            const int ch = c / (TH * TW), px = c - ch * (TH * TW);
             const int yy = y0 + px / TW, xx = x0 + px % TW;
             if (yy >= H || xx >= W) continue;
             uint4 v = *reinterpret_cast<const uint4*>(cur + swz(px, ch));
-            const int64_t o = ((int64_t)yy * W + xx) * kC + ch * 8;
+            const int64_t o = act_off(k, yy, xx, 8 * ch, H, W);
             if (EPI == 1) {
-                const uint4 m = __ldg(reinterpret_cast<const uint4*>(msk + o));
+                const uint4 m = __ldg(reinterpret_cast<const uint4*>(mask + o));
                 const uint32_t* mw = reinterpret_cast<const uint32_t*>(&m);
                 uint32_t* vw = reinterpret_cast<uint32_t*>(&v);
 #pragma unroll
@@ -243,7 +242,7 @@ __global__ void __launch_bounds__(256, 3) conv32_kernel(const __nv_bfloat16* __r
                     vw[e] &= keep_lo | keep_hi;
                 }
             }
-            *reinterpret_cast<uint4*>(dst + o) = v;
+            *reinterpret_cast<uint4*>(out + o) = v;
         }
         __syncthreads();                     // `cur` is staged into again two tiles later
     }
@@ -349,89 +348,13 @@ __global__ void __launch_bounds__(256) cnn_first_tc_kernel(const float* __restri
             }
         }
     __syncthreads();
-    __nv_bfloat16* dst = out + (int64_t)k * H * W * kC;
     for (int c = t; c < TH * TW * 4; c += 256) {
-        const int px = c >> 2, ch = c & 3;
+        const int ch = c / (TH * TW), px = c - ch * (TH * TW);
         const int yy = y0 + px / TW, xx = x0 + px % TW;
         if (yy >= H || xx >= W) continue;
-        *reinterpret_cast<uint4*>(dst + ((int64_t)yy * W + xx) * kC + ch * 8) =
+        *reinterpret_cast<uint4*>(out + act_off(k, yy, xx, 8 * ch, H, W)) =
             *reinterpret_cast<const uint4*>(tout + px * PXS + ch * 8);
     }
-}
-
-// ---------------------------------------------------------------------------
-// Last layer 32 -> 1 on the tensor cores: the 32 -> 32 implicit GEMM with
-// one useful output column; the FP32 weights enter as BF16 hi + lo (two
-// products), the activations are BF16 already, so the sum is FP32-accurate.
-// mode 0: out = r - 255 (acc + b) (the denoised image); mode 1: out = acc + b.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) cnn_last_tc_kernel(const __nv_bfloat16* __restrict__ in,
-                                                          const float* __restrict__ r, int H, int W,
-                                                          const CnnPacked* __restrict__ P, int mode,
-                                                          float* __restrict__ out) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __nv_bfloat16* tin = reinterpret_cast<__nv_bfloat16*>(smem);     // [IH*IW][PXS]
-    griddep_wait();
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = lane >> 2, q = lane & 3;
-    const int k = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
-    const __nv_bfloat16* img = in + (int64_t)k * H * W * kC;
-    for (int c = t; c < IH * IW * 4; c += 256) {
-        const int px = c >> 2, ch = c & 3;
-        const int yy = y0 - 1 + px / IW, xx = x0 - 1 + px % IW;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-            v = __ldg(reinterpret_cast<const uint4*>(img + ((int64_t)yy * W + xx) * kC) + ch);
-        *reinterpret_cast<uint4*>(tin + px * PXS + ch * 8) = v;
-    }
-    // B column 0: w7[ci][tap] split into BF16 hi + lo; lanes with g != 0 hold zeros
-    uint32_t bh[9][2][2], bl[9][2][2];
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap)
-#pragma unroll
-        for (int ks = 0; ks < 2; ++ks)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int ci = 16 * ks + 2 * q + 8 * j;
-                const float w0 = g == 0 ? __ldg(&P->w7[ci][tap]) : 0.f, w1 = g == 0 ? __ldg(&P->w7[ci + 1][tap]) : 0.f;
-                const __nv_bfloat162 hi = __floats2bfloat162_rn(w0, w1);
-                const float2 hf = __bfloat1622float2(hi);
-                bh[tap][ks][j] = *reinterpret_cast<const uint32_t*>(&hi);
-                bl[tap][ks][j] = pack_bf16(w0 - hf.x, w1 - hf.y);
-            }
-    __syncthreads();
-    float acc[2][4];
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[h][e] = 0.f;
-    const int arow = lane & 15, acol = (lane >> 4) * 8;
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;
-#pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-            uint32_t a0[4], a1[4];
-            const __nv_bfloat16* ap = tin + ((warp + dy) * IW + dx + arow) * PXS + ks * 16 + acol;
-            ldmatrix_x4(a0, ap);
-            ldmatrix_x4(a1, ap + 16 * PXS);
-            mma_bf16(acc[0], a0, bh[tap][ks][0], bh[tap][ks][1]);
-            mma_bf16(acc[0], a0, bl[tap][ks][0], bl[tap][ks][1]);
-            mma_bf16(acc[1], a1, bh[tap][ks][0], bh[tap][ks][1]);
-            mma_bf16(acc[1], a1, bl[tap][ks][0], bl[tap][ks][1]);
-        }
-    }
-    if (q != 0) return;                                  // column 0 lives in lanes q = 0 (c0, c2)
-    const float b7 = __ldg(&P->b7);
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int yy = y0 + warp, xx = x0 + 16 * h + g + 8 * half;
-            if (yy >= H || xx >= W) continue;
-            const float a = acc[h][2 * half] + b7;
-            const int64_t o = (int64_t)k * H * W + (int64_t)yy * W + xx;
-            out[o] = mode == 0 ? __ldg(r + o) - 255.f * a : a;
-        }
 }
 
 // ---------------------------------------------------------------------------
@@ -450,6 +373,13 @@ __global__ void cnn_pack_kernel(const float* __restrict__ prm, CnnPacked* __rest
     }
     if (i < kMid * kBm) P->bm[i / kBm][i % kBm] = prm[param_off_b(i / kBm + 1) + i % kBm];
     if (i < kW7) (&P->w7[0][0])[i] = prm[param_off_w(7) + i];              // [ci][tap] == [0][ci][3][3]
+    if (i < 9 * 16 * kC) {                                                  // [tap][col][ci]
+        const int tap = i / (16 * kC), col = (i / kC) % 16, ci = i % kC;
+        const float w = prm[param_off_w(7) + ci * 9 + tap];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(w - __bfloat162float(hi));
+        P->w7t[tap][col][ci] = col == 0 ? hi : (col == 1 ? lo : __float2bfloat16_rn(0.f));
+    }
     if (i == 0) P->b7 = prm[param_off_b(7)];
 }
 
@@ -492,8 +422,6 @@ __global__ void __launch_bounds__(256) cnn_last_bwd_kernel(const float* __restri
     float gv[9];
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) gv[tap] = tg[(py + 2 - tap / 3) * IW + (px + 2 - tap % 3)];
-    const int64_t o = ((int64_t)k * H * W + (int64_t)yy * W + xx) * kC;
-    const __nv_bfloat162* a2 = reinterpret_cast<const __nv_bfloat162*>(act + o);
     uint32_t res[16];
 #pragma unroll
     for (int ci = 0; ci < kC; ci += 2) {
@@ -502,12 +430,13 @@ __global__ void __launch_bounds__(256) cnn_last_bwd_kernel(const float* __restri
         for (int e = 0; e < 2; ++e)
 #pragma unroll
             for (int tap = 0; tap < 9; ++tap) v[e] = fmaf(sw[(ci + e) * 9 + tap], gv[tap], v[e]);
-        const float2 av = __bfloat1622float2(a2[ci / 2]);
+        const float2 av = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(act + act_off(k, yy, xx, ci, H, W)));
         res[ci / 2] = pack_bf16(av.x > 0.f ? v[0] : 0.f, av.y > 0.f ? v[1] : 0.f);
     }
-    uint4* dd = reinterpret_cast<uint4*>(d + o);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) dd[c] = make_uint4(res[4 * c], res[4 * c + 1], res[4 * c + 2], res[4 * c + 3]);
+    for (int c = 0; c < 4; ++c)
+        *reinterpret_cast<uint4*>(d + act_off(k, yy, xx, 8 * c, H, W)) =
+            make_uint4(res[4 * c], res[4 * c + 1], res[4 * c + 2], res[4 * c + 3]);
 }
 
 // Weight gradients of a 32 -> 32 layer: dW[co][ci][tap] = sum_p g[p][co] in[p + off(tap)][ci],
@@ -539,7 +468,7 @@ __global__ void __launch_bounds__(256) wgrad32_kernel(const __nv_bfloat16* __res
             float2 v = make_float2(0.f, 0.f);
             if (yy >= 0 && yy < H && xx >= 0 && xx < W)
                 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(
-                    in + (((int64_t)k * H + yy) * W + xx) * kC + cp));
+                    in + act_off(k, yy, xx, cp, H, W)));
             tin[px * 33 + cp] = v.x;
             tin[px * 33 + cp + 1] = v.y;
         }
@@ -549,7 +478,7 @@ __global__ void __launch_bounds__(256) wgrad32_kernel(const __nv_bfloat16* __res
             float2 v = make_float2(0.f, 0.f);
             if (yy < H && xx < W)
                 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(
-                    g + (((int64_t)k * H + yy) * W + xx) * kC + cp));
+                    g + act_off(k, yy, xx, cp, H, W)));
             tgg[px * 33 + cp] = v.x;
             tgg[px * 33 + cp + 1] = v.y;
         }
@@ -608,7 +537,7 @@ __global__ void __launch_bounds__(256) wgrad_first_kernel(const float* __restric
             float2 v = make_float2(0.f, 0.f);
             if (yy < H && xx < W)
                 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(
-                    g + (((int64_t)k * H + yy) * W + xx) * kC + cp));
+                    g + act_off(k, yy, xx, cp, H, W)));
             tgg[px][cp] = v.x;
             tgg[px][cp + 1] = v.y;
         }
@@ -659,7 +588,7 @@ __global__ void __launch_bounds__(256) wgrad_last_kernel(const __nv_bfloat16* __
             float2 v = make_float2(0.f, 0.f);
             if (yy >= 0 && yy < H && xx >= 0 && xx < W)
                 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(
-                    in + (((int64_t)k * H + yy) * W + xx) * kC + cp));
+                    in + act_off(k, yy, xx, cp, H, W)));
             tin[px * 33 + cp] = v.x;
             tin[px * 33 + cp + 1] = v.y;
         }
@@ -731,15 +660,18 @@ cudaError_t cnn_pack(const float* params, void* packed, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // 32 -> 32 forward layer on the 5th-generation tensor cores (tcgen05, TMEM
-// accumulators, TMA).  Per output row of 128 pixels and per tap (dy, dx)
-// one row-level implicit GEMM:
-//   D[128 px][32 co] += A[128 px][32 ci] B[32 ci][32 co]
-// as two MMAs of K = 16 (M = 128, N = 32), FP32 accumulation in tensor memory.
+// accumulators, TMA).  Per input row i of 130 pixels and per dx one
+// row-level implicit GEMM against the three dy taps at once:
+//   D[128 px][dy, co] += A[128 px][32 ci] B[32 ci][dy, co]
+// as two MMAs of K = 16 (M = 128, N up to 96), FP32 accumulation in tensor
+// memory; the dy column block lands on output row i - dy's accumulator
+// (rows are kept in reverse order, so those blocks are adjacent).
 // A is read straight from the staged input tile: the tile is kept
 // k-chunk-major (four planes of 8 channels, 16 bytes per pixel, pixels
-// contiguous), which is exactly what a TMA box of 8 channels x 130 pixels x
-// 6 rows of the NHWC activations lands as, so the A matrix of tap (dy, dx)
-// is the same no-swizzle K-major layout starting (dy * 130 + dx) pixels on.
+// contiguous), which is exactly what one TMA box of 8 channels x 130 pixels
+// x 6 rows x 4 chunks of the chunk-planar activations lands as, so the A
+// matrix of input row i and column shift dx is the same no-swizzle K-major
+// layout starting (i * 130 + dx) pixels on.
 //   tile: 4 output rows x 128 pixels; input 6 x 130 pixels (TMA zero-fills
 //   the halo outside the image)
 //   warp 0: TMA producer (3 input buffers, full/empty mbarriers)
@@ -747,23 +679,21 @@ cudaError_t cnn_pack(const float* params, void* packed, cudaStream_t s) {
 //           buffers of 4 rows x 32 columns)
 //   warps 2-9: epilogue; warp w reads TMEM lanes 32 (w % 4) of rows
 //           (w - 2) / 4 and (w - 2) / 4 + 2 (tcgen05.ld), adds the bias,
-//           applies the ReLU, converts to BF16, 64-byte stores
+//           applies the ReLU, converts to BF16; each store of a warp
+//           covers 32 consecutive pixels of one plane (512 bytes)
 // Every mbarrier wait is bounded; a wait that expires sets ABCS_DEV_TIMEOUT
 // and an abort flag that ends every role, and the CTA frees its tensor
 // memory before it leaves.
 // ---------------------------------------------------------------------------
 constexpr int T5_TH = 4, T5_TW = 128, T5_IH = T5_TH + 2, T5_IW = T5_TW + 2;
 constexpr int T5_EPI_WARPS = 8, T5_THREADS = 32 * (2 + T5_EPI_WARPS);
-constexpr uint32_t T5_BOX = T5_IH * T5_IW * 16;            // bytes of one TMA box (8 channels)
-constexpr uint32_t T5_PLANE = (T5_BOX + 127) / 128 * 128;  // plane stride: TMA destinations 128-byte aligned
-constexpr uint32_t T5_TILE = 4 * T5_PLANE;
-constexpr uint32_t T5_TX = 4 * T5_BOX;                     // bytes the 4 loads of a tile deliver
+constexpr uint32_t T5_PLANE = T5_IH * T5_IW * 16;          // bytes of one 8-channel plane of a tile
+constexpr uint32_t T5_TILE = 4 * T5_PLANE;                 // one TMA box: 4 planes x 6 rows x 130 pixels
+static_assert(T5_TILE % 128 == 0, "TMA destinations stay 128-byte aligned");
 constexpr int T5_NBUF = 3;
 constexpr uint32_t T5_WOFF = T5_NBUF * T5_TILE;            // weights after the tiles
-constexpr uint32_t T5_WTAP = kC * kC * 2;                  // bytes of one tap's weights
-constexpr uint32_t T5_MISC = T5_WOFF + 9 * T5_WTAP;        // mbarriers, tensor-memory address, abort flag
+constexpr uint32_t T5_MISC = T5_WOFF + 9 * kC * kC * 2;    // mbarriers, tensor-memory address, abort flag
 constexpr size_t T5_SMEM = T5_MISC + 128;
-constexpr uint32_t T5_TMEM_COLS = 2 * T5_TH * 32;          // 2 buffers x 4 rows x 32 channels
 static_assert(T5_SMEM <= 232448, "tcgen05 conv shared layout");
 // mbarriers in the misc area: full[3], empty[3], acc_full[2], acc_empty[2]
 constexpr uint32_t T5_FULL = 0, T5_EMPTY = 24, T5_AFULL = 48, T5_AEMPTY = 64, T5_SLOT = 80, T5_ABORT = 84;
@@ -780,14 +710,14 @@ ABCS_D uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     return d;                                              // base offset 0, no swizzle
 }
 
-// instruction descriptor, kind::f16: D F32, A and B BF16, both K-major, N = 32, M = 128
-constexpr uint32_t T5_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor, kind::f16: D F32, A and B BF16, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t t5_idesc(uint32_t n) { return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24); }
 
-ABCS_D void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+ABCS_D void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(T5_IDESC), "r"(accum));
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
 }
 
 ABCS_D void umma_commit(uint32_t mbar) {
@@ -833,12 +763,21 @@ ABCS_D bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag, 
     return false;
 }
 
+// NC = 32: a 32 -> 32 layer (bias, ReLU, BF16 chunk-planar out).  NC = 16: the last
+// layer; B columns 0 and 1 hold the BF16 hi and lo parts of its FP32
+// weights (the rest zero) and the epilogue writes mode 0: r - 255 (c0 + c1
+// + b), mode 1: c0 + c1 + b, in FP32.
+template <int NC>
 __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __grid_constant__ CUtensorMap tin,
                                                                    int n, int H, int W,
                                                                    const __nv_bfloat16* __restrict__ wts,
                                                                    const float* __restrict__ bias,
                                                                    __nv_bfloat16* __restrict__ out,
+                                                                   const float* __restrict__ r_in, int mode,
+                                                                   float* __restrict__ fout,
                                                                    uint32_t* status) {
+    // weights: per dx, per 16-byte K chunk, rows n = dy NC + co (the three dy taps side by side in N)
+    constexpr uint32_t WCHUNK = 3 * NC * 16, WDX = 4 * WCHUNK, TMEM_COLS = 2 * T5_TH * NC;
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t sb = smem_u32(smem), mb = sb + T5_MISC;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + T5_MISC + T5_SLOT);
@@ -858,15 +797,15 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __grid_
     };
 
     // the layer's weights (tap, 16-byte chunk c = ci 8c .. 8c+7, row co), barriers, tensor memory
-    for (int i = t; i < 9 * kC * 4; i += T5_THREADS) {
-        const int tap = i >> 7, co = (i >> 2) & 31, c = i & 3;
-        cp_async16_zfill(smem + T5_WOFF + tap * T5_WTAP + c * 512 + co * 16, wts + (tap * kC + co) * kC + c * 8,
-                         true);
+    for (int i = t; i < 9 * NC * 4; i += T5_THREADS) {
+        const int tap = i / (NC * 4), co = (i >> 2) % NC, c = i & 3, dy = tap / 3, dx = tap % 3;
+        cp_async16_zfill(smem + T5_WOFF + dx * WDX + c * WCHUNK + (dy * NC + co) * 16,
+                         wts + (tap * NC + co) * kC + c * 8, true);
     }
     cp_async_commit();
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
-                     "r"(T5_TMEM_COLS)
+                     "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
@@ -902,38 +841,48 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __grid_
                 int k, y0, x0;
                 origin(j, k, y0, x0);
                 const uint32_t full = mb + T5_FULL + 8 * b;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full), "r"(T5_TX)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full), "r"(T5_TILE)
                              : "memory");
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    asm volatile(
-                        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-                        " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(sb + b * T5_TILE + c * T5_PLANE),
-                        "l"(tmap), "r"(8 * c), "r"(x0 - 1), "r"(y0 - 1), "r"(k), "r"(full)
-                        : "memory");
+                asm volatile(
+                    "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(sb + b * T5_TILE),
+                    "l"(tmap), "r"(0), "r"(x0 - 1), "r"(y0 - 1), "r"(0), "r"(k), "r"(full)
+                    : "memory");
             }
         }
     } else if (warp == 1) {
         // ---- MMA issuer
         if (lane == 0) {
-            const uint64_t bdesc0 = umma_desc(sb + T5_WOFF, 512, 128);
+            const uint64_t bdesc0 = umma_desc(sb + T5_WOFF, WCHUNK, 128);
             for (int j = 0; j < my_n; ++j) {
                 const int b = j % T5_NBUF, a = j & 1;
                 if (!mbar_wait(mb + T5_FULL + 8 * b, (j / T5_NBUF) & 1, abort_flag, status)) break;
                 if (!mbar_wait(mb + T5_AEMPTY + 8 * a, ((j >> 1) & 1) ^ 1, abort_flag, status)) break;
                 tc5_fence_after();
                 const uint64_t adesc0 = umma_desc(sb + b * T5_TILE, T5_PLANE, 128);
+                // output row r accumulates at column (T - 1 - r) NC, so input row i
+                // feeds rows i - dy_lo .. i - dy_hi through one MMA whose N
+                // covers the dy taps side by side; row r starts fresh at i = r
+                const uint32_t d0 = tmem + (uint32_t)(a * (T5_TH * NC));
 #pragma unroll
-                for (int r = 0; r < T5_TH; ++r) {
-                    const uint32_t d = tmem + (uint32_t)(a * (T5_TH * 32) + r * 32);
+                for (int i = 0; i < T5_IH; ++i) {
+                    const int dy_lo = i - (T5_TH - 1) > 0 ? i - (T5_TH - 1) : 0, dy_hi = i < 2 ? i : 2;
 #pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const int dy = tap / 3, dx = tap % 3;
+                    for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
-                            const uint64_t ad = adesc0 + (uint64_t)((((r + dy) * T5_IW + dx) * 16 + 2 * h * T5_PLANE) >> 4);
-                            const uint64_t bd = bdesc0 + (uint64_t)((tap * T5_WTAP + 2 * h * 512) >> 4);
-                            umma_bf16(d, ad, bd, (tap | h) != 0);
+                            const uint64_t ad = adesc0 + (uint64_t)(((i * T5_IW + dx) * 16 + 2 * h * T5_PLANE) >> 4);
+                            const uint32_t bb = dx * WDX + 2 * h * WCHUNK;
+                            if (dx == 0 && h == 0 && dy_lo == 0) {
+                                umma_bf16(d0 + (T5_TH - 1 - i) * NC, ad, bdesc0 + (bb >> 4), t5_idesc(NC), 0);
+                                if (dy_hi >= 1)
+                                    umma_bf16(d0 + (T5_TH - i) * NC, ad, bdesc0 + ((bb + NC * 16) >> 4),
+                                              t5_idesc(dy_hi * NC), 1);
+                            } else {
+                                umma_bf16(d0 + (T5_TH - 1 - i + dy_lo) * NC, ad,
+                                          bdesc0 + ((bb + dy_lo * NC * 16) >> 4),
+                                          t5_idesc((dy_hi - dy_lo + 1) * NC), 1);
+                            }
                         }
                     }
                 }
@@ -944,9 +893,9 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __grid_
     } else {
         // ---- epilogue
         const int e = warp - 2, lg = warp & 3, r0 = e >> 2;
-        float bz[32];
+        float bz[NC == 32 ? 32 : 1];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) bz[c] = __ldg(bias + c);
+        for (int c = 0; c < (NC == 32 ? 32 : 1); ++c) bz[c] = __ldg(bias + c);
         for (int j = 0; j < my_n; ++j) {
             const int a = j & 1;
             if (!mbar_wait(mb + T5_AFULL + 8 * a, (j >> 1) & 1, abort_flag, status)) break;
@@ -956,18 +905,33 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __grid_
             const int x = x0 + 32 * lg + lane;
 #pragma unroll
             for (int r = r0; r < T5_TH; r += 2) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(a * (T5_TH * 32) + r * 32), v);
+                const uint32_t ta = tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(a * (T5_TH * NC) + (T5_TH - 1 - r) * NC);
                 const int y = y0 + r;
-                if (x < W && y < H) {
-                    uint32_t o[16];
+                if constexpr (NC == 32) {
+                    uint32_t v[32];
+                    tmem_ld32(ta, v);
+                    if (x < W && y < H) {
+                        uint32_t o[16];
 #pragma unroll
-                    for (int c = 0; c < 16; ++c)
-                        o[c] = pack_bf16(fmaxf(__uint_as_float(v[2 * c]) + bz[2 * c], 0.f),
-                                         fmaxf(__uint_as_float(v[2 * c + 1]) + bz[2 * c + 1], 0.f));
-                    uint4* dst = reinterpret_cast<uint4*>(out + (((int64_t)k * H + y) * W + x) * kC);
+                        for (int c = 0; c < 16; ++c)
+                            o[c] = pack_bf16(fmaxf(__uint_as_float(v[2 * c]) + bz[2 * c], 0.f),
+                                             fmaxf(__uint_as_float(v[2 * c + 1]) + bz[2 * c + 1], 0.f));
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) dst[c] = make_uint4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
+                        for (int c = 0; c < 4; ++c)
+                            *reinterpret_cast<uint4*>(out + act_off(k, y, x, 8 * c, H, W)) =
+                                make_uint4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
+                    }
+                } else {
+                    uint32_t v0, v1;
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];\n"
+                                 : "=r"(v0), "=r"(v1)
+                                 : "r"(ta));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    if (x < W && y < H) {
+                        const float a_ = __uint_as_float(v0) + __uint_as_float(v1) + bz[0];
+                        const int64_t o = ((int64_t)k * H + y) * W + x;
+                        fout[o] = mode == 0 ? __ldg(r_in + o) - 255.f * a_ : a_;
+                    }
                 }
             }
             tc5_fence_before();
@@ -979,12 +943,12 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __grid_
     __syncthreads();
     tc5_fence_after();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(T5_TMEM_COLS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS)
                      : "memory");
 }
 
-// TMA descriptor of an NHWC BF16 activation plane set: dims (32 channels, W, H, n),
-// box (8 channels, 130 pixels, 6 rows, 1 image), zero fill outside
+// TMA descriptor of a chunk-planar BF16 activation set: dims (8 channels, W, H,
+// 4 chunks, n), box (8, 130 pixels, 6 rows, 4 chunks, 1 image), zero fill outside
 static cudaError_t make_act_tmap(const __nv_bfloat16* act, int n, int H, int W, CUtensorMap* map) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -994,29 +958,37 @@ static cudaError_t make_act_tmap(const __nv_bfloat16* act, int n, int H, int W, 
         if (e || q != cudaDriverEntryPointSuccess || !fn) return e ? e : cudaErrorNotSupported;
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    const cuuint64_t dims[4] = {(cuuint64_t)kC, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
-    const cuuint64_t strides[3] = {(cuuint64_t)kC * 2, (cuuint64_t)W * kC * 2, (cuuint64_t)H * W * kC * 2};
-    const cuuint32_t box[4] = {8, (cuuint32_t)T5_IW, (cuuint32_t)T5_IH, 1};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(act), dims,
+    const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, 4, (cuuint64_t)n};
+    const cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)H * W * 16, (cuuint64_t)4 * H * W * 16};
+    const cuuint32_t box[5] = {8, (cuuint32_t)T5_IW, (cuuint32_t)T5_IH, 4, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(act), dims,
                               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-static cudaError_t conv32_tc5_launch(const __nv_bfloat16* in, int n, int H, int W, const __nv_bfloat16* wts,
-                                     const float* bias, __nv_bfloat16* out, uint32_t* status, cudaStream_t s) {
+template <int NC>
+static cudaError_t tc5_launch(const __nv_bfloat16* in, int n, int H, int W, const __nv_bfloat16* wts,
+                              const float* bias, __nv_bfloat16* out, const float* r_in, int mode, float* fout,
+                              uint32_t* status, cudaStream_t s) {
     CUtensorMap map;
     cudaError_t e = make_act_tmap(in, n, H, W, &map);
-    if (!e) e = cudaFuncSetAttribute(conv32_tc5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T5_SMEM);
+    if (!e)
+        e = cudaFuncSetAttribute(conv32_tc5_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T5_SMEM);
     int dev, sms;
     if (!e) e = cudaGetDevice(&dev);
     if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e) return e;
     const int64_t tiles = (int64_t)((W + T5_TW - 1) / T5_TW) * ((H + T5_TH - 1) / T5_TH) * n;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    return launch_pdl(conv32_tc5_kernel, dim3(grid), dim3(T5_THREADS), T5_SMEM, s, map, n, H, W, wts, bias, out,
-                      status);
+    return launch_pdl(conv32_tc5_kernel<NC>, dim3(grid), dim3(T5_THREADS), T5_SMEM, s, map, n, H, W, wts, bias,
+                      out, r_in, mode, fout, status);
+}
+
+static cudaError_t conv32_tc5_launch(const __nv_bfloat16* in, int n, int H, int W, const __nv_bfloat16* wts,
+                                     const float* bias, __nv_bfloat16* out, uint32_t* status, cudaStream_t s) {
+    return tc5_launch<32>(in, n, H, W, wts, bias, out, nullptr, 0, nullptr, status, s);
 }
 
 template <int EPI>
@@ -1054,11 +1026,7 @@ cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, 
     for (int l = 1; l <= kMid && !e; ++l)
         e = conv32_tc5_launch(A(l - 1), n, H, W, &P->wc[l - 1][0][0][0], &P->bm[l - 1][0], A(l), status, s);
     if (e) return e;
-    const size_t smem = (size_t)IH * IW * PXS * 2;
-    if ((e = cudaFuncSetAttribute(cnn_last_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-        return e;
-    return launch_pdl(cnn_last_tc_kernel, grid, dim3(256), smem, s, (const __nv_bfloat16*)A(kMid), r, H, W, P, mode,
-                      out);
+    return tc5_launch<16>(A(kMid), n, H, W, &P->w7t[0][0][0], &P->b7, nullptr, r, mode, out, status, s);
 }
 
 // Loss and gradients (FP32, parameter layout) of a batch of n crops.
