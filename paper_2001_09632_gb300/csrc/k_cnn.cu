@@ -5,8 +5,8 @@
 // Activations and mid-layer weights are BF16 (activations chunk-planar:
 // four planes of 8 channels per image); every sum accumulates in FP32.  All
 // layers are implicit GEMMs on the tensor cores: the forward 32->32 layers
-// and the last (32 -> 1, weights split BF16 hi + lo) on tcgen05 (TMA-fed,
-// TMEM accumulators, 128-pixel rows, operands read from shared memory by
+// and the last (32 -> 1, weights split BF16 hi + lo) on tcgen05 (bulk-copy
+// fed, TMEM accumulators, 128-pixel rows, operands read from shared memory by
 // descriptor), the input-gradient 32->32 layers on mma.sync (persistent
 // CTAs, weights resident, double-buffered tiles fed with ldmatrix), the
 // first layer (3 channels: r / 255, sigma / 255, d) in FP16 mma.sync.
@@ -15,8 +15,6 @@
 // gradient (weights transposed in (ci, co) and flipped in the tap, epilogue
 // = ReLU mask of the layer below); weight gradients are accumulated per CTA
 // in FP32 and reduced in a fixed order (deterministic).
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -660,7 +658,7 @@ cudaError_t cnn_pack(const float* params, void* packed, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // 32 -> 32 forward layer on the 5th-generation tensor cores (tcgen05, TMEM
-// accumulators, TMA).  Per input row i of 130 pixels and per dx one
+// accumulators, bulk asynchronous copies).  Per input row i of 130 pixels and per dx one
 // row-level implicit GEMM against the three dy taps at once:
 //   D[128 px][dy, co] += A[128 px][32 ci] B[32 ci][dy, co]
 // as two MMAs of K = 16 (M = 128, N up to 96), FP32 accumulation in tensor
@@ -668,13 +666,15 @@ cudaError_t cnn_pack(const float* params, void* packed, cudaStream_t s) {
 // (rows are kept in reverse order, so those blocks are adjacent).
 // A is read straight from the staged input tile: the tile is kept
 // k-chunk-major (four planes of 8 channels, 16 bytes per pixel, pixels
-// contiguous), which is exactly what one TMA box of 8 channels x 130 pixels
-// x 6 rows x 4 chunks of the chunk-planar activations lands as, so the A
-// matrix of input row i and column shift dx is the same no-swizzle K-major
-// layout starting (i * 130 + dx) pixels on.
-//   tile: 4 output rows x 128 pixels; input 6 x 130 pixels (TMA zero-fills
-//   the halo outside the image)
-//   warp 0: TMA producer (3 input buffers, full/empty mbarriers)
+// contiguous), so each (plane, input row) of the tile is one contiguous run
+// of the chunk-planar activations (one bulk copy of up to 2080 bytes), and
+// the A matrix of input row i and column shift dx is the same no-swizzle
+// K-major layout starting (i * 130 + dx) pixels on.  (A tensor-map copy of
+// 8-channel boxes moves 16 bytes per request; whole runs move full lines.)
+//   tile: 4 output rows x 128 pixels; input 6 x 130 pixels (the producer
+//   zeroes the halo outside the image)
+//   warp 0: producer, 24 bulk copies per tile (3 input buffers,
+//           full/empty mbarriers, the full one counting the bytes)
 //   warp 1: tensor-memory allocation and the MMA issuer (2 accumulator
 //           buffers of 4 rows x 32 columns)
 //   warps 2-9: epilogue; warp w reads TMEM lanes 32 (w % 4) of rows
@@ -688,8 +688,8 @@ cudaError_t cnn_pack(const float* params, void* packed, cudaStream_t s) {
 constexpr int T5_TH = 4, T5_TW = 128, T5_IH = T5_TH + 2, T5_IW = T5_TW + 2;
 constexpr int T5_EPI_WARPS = 8, T5_THREADS = 32 * (2 + T5_EPI_WARPS);
 constexpr uint32_t T5_PLANE = T5_IH * T5_IW * 16;          // bytes of one 8-channel plane of a tile
-constexpr uint32_t T5_TILE = 4 * T5_PLANE;                 // one TMA box: 4 planes x 6 rows x 130 pixels
-static_assert(T5_TILE % 128 == 0, "TMA destinations stay 128-byte aligned");
+constexpr uint32_t T5_TILE = 4 * T5_PLANE;                 // 4 planes x 6 rows x 130 pixels
+static_assert(T5_PLANE % 16 == 0 && T5_TILE % 128 == 0, "bulk-copy destinations stay 16-byte aligned");
 constexpr int T5_NBUF = 3;
 constexpr uint32_t T5_WOFF = T5_NBUF * T5_TILE;            // weights after the tiles
 constexpr uint32_t T5_MISC = T5_WOFF + 9 * kC * kC * 2;    // mbarriers, tensor-memory address, abort flag
@@ -768,7 +768,7 @@ ABCS_D bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag, 
 // weights (the rest zero) and the epilogue writes mode 0: r - 255 (c0 + c1
 // + b), mode 1: c0 + c1 + b, in FP32.
 template <int NC>
-__global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __grid_constant__ CUtensorMap tin,
+__global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __nv_bfloat16* __restrict__ in,
                                                                    int n, int H, int W,
                                                                    const __nv_bfloat16* __restrict__ wts,
                                                                    const float* __restrict__ bias,
@@ -832,23 +832,45 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __grid_
     griddep_wait();
 
     if (warp == 0) {
-        // ---- TMA producer
-        if (lane == 0) {
-            const uint64_t tmap = reinterpret_cast<uint64_t>(&tin);
-            for (int j = 0; j < my_n; ++j) {
-                const int b = j % T5_NBUF;
-                if (!mbar_wait(mb + T5_EMPTY + 8 * b, ((j / T5_NBUF) & 1) ^ 1, abort_flag, status)) break;
-                int k, y0, x0;
-                origin(j, k, y0, x0);
-                const uint32_t full = mb + T5_FULL + 8 * b;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full), "r"(T5_TILE)
-                             : "memory");
-                asm volatile(
-                    "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
-                    " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(sb + b * T5_TILE),
-                    "l"(tmap), "r"(0), "r"(x0 - 1), "r"(y0 - 1), "r"(0), "r"(k), "r"(full)
-                    : "memory");
+        // ---- producer: lane l < 24 moves (plane l / 6, input row l % 6) of a
+        // tile, one bulk copy of the in-image pixels (a contiguous run of the
+        // chunk-planar activations); pixels outside the image are zeroed here
+        const int c = lane / T5_IH, i = lane - c * T5_IH;
+        for (int j = 0; j < my_n; ++j) {
+            const int b = j % T5_NBUF;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(mb + T5_EMPTY + 8 * b, ((j / T5_NBUF) & 1) ^ 1, abort_flag, status);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            int k, y0, x0;
+            origin(j, k, y0, x0);
+            const int y = y0 - 1 + i, xa = x0 - 1 > 0 ? x0 - 1 : 0, xb = x0 + T5_TW + 1 < W ? x0 + T5_TW + 1 : W;
+            const bool mine = lane < 4 * T5_IH;
+            const bool row_in = mine && y >= 0 && y < H && xb > xa;
+            const uint32_t nbytes = row_in ? (uint32_t)(xb - xa) * 16u : 0u;
+            const uint32_t seg = sb + b * T5_TILE + c * T5_PLANE + i * T5_IW * 16;
+            if (mine) {
+                const int za = row_in ? xa - (x0 - 1) : T5_IW, zb = row_in ? xb - (x0 - 1) : T5_IW;
+                for (int p = 0; p < za; ++p)          // left halo (and whole rows outside the image)
+                    asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(seg + 16 * p), "r"(0) : "memory");
+                for (int p = zb; p < T5_IW; ++p)      // right halo
+                    asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(seg + 16 * p), "r"(0) : "memory");
             }
+            uint32_t total = nbytes;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncwarp();
+            const uint32_t full = mb + T5_FULL + 8 * b;
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full), "r"(total)
+                             : "memory");
+            __syncwarp();
+            if (nbytes)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                        seg + (uint32_t)(xa - (x0 - 1)) * 16u),
+                    "l"(in + act_off(k, y, xa, 8 * c, H, W)), "r"(nbytes), "r"(full)
+                    : "memory");
         }
     } else if (warp == 1) {
         // ---- MMA issuer
@@ -947,42 +969,19 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __grid_
                      : "memory");
 }
 
-// TMA descriptor of a chunk-planar BF16 activation set: dims (8 channels, W, H,
-// 4 chunks, n), box (8, 130 pixels, 6 rows, 4 chunks, 1 image), zero fill outside
-static cudaError_t make_act_tmap(const __nv_bfloat16* act, int n, int H, int W, CUtensorMap* map) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        void* fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-        if (e || q != cudaDriverEntryPointSuccess || !fn) return e ? e : cudaErrorNotSupported;
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
-    const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, 4, (cuuint64_t)n};
-    const cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)H * W * 16, (cuuint64_t)4 * H * W * 16};
-    const cuuint32_t box[5] = {8, (cuuint32_t)T5_IW, (cuuint32_t)T5_IH, 4, 1};
-    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(act), dims,
-                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 template <int NC>
 static cudaError_t tc5_launch(const __nv_bfloat16* in, int n, int H, int W, const __nv_bfloat16* wts,
                               const float* bias, __nv_bfloat16* out, const float* r_in, int mode, float* fout,
                               uint32_t* status, cudaStream_t s) {
-    CUtensorMap map;
-    cudaError_t e = make_act_tmap(in, n, H, W, &map);
-    if (!e)
-        e = cudaFuncSetAttribute(conv32_tc5_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T5_SMEM);
+    cudaError_t e =
+        cudaFuncSetAttribute(conv32_tc5_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T5_SMEM);
     int dev, sms;
     if (!e) e = cudaGetDevice(&dev);
     if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e) return e;
     const int64_t tiles = (int64_t)((W + T5_TW - 1) / T5_TW) * ((H + T5_TH - 1) / T5_TH) * n;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    return launch_pdl(conv32_tc5_kernel<NC>, dim3(grid), dim3(T5_THREADS), T5_SMEM, s, map, n, H, W, wts, bias,
+    return launch_pdl(conv32_tc5_kernel<NC>, dim3(grid), dim3(T5_THREADS), T5_SMEM, s, in, n, H, W, wts, bias,
                       out, r_in, mode, fout, status);
 }
 
