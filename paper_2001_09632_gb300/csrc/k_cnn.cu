@@ -54,7 +54,7 @@ struct CnnPacked {
 
 namespace {
 
-constexpr int TH = 8, TW = 32, IH = TH + 2, IW = TW + 2, PXS = 40;   // PXS: bf16 per pixel in smem
+constexpr int TH = 8, TW = 32, IH = TH + 2, IW = TW + 2;
 
 // Activations and their gradients are stored chunk-planar, [n][4][H][W][8]:
 // image k, 16-byte chunk c / 8 (channels 8 (c / 8) .. 8 (c / 8) + 7), row y,
@@ -82,6 +82,13 @@ ABCS_D void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_
 ABCS_D uint32_t pack_bf16(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// (max(a, 0), max(b, 0)) rounded to BF16 and packed, a in the low half
+ABCS_D uint32_t pack_bf16_relu(float a, float b) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;\n" : "=r"(d) : "f"(b), "f"(a));
+    return d;
 }
 
 
@@ -253,7 +260,9 @@ __global__ void __launch_bounds__(256, 3) conv32_kernel(const __nv_bfloat16* __r
 // zero-padded to 48, FP16 operands, FP32 accumulation.  Each shared pixel
 // holds the two pairs (r / 255, sigma / 255) and (d, 0) as FP16x2 words
 // (zero outside the image: the zero padding of every channel), so one
-// 32-bit shared load is one A-fragment register.
+// 32-bit shared load is one A-fragment register.  Persistent CTAs keep the
+// weight fragments in registers, prefetch the next tile's inputs during
+// the current tile's MMAs, and store straight from the accumulators.
 // ---------------------------------------------------------------------------
 ABCS_D void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -275,83 +284,119 @@ ABCS_D uint32_t w0_pair(const CnnPacked* P, int co, int p) {
                    : pack_f16(__ldg(&P->w0[co][0][tap]), __ldg(&P->w0[co][1][tap]));
 }
 
-__global__ void __launch_bounds__(256) cnn_first_tc_kernel(const float* __restrict__ r,
-                                                           const float* __restrict__ sigma,
-                                                           const float* __restrict__ dens, int H, int W,
-                                                           const CnnPacked* __restrict__ P,
-                                                           __nv_bfloat16* __restrict__ out) {
+__global__ void __launch_bounds__(256, 2) cnn_first_tc_kernel(const float* __restrict__ r,
+                                                              const float* __restrict__ sigma,
+                                                              const float* __restrict__ dens, int n, int H, int W,
+                                                              const CnnPacked* __restrict__ P,
+                                                              __nv_bfloat16* __restrict__ out) {
     __shared__ uint32_t tin[IH * IW * 2];                 // per pixel: (r, sigma), (d, 0) as FP16x2
-    __shared__ __align__(16) __nv_bfloat16 tout[TH * TW * PXS];
-    griddep_wait();
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = lane >> 2, q = lane & 3;
-    const int k = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
-    const float* img = r + (int64_t)k * H * W;
-    const float* dk = dens ? dens + (int64_t)k * H * W : nullptr;
-    const float s255 = __ldg(sigma + k) * (1.f / 255.f);
-    for (int c = t; c < IH * IW; c += 256) {
-        const int yy = y0 - 1 + c / IW, xx = x0 - 1 + c % IW;
-        const bool in_img = yy >= 0 && yy < H && xx >= 0 && xx < W;
-        const int64_t o = (int64_t)yy * W + xx;
-        tin[2 * c] = in_img ? pack_f16(__ldg(img + o) * (1.f / 255.f), s255) : 0u;
-        tin[2 * c + 1] = (in_img && dk) ? pack_f16(__ldg(dk + o), 0.f) : 0u;
-    }
+    const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH, per_img = tx * ty, ntiles = per_img * n;
+    const int G = gridDim.x;
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;
     // B fragments: ks covers pairs 8 ks .. 8 ks + 7; b0 = pair 8 ks + q, b1 = pair 8 ks + q + 4
-    uint32_t b[3][4][2];
+    uint32_t bf[3][4][2];
+    float bias[4][2];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+#pragma unroll
+        for (int ks = 0; ks < 3; ++ks) {
+            bf[ks][nt][0] = w0_pair(P, 8 * nt + g, 8 * ks + q);
+            bf[ks][nt][1] = w0_pair(P, 8 * nt + g, 8 * ks + q + 4);
+        }
+        bias[nt][0] = __ldg(&P->b0[8 * nt + 2 * q]);
+        bias[nt][1] = __ldg(&P->b0[8 * nt + 2 * q + 1]);
+    }
+    // A fragments: pair p = 8 ks + q + 4 j (tap p / 2, half p % 2) of pixel (row, col) is
+    // the shared word 2 ((row + dy) IW + col + dx) + half; pairs 18.. are the K padding
+    int aoff[3][2];
 #pragma unroll
     for (int ks = 0; ks < 3; ++ks)
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            b[ks][nt][0] = w0_pair(P, 8 * nt + g, 8 * ks + q);
-            b[ks][nt][1] = w0_pair(P, 8 * nt + g, 8 * ks + q + 4);
+        for (int j = 0; j < 2; ++j) {
+            const int p = 8 * ks + q + 4 * j, tap = p >> 1;
+            aoff[ks][j] = p < 18 ? 2 * ((tap / 3) * IW + tap % 3) + (p & 1) : -1;
         }
-    __syncthreads();
-    float acc[2][4][4];
+    constexpr int NPT = (IH * IW + 255) / 256;
+    int fy[NPT], fx[NPT];                                 // this thread's halo pixels in a tile
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[h][nt][e] = 0.f;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        // pixel (warp, 16 h + g + 8 row8); pair p = 2 tap + half reads input (warp + dy, col + dx)
-        auto at = [&](int row8, int p) -> uint32_t {
-            if (p >= 18) return 0u;
-            const int tap = p >> 1;
-            return tin[2 * ((warp + tap / 3) * IW + 16 * h + g + 8 * row8 + tap % 3) + (p & 1)];
-        };
-#pragma unroll
-        for (int ks = 0; ks < 3; ++ks) {
-            uint32_t a[4];
-            a[0] = at(0, 8 * ks + q);
-            a[1] = at(1, 8 * ks + q);
-            a[2] = at(0, 8 * ks + q + 4);
-            a[3] = at(1, 8 * ks + q + 4);
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) mma_f16(acc[h][nt], a, b[ks][nt][0], b[ks][nt][1]);
-        }
+    for (int e = 0; e < NPT; ++e) {
+        const int c = t + 256 * e;
+        fy[e] = c < IH * IW ? c / IW - 1 : -(1 << 20);    // -> outside every image when unused
+        fx[e] = c % IW - 1;
     }
-    // epilogue through shared memory: bias, ReLU, BF16, 16-byte stores
+    const int64_t ps = (int64_t)H * W * 8;                // elements per chunk plane
+    griddep_wait();
+    uint32_t pre[NPT][2];
+    auto origin = [&](int tl, int& k, int& y0, int& x0) {
+        k = tl / per_img;
+        const int rem = tl - k * per_img, by = rem / tx;
+        y0 = by * TH;
+        x0 = (rem - by * tx) * TW;
+    };
+    auto fetch = [&](int tl) {
+        int k, y0, x0;
+        origin(tl, k, y0, x0);
+        const float s255 = __ldg(sigma + k) * (1.f / 255.f);
+        const float* rk = r + (int64_t)k * H * W;
+        const float* dk = dens ? dens + (int64_t)k * H * W : nullptr;
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+        for (int e = 0; e < NPT; ++e) {
+            const int yy = y0 + fy[e], xx = x0 + fx[e];
+            const bool in_img = yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const int o = yy * W + xx;
+            pre[e][0] = in_img ? pack_f16(__ldg(rk + o) * (1.f / 255.f), s255) : 0u;
+            pre[e][1] = (in_img && dk) ? pack_f16(__ldg(dk + o), 0.f) : 0u;
+        }
+    };
+    fetch(tile);
+    for (; tile < ntiles; tile += G) {
+        __syncthreads();                                  // the previous tile's reads of tin are done
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const int co = nt * 8 + 2 * q;
-            const float b0 = __ldg(&P->b0[co]), b1 = __ldg(&P->b0[co + 1]);
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int px = warp * TW + h * 16 + g + 8 * half;
-                const float v0 = fmaxf(acc[h][nt][2 * half] + b0, 0.f), v1 = fmaxf(acc[h][nt][2 * half + 1] + b1, 0.f);
-                *reinterpret_cast<uint32_t*>(tout + px * PXS + co) = pack_bf16(v0, v1);
+        for (int e = 0; e < NPT; ++e) {
+            const int c = t + 256 * e;
+            if (c < IH * IW) {
+                tin[2 * c] = pre[e][0];
+                tin[2 * c + 1] = pre[e][1];
             }
         }
-    __syncthreads();
-    for (int c = t; c < TH * TW * 4; c += 256) {
-        const int ch = c / (TH * TW), px = c - ch * (TH * TW);
-        const int yy = y0 + px / TW, xx = x0 + px % TW;
-        if (yy >= H || xx >= W) continue;
-        *reinterpret_cast<uint4*>(out + act_off(k, yy, xx, 8 * ch, H, W)) =
-            *reinterpret_cast<const uint4*>(tout + px * PXS + ch * 8);
+        __syncthreads();
+        if (tile + G < ntiles) fetch(tile + G);           // in flight during this tile's MMAs and stores
+        int k, y0, x0;
+        origin(tile, k, y0, x0);
+        const int y = y0 + warp;
+        __nv_bfloat16* ob = out + (int64_t)k * 4 * ps + ((int64_t)y * W + x0 + g) * 8 + 2 * q;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float acc[4][4];                              // starts at the bias
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[nt][e] = bias[nt][e & 1];
+            const int base = 2 * (warp * IW + 16 * h + g);
+#pragma unroll
+            for (int ks = 0; ks < 3; ++ks) {
+                uint32_t a[4];
+                a[0] = aoff[ks][0] >= 0 ? tin[base + aoff[ks][0]] : 0u;
+                a[1] = aoff[ks][0] >= 0 ? tin[base + 16 + aoff[ks][0]] : 0u;
+                a[2] = aoff[ks][1] >= 0 ? tin[base + aoff[ks][1]] : 0u;
+                a[3] = aoff[ks][1] >= 0 ? tin[base + 16 + aoff[ks][1]] : 0u;
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) mma_f16(acc[nt], a, bf[ks][nt][0], bf[ks][nt][1]);
+            }
+            // bias, ReLU, BF16: lanes (g, q) of one store cover 8 pixels x 16 bytes, one full line
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int x = x0 + 16 * h + g + 8 * half;
+                if (y < H && x < W) {
+#pragma unroll
+                    for (int nt = 0; nt < 4; ++nt)
+                        *reinterpret_cast<uint32_t*>(ob + nt * ps + (16 * h + 8 * half) * 8) =
+                            pack_bf16_relu(acc[nt][2 * half], acc[nt][2 * half + 1]);
+                }
+            }
+        }
     }
 }
 
@@ -936,8 +981,8 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __nv_bf
                         uint32_t o[16];
 #pragma unroll
                         for (int c = 0; c < 16; ++c)
-                            o[c] = pack_bf16(fmaxf(__uint_as_float(v[2 * c]) + bz[2 * c], 0.f),
-                                             fmaxf(__uint_as_float(v[2 * c + 1]) + bz[2 * c + 1], 0.f));
+                            o[c] = pack_bf16_relu(__uint_as_float(v[2 * c]) + bz[2 * c],
+                                                  __uint_as_float(v[2 * c + 1]) + bz[2 * c + 1]);
 #pragma unroll
                         for (int c = 0; c < 4; ++c)
                             *reinterpret_cast<uint4*>(out + act_off(k, y, x, 8 * c, H, W)) =
@@ -1020,8 +1065,15 @@ cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, 
     const int64_t plane = (int64_t)n * H * W * kC;
     __nv_bfloat16* act = static_cast<__nv_bfloat16*>(act_buf);
     auto A = [&](int l) { return act + (keep_all ? l : (l & 1)) * plane; };
-    dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, n);
-    cudaError_t e = launch_pdl(cnn_first_tc_kernel, grid, dim3(256), 0, s, r, sigma, dens, H, W, P, A(0));
+    int dev, sms, per_sm;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cnn_first_tc_kernel, 256, 0);
+    if (e) return e;
+    const int64_t tiles = (int64_t)((W + TW - 1) / TW) * ((H + TH - 1) / TH) * n;
+    const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    e = launch_pdl(cnn_first_tc_kernel, dim3((unsigned)(tiles < cap ? tiles : cap)), dim3(256), 0, s, r, sigma,
+                   dens, n, H, W, P, A(0));
     for (int l = 1; l <= kMid && !e; ++l)
         e = conv32_tc5_launch(A(l - 1), n, H, W, &P->wc[l - 1][0][0][0], &P->bm[l - 1][0], A(l), status, s);
     if (e) return e;
