@@ -428,25 +428,26 @@ __global__ void __launch_bounds__(256, ABCS_BATCH_MINB) ida_batch_kernel(BatchAr
     }
 }
 
-// d[k][y][x] = m_i / B^2 of the block holding pixel (y, x) of image k
+// d[k][y][x] = m_i / B^2 of the block holding pixel (y, x) of image k; one
+// image row per CTA step, B a power of two
 __global__ void __launch_bounds__(256) density_kernel(ImgGeom g, const int32_t* __restrict__ counts,
                                                       float* __restrict__ out) {
     griddep_wait();
-    const int64_t npx = (int64_t)g.n_img * g.Hc * g.Wc;
+    const int rows = g.n_img * g.Hc, lb = __ffs(g.B) - 1;
     const float inv = 1.f / (float)(g.B * g.B);
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = p / ((int64_t)g.Hc * g.Wc);
-        const int rem = (int)(p - k * g.Hc * g.Wc), y = rem / g.Wc, x = rem - y * g.Wc;
-        out[p] = (float)__ldg(counts + k * g.n_blocks + (int64_t)(y / g.B) * g.nbw + x / g.B) * inv;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int k = row / g.Hc, y = row - k * g.Hc;
+        const int32_t* ck = counts + (int64_t)k * g.n_blocks + (int64_t)(y >> lb) * g.nbw;
+        float* o = out + (int64_t)row * g.Wc;
+        for (int x = threadIdx.x; x < g.Wc; x += blockDim.x) o[x] = (float)__ldg(ck + (x >> lb)) * inv;
     }
 }
 
 }  // namespace
 
 cudaError_t launch_density(const ImgGeom& g, const int32_t* counts, float* out, cudaStream_t s) {
-    const int64_t npx = (int64_t)g.n_img * g.Hc * g.Wc;
-    const int64_t want = (npx + 255) / 256;
-    const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+    const int rows = g.n_img * g.Hc;
+    const unsigned grid = (unsigned)(rows < 152 * 8 ? rows : 152 * 8);
     return launch_pdl(density_kernel, dim3(grid > 0 ? grid : 1), dim3(256), 0, s, g, counts, out);
 }
 
