@@ -716,30 +716,36 @@ cudaError_t cnn_pack(const float* params, void* packed, cudaStream_t s) {
 // the A matrix of input row i and column shift dx is the same no-swizzle
 // K-major layout starting (i * 130 + dx) pixels on.  (A tensor-map copy of
 // 8-channel boxes moves 16 bytes per request; whole runs move full lines.)
-//   tile: 4 output rows x 128 pixels; input 6 x 130 pixels (the producer
-//   zeroes the halo outside the image)
-//   warp 0: producer, 24 bulk copies per tile (3 input buffers,
-//           full/empty mbarriers, the full one counting the bytes)
+//   tile: TH output rows x 128 pixels; input TH + 2 rows x 130 pixels (the
+//   producer zeroes the halo outside the image); TH = 4 for the 32 -> 32
+//   layers (3 input buffers), TH = 8 for the last layer (2 input buffers)
+//   warp 0: producer, 4 (TH + 2) bulk copies per tile (full/empty
+//           mbarriers, the full one counting the bytes)
 //   warp 1: tensor-memory allocation and the MMA issuer (2 accumulator
-//           buffers of 4 rows x 32 columns)
+//           buffers of TH rows x NC columns)
 //   warps 2-9: epilogue; warp w reads TMEM lanes 32 (w % 4) of rows
-//           (w - 2) / 4 and (w - 2) / 4 + 2 (tcgen05.ld), adds the bias,
+//           (w - 2) / 4 + 2 m (tcgen05.ld), adds the bias,
 //           applies the ReLU, converts to BF16; each store of a warp
 //           covers 32 consecutive pixels of one plane (512 bytes)
 // Every mbarrier wait is bounded; a wait that expires sets ABCS_DEV_TIMEOUT
 // and an abort flag that ends every role, and the CTA frees its tensor
 // memory before it leaves.
 // ---------------------------------------------------------------------------
-constexpr int T5_TH = 4, T5_TW = 128, T5_IH = T5_TH + 2, T5_IW = T5_TW + 2;
+constexpr int T5_TW = 128, T5_IW = T5_TW + 2;
 constexpr int T5_EPI_WARPS = 8, T5_THREADS = 32 * (2 + T5_EPI_WARPS);
-constexpr uint32_t T5_PLANE = T5_IH * T5_IW * 16;          // bytes of one 8-channel plane of a tile
-constexpr uint32_t T5_TILE = 4 * T5_PLANE;                 // 4 planes x 6 rows x 130 pixels
-static_assert(T5_PLANE % 16 == 0 && T5_TILE % 128 == 0, "bulk-copy destinations stay 16-byte aligned");
-constexpr int T5_NBUF = 3;
-constexpr uint32_t T5_WOFF = T5_NBUF * T5_TILE;            // weights after the tiles
-constexpr uint32_t T5_MISC = T5_WOFF + 9 * kC * kC * 2;    // mbarriers, tensor-memory address, abort flag
-constexpr size_t T5_SMEM = T5_MISC + 128;
-static_assert(T5_SMEM <= 232448, "tcgen05 conv shared layout");
+// shared layout of a tile height TH: NBUF input tiles, the weights, misc
+template <int TH>
+struct T5Tile {
+    static constexpr int IH = TH + 2;
+    static constexpr uint32_t PLANE = IH * T5_IW * 16;     // bytes of one 8-channel plane of a tile
+    static constexpr uint32_t TILE = 4 * PLANE;            // 4 planes x IH rows x 130 pixels
+    static constexpr int NBUF = TH == 4 ? 3 : 2;
+    static constexpr uint32_t WOFF = NBUF * TILE;          // weights after the tiles
+    static constexpr uint32_t MISC = WOFF + 9 * kC * kC * 2;   // mbarriers, tensor-memory address, abort flag
+    static constexpr size_t SMEM = MISC + 128;
+    static_assert(PLANE % 16 == 0 && TILE % 128 == 0, "bulk-copy destinations stay 16-byte aligned");
+    static_assert(SMEM <= 232448 && NBUF <= 3 && 2 * TH * 32 <= 512, "tcgen05 conv shared / tensor memory layout");
+};
 // mbarriers in the misc area: full[3], empty[3], acc_full[2], acc_empty[2]
 constexpr uint32_t T5_FULL = 0, T5_EMPTY = 24, T5_AFULL = 48, T5_AEMPTY = 64, T5_SLOT = 80, T5_ABORT = 84;
 
@@ -812,7 +818,7 @@ ABCS_D bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag, 
 // layer; B columns 0 and 1 hold the BF16 hi and lo parts of its FP32
 // weights (the rest zero) and the epilogue writes mode 0: r - 255 (c0 + c1
 // + b), mode 1: c0 + c1 + b, in FP32.
-template <int NC>
+template <int NC, int TH>
 __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __nv_bfloat16* __restrict__ in,
                                                                    int n, int H, int W,
                                                                    const __nv_bfloat16* __restrict__ wts,
@@ -822,13 +828,14 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __nv_bf
                                                                    float* __restrict__ fout,
                                                                    uint32_t* status) {
     // weights: per dx, per 16-byte K chunk, rows n = dy NC + co (the three dy taps side by side in N)
-    constexpr uint32_t WCHUNK = 3 * NC * 16, WDX = 4 * WCHUNK, TMEM_COLS = 2 * T5_TH * NC;
+    using L = T5Tile<TH>;
+    constexpr uint32_t WCHUNK = 3 * NC * 16, WDX = 4 * WCHUNK, TMEM_COLS = 2 * TH * NC;
     extern __shared__ __align__(1024) unsigned char smem[];
-    const uint32_t sb = smem_u32(smem), mb = sb + T5_MISC;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + T5_MISC + T5_SLOT);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + T5_MISC + T5_ABORT);
+    const uint32_t sb = smem_u32(smem), mb = sb + L::MISC;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::MISC + T5_SLOT);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::MISC + T5_ABORT);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int tx = (W + T5_TW - 1) / T5_TW, ty = (H + T5_TH - 1) / T5_TH, per_img = tx * ty;
+    const int tx = (W + T5_TW - 1) / T5_TW, ty = (H + TH - 1) / TH, per_img = tx * ty;
     const int ntiles = per_img * n;
     const int G = gridDim.x;
     if ((int)blockIdx.x >= ntiles) return;
@@ -837,14 +844,14 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __nv_bf
         const int tile = (int)blockIdx.x + j * G;
         k = tile / per_img;
         const int rem = tile - k * per_img, by = rem / tx;
-        y0 = by * T5_TH;
+        y0 = by * TH;
         x0 = (rem - by * tx) * T5_TW;
     };
 
     // the layer's weights (tap, 16-byte chunk c = ci 8c .. 8c+7, row co), barriers, tensor memory
     for (int i = t; i < 9 * NC * 4; i += T5_THREADS) {
         const int tap = i / (NC * 4), co = (i >> 2) % NC, c = i & 3, dy = tap / 3, dx = tap % 3;
-        cp_async16_zfill(smem + T5_WOFF + dx * WDX + c * WCHUNK + (dy * NC + co) * 16,
+        cp_async16_zfill(smem + L::WOFF + dx * WDX + c * WCHUNK + (dy * NC + co) * 16,
                          wts + (tap * NC + co) * kC + c * 8, true);
     }
     cp_async_commit();
@@ -855,7 +862,7 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __nv_bf
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (t == 0) {
-        for (int b = 0; b < T5_NBUF; ++b) {
+        for (int b = 0; b < L::NBUF; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb + T5_FULL + 8 * b) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb + T5_EMPTY + 8 * b) : "memory");
         }
@@ -877,30 +884,35 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __nv_bf
     griddep_wait();
 
     if (warp == 0) {
-        // ---- producer: lane l < 24 moves (plane l / 6, input row l % 6) of a
-        // tile, one bulk copy of the in-image pixels (a contiguous run of the
-        // chunk-planar activations); pixels outside the image are zeroed here
-        const int c = lane / T5_IH, i = lane - c * T5_IH;
+        // ---- producer: run q = lane + 32 u (plane q / IH, input row q % IH) of
+        // a tile is one bulk copy of its in-image pixels (a contiguous run of
+        // the chunk-planar activations); pixels outside the image are zeroed here
+        constexpr int RUNS = 4 * L::IH, NP = (RUNS + 31) / 32;
         for (int j = 0; j < my_n; ++j) {
-            const int b = j % T5_NBUF;
+            const int b = j % L::NBUF;
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(mb + T5_EMPTY + 8 * b, ((j / T5_NBUF) & 1) ^ 1, abort_flag, status);
+            if (lane == 0) ok = mbar_wait(mb + T5_EMPTY + 8 * b, ((j / L::NBUF) & 1) ^ 1, abort_flag, status);
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             int k, y0, x0;
             origin(j, k, y0, x0);
-            const int y = y0 - 1 + i, xa = x0 - 1 > 0 ? x0 - 1 : 0, xb = x0 + T5_TW + 1 < W ? x0 + T5_TW + 1 : W;
-            const bool mine = lane < 4 * T5_IH;
-            const bool row_in = mine && y >= 0 && y < H && xb > xa;
-            const uint32_t nbytes = row_in ? (uint32_t)(xb - xa) * 16u : 0u;
-            const uint32_t seg = sb + b * T5_TILE + c * T5_PLANE + i * T5_IW * 16;
-            if (mine) {
-                const int za = row_in ? xa - (x0 - 1) : T5_IW, zb = row_in ? xb - (x0 - 1) : T5_IW;
-                for (int p = 0; p < za; ++p)          // left halo (and whole rows outside the image)
-                    asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(seg + 16 * p), "r"(0) : "memory");
-                for (int p = zb; p < T5_IW; ++p)      // right halo
-                    asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(seg + 16 * p), "r"(0) : "memory");
+            const int xa = x0 - 1 > 0 ? x0 - 1 : 0, xb = x0 + T5_TW + 1 < W ? x0 + T5_TW + 1 : W;
+            uint32_t nb[NP], total = 0;
+#pragma unroll
+            for (int u = 0; u < NP; ++u) {
+                const int q = lane + 32 * u, c = q / L::IH, i = q - c * L::IH, y = y0 - 1 + i;
+                const bool mine = q < RUNS;
+                const bool row_in = mine && y >= 0 && y < H && xb > xa;
+                nb[u] = row_in ? (uint32_t)(xb - xa) * 16u : 0u;
+                total += nb[u];
+                if (mine) {
+                    const uint32_t seg = sb + b * L::TILE + c * L::PLANE + i * T5_IW * 16;
+                    const int za = row_in ? xa - (x0 - 1) : T5_IW, zb = row_in ? xb - (x0 - 1) : T5_IW;
+                    for (int p = 0; p < za; ++p)      // left halo (and whole rows outside the image)
+                        asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(seg + 16 * p), "r"(0) : "memory");
+                    for (int p = zb; p < T5_IW; ++p)  // right halo
+                        asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(seg + 16 * p), "r"(0) : "memory");
+                }
             }
-            uint32_t total = nbytes;
 #pragma unroll
             for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -910,43 +922,49 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __nv_bf
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full), "r"(total)
                              : "memory");
             __syncwarp();
-            if (nbytes)
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                        seg + (uint32_t)(xa - (x0 - 1)) * 16u),
-                    "l"(in + act_off(k, y, xa, 8 * c, H, W)), "r"(nbytes), "r"(full)
-                    : "memory");
+#pragma unroll
+            for (int u = 0; u < NP; ++u) {
+                if (nb[u]) {
+                    const int q = lane + 32 * u, c = q / L::IH, i = q - c * L::IH, y = y0 - 1 + i;
+                    const uint32_t seg = sb + b * L::TILE + c * L::PLANE + i * T5_IW * 16;
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                            seg + (uint32_t)(xa - (x0 - 1)) * 16u),
+                        "l"(in + act_off(k, y, xa, 8 * c, H, W)), "r"(nb[u]), "r"(full)
+                        : "memory");
+                }
+            }
         }
     } else if (warp == 1) {
         // ---- MMA issuer
         if (lane == 0) {
-            const uint64_t bdesc0 = umma_desc(sb + T5_WOFF, WCHUNK, 128);
+            const uint64_t bdesc0 = umma_desc(sb + L::WOFF, WCHUNK, 128);
             for (int j = 0; j < my_n; ++j) {
-                const int b = j % T5_NBUF, a = j & 1;
-                if (!mbar_wait(mb + T5_FULL + 8 * b, (j / T5_NBUF) & 1, abort_flag, status)) break;
+                const int b = j % L::NBUF, a = j & 1;
+                if (!mbar_wait(mb + T5_FULL + 8 * b, (j / L::NBUF) & 1, abort_flag, status)) break;
                 if (!mbar_wait(mb + T5_AEMPTY + 8 * a, ((j >> 1) & 1) ^ 1, abort_flag, status)) break;
                 tc5_fence_after();
-                const uint64_t adesc0 = umma_desc(sb + b * T5_TILE, T5_PLANE, 128);
+                const uint64_t adesc0 = umma_desc(sb + b * L::TILE, L::PLANE, 128);
                 // output row r accumulates at column (T - 1 - r) NC, so input row i
                 // feeds rows i - dy_lo .. i - dy_hi through one MMA whose N
                 // covers the dy taps side by side; row r starts fresh at i = r
-                const uint32_t d0 = tmem + (uint32_t)(a * (T5_TH * NC));
+                const uint32_t d0 = tmem + (uint32_t)(a * (TH * NC));
 #pragma unroll
-                for (int i = 0; i < T5_IH; ++i) {
-                    const int dy_lo = i - (T5_TH - 1) > 0 ? i - (T5_TH - 1) : 0, dy_hi = i < 2 ? i : 2;
+                for (int i = 0; i < L::IH; ++i) {
+                    const int dy_lo = i - (TH - 1) > 0 ? i - (TH - 1) : 0, dy_hi = i < 2 ? i : 2;
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
-                            const uint64_t ad = adesc0 + (uint64_t)(((i * T5_IW + dx) * 16 + 2 * h * T5_PLANE) >> 4);
+                            const uint64_t ad = adesc0 + (uint64_t)(((i * T5_IW + dx) * 16 + 2 * h * L::PLANE) >> 4);
                             const uint32_t bb = dx * WDX + 2 * h * WCHUNK;
                             if (dx == 0 && h == 0 && dy_lo == 0) {
-                                umma_bf16(d0 + (T5_TH - 1 - i) * NC, ad, bdesc0 + (bb >> 4), t5_idesc(NC), 0);
+                                umma_bf16(d0 + (TH - 1 - i) * NC, ad, bdesc0 + (bb >> 4), t5_idesc(NC), 0);
                                 if (dy_hi >= 1)
-                                    umma_bf16(d0 + (T5_TH - i) * NC, ad, bdesc0 + ((bb + NC * 16) >> 4),
+                                    umma_bf16(d0 + (TH - i) * NC, ad, bdesc0 + ((bb + NC * 16) >> 4),
                                               t5_idesc(dy_hi * NC), 1);
                             } else {
-                                umma_bf16(d0 + (T5_TH - 1 - i + dy_lo) * NC, ad,
+                                umma_bf16(d0 + (TH - 1 - i + dy_lo) * NC, ad,
                                           bdesc0 + ((bb + dy_lo * NC * 16) >> 4),
                                           t5_idesc((dy_hi - dy_lo + 1) * NC), 1);
                             }
@@ -971,8 +989,8 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __nv_bf
             origin(j, k, y0, x0);
             const int x = x0 + 32 * lg + lane;
 #pragma unroll
-            for (int r = r0; r < T5_TH; r += 2) {
-                const uint32_t ta = tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(a * (T5_TH * NC) + (T5_TH - 1 - r) * NC);
+            for (int r = r0; r < TH; r += 2) {
+                const uint32_t ta = tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(a * (TH * NC) + (TH - 1 - r) * NC);
                 const int y = y0 + r;
                 if constexpr (NC == 32) {
                     uint32_t v[32];
@@ -1014,25 +1032,26 @@ __global__ void __launch_bounds__(T5_THREADS, 1) conv32_tc5_kernel(const __nv_bf
                      : "memory");
 }
 
-template <int NC>
+template <int NC, int TH>
 static cudaError_t tc5_launch(const __nv_bfloat16* in, int n, int H, int W, const __nv_bfloat16* wts,
                               const float* bias, __nv_bfloat16* out, const float* r_in, int mode, float* fout,
                               uint32_t* status, cudaStream_t s) {
+    using L = T5Tile<TH>;
     cudaError_t e =
-        cudaFuncSetAttribute(conv32_tc5_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T5_SMEM);
+        cudaFuncSetAttribute((conv32_tc5_kernel<NC, TH>), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM);
     int dev, sms;
     if (!e) e = cudaGetDevice(&dev);
     if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e) return e;
-    const int64_t tiles = (int64_t)((W + T5_TW - 1) / T5_TW) * ((H + T5_TH - 1) / T5_TH) * n;
+    const int64_t tiles = (int64_t)((W + T5_TW - 1) / T5_TW) * ((H + TH - 1) / TH) * n;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    return launch_pdl(conv32_tc5_kernel<NC>, dim3(grid), dim3(T5_THREADS), T5_SMEM, s, in, n, H, W, wts, bias,
+    return launch_pdl((conv32_tc5_kernel<NC, TH>), dim3(grid), dim3(T5_THREADS), L::SMEM, s, in, n, H, W, wts, bias,
                       out, r_in, mode, fout, status);
 }
 
 static cudaError_t conv32_tc5_launch(const __nv_bfloat16* in, int n, int H, int W, const __nv_bfloat16* wts,
                                      const float* bias, __nv_bfloat16* out, uint32_t* status, cudaStream_t s) {
-    return tc5_launch<32>(in, n, H, W, wts, bias, out, nullptr, 0, nullptr, status, s);
+    return tc5_launch<32, 4>(in, n, H, W, wts, bias, out, nullptr, 0, nullptr, status, s);
 }
 
 template <int EPI>
@@ -1077,7 +1096,7 @@ cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, 
     for (int l = 1; l <= kMid && !e; ++l)
         e = conv32_tc5_launch(A(l - 1), n, H, W, &P->wc[l - 1][0][0][0], &P->bm[l - 1][0], A(l), status, s);
     if (e) return e;
-    return tc5_launch<16>(A(kMid), n, H, W, &P->w7t[0][0][0], &P->b7, nullptr, r, mode, out, status, s);
+    return tc5_launch<16, 8>(A(kMid), n, H, W, &P->w7t[0][0][0], &P->b7, nullptr, r, mode, out, status, s);
 }
 
 // Loss and gradients (FP32, parameter layout) of a batch of n crops.

@@ -28,7 +28,7 @@ def _oracle(imgs, B, r, variant):
 
 @pytest.mark.parametrize("prec", [abcs.TC_FP16X2, abcs.TC_BF16X2, abcs.TC_BF16])
 @pytest.mark.parametrize("variant", [O.ZZ, O.BBV, O.DD])
-@pytest.mark.parametrize("shape", [(2, 96, 336), (1, 64, 1040), (3, 48, 48)])
+@pytest.mark.parametrize("shape", [(2, 96, 336), (1, 64, 1040), (3, 48, 48), (5, 160, 208)])
 def test_tc_sense_and_reconstruct(handle, prec, variant, shape):
     n, H, W = shape
     B, r = 16, 0.3
@@ -36,6 +36,8 @@ def test_tc_sense_and_reconstruct(handle, prec, variant, shape):
     outs, c_ref, y_ref = _oracle(imgs, B, r, variant)
     got = G.sense(handle, imgs, B, r, variant, precision=prec)
     assert got["bits"] == 0
+    if variant != O.ZZ:
+        assert np.array_equal(got["pilot"], np.concatenate([o["pilot"] for o in outs]))
     assert np.array_equal(got["counts"], c_ref)
     assert np.array_equal(got["offsets"], np.concatenate([[0], np.cumsum(c_ref)]))
     ey = G.rel_l2(got["y"], y_ref)
@@ -69,6 +71,31 @@ def test_precision_table(handle, capsys):
         assert ey <= BOUND[prec] and ex <= BOUND[prec]
     with capsys.disabled():
         print("\n" + "\n".join(lines))
+
+
+def test_sense_full_batch_counts_and_samples(handle):
+    """The bench workload (64 x 512x512, BBV r = 0.3, FP16x2) in the launch
+    configuration the bench times: pilot values and counts of every image
+    bit-exact against the oracle's BBV and allocation of the same images,
+    offsets their exclusive prefix, coefficients of 4 sampled images within
+    the FP32 bar."""
+    B, r, n = 16, 0.3, 64
+    imgs = synth.gen_batch(n, 512, 512, 1234)
+    got = G.sense(handle, imgs, B, r, O.BBV, precision=abcs.TC_FP16X2)
+    assert got["bits"] == 0
+    nB = got["plan"]["n_blocks"]
+    p = O.plan(512, 512, B, r, O.BBV)
+    for k in range(n):
+        Xc = imgs[k].astype(np.int64)
+        pilot = O.bbv(Xc, B, p["L"], p["X0"], p["nS"]).reshape(-1)
+        assert np.array_equal(got["pilot"][k * nB:(k + 1) * nB], pilot), k
+        assert np.array_equal(got["counts"][k * nB:(k + 1) * nB], O.allocate(pilot, p["R"], p["cap"])), k
+    assert np.array_equal(got["offsets"], np.concatenate([[0], np.cumsum(got["counts"])]))
+    off = got["offsets"]
+    for k in (0, 17, 40, 63):
+        ref = O.sense(imgs[k], B, r, O.BBV)
+        y = got["y"][off[k * nB] - off[0]: off[(k + 1) * nB] - off[0]]
+        assert G.rel_l2(y, ref["y"]) <= 1e-5
 
 
 def test_tc_rejects_other_block_sizes(handle):
