@@ -26,6 +26,8 @@ Functions and the passages they follow:
   tidct_denoise ................... the plain denoiser D_sigma (stand-in; see docstring)
   cnn_*, density_map, adam_step ... the learned residual denoiser (DnCNN-style, Sec. VI-4)
   psnr, ssim ...................... quality measures (Sec. I, ref. [18])
+  full_coefficients, thi_* ........ THI: full sensing, one threshold for the whole image
+                                    (Sec. IV; Sec. V-B and Table 2), Pearson correlation
 """
 from __future__ import annotations
 
@@ -572,6 +574,65 @@ def adam_step(p: np.ndarray, g: np.ndarray, m: np.ndarray, v: np.ndarray, t: int
     mh = m / (1.0 - b1 ** t)
     vh = v / (1.0 - b2 ** t)
     return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# --------------------------------------------------------------------------
+# THI (Sec. IV; Sec. V-B): with every coefficient sensed, keep the M of
+# largest magnitude in the whole image, irrespective of their block.  By
+# the DCT's orthogonality (Parseval) these carry the most energy, so THI is
+# the adaptive upper bound; Table 2 correlates its per-block counts with
+# the counts BBV and DD estimate.
+# --------------------------------------------------------------------------
+def full_coefficients(img: np.ndarray, B: int) -> np.ndarray:
+    """(n_B, B*B): every DCT coefficient of every block (blocks in raster
+    order), each row in zigzag-rank order."""
+    C = dct2_blocks(img, B)
+    nbh, nbw = C.shape[:2]
+    Z = np.empty((nbh * nbw, B * B))
+    Z[:, zigzag_rank(B).reshape(-1)] = C.reshape(nbh * nbw, B * B)
+    return Z
+
+
+def thi_select(Z: np.ndarray, M: int) -> np.ndarray:
+    """Boolean mask of Z's shape: the M entries of largest |Z|.
+
+    Reading: the paper defers THI's formal definition to its supplement,
+    which is not available.  Exactly M coefficients are kept; among equal
+    magnitudes the lower (block, zigzag rank) index is kept first.
+    """
+    mag = np.abs(np.asarray(Z, dtype=np.float64)).reshape(-1)
+    order = np.lexsort((np.arange(mag.size), -mag))      # |c| descending, then index ascending
+    keep = np.zeros(mag.size, dtype=bool)
+    keep[order[:M]] = True
+    return keep.reshape(np.shape(Z))
+
+
+def thi_counts(img: np.ndarray, B: int, M: int) -> np.ndarray:
+    """Per-block number of coefficients THI keeps (the m_i that maximise PSNR)."""
+    return thi_select(full_coefficients(img, B), M).sum(axis=1).astype(np.int64)
+
+
+def thi_reconstruct(img: np.ndarray, B: int, M: int) -> np.ndarray:
+    """Block IDCT of the THI-kept coefficients (zeros elsewhere)."""
+    Z = full_coefficients(img, B)
+    Zk = np.where(thi_select(Z, M), Z, 0.0)
+    H, W = np.shape(img)
+    nbh, nbw = H // B, W // B
+    C = Zk[:, zigzag_rank(B).reshape(-1)].reshape(nbh, nbw, B, B)
+    return idct2_blocks(C)
+
+
+def pearson(a, b) -> float:
+    """Correlation coefficient rho of two equally long sequences (Table 2's
+    rho between per-block counts): cov(a, b) / (std(a) std(b)).
+    Reading: 0 when either sequence is constant (rho is undefined there)."""
+    x = np.asarray(a, dtype=np.float64)
+    y = np.asarray(b, dtype=np.float64)
+    dx, dy = x - x.mean(), y - y.mean()
+    sx, sy = math.sqrt(float(np.sum(dx * dx))), math.sqrt(float(np.sum(dy * dy)))
+    if sx == 0.0 or sy == 0.0:
+        return 0.0
+    return float(np.sum(dx * dy)) / (sx * sy)
 
 
 # --------------------------------------------------------------------------
