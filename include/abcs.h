@@ -266,6 +266,32 @@ abcs_status abcs_cnn_train_step(abcs_handle* h, float* params, float* adam_m, fl
 abcs_status abcs_density_map(abcs_handle* h, const int32_t* counts, int n_img, int H, int W, int B,
                              float* out, void* stream);
 
+/* THI (Sec. IV; Sec. V-B, Table 2): full sensing with one threshold for the
+ * whole image.  Per image, keep the M coefficients of largest magnitude,
+ * irrespective of their block (by Parseval they carry the most energy, so
+ * THI bounds what any adaptive per-block allocation can reach), and count
+ * how many each block keeps.
+ *   coeffs     [device] float [n_img][n_B][B*B]: every coefficient of every
+ *              block of the cropped image, each block in zigzag-rank order
+ *              (what abcs_sense writes with ABCS_ZZ at subrate 1).
+ *   M          coefficients kept per image, 1 <= M <= n_B B^2.
+ *   adaptive   [device] int32 [n_img * n_B] counts to correlate with (the
+ *              counts abcs_sense writes for BBV or DD), or NULL.
+ *   thi_counts [device] int32 [n_img * n_B] out: kept coefficients per block.
+ *   rho        [device] double [n_img] out, or NULL (needs adaptive): the
+ *              correlation coefficient of thi_counts and adaptive over the
+ *              image's blocks, from exact integer sums; 0 when either
+ *              sequence is constant.
+ *   masked     [device] float, the layout of coeffs, out, or NULL: the kept
+ *              coefficients, zeros elsewhere (abcs_reconstruct with counts
+ *              B^2 then gives the THI image).
+ * The magnitudes are ranked as the FP32 values given.  Among equal
+ * magnitudes the lower (block, zigzag rank) index is kept first, so exactly
+ * M coefficients are kept.  A NaN coefficient sets ABCS_DEV_NONFINITE.
+ * Uses the handle's workspace (reallocated when too small). */
+abcs_status abcs_thi(abcs_handle* h, const float* coeffs, int n_img, int H, int W, int B, int64_t M,
+                     const int32_t* adaptive, int32_t* thi_counts, double* rho, float* masked, void* stream);
+
 /* abcs_sense without any device allocation (the paper has no counterpart;
  * this is a library service).  For callers that may not call cudaMalloc
  * while running: a sensing loop whose device memory is reserved once at

@@ -74,6 +74,7 @@ _SIGS = {
     "abcs_cnn_grad": [_P, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P, _P],
     "abcs_cnn_train_step": [_P, _P, _P, _P, _I, _D, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P],
     "abcs_density_map": [_P, _P, _I, _I, _I, _I, _P, _P],
+    "abcs_thi": [_P, _P, _I, _I, _I, _I, C.c_int64, _P, _P, _P, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -206,6 +207,13 @@ def abcs_cnn_train_step(h, params, adam_m, adam_v, step, lr, packed, r, clean, s
 def abcs_density_map(h, counts, n_img, H, W, B, out, stream=None) -> None:
     """out[k][y][x] = m_i / B^2 of the block holding pixel (y, x)."""
     _check(lib.abcs_density_map(h, _ptr(counts), n_img, H, W, B, _ptr(out), _stream(stream)))
+
+def abcs_thi(h, coeffs, n_img, H, W, B, M, adaptive, thi_counts, rho=None, masked=None, stream=None) -> None:
+    """THI: per image the M coefficients of largest magnitude (coeffs: every
+    coefficient, zigzag order per block); thi_counts per block, rho against
+    `adaptive` counts (or None), masked coefficients (or None)."""
+    _check(lib.abcs_thi(h, _ptr(coeffs), n_img, H, W, B, M, _ptr(adaptive), _ptr(thi_counts), _ptr(rho),
+                        _ptr(masked), _stream(stream)))
 
 
 def abcs_sync_status(h, stream=None) -> int:

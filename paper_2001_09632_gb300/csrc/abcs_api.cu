@@ -651,6 +651,35 @@ abcs_status abcs_density_map(abcs_handle* h, const int32_t* counts, int n_img, i
     return ABCS_OK;
 }
 
+abcs_status abcs_thi(abcs_handle* h, const float* coeffs, int n_img, int H, int W, int B, int64_t M,
+                     const int32_t* adaptive, int32_t* thi_counts, double* rho, float* masked, void* stream) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    if (!coeffs || !thi_counts) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (rho && !adaptive) return fail(ABCS_ERR_INVALID_ARG, "rho needs the adaptive counts");
+    if (!valid_B(B)) return fail(ABCS_ERR_INVALID_ARG, "B must be 4, 8, 16 or 32");
+    if (H < B || W < B) return fail(ABCS_ERR_INVALID_ARG, "image smaller than one block");
+    if (n_img < 1 || n_img > 65535) return fail(ABCS_ERR_INVALID_ARG, "n_img must be in [1, 65535]");
+    const int64_t nB = (int64_t)(H / B) * (W / B), per_img = nB * B * B;
+    if ((int64_t)n_img * nB >= (1LL << 31)) return fail(ABCS_ERR_INVALID_ARG, "more than 2^31 - 1 blocks in one call");
+    if (M < 1 || M > per_img)
+        return fail(ABCS_ERR_INVALID_ARG, "M must be in [1, %lld] (got %lld)", (long long)per_img, (long long)M);
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(ABCS_ERR_CUDA, "cannot select the handle's device");
+    Carver c;
+    const size_t o_pre = c.take<uint32_t>(n_img);
+    const size_t o_rem = c.take<int64_t>(n_img);
+    const size_t o_hist = c.take<uint32_t>((size_t)n_img * 256);
+    const size_t o_gt = c.take<int32_t>((size_t)n_img * nB);
+    const size_t o_eq = c.take<int32_t>((size_t)n_img * nB);
+    abcs_status st = ensure_ws(h, c.off);
+    if (st) return st;
+    ABCS_CUDA(launch_thi(coeffs, n_img, (int)nB, B * B, M, adaptive, thi_counts, rho, masked, at<uint32_t>(h, o_pre),
+                         at<int64_t>(h, o_rem), at<uint32_t>(h, o_hist), at<int32_t>(h, o_gt), at<int32_t>(h, o_eq),
+                         h->status, static_cast<cudaStream_t>(stream)),
+              "thi launch");
+    return ABCS_OK;
+}
+
 int64_t abcs_cnn_param_count(void) { return cnn_param_count(); }
 size_t abcs_cnn_packed_bytes(void) { return cnn_packed_bytes(); }
 

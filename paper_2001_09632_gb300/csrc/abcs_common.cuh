@@ -258,6 +258,11 @@ cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, con
                      int n, int H, int W, void* ws, float* grad, float* loss, uint32_t* status, cudaStream_t s);
 // per-pixel measured fraction m_i / B^2 of the pixel's block (k_ida.cu)
 cudaError_t launch_density(const ImgGeom& g, const int32_t* counts, float* out, cudaStream_t s);
+// THI selection (k_thi.cu): coeffs n_img x nB x bb (zigzag rank order);
+// workspace prefix/rem (n_img), hist (n_img x 256), gt/eq (n_img x nB)
+cudaError_t launch_thi(const float* coeffs, int n_img, int nB, int bb, int64_t M, const int32_t* adaptive,
+                       int32_t* counts, double* rho, float* masked, uint32_t* prefix, int64_t* rem, uint32_t* hist,
+                       int32_t* gt, int32_t* eq, uint32_t* status, cudaStream_t s);
 size_t cnn_grad_ws_bytes(int n, int H, int W);
 cudaError_t cnn_adam(float* params, const float* grad, float* m, float* v, int step, float lr, cudaStream_t s);
 }  // namespace abcs
