@@ -252,6 +252,71 @@ def images_learned_vs_plain(h, n=32):
                                 "equal": v["equal"]} for r, v in out.items()}}
 
 
+def thi_correlation(h, n=64, H=512, W=512, B=16, reps=5):
+    """THI (Sec. IV, Sec. V-B): the correlation coefficient rho between the
+    per-block counts BBV / DD allocate and the counts THI keeps at the same
+    M, mean over n held-out images per subrate (the analogue of Table 2 on
+    synthetic images; the paper's own values, on its image set, are quoted
+    as context), the PSNR of THI's image against the adaptive IDCT images
+    at r = 0.3, and the time of one abcs_thi call over the batch."""
+    import torch
+    from paper_2001_09632_gb300 import abcs, synth
+    imgs = synth.gen_batch(n, H, W, 4321)
+    d_img = torch.from_numpy(imgs).cuda()
+    nB = (H // B) * (W // B)
+    N = nB * B * B
+
+    def sense(r, variant):
+        plan = abcs.abcs_plan(H, W, B, r, variant)
+        c = torch.empty(n * nB, dtype=torch.int32, device="cuda")
+        o = torch.empty(n * nB + 1, dtype=torch.int64, device="cuda")
+        y = torch.empty(max(n * plan["M"], 1), dtype=torch.float32, device="cuda")
+        abcs.abcs_sense(h, d_img, n, H, W, W, H * W, B, r, variant, abcs.FP32, c, o, y, n * plan["M"])
+        return plan, c, o, y
+
+    def psnr_of(rec):
+        d = rec.clamp(0, 255) - d_img.float()
+        mse = (d * d).flatten(1).mean(1)
+        return float((10.0 * torch.log10(255.0 ** 2 / mse)).mean())
+
+    _, _, _, full = sense(1.0, abcs.ZZ)                      # every coefficient, zigzag order
+    cnt = torch.empty(n * nB, dtype=torch.int32, device="cuda")
+    rho = torch.empty(n, dtype=torch.float64, device="cuda")
+    out = {"images": n, "size": [H, W], "B": B, "rho": {"bbv": {}, "dd": {}}}
+    rec = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
+    for name, variant in (("bbv", abcs.BBV), ("dd", abcs.DD)):
+        for r in (0.1, 0.2, 0.3, 0.4, 0.5):
+            plan, c, o, y = sense(r, variant)
+            abcs.abcs_thi(h, full, n, H, W, B, plan["M"], c, cnt, rho, None)
+            out["rho"][name][str(r)] = float(rho.mean())
+            if r == 0.3:
+                abcs.abcs_reconstruct(h, c, o, y, n, H, W, B, abcs.FP32, rec)
+                out.setdefault("psnr_r03", {})[name + "_idct"] = psnr_of(rec)
+    assert abcs.abcs_sync_status(h) == 0
+    M = abcs.abcs_plan(H, W, B, 0.3, abcs.BBV)["M"]
+    masked = torch.empty_like(full[: n * N])
+    allc = torch.full((n * nB,), B * B, dtype=torch.int32, device="cuda")
+    offs = torch.arange(0, n * nB + 1, dtype=torch.int64, device="cuda") * (B * B)
+    abcs.abcs_thi(h, full, n, H, W, B, M, None, cnt, None, masked)
+    abcs.abcs_reconstruct(h, allc, offs, masked, n, H, W, B, abcs.FP32, rec)
+    out["psnr_r03"]["thi"] = psnr_of(rec)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    abcs.abcs_thi(h, full, n, H, W, B, M, None, cnt, None, None)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        abcs.abcs_thi(h, full, n, H, W, B, M, None, cnt, None, None)
+    e1.record()
+    torch.cuda.synchronize()
+    assert abcs.abcs_sync_status(h) == 0
+    ms = e0.elapsed_time(e1) / reps
+    out["thi_ms"] = ms
+    out["thi_Mpx_per_s"] = n * H * W / (ms * 1e-3) / 1e6
+    out["paper_table2_512_context"] = {"dd": [0.741, 0.818, 0.818, 0.807, 0.852],
+                                       "bbv": [0.719, 0.784, 0.795, 0.786, 0.802]}
+    return out
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -398,6 +463,7 @@ def main():
         if rank == 0:
             extras["learned_vs_plain"] = {"video_1920x1088_dd_r025": video_learned_vs_plain(h),
                                           "images_512": images_learned_vs_plain(h)}
+            extras["thi"] = thi_correlation(h)
 
     if rank != 0:
         abcs.abcs_destroy(h)
