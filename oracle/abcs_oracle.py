@@ -26,6 +26,7 @@ Functions and the passages they follow:
   tidct_denoise ................... the plain denoiser D_sigma (stand-in; see docstring)
   cnn_*, density_map, adam_step ... the learned residual denoiser (DnCNN-style, Sec. VI-4)
   psnr, ssim ...................... quality measures (Sec. I, ref. [18])
+  mc_divergence, damp ............. D-AMP (Eq. 24) and DAMP-D (Eq. 27) with a Monte-Carlo divergence
   full_coefficients, thi_* ........ THI: full sensing, one threshold for the whole image
                                     (Sec. IV; Sec. V-B and Table 2), Pearson correlation
 """
@@ -459,6 +460,57 @@ def ida(y: np.ndarray, counts: np.ndarray, Hc: int, Wc: int, B: int, iters: int,
     if trace:
         return x, sigmas, rs, zs
     return x, sigmas
+
+
+# --------------------------------------------------------------------------
+# Eqs. 24 and 27: D-AMP and its damped form DAMP-D.  The Onsager term is
+# alpha^t z^{t-1} with alpha^t from the divergence of the denoiser at the
+# previous iteration's input.
+# --------------------------------------------------------------------------
+def mc_divergence(denoiser, r: np.ndarray, sigma: float, x: np.ndarray, probe: np.ndarray,
+                  eps_rel: float = 1e-3) -> float:
+    """div D(r) ~ b^T (D(r + eps b) - D(r)) / eps, eps = eps_rel max|r|.
+
+    Reading: the paper does not define the estimator; this is the
+    Monte-Carlo estimate D-AMP (ref. [13]) uses, with the probe b given (the
+    GPU path takes the same b as input) and D-AMP's eps = max|r| / 1000.
+    x = D(r) is passed in (already computed).
+    """
+    eps = eps_rel * float(np.max(np.abs(r)))
+    if eps == 0.0:
+        eps = eps_rel
+    xp = r + eps * probe if denoiser is None else denoiser(r + eps * probe, sigma)
+    return float(np.sum(probe * (xp - x))) / eps
+
+
+def damp(y: np.ndarray, counts: np.ndarray, Hc: int, Wc: int, B: int, iters: int, probe: np.ndarray,
+         DF: float = 1.0, denoiser=None):
+    """D-AMP (D_F = 1, Eq. 24) / DAMP-D (Eq. 27):
+    z^t = y - A x^t + alpha^t z^{t-1},  alpha^t = div[D(x^{t-1} + A^T z^{t-1})] / (M D_F),
+    the rest as in IDA (Eqs. 13, 15, 25).
+
+    Reading of Eq. 24's normalisation: (1/delta) div / m is AMP's
+    (1/delta) <eta'> (Sec. III: <u> is the mean over the N components,
+    delta = M / N), i.e. div / M with M the image's measurement count.
+    probe: one (Hc, Wc) array b used at every iteration.
+    Returns x^T, the sigma^t and the alpha^t (alpha^0 = 0: z^{-1} = 0).
+    """
+    m = len(y)
+    x = np.zeros((Hc, Wc))
+    z_prev = np.zeros(m)
+    alpha = 0.0
+    sigmas, alphas = [], []
+    for t in range(iters):
+        z = y - A(x, counts, B) + alpha * z_prev
+        sigma = math.sqrt(float(np.dot(z, z)) / m)
+        rt = x + At(z, counts, B, Hc, Wc)
+        xn = rt if denoiser is None else denoiser(rt, sigma)
+        sigmas.append(sigma)
+        alphas.append(alpha)
+        if t + 1 < iters:
+            alpha = mc_divergence(denoiser, rt, sigma, xn, probe) / (m * DF)
+        x, z_prev = xn, z
+    return x, sigmas, alphas
 
 
 # --------------------------------------------------------------------------
