@@ -173,6 +173,23 @@ abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offse
                      int denoiser, double lambda, const void* cnn_weights,
                      float* x_out, float* sigma_trace, void* stream);
 
+/* D-AMP (Eq. 24) and its damped form DAMP-D (Eq. 27): IDA with the Onsager
+ * coefficient taken from the denoiser's divergence instead of 1 / damping:
+ *   z^t = y - A x^t + alpha^t z^{t-1},
+ *   alpha^t = div[D_{sigma^{t-1}}(r^{t-1})] / (m_img damping),  alpha^0 = 0,
+ * damping = 1 gives D-AMP.  The divergence is the Monte-Carlo estimate
+ *   div ~ b^T (D(r + eps b) - D(r)) / eps,  eps = max|r| / 1000 per image,
+ * with the caller's probe b, so every iteration but the last runs the
+ * denoiser twice.  (The paper's (1/delta) div / m is read as AMP's
+ * (1/delta) <eta'> = div / m_img.)
+ *   probe       [device] float [n_img][Hc][Wc], e.g. +-1 entries
+ *   alpha_trace [device] float [n_img][iters] or NULL, out: alpha^t
+ * Other arguments as abcs_ida. */
+abcs_status abcs_damp(abcs_handle* h, const int32_t* counts, const int64_t* offsets, const float* y,
+                      int n_img, int H, int W, int B, int iters, double damping, int denoiser,
+                      double lambda, const void* cnn_weights, const float* probe, float* x_out,
+                      float* sigma_trace, float* alpha_trace, void* stream);
+
 /* One image of an uneven batch (abcs_ida_batch). */
 typedef struct abcs_image_desc {
     int32_t H, W, B;         /* image size in pixels, block size (4, 8, 16 or 32) */

@@ -75,6 +75,7 @@ _SIGS = {
     "abcs_cnn_train_step": [_P, _P, _P, _P, _I, _D, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P],
     "abcs_density_map": [_P, _P, _I, _I, _I, _I, _P, _P],
     "abcs_thi": [_P, _P, _I, _I, _I, _I, C.c_int64, _P, _P, _P, _P, _P],
+    "abcs_damp": [_P, _P, _P, _P, _I, _I, _I, _I, _I, C.c_double, _I, C.c_double, _P, _P, _P, _P, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -207,6 +208,15 @@ def abcs_cnn_train_step(h, params, adam_m, adam_v, step, lr, packed, r, clean, s
 def abcs_density_map(h, counts, n_img, H, W, B, out, stream=None) -> None:
     """out[k][y][x] = m_i / B^2 of the block holding pixel (y, x)."""
     _check(lib.abcs_density_map(h, _ptr(counts), n_img, H, W, B, _ptr(out), _stream(stream)))
+
+def abcs_damp(h, counts, offsets, y, n_img, H, W, B, iters, damping, denoiser, lam, cnn_weights, probe, x_out,
+              sigma_trace=None, alpha_trace=None, stream=None) -> None:
+    """D-AMP (damping 1) / DAMP-D: IDA with the Onsager coefficient from the
+    Monte-Carlo divergence of the denoiser with the given probe."""
+    _check(lib.abcs_damp(h, _ptr(counts), _ptr(offsets), _ptr(y), n_img, H, W, B, iters, damping, denoiser, lam,
+                         _ptr(cnn_weights), _ptr(probe), _ptr(x_out), _ptr(sigma_trace), _ptr(alpha_trace),
+                         _stream(stream)))
+
 
 def abcs_thi(h, coeffs, n_img, H, W, B, M, adaptive, thi_counts, rho=None, masked=None, stream=None) -> None:
     """THI: per image the M coefficients of largest magnitude (coeffs: every

@@ -348,11 +348,14 @@ abcs_status abcs_denoise_tidct(abcs_handle* h, const float* in, int n_img, int H
 
 // IDA runner: `iters` full iterations into x_out; with capture >= 0 it
 // stops after the linear part of iteration `capture` and copies r^t and
-// sigma^t to r_cap / sig_cap instead.
+// sigma^t to r_cap / sig_cap instead.  With a probe, the Onsager coefficient
+// is D-AMP's (Eq. 24; DAMP-D, Eq. 27, for damping != 1) from the Monte-Carlo
+// divergence of the denoiser with that probe, instead of IDA's 1 / damping.
 static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t* offsets, const float* y,
                            int n_img, int H, int W, int B, int iters, double damping, int denoiser,
                            double lambda, const void* cnn_weights, float* x_out, float* sigma_trace,
-                           int capture, float* r_cap, float* sig_cap, void* stream);
+                           int capture, float* r_cap, float* sig_cap, void* stream,
+                           const float* probe = nullptr, float* alpha_trace = nullptr);
 
 abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offsets, const float* y,
                      int n_img, int H, int W, int B, int iters, double damping, int denoiser,
@@ -361,6 +364,15 @@ abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offse
     if (!x_out) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
     return ida_run(h, counts, offsets, y, n_img, H, W, B, iters, damping, denoiser, lambda, cnn_weights, x_out,
                    sigma_trace, -1, nullptr, nullptr, stream);
+}
+
+abcs_status abcs_damp(abcs_handle* h, const int32_t* counts, const int64_t* offsets, const float* y, int n_img,
+                      int H, int W, int B, int iters, double damping, int denoiser, double lambda,
+                      const void* cnn_weights, const float* probe, float* x_out, float* sigma_trace,
+                      float* alpha_trace, void* stream) {
+    if (!x_out || !probe) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    return ida_run(h, counts, offsets, y, n_img, H, W, B, iters, damping, denoiser, lambda, cnn_weights, x_out,
+                   sigma_trace, -1, nullptr, nullptr, stream, probe, alpha_trace);
 }
 
 abcs_status abcs_ida_capture(abcs_handle* h, const int32_t* counts, const int64_t* offsets, const float* y,
@@ -375,7 +387,8 @@ abcs_status abcs_ida_capture(abcs_handle* h, const int32_t* counts, const int64_
 static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t* offsets, const float* y,
                            int n_img, int H, int W, int B, int iters, double damping, int denoiser,
                            double lambda, const void* cnn_weights, float* x_out, float* sigma_trace,
-                           int capture, float* r_cap, float* sig_cap, void* stream) {
+                           int capture, float* r_cap, float* sig_cap, void* stream,
+                           const float* probe, float* alpha_trace) {
     if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
     if (!valid_B(B)) return fail(ABCS_ERR_INVALID_ARG, "B must be 4, 8, 16 or 32");
     if (H < B || W < B) return fail(ABCS_ERR_INVALID_ARG, "image smaller than one block");
@@ -411,6 +424,14 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
     const size_t o_act = c.take<uint16_t>(denoiser == ABCS_DEN_CNN ? (size_t)2 * npx * 32 : 0);
     const size_t o_den = c.take<float>(denoiser == ABCS_DEN_CNN ? npx : 0);
     const size_t o_x = c.take<float>(capturing ? npx : 0);
+    // D-AMP / DAMP-D: perturbed input and its denoised image, max |r|, divergence partials, alpha
+    const bool damp = probe != nullptr;
+    const int dchunks = damp ? damp_chunks(g) : 0;
+    const size_t o_rp = c.take<float>(damp ? npx : 0);
+    const size_t o_xp = c.take<float>(damp ? npx : 0);
+    const size_t o_amax = c.take<unsigned>(damp ? n_img : 0);
+    const size_t o_dpart = c.take<double>(damp ? (size_t)n_img * dchunks : 0);
+    const size_t o_alpha = c.take<float>(damp ? n_img : 0);
     abcs_status st = ensure_ws(h, c.off);
     if (st) return st;
     float* rbuf[2] = {at<float>(h, o_r0), at<float>(h, o_r1)};
@@ -424,7 +445,12 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
     a.y = y;
     a.partial = at<double>(h, o_part);
     a.inv_df = (float)(1.0 / damping);
+    a.alpha = damp ? at<float>(h, o_alpha) : nullptr;
     a.status = h->status;
+    if (damp) {
+        ABCS_CUDA(cudaMemsetAsync(at<float>(h, o_alpha), 0, n_img * sizeof(float), s), "memset");   // alpha^0 = 0
+        if (alpha_trace) ABCS_CUDA(cudaMemsetAsync(alpha_trace, 0, (size_t)n_img * iters * sizeof(float), s), "memset");
+    }
     if (capturing) x_out = at<float>(h, o_x);
     float* dens = at<float>(h, o_den);
     if (denoiser == ABCS_DEN_CNN) ABCS_CUDA(launch_density(g, counts, dens, s), "density launch");
@@ -454,6 +480,28 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
             x_cur = x_out;
         } else {
             x_cur = a.r;                  // identity: x^{t+1} = r^t
+        }
+        if (damp && t + 1 < iters) {
+            // alpha^{t+1} = div[D(r^t)] / (M D_F), div ~ b^T (D(r^t + eps b) - D(r^t)) / eps
+            const float eps_rel = 1e-3f;
+            float* rp = at<float>(h, o_rp);
+            float* xp = at<float>(h, o_xp);
+            unsigned* amax = at<unsigned>(h, o_amax);
+            ABCS_CUDA(launch_damp_perturb(g, a.r, probe, eps_rel, amax, rp, s), "damp perturb launch");
+            const float* xq = rp;         // identity
+            if (denoiser == ABCS_DEN_TIDCT) {
+                ABCS_CUDA(launch_tidct(rp, xp, n_img, g.Hc, g.Wc, sig, (float)lambda, s), "tidct launch");
+                xq = xp;
+            } else if (denoiser == ABCS_DEN_CNN) {
+                ABCS_CUDA(cnn_forward(cnn_weights, rp, sig, dens, n_img, g.Hc, g.Wc, at<void>(h, o_act), 0, 0, xp,
+                                      h->status, s),
+                          "cnn launch");
+                xq = xp;
+            }
+            ABCS_CUDA(launch_damp_alpha(g, offsets, probe, xq, x_cur, amax, eps_rel, a.inv_df,
+                                        at<double>(h, o_dpart), at<float>(h, o_alpha), alpha_trace, iters, t,
+                                        h->status, s),
+                      "damp alpha launch");
         }
         z_prev = a.z;
     }

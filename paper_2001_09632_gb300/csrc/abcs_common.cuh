@@ -203,10 +203,20 @@ struct IdaLinArgs {
     float* z;
     float* r;
     double* partial;       // one per CTA
-    float inv_df;
+    float inv_df;          // Onsager coefficient of IDA (Eq. 28) ...
+    const float* alpha;    // ... or per image (D-AMP / DAMP-D, Eqs. 24, 27), if not NULL
     uint32_t* status;
 };
 cudaError_t launch_ida_linear(const IdaLinArgs& a, cudaStream_t s);
+// D-AMP / DAMP-D Onsager coefficient (k_ida.cu): per image
+//   alpha[k] = inv_df * div_k / M_k,  div_k = b^T (xp - x) / eps_k,  eps_k = eps_rel max|r|
+// amax: n_img words (cleared here); partial: n_img x chunks doubles
+cudaError_t launch_damp_perturb(const ImgGeom& g, const float* r, const float* probe, float eps_rel,
+                                unsigned* amax, float* rp, cudaStream_t s);
+cudaError_t launch_damp_alpha(const ImgGeom& g, const int64_t* offsets, const float* probe, const float* xp,
+                              const float* x, const unsigned* amax, float eps_rel, float inv_df, double* partial,
+                              float* alpha, float* alpha_trace, int iters, int t, uint32_t* status, cudaStream_t s);
+int damp_chunks(const ImgGeom& g);
 cudaError_t launch_ida_sigma(const ImgGeom& g, const int64_t* offsets, const double* partial,
                              float* sigma, float* sigma_trace, int iters, int t, uint32_t* status,
                              cudaStream_t s);

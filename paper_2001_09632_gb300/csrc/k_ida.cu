@@ -134,9 +134,9 @@ __global__ void __launch_bounds__(256, (B == 16 ? 3 : 4)) ida_linear_kernel(IdaL
     L.pix = (int64_t)k * g.Hc * g.Wc + (int64_t)(bi * B) * g.Wc + bj0 * B;
     L.Wc = g.Wc;
     L.nblk = min(Tl::NB, g.nbw - bj0);
-    L.inv_df = a.inv_df;
     L.status = a.status;
     griddep_wait();
+    L.inv_df = a.alpha ? a.alpha[k] : a.inv_df;
     const double nz = linear_tile<B>(L, smem, rel, &s_start, shd);
     if (threadIdx.x == 0)
         a.partial[(int64_t)k * gridDim.x * gridDim.y + (int64_t)blockIdx.y * gridDim.x + blockIdx.x] = nz;
@@ -170,6 +170,87 @@ __global__ void ida_sigma_kernel(const double* __restrict__ partial, int cpi,
         if (!isfinite(v)) set_status(status, ABCS_DEV_NONFINITE);
         sigma[k] = (float)v;
         if (trace) trace[(int64_t)k * iters + t] = (float)v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// D-AMP / DAMP-D (Eqs. 24, 27): the Onsager coefficient from a Monte-Carlo
+// estimate of the denoiser's divergence, div ~ b^T (D(r + eps b) - D(r)) / eps
+// with eps = eps_rel max|r| per image and the caller's probe b.
+// Grid (chunks, images) for the element-wise kernels.
+// ---------------------------------------------------------------------------
+constexpr int kDampThreads = 256;
+
+// amax[k] = bits of max |r| over image k (non-negative floats order as
+// unsigned integers); cleared by damp_clear_kernel first
+__global__ void damp_clear_kernel(unsigned* __restrict__ amax) {
+    griddep_wait();
+    amax[blockIdx.x] = 0u;
+}
+
+__global__ void __launch_bounds__(kDampThreads) damp_amax_kernel(const float* __restrict__ r, int64_t per_img,
+                                                                 unsigned* __restrict__ amax) {
+    griddep_wait();
+    const int k = blockIdx.y;
+    const float* rk = r + (int64_t)k * per_img;
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_img; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(rk[i]));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(amax + k, __float_as_uint(m));
+}
+
+ABCS_D float damp_eps(unsigned amax_bits, float eps_rel) {
+    const float e = eps_rel * __uint_as_float(amax_bits);
+    return e > 0.f ? e : eps_rel;
+}
+
+__global__ void __launch_bounds__(kDampThreads) damp_perturb_kernel(const float* __restrict__ r,
+                                                                    const float* __restrict__ probe, int64_t per_img,
+                                                                    const unsigned* __restrict__ amax, float eps_rel,
+                                                                    float* __restrict__ rp) {
+    griddep_wait();
+    const int k = blockIdx.y;
+    const float eps = damp_eps(amax[k], eps_rel);
+    const int64_t o = (int64_t)k * per_img;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_img; i += (int64_t)gridDim.x * blockDim.x)
+        rp[o + i] = fmaf(eps, __ldg(probe + o + i), r[o + i]);
+}
+
+// per CTA: sum of b (xp - x) in FP64
+__global__ void __launch_bounds__(kDampThreads) damp_div_kernel(const float* __restrict__ probe,
+                                                                const float* __restrict__ xp,
+                                                                const float* __restrict__ x, int64_t per_img,
+                                                                double* __restrict__ partial) {
+    __shared__ double sh[32];
+    griddep_wait();
+    const int k = blockIdx.y;
+    const int64_t o = (int64_t)k * per_img;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_img; i += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)__ldg(probe + o + i) * ((double)xp[o + i] - (double)x[o + i]);
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[(int64_t)k * gridDim.x + blockIdx.x] = acc;
+}
+
+// one warp per image: partials in a fixed order, alpha = inv_df div / M
+__global__ void damp_alpha_kernel(const double* __restrict__ partial, int chunks, const int64_t* __restrict__ offsets,
+                                  int64_t nB, const unsigned* __restrict__ amax, float eps_rel, float inv_df,
+                                  float* __restrict__ alpha, float* __restrict__ trace, int iters, int t,
+                                  uint32_t* status) {
+    griddep_wait();
+    const int k = blockIdx.x;
+    double s = 0.0;
+    for (int j = threadIdx.x; j < chunks; j += 32) s += partial[(int64_t)k * chunks + j];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) {
+        const int64_t m = offsets[(int64_t)(k + 1) * nB] - offsets[(int64_t)k * nB];
+        const double div = s / (double)damp_eps(amax[k], eps_rel);
+        const double v = m > 0 ? (double)inv_df * div / (double)m : 0.0;
+        if (!isfinite(v)) set_status(status, ABCS_DEV_NONFINITE);
+        alpha[k] = (float)v;
+        if (trace) trace[(int64_t)k * iters + t + 1] = (float)v;
     }
 }
 
@@ -471,6 +552,37 @@ cudaError_t launch_ida_sigma(const ImgGeom& g, const int64_t* offsets, const dou
                              cudaStream_t s) {
     return launch_pdl(ida_sigma_kernel, dim3(g.n_img), dim3(32), 0, s, partial, ida_ctas_per_image(g), offsets,
                       (int64_t)g.n_blocks, sigma, sigma_trace, iters, t, status);
+}
+
+int damp_chunks(const ImgGeom& g) {
+    const int64_t per_img = (int64_t)g.Hc * g.Wc;
+    const int64_t want = (152 * 8 + g.n_img - 1) / g.n_img, cap = (per_img + 4 * kDampThreads - 1) / (4 * kDampThreads);
+    return (int)(want < cap ? (want > 0 ? want : 1) : (cap > 0 ? cap : 1));
+}
+
+cudaError_t launch_damp_perturb(const ImgGeom& g, const float* r, const float* probe, float eps_rel,
+                                unsigned* amax, float* rp, cudaStream_t s) {
+    const int64_t per_img = (int64_t)g.Hc * g.Wc;
+    const dim3 grid((unsigned)damp_chunks(g), (unsigned)g.n_img);
+    cudaError_t e = launch_pdl(damp_clear_kernel, dim3((unsigned)g.n_img), dim3(1), 0, s, amax);
+    if (!e) e = launch_pdl(damp_amax_kernel, grid, dim3(kDampThreads), 0, s, r, per_img, amax);
+    if (!e)
+        e = launch_pdl(damp_perturb_kernel, grid, dim3(kDampThreads), 0, s, r, probe, per_img, (const unsigned*)amax,
+                       eps_rel, rp);
+    return e;
+}
+
+cudaError_t launch_damp_alpha(const ImgGeom& g, const int64_t* offsets, const float* probe, const float* xp,
+                              const float* x, const unsigned* amax, float eps_rel, float inv_df, double* partial,
+                              float* alpha, float* alpha_trace, int iters, int t, uint32_t* status, cudaStream_t s) {
+    const int64_t per_img = (int64_t)g.Hc * g.Wc;
+    const int chunks = damp_chunks(g);
+    cudaError_t e = launch_pdl(damp_div_kernel, dim3((unsigned)chunks, (unsigned)g.n_img), dim3(kDampThreads), 0, s,
+                               probe, xp, x, per_img, partial);
+    if (!e)
+        e = launch_pdl(damp_alpha_kernel, dim3((unsigned)g.n_img), dim3(32), 0, s, (const double*)partial, chunks,
+                       offsets, (int64_t)g.n_blocks, amax, eps_rel, inv_df, alpha, alpha_trace, iters, t, status);
+    return e;
 }
 
 size_t ida_batch_smem(unsigned used_b_mask) {
