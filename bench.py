@@ -252,6 +252,64 @@ def images_learned_vs_plain(h, n=32):
                                 "equal": v["equal"]} for r, v in out.items()}}
 
 
+def damp_vs_ida(h, n=16, H=512, W=512, B=16, iters=(10, 30)):
+    """Sec. VI-1/2, Figs. 7-8: D-AMP (Eq. 24, D_F = 1), DAMP-D (Eq. 27,
+    D_F = 2) and IDA (Eq. 28, D_F = 2), all with the TI-DCT denoiser, on n
+    held-out 512x512 images sensed with AL-DCT-DD and AL-DCT-BBV at
+    r = 0.1 and 0.3: mean PSNR after each iteration count, and the time per
+    iteration of each (D-AMP runs the denoiser twice per iteration)."""
+    import torch
+    from paper_2001_09632_gb300 import abcs, synth
+    imgs = synth.gen_batch(n, H, W, 8765)
+    d_img = torch.from_numpy(imgs).cuda()
+    clean = d_img.float()
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    probe = torch.where(torch.rand((n, H, W), device="cuda", generator=gen) < 0.5, -1.0, 1.0)
+    nB = (H // B) * (W // B)
+    x = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
+    lam = 2.3
+
+    def psnr():
+        d = x.clamp(0, 255) - clean
+        mse = (d * d).flatten(1).mean(1)
+        return float((10.0 * torch.log10(255.0 ** 2 / mse)).mean())
+
+    out = {"images": n, "size": [H, W], "B": B, "denoiser": "tidct", "lambda": lam, "psnr": {}, "ms_per_iter": {}}
+    for vname, variant in (("dd", abcs.DD), ("bbv", abcs.BBV)):
+        for r in (0.1, 0.3):
+            plan = abcs.abcs_plan(H, W, B, r, variant)
+            c = torch.empty(n * nB, dtype=torch.int32, device="cuda")
+            o = torch.empty(n * nB + 1, dtype=torch.int64, device="cuda")
+            y = torch.empty(n * plan["M"], dtype=torch.float32, device="cuda")
+            abcs.abcs_sense(h, d_img, n, H, W, W, H * W, B, r, variant, abcs.FP32, c, o, y, n * plan["M"])
+            row = {}
+            for name in ("ida", "damp_d", "d_amp"):
+                for it in iters:
+                    if name == "ida":
+                        abcs.abcs_ida(h, c, o, y, n, H, W, B, it, 2.0, abcs.DEN_TIDCT, lam, None, x)
+                    else:
+                        abcs.abcs_damp(h, c, o, y, n, H, W, B, it, 2.0 if name == "damp_d" else 1.0,
+                                       abcs.DEN_TIDCT, lam, None, probe, x)
+                    row[f"{name}_{it}"] = psnr()
+            out["psnr"][f"{vname}_r{r}"] = row
+    assert abcs.abcs_sync_status(h) == 0
+    # time per iteration at DD r = 0.1
+    for name in ("ida", "damp_d", "d_amp"):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        if name == "ida":
+            abcs.abcs_ida(h, c, o, y, n, H, W, B, 10, 2.0, abcs.DEN_TIDCT, lam, None, x)
+        else:
+            abcs.abcs_damp(h, c, o, y, n, H, W, B, 10, 2.0 if name == "damp_d" else 1.0, abcs.DEN_TIDCT, lam,
+                           None, probe, x)
+        e1.record()
+        torch.cuda.synchronize()
+        out["ms_per_iter"][name] = e0.elapsed_time(e1) / 10
+    assert abcs.abcs_sync_status(h) == 0
+    return out
+
+
 def thi_correlation(h, n=64, H=512, W=512, B=16, reps=5):
     """THI (Sec. IV, Sec. V-B): the correlation coefficient rho between the
     per-block counts BBV / DD allocate and the counts THI keeps at the same
@@ -464,6 +522,7 @@ def main():
             extras["learned_vs_plain"] = {"video_1920x1088_dd_r025": video_learned_vs_plain(h),
                                           "images_512": images_learned_vs_plain(h)}
             extras["thi"] = thi_correlation(h)
+            extras["damp_vs_ida"] = damp_vs_ida(h)
 
     if rank != 0:
         abcs.abcs_destroy(h)
