@@ -252,6 +252,50 @@ def images_learned_vs_plain(h, n=32):
                                 "equal": v["equal"]} for r, v in out.items()}}
 
 
+def video_stream(h, n_frames=120, H=1088, W=1920, fpb=30):
+    """C5 as a stream (SURVEY next row 4): 120 frames of 1920x1088 in pinned
+    host memory, 30 per batch, each batch copied to the device, sensed with
+    AL-DCT-DD at r = 0.25 and reconstructed by IDA; Mpixel/s from the first
+    copy to the last image, with the stages of consecutive batches run one
+    after another or overlapped on three streams (paper_2001_09632_gb300.video;
+    identical images either way).  Learned IDA (1 iteration) and plain IDA
+    (30 iterations)."""
+    import numpy as np
+    import torch
+    from paper_2001_09632_gb300 import abcs, synth, train
+    from paper_2001_09632_gb300.video import VideoPipeline
+    seed = train.EVAL_SEED + 7
+    frames = torch.from_numpy(np.concatenate([synth.gen_video(min(fpb, n_frames - f0), H, W, seed, first_frame=f0)
+                                              for f0 in range(0, n_frames, fpb)])).pin_memory()
+    p = torch.tensor(train.load_weights(), device="cuda")
+    packed = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
+    abcs.abcs_cnn_pack(h, p, packed)
+    out = {"frames": n_frames, "size": [H, W], "frames_per_batch": fpb, "variant": "DD", "subrate": 0.25,
+           "from": "pinned host frames (H2D copy inside the timed region)"}
+    for name, iters, den in (("learned_1", 1, abcs.DEN_CNN), ("plain_30", 30, abcs.DEN_TIDCT)):
+        vp = VideoPipeline(H, W, 16, 0.25, abcs.DD, fpb, iters, den, cnn_packed=packed)
+        x = torch.empty((n_frames, vp.Hc, vp.Wc), dtype=torch.float32, device="cuda")
+        vp.run(frames, x, overlap=True)                          # warm-up
+        row = {}
+        for mode, ov in (("sequential", False), ("overlapped", True)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            vp.run(frames, x, overlap=ov)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            row[mode] = {"ms": ms, "Mpx_per_s": n_frames * vp.Hc * vp.Wc / (ms * 1e-3) / 1e6}
+        clean = frames[:, :vp.Hc, :vp.Wc].cuda().float()
+        d = x.clamp(0, 255) - clean
+        row["psnr"] = float((10.0 * torch.log10(255.0 ** 2 / (d * d).flatten(1).mean(1))).mean())
+        row["overlap_gain"] = row["sequential"]["ms"] / row["overlapped"]["ms"]
+        out[name] = row
+        vp.close()
+        del x, clean, d
+    return out
+
+
 def damp_vs_ida(h, n=16, H=512, W=512, B=16, iters=(10, 30)):
     """Sec. VI-1/2, Figs. 7-8: D-AMP (Eq. 24, D_F = 1), DAMP-D (Eq. 27,
     D_F = 2) and IDA (Eq. 28, D_F = 2), all with the TI-DCT denoiser, on n
@@ -523,6 +567,7 @@ def main():
                                           "images_512": images_learned_vs_plain(h)}
             extras["thi"] = thi_correlation(h)
             extras["damp_vs_ida"] = damp_vs_ida(h)
+            extras["video_stream"] = video_stream(h)
 
     if rank != 0:
         abcs.abcs_destroy(h)
