@@ -27,6 +27,8 @@ Functions and the passages they follow:
   cnn_*, density_map, adam_step ... the learned residual denoiser (DnCNN-style, Sec. VI-4)
   psnr, ssim ...................... quality measures (Sec. I, ref. [18])
   mc_divergence, damp ............. D-AMP (Eq. 24) and DAMP-D (Eq. 27) with a Monte-Carlo divergence
+  haar_matrix, bm3d_ht ............ BM3D's hard-thresholding step (the plain denoiser the paper
+                                    names in Sec. VII, ref. [22]; stated readings)
   full_coefficients, thi_* ........ THI: full sensing, one threshold for the whole image
                                     (Sec. IV; Sec. V-B and Table 2), Pearson correlation
 """
@@ -460,6 +462,88 @@ def ida(y: np.ndarray, counts: np.ndarray, Hc: int, Wc: int, B: int, iters: int,
     if trace:
         return x, sigmas, rs, zs
     return x, sigmas
+
+
+# --------------------------------------------------------------------------
+# BM3D, hard-thresholding step (Dabov et al., ref. [22]): the plain
+# denoiser the paper pairs with IDA besides DnCNN (Sec. VII, Fig. 7a).  The
+# paper only names it; the steps below follow the published algorithm, with
+# its parameters for the hard-thresholding step, and the choices it leaves
+# open are stated.
+# --------------------------------------------------------------------------
+def haar_matrix(n: int) -> np.ndarray:
+    """Orthonormal Haar transform of length n = 2^k (row 0 = the mean):
+    H_1 = [1], H_2n = [H_n (x) [1, 1]; I_n (x) [1, -1]] / sqrt(2)."""
+    H = np.ones((1, 1))
+    while H.shape[0] < n:
+        m = H.shape[0]
+        H = np.vstack([np.kron(H, [1.0, 1.0]), np.kron(np.eye(m), [1.0, -1.0])]) / math.sqrt(2.0)
+    return H
+
+
+def bm3d_ht(r: np.ndarray, sigma: float, lam3d: float = 2.7, N1: int = 8, N2: int = 16, Ns: int = 39,
+            Nstep: int = 3, beta: float = 2.0) -> np.ndarray:
+    """BM3D's basic estimate of r (noise level sigma).
+
+    - Reference patches (N1 x N1) at rows 0, Nstep, 2 Nstep, ... and the
+      last row H - N1 (the same for columns).
+    - Candidates: every patch whose top-left corner lies within Ns // 2 of
+      the reference's, inside the image.
+    - Distance d = ||P_ref - P||^2 / N1^2 on the noisy patches.  Reading:
+      no prefiltering; tau = 2500 for sigma <= 40, else 5000.
+    - The group: the reference first, then the other candidates with
+      d <= tau ordered by (d, row, column); the first min(N2, count) rounded
+      down to a power of two.
+    - 3D transform: orthonormal 2D DCT of every patch, then the orthonormal
+      Haar transform along the group.
+    - Hard threshold: zero the coefficients with |c| <= lam3d sigma.  Reading:
+      the group's 3D DC coefficient is kept.
+    - Weight w = 1 / (kept coefficients); inverse transforms; aggregation
+      x = sum w K P / sum w K with the Kaiser window K = k k^T,
+      k = kaiser(N1, beta).
+    """
+    r = np.asarray(r, dtype=np.float64)
+    H, W = r.shape
+    D = dct_matrix(N1)
+    tau = 2500.0 if sigma <= 40.0 else 5000.0
+    k1 = np.kaiser(N1, beta)
+    K = np.outer(k1, k1)
+    num = np.zeros((H, W))
+    den = np.zeros((H, W))
+    ys = sorted(set(list(range(0, H - N1 + 1, Nstep)) + [H - N1]))
+    xs = sorted(set(list(range(0, W - N1 + 1, Nstep)) + [W - N1]))
+    half = Ns // 2
+    thr = lam3d * sigma
+    for y in ys:
+        for x in xs:
+            ref = r[y:y + N1, x:x + N1]
+            cands = []
+            for yy in range(max(0, y - half), min(H - N1, y + half) + 1):
+                for xx in range(max(0, x - half), min(W - N1, x + half) + 1):
+                    if (yy, xx) == (y, x):
+                        continue
+                    d = float(np.sum((ref - r[yy:yy + N1, xx:xx + N1]) ** 2)) / (N1 * N1)
+                    if d <= tau:
+                        cands.append((d, yy, xx))
+            cands.sort()
+            cands = [(0.0, y, x)] + cands                                        # the reference first
+            n = 1
+            while 2 * n <= min(N2, len(cands)):
+                n *= 2
+            grp = cands[:n]
+            P = np.stack([r[yy:yy + N1, xx:xx + N1] for _, yy, xx in grp])       # n, N1, N1
+            C = D @ P @ D.T                                                      # 2D DCT per patch
+            Hn = haar_matrix(n)
+            T = np.tensordot(Hn, C, axes=(1, 0))                                 # Haar along the group
+            keep = np.abs(T) > thr
+            keep[0, 0, 0] = True
+            T = np.where(keep, T, 0.0)
+            w = 1.0 / float(np.count_nonzero(keep))
+            Pe = D.T @ np.tensordot(Hn.T, T, axes=(1, 0)) @ D
+            for (_, yy, xx), pe in zip(grp, Pe):
+                num[yy:yy + N1, xx:xx + N1] += w * K * pe
+                den[yy:yy + N1, xx:xx + N1] += w * K
+    return num / den
 
 
 # --------------------------------------------------------------------------
