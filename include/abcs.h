@@ -90,7 +90,8 @@ typedef enum abcs_precision {
 typedef enum abcs_denoiser {
     ABCS_DEN_NONE = 0,    /* identity: x^{t+1} = x^t + A^T z^t (used to check the linear part) */
     ABCS_DEN_TIDCT = 1,   /* plain: shift-averaged 8x8 DCT hard thresholding at lambda * sigma */
-    ABCS_DEN_CNN = 2      /* learned: residual CNN, weights from abcs_cnn_* */
+    ABCS_DEN_CNN = 2,     /* learned: residual CNN, weights from abcs_cnn_* */
+    ABCS_DEN_BM3D = 3     /* plain: BM3D's hard-thresholding step (abcs_bm3d_denoise); lambda = lambda_3D */
 } abcs_denoiser;
 
 typedef struct abcs_handle abcs_handle;
@@ -235,6 +236,25 @@ abcs_status abcs_ida_capture(abcs_handle* h, const int32_t* counts, const int64_
  *   sigma   [device] float [n_img] */
 abcs_status abcs_denoise_tidct(abcs_handle* h, const float* in, int n_img, int H, int W,
                                const float* sigma, double lambda, float* out, void* stream);
+
+/* BM3D's hard-thresholding step (Dabov et al., ref. [22] of the paper; the
+ * plain denoiser it pairs with IDA in Sec. VII) applied to every image:
+ *   8 x 8 reference patches every 3 pixels (and at the last row / column);
+ *   block matching over every position within 19 pixels, distance
+ *   ||P_ref - P||^2 / 64, threshold tau = 2500 (sigma <= 40) or 5000;
+ *   groups of the reference and its closest matches, at most 16, a power of
+ *   two, ties in (distance, row, column) order;
+ *   2D DCT of each patch, orthonormal Haar along the group, coefficients with
+ *   |c| <= lambda sigma zeroed (the 3D DC kept), inverse transforms;
+ *   aggregation weighted by 1 / (kept coefficients) and an 8 x 8 Kaiser
+ *   window (beta 2).  BM3D uses lambda = 2.7.
+ *   in, out [device] float [n_img][H][W] (in != out), H, W >= 8;
+ *   sigma [device] float [n_img].
+ * Uses the handle's workspace (two planes of the batch's size).  The
+ * aggregation uses atomic adds, so results may differ in the last bits
+ * between runs. */
+abcs_status abcs_denoise_bm3d(abcs_handle* h, const float* in, int n_img, int H, int W, const float* sigma,
+                              double lambda, float* out, void* stream);
 
 /* Learned denoiser.  The paper plugs a pretrained 17-layer DnCNN into IDA
  * (Sec. VI-4); this library's learned denoiser is a smaller residual CNN of

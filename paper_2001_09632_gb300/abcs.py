@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_PKG, "libabcs.so")
 
 ZZ, BBV, DD = 0, 1, 2
 FP32, TC_FP16X2, TC_BF16X2, TC_BF16 = 0, 1, 2, 3
-DEN_NONE, DEN_TIDCT, DEN_CNN = 0, 1, 2
+DEN_NONE, DEN_TIDCT, DEN_CNN, DEN_BM3D = 0, 1, 2, 3
 VARIANTS = {"zz": ZZ, "bbv": BBV, "dd": DD}
 PRECISIONS = {"fp32": FP32, "fp16x2": TC_FP16X2, "bf16x2": TC_BF16X2, "bf16": TC_BF16}
 
@@ -63,6 +63,7 @@ _SIGS = {
     "abcs_reconstruct": [_P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P],
     "abcs_ida": [_P, _P, _P, _P, _I, _I, _I, _I, _I, _D, _I, _D, _P, _P, _P, _P],
     "abcs_denoise_tidct": [_P, _P, _I, _I, _I, _P, _D, _P, _P],
+    "abcs_denoise_bm3d": [_P, _P, _I, _I, _I, _P, _D, _P, _P],
     "abcs_sync_status": [_P, _P, C.POINTER(C.c_uint32)],
     "abcs_sense_noalloc": [_P, _I, _I, _I, _L, _L, _I, _D, _I, _I, _P, _P, _P, _L, _P, _P],
     "abcs_ida_batch": [_P, _P, _I, _P, _P, _P, _L, _I, _D, _I, _D, _P, _P, _P],
@@ -160,6 +161,11 @@ def abcs_ida_capture(h, counts, offsets, y, n_img, H, W, B, t, damping, denoiser
     _check(lib.abcs_ida_capture(h, _ptr(counts), _ptr(offsets), _ptr(y), n_img, H, W, B, t, damping,
                                 denoiser, lam, _ptr(cnn_weights), _ptr(r_out), _ptr(sigma_out),
                                 _stream(stream)))
+
+
+def abcs_denoise_bm3d(h, inp, n_img, H, W, sigma, lam, out, stream=None) -> None:
+    """BM3D's hard-thresholding step (lam = lambda_3D, 2.7 in BM3D)."""
+    _check(lib.abcs_denoise_bm3d(h, _ptr(inp), n_img, H, W, _ptr(sigma), lam, _ptr(out), _stream(stream)))
 
 
 def abcs_denoise_tidct(h, inp, n_img, H, W, sigma, lam, out, stream=None) -> None:

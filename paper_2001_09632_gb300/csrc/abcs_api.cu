@@ -182,6 +182,7 @@ abcs_status abcs_create(abcs_handle** out) {
     ABCS_CUDA(upload_tables_dct(), "upload tables");
     ABCS_CUDA(upload_tables_ida(), "upload tables");
     ABCS_CUDA(upload_tables_tc(), "upload tables");
+    ABCS_CUDA(setup_bm3d_tables(), "upload tables");
     ABCS_CUDA(setup_tc_fragments(), "tensor-core fragment setup");
     abcs_handle* h = new abcs_handle;
     h->device = dev;
@@ -332,6 +333,27 @@ abcs_status abcs_reconstruct(abcs_handle* h, const int32_t* counts, const int64_
     return ABCS_OK;
 }
 
+abcs_status abcs_denoise_bm3d(abcs_handle* h, const float* in, int n_img, int H, int W, const float* sigma,
+                              double lambda, float* out, void* stream) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    if (!in || !out || !sigma) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (in == out) return fail(ABCS_ERR_INVALID_ARG, "in and out must differ");
+    if (H < 8 || W < 8 || n_img < 1 || n_img > 65535) return fail(ABCS_ERR_INVALID_ARG, "bad size");
+    if (!(lambda >= 0.0)) return fail(ABCS_ERR_INVALID_ARG, "lambda must be >= 0");
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(ABCS_ERR_CUDA, "cannot select the handle's device");
+    const int64_t npx = (int64_t)n_img * H * W;
+    Carver c;
+    const size_t o_num = c.take<float>(npx);
+    const size_t o_den = c.take<float>(npx);
+    abcs_status st = ensure_ws(h, c.off);
+    if (st) return st;
+    ABCS_CUDA(launch_bm3d(in, out, n_img, H, W, sigma, (float)lambda, at<float>(h, o_num), at<float>(h, o_den),
+                          static_cast<cudaStream_t>(stream)),
+              "bm3d launch");
+    return ABCS_OK;
+}
+
 abcs_status abcs_denoise_tidct(abcs_handle* h, const float* in, int n_img, int H, int W,
                                const float* sigma, double lambda, float* out, void* stream) {
     if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
@@ -396,10 +418,12 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
     if (!counts || !offsets || !y) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
     if (iters < 0) return fail(ABCS_ERR_INVALID_ARG, "iters must be >= 0");
     if (!(damping > 0.0)) return fail(ABCS_ERR_INVALID_ARG, "damping must be > 0");
-    if (denoiser < ABCS_DEN_NONE || denoiser > ABCS_DEN_CNN)
+    if (denoiser < ABCS_DEN_NONE || denoiser > ABCS_DEN_BM3D)
         return fail(ABCS_ERR_INVALID_ARG, "bad denoiser %d", denoiser);
-    if (denoiser == ABCS_DEN_TIDCT && !(lambda >= 0.0))
+    if ((denoiser == ABCS_DEN_TIDCT || denoiser == ABCS_DEN_BM3D) && !(lambda >= 0.0))
         return fail(ABCS_ERR_INVALID_ARG, "lambda must be >= 0");
+    if (denoiser == ABCS_DEN_BM3D && (H < 8 || W < 8))
+        return fail(ABCS_ERR_INVALID_ARG, "BM3D needs at least 8 x 8 pixels");
     if (denoiser == ABCS_DEN_CNN && !cnn_weights)
         return fail(ABCS_ERR_INVALID_ARG, "CNN denoiser needs packed weights (abcs_cnn_pack)");
     DeviceGuard dg(h->device);
@@ -423,6 +447,8 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
     const size_t o_sig = c.take<float>(n_img);
     const size_t o_act = c.take<uint16_t>(denoiser == ABCS_DEN_CNN ? (size_t)2 * npx * 32 : 0);
     const size_t o_den = c.take<float>(denoiser == ABCS_DEN_CNN ? npx : 0);
+    const size_t o_bnum = c.take<float>(denoiser == ABCS_DEN_BM3D ? npx : 0);
+    const size_t o_bden = c.take<float>(denoiser == ABCS_DEN_BM3D ? npx : 0);
     const size_t o_x = c.take<float>(capturing ? npx : 0);
     // D-AMP / DAMP-D: perturbed input and its denoised image, max |r|, divergence partials, alpha
     const bool damp = probe != nullptr;
@@ -473,6 +499,11 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
         if (denoiser == ABCS_DEN_TIDCT) {
             ABCS_CUDA(launch_tidct(a.r, x_out, n_img, g.Hc, g.Wc, sig, (float)lambda, s), "tidct launch");
             x_cur = x_out;
+        } else if (denoiser == ABCS_DEN_BM3D) {
+            ABCS_CUDA(launch_bm3d(a.r, x_out, n_img, g.Hc, g.Wc, sig, (float)lambda, at<float>(h, o_bnum),
+                                  at<float>(h, o_bden), s),
+                      "bm3d launch");
+            x_cur = x_out;
         } else if (denoiser == ABCS_DEN_CNN) {
             ABCS_CUDA(cnn_forward(cnn_weights, a.r, sig, dens, n_img, g.Hc, g.Wc, at<void>(h, o_act), 0, 0, x_out,
                                   h->status, s),
@@ -491,6 +522,11 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
             const float* xq = rp;         // identity
             if (denoiser == ABCS_DEN_TIDCT) {
                 ABCS_CUDA(launch_tidct(rp, xp, n_img, g.Hc, g.Wc, sig, (float)lambda, s), "tidct launch");
+                xq = xp;
+            } else if (denoiser == ABCS_DEN_BM3D) {
+                ABCS_CUDA(launch_bm3d(rp, xp, n_img, g.Hc, g.Wc, sig, (float)lambda, at<float>(h, o_bnum),
+                                      at<float>(h, o_bden), s),
+                          "bm3d launch");
                 xq = xp;
             } else if (denoiser == ABCS_DEN_CNN) {
                 ABCS_CUDA(cnn_forward(cnn_weights, rp, sig, dens, n_img, g.Hc, g.Wc, at<void>(h, o_act), 0, 0, xp,

@@ -268,6 +268,11 @@ cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, con
                      int n, int H, int W, void* ws, float* grad, float* loss, uint32_t* status, cudaStream_t s);
 // per-pixel measured fraction m_i / B^2 of the pixel's block (k_ida.cu)
 cudaError_t launch_density(const ImgGeom& g, const int32_t* counts, float* out, cudaStream_t s);
+// BM3D hard-thresholding step (k_bm3d.cu): in, out [n_img][H][W]; num, den
+// workspace of the same size; tables uploaded once per device
+cudaError_t setup_bm3d_tables();
+cudaError_t launch_bm3d(const float* in, float* out, int n_img, int H, int W, const float* sigma, float lambda,
+                        float* num, float* den, cudaStream_t s);
 // THI selection (k_thi.cu): coeffs n_img x nB x bb (zigzag rank order);
 // workspace prefix/rem (n_img), hist (n_img x 256), gt/eq (n_img x nB)
 cudaError_t launch_thi(const float* coeffs, int n_img, int nB, int bb, int64_t M, const int32_t* adaptive,
