@@ -296,6 +296,59 @@ def video_stream(h, n_frames=120, H=1088, W=1920, fpb=30):
     return out
 
 
+def bm3d_judge(h, n=16, H=512, W=512, B=16, iters=(10, 30)):
+    """BM3D (hard-thresholding step) as IDA's plain denoiser, the one the
+    paper pairs with IDA (Sec. VII, Fig. 7a), beside TI-DCT and the learned
+    CNN: mean PSNR on n held-out 512x512 images (DD and BBV at r = 0.1 and
+    0.3) and Mpixel/s of each; learned IDA (1 iteration) against plain IDA
+    with BM3D (30 iterations)."""
+    import torch
+    from paper_2001_09632_gb300 import abcs, synth, train
+    imgs = synth.gen_batch(n, H, W, 8765)
+    d_img = torch.from_numpy(imgs).cuda()
+    clean = d_img.float()
+    nB = (H // B) * (W // B)
+    x = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
+    p = torch.tensor(train.load_weights(), device="cuda")
+    packed = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
+    abcs.abcs_cnn_pack(h, p, packed)
+
+    def psnr():
+        d = x.clamp(0, 255) - clean
+        return float((10.0 * torch.log10(255.0 ** 2 / (d * d).flatten(1).mean(1))).mean())
+
+    def run(c, o, y, it, den, lam, pk):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        abcs.abcs_ida(h, c, o, y, n, H, W, B, it, 2.0, den, lam, pk, x)
+        e1.record()
+        torch.cuda.synchronize()
+        return psnr(), n * H * W / (e0.elapsed_time(e1) * 1e-3) / 1e6
+
+    out = {"images": n, "size": [H, W], "B": B, "lambda_tidct": 2.3, "lambda_bm3d": 2.7, "cases": {}}
+    for vname, variant in (("dd", abcs.DD), ("bbv", abcs.BBV)):
+        for r in (0.1, 0.3):
+            plan = abcs.abcs_plan(H, W, B, r, variant)
+            c = torch.empty(n * nB, dtype=torch.int32, device="cuda")
+            o = torch.empty(n * nB + 1, dtype=torch.int64, device="cuda")
+            y = torch.empty(n * plan["M"], dtype=torch.float32, device="cuda")
+            abcs.abcs_sense(h, d_img, n, H, W, W, H * W, B, r, variant, abcs.FP32, c, o, y, n * plan["M"])
+            row = {}
+            run(c, o, y, 1, abcs.DEN_BM3D, 2.7, None)                   # warm-up
+            for it in iters:
+                for name, den, lam, pk in (("tidct", abcs.DEN_TIDCT, 2.3, None), ("bm3d", abcs.DEN_BM3D, 2.7, None)):
+                    ps, mpx = run(c, o, y, it, den, lam, pk)
+                    row[f"{name}_{it}"] = {"psnr": ps, "Mpx_per_s": mpx}
+            ps, mpx = run(c, o, y, 1, abcs.DEN_CNN, 0.0, packed)
+            row["learned_1"] = {"psnr": ps, "Mpx_per_s": mpx}
+            ref = row[f"bm3d_{iters[-1]}"]
+            row["learned_1_vs_bm3d"] = {"dpsnr": ps - ref["psnr"], "speedup": mpx / ref["Mpx_per_s"]}
+            out["cases"][f"{vname}_r{r}"] = row
+    assert abcs.abcs_sync_status(h) == 0
+    return out
+
+
 def damp_vs_ida(h, n=16, H=512, W=512, B=16, iters=(10, 30)):
     """Sec. VI-1/2, Figs. 7-8: D-AMP (Eq. 24, D_F = 1), DAMP-D (Eq. 27,
     D_F = 2) and IDA (Eq. 28, D_F = 2), all with the TI-DCT denoiser, on n
@@ -568,6 +621,7 @@ def main():
             extras["thi"] = thi_correlation(h)
             extras["damp_vs_ida"] = damp_vs_ida(h)
             extras["video_stream"] = video_stream(h)
+            extras["bm3d_judge"] = bm3d_judge(h)
 
     if rank != 0:
         abcs.abcs_destroy(h)

@@ -5,7 +5,9 @@
 //   - distances d = ||P_ref - P||^2 / 64 of every candidate position;
 //   - the group: the reference, then the candidates with d <= tau ordered by
 //     (d, row, column), n = the largest power of two <= min(16, count),
-//     chosen by repeated block-wide minimum of 64-bit keys (d's bits, index);
+//     chosen by repeated block-wide minimum of 64-bit keys (d's bits, index)
+//     held in registers (a thread owns a strip of 8 candidates of one row,
+//     whose distances share each loaded row segment);
 //   - 2D DCT of each patch, orthonormal Haar along the group, hard threshold
 //     at lambda sigma (the group's 3D DC kept), count, inverses;
 //   - aggregation of w K P (w = 1 / kept, K the 8 x 8 Kaiser window) and of
@@ -19,27 +21,82 @@ namespace abcs {
 
 namespace {
 
-constexpr int kN1 = 8, kN2 = 16, kHalf = 19, kStep = 3;
+constexpr int kN1 = 8, kN2 = 16, kHalf = 19, kStep = 3, kStrip = 8;
 constexpr int kWin = 2 * kHalf + kN1;          // 46: neighbourhood side
 constexpr int kWinLd = kWin + 1;
-constexpr int kMaxCand = (2 * kHalf + 1) * (2 * kHalf + 1);   // 1521
 constexpr int kBm3dThreads = 256;
 
 __constant__ float c_bm_dct[8][8];      // D[k][n], orthonormal DCT-II
-__constant__ float c_bm_haar[5][16][16];  // orthonormal Haar of length 1, 2, 4, 8, 16
 __constant__ float c_bm_kaiser[8];
 
 ABCS_D unsigned long long bm_min(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
 
+// Orthonormal Haar of length N by butterflies, H_2n = [H_n (x) (1, 1); I_n (x) (1, -1)] / sqrt 2:
+// the pairwise sums recurse, the pairwise differences are the last n outputs.
+template <int N>
+ABCS_D void haar_fwd(float (&x)[16]) {
+    if constexpr (N > 1) {
+        float s[N / 2], d[N / 2];
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            s[i] = (x[2 * i] + x[2 * i + 1]) * 0.70710678118654752f;
+            d[i] = (x[2 * i] - x[2 * i + 1]) * 0.70710678118654752f;
+        }
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            x[i] = s[i];
+            x[N / 2 + i] = d[i];
+        }
+        haar_fwd<N / 2>(x);
+    }
+}
+
+template <int N>
+ABCS_D void haar_inv(float (&x)[16]) {
+    if constexpr (N > 1) {
+        haar_inv<N / 2>(x);
+        float y[N];
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            y[2 * i] = (x[i] + x[N / 2 + i]) * 0.70710678118654752f;
+            y[2 * i + 1] = (x[i] - x[N / 2 + i]) * 0.70710678118654752f;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] = y[i];
+    }
+}
+
+// coefficient (u, v) of the group's N patches: Haar, zero |c| <= thr (the
+// 3D DC kept when dc), inverse into T; returns the coefficients kept
+template <int N>
+ABCS_D int haar_threshold(const float (&P)[kN2][kN1][kN1 + 1], float (&T)[kN2][kN1][kN1 + 1], int u, int v,
+                          float thr, bool dc) {
+    float z[16];
+#pragma unroll
+    for (int g = 0; g < N; ++g) z[g] = P[g][u][v];
+    haar_fwd<N>(z);
+    int kept = 0;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        const bool keep = fabsf(z[q]) > thr || (q == 0 && dc);
+        z[q] = keep ? z[q] : 0.f;
+        kept += keep;
+    }
+    haar_inv<N>(z);
+#pragma unroll
+    for (int g = 0; g < N; ++g) T[g][u][v] = z[g];
+    return kept;
+}
+
 // reference position j of a dimension of n pixels: 3 j, the last one n - 8
 ABCS_D int bm_ref_pos(int j, int n) { return min(kStep * j, n - kN1); }
 
-__global__ void __launch_bounds__(kBm3dThreads) bm3d_ht_kernel(const float* __restrict__ in, int H, int W,
+__global__ void __launch_bounds__(kBm3dThreads, 4) bm3d_ht_kernel(const float* __restrict__ in, int H, int W,
                                                                const float* __restrict__ sigma, float lam,
                                                                float* __restrict__ num, float* __restrict__ den) {
     __shared__ float nb[kWin * kWinLd];
-    __shared__ unsigned long long key[kMaxCand];
-    __shared__ unsigned long long red[kBm3dThreads / 32];
+    __shared__ unsigned long long red[2][kBm3dThreads / 32];
+    __shared__ unsigned long long wtop[kBm3dThreads / 32 * kN2];
     __shared__ int sel[kN2];
     __shared__ float P[kN2][kN1][kN1 + 1];
     __shared__ float T[kN2][kN1][kN1 + 1];
@@ -54,40 +111,63 @@ __global__ void __launch_bounds__(kBm3dThreads) bm3d_ht_kernel(const float* __re
     const int cy0 = max(0, y - kHalf), cy1 = min(H - kN1, y + kHalf);
     const int cx0 = max(0, x - kHalf), cx1 = min(W - kN1, x + kHalf);
     const int ncy = cy1 - cy0 + 1, ncx = cx1 - cx0 + 1, nh = ncy + kN1 - 1, nw = ncx + kN1 - 1;
-    for (int i = t; i < nh * nw; i += kBm3dThreads) {
-        const int r = i / nw, c = i - r * nw;
-        nb[r * kWinLd + c] = __ldg(img + (int64_t)(cy0 + r) * W + cx0 + c);
+    for (int i = t; i < nh * 64; i += kBm3dThreads) {          // nw <= 46 < 64
+        const int r = i >> 6, c = i & 63;
+        if (c < nw) nb[r * kWinLd + c] = __ldg(img + (int64_t)(cy0 + r) * W + cx0 + c);
     }
     __syncthreads();
-    const int ry = y - cy0, rx = x - cx0, ncand = ncy * ncx, ref = ry * ncx + rx;
+    const int ry = y - cy0, rx = x - cx0, ref = ry * ncx + rx;
+    // thread t takes the strip of up to 8 consecutive candidates (oy, 8 sx .. 8 sx + 7):
+    // one row segment of 15 pixels per patch row serves all 8 distances.
     // keys: the reference 0, others (bits of d) << 32 | (index + 1); beyond tau: max
-    for (int c = t; c < ncand; c += kBm3dThreads) {
-        const int oy = c / ncx, ox = c - oy * ncx;
-        float acc = 0.f;
+    const int spr = (ncx + kStrip - 1) / kStrip, oy = t / spr, ox0 = (t - oy * spr) * kStrip;
+    const bool mine = oy < ncy;
+    unsigned long long kr[kStrip];
+    {
+        float acc[kStrip];
 #pragma unroll
-        for (int i = 0; i < kN1; ++i)
+        for (int q = 0; q < kStrip; ++q) acc[q] = 0.f;
+        if (mine) {
 #pragma unroll
-            for (int j = 0; j < kN1; ++j) {
-                const float d = nb[(ry + i) * kWinLd + rx + j] - nb[(oy + i) * kWinLd + ox + j];
-                acc = fmaf(d, d, acc);
+            for (int i = 0; i < kN1; ++i) {
+                float row[kStrip + kN1 - 1], rf[kN1];
+#pragma unroll
+                for (int j = 0; j < kStrip + kN1 - 1; ++j)
+                    row[j] = ox0 + j < nw ? nb[(oy + i) * kWinLd + ox0 + j] : 0.f;
+#pragma unroll
+                for (int j = 0; j < kN1; ++j) rf[j] = nb[(ry + i) * kWinLd + rx + j];
+#pragma unroll
+                for (int q = 0; q < kStrip; ++q)
+#pragma unroll
+                    for (int j = 0; j < kN1; ++j) {
+                        const float d = rf[j] - row[q + j];
+                        acc[q] = fmaf(d, d, acc[q]);
+                    }
             }
-        const float d = acc * (1.f / 64.f);
-        unsigned long long kk = ~0ull;
-        if (c == ref) kk = 0ull;
-        else if (d <= tau) kk = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)(c + 1);
-        key[c] = kk;
+        }
+#pragma unroll
+        for (int q = 0; q < kStrip; ++q) {
+            const int ox = ox0 + q, c = oy * ncx + ox;
+            const float d = acc[q] * (1.f / 64.f);
+            unsigned long long kk = ~0ull;
+            if (mine && ox < ncx) {
+                if (c == ref) kk = 0ull;
+                else if (d <= tau) kk = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)(c + 1);
+            }
+            kr[q] = kk;
+        }
     }
-    __syncthreads();
     // group size: the largest power of two <= min(16, candidates within tau)
     {
         int cnt = 0;
-        for (int c = t; c < ncand; c += kBm3dThreads) cnt += key[c] != ~0ull;
+#pragma unroll
+        for (int q = 0; q < kStrip; ++q) cnt += kr[q] != ~0ull;
         cnt = warp_sum(cnt);
-        if (lane == 0) red[warp] = (unsigned long long)cnt;
+        if (lane == 0) red[0][warp] = (unsigned long long)cnt;
         __syncthreads();
         if (t == 0) {
             unsigned long long tot = 0;
-            for (int w = 0; w < kBm3dThreads / 32; ++w) tot += red[w];
+            for (int w = 0; w < kBm3dThreads / 32; ++w) tot += red[0][w];
             const int lim = tot < (unsigned long long)kN2 ? (int)tot : kN2;
             int n = 1;
             while (2 * n <= lim) n *= 2;
@@ -96,22 +176,55 @@ __global__ void __launch_bounds__(kBm3dThreads) bm3d_ht_kernel(const float* __re
         __syncthreads();
     }
     const int n = s_cnt;
-    for (int g = 0; g < n; ++g) {                 // repeated minimum: the n smallest keys in order
-        unsigned long long m = ~0ull;
-        for (int c = t; c < ncand; c += kBm3dThreads) m = bm_min(m, key[c]);
+    // the n smallest keys in order, in two levels: every warp takes the n
+    // smallest of its own keys (registers, shuffles), then warp 0 the n
+    // smallest of those 8 n.  Keys are distinct; the lane that owned the
+    // chosen key drops it and recomputes its minimum.
+    {
+        unsigned long long lmin = ~0ull;
 #pragma unroll
-        for (int o = 16; o; o >>= 1) m = bm_min(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) red[warp] = m;
-        __syncthreads();
-        if (t == 0) {
-            unsigned long long b = red[0];
-            for (int w = 1; w < kBm3dThreads / 32; ++w) b = bm_min(b, red[w]);
-            const int c = b == 0ull ? ref : (int)(b & 0xFFFFFFFFull) - 1;
-            sel[g] = c;
-            key[c] = ~0ull;
+        for (int q = 0; q < kStrip; ++q) lmin = bm_min(lmin, kr[q]);
+        for (int g = 0; g < n; ++g) {
+            unsigned long long b = lmin;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) b = bm_min(b, __shfl_xor_sync(0xffffffffu, b, o));
+            if (b == lmin && b != ~0ull) {
+                lmin = ~0ull;
+#pragma unroll
+                for (int q = 0; q < kStrip; ++q) {
+                    if (kr[q] == b) kr[q] = ~0ull;
+                    lmin = bm_min(lmin, kr[q]);
+                }
+            }
+            if (lane == 0) wtop[warp * kN2 + g] = b;
         }
-        __syncthreads();
     }
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int PER = kBm3dThreads / 32 * kN2 / 32;          // 4 per lane
+        unsigned long long v[PER], lmin = ~0ull;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int i = lane * PER + q, w = i / kN2, g = i % kN2;
+            v[q] = g < n ? wtop[w * kN2 + g] : ~0ull;
+            lmin = bm_min(lmin, v[q]);
+        }
+        for (int g = 0; g < n; ++g) {
+            unsigned long long b = lmin;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) b = bm_min(b, __shfl_xor_sync(0xffffffffu, b, o));
+            if (b == lmin) {
+                lmin = ~0ull;
+#pragma unroll
+                for (int q = 0; q < PER; ++q) {
+                    if (v[q] == b) v[q] = ~0ull;
+                    lmin = bm_min(lmin, v[q]);
+                }
+            }
+            if (lane == 0) sel[g] = b == 0ull ? ref : (int)(b & 0xFFFFFFFFull) - 1;
+        }
+    }
+    __syncthreads();
     // patches of the group
     for (int i = t; i < n * 64; i += kBm3dThreads) {
         const int g = i >> 6, py = (i >> 3) & 7, px = i & 7, c = sel[g];
@@ -136,30 +249,23 @@ __global__ void __launch_bounds__(kBm3dThreads) bm3d_ht_kernel(const float* __re
         P[g][u][v] = a;
     }
     __syncthreads();
-    // Haar along the group per coefficient (u, v), threshold, count, inverse Haar
-    const int ln = 31 - __clz(n);
+    // Haar along the group per coefficient (u, v) (butterflies in registers),
+    // threshold, count, inverse Haar
     int kept = 0;
     if (t < 64) {
         const int u = t >> 3, v = t & 7;
-        float z[kN2], w3[kN2];
-        for (int g = 0; g < n; ++g) z[g] = P[g][u][v];
-        for (int q = 0; q < n; ++q) {
-            float a = 0.f;
-            for (int g = 0; g < n; ++g) a = fmaf(c_bm_haar[ln][q][g], z[g], a);
-            const bool keep = fabsf(a) > thr || (q == 0 && t == 0);
-            w3[q] = keep ? a : 0.f;
-            kept += keep;
-        }
-        for (int g = 0; g < n; ++g) {
-            float a = 0.f;
-            for (int q = 0; q < n; ++q) a = fmaf(c_bm_haar[ln][q][g], w3[q], a);
-            T[g][u][v] = a;
+        switch (n) {
+            case 1: kept = haar_threshold<1>(P, T, u, v, thr, t == 0); break;
+            case 2: kept = haar_threshold<2>(P, T, u, v, thr, t == 0); break;
+            case 4: kept = haar_threshold<4>(P, T, u, v, thr, t == 0); break;
+            case 8: kept = haar_threshold<8>(P, T, u, v, thr, t == 0); break;
+            default: kept = haar_threshold<16>(P, T, u, v, thr, t == 0); break;
         }
     }
     kept = warp_sum(kept);
-    if (lane == 0) red[warp] = (unsigned long long)kept;
+    if (lane == 0) red[0][warp] = (unsigned long long)kept;
     __syncthreads();
-    const float wgt = 1.f / (float)(red[0] + red[1]);          // threads 0..63 are warps 0 and 1
+    const float wgt = 1.f / (float)(red[0][0] + red[0][1]);    // threads 0..63 are warps 0 and 1
     // inverse 2D DCT: P = T D (rows of D^T C), then D^T P
     for (int i = t; i < n * 64; i += kBm3dThreads) {
         const int g = i >> 6, u = (i >> 3) & 7, j = i & 7;
@@ -192,33 +298,11 @@ __global__ void bm3d_div_kernel(const float* __restrict__ num, const float* __re
 }  // namespace
 
 cudaError_t setup_bm3d_tables() {
-    float d[8][8], haar[5][16][16] = {}, kai[8];
+    float d[8][8], kai[8];
     for (int kk = 0; kk < 8; ++kk)
         for (int nn = 0; nn < 8; ++nn)
             d[kk][nn] = (float)((kk == 0 ? std::sqrt(1.0 / 8) : std::sqrt(2.0 / 8)) *
                                 std::cos(3.14159265358979323846 * (2 * nn + 1) * kk / 16.0));
-    // orthonormal Haar by doubling: H_2n = [H_n (x) (1, 1); I_n (x) (1, -1)] / sqrt 2
-    double Hm[16][16] = {{1.0}};
-    int m = 1;
-    haar[0][0][0] = 1.f;
-    for (int l = 1; l < 5; ++l) {
-        double Hn[16][16] = {};
-        for (int i = 0; i < m; ++i)
-            for (int j = 0; j < m; ++j) {
-                Hn[i][2 * j] = Hm[i][j] / std::sqrt(2.0);
-                Hn[i][2 * j + 1] = Hm[i][j] / std::sqrt(2.0);
-            }
-        for (int i = 0; i < m; ++i) {
-            Hn[m + i][2 * i] = 1.0 / std::sqrt(2.0);
-            Hn[m + i][2 * i + 1] = -1.0 / std::sqrt(2.0);
-        }
-        m *= 2;
-        for (int i = 0; i < m; ++i)
-            for (int j = 0; j < m; ++j) {
-                Hm[i][j] = Hn[i][j];
-                haar[l][i][j] = (float)Hn[i][j];
-            }
-    }
     // Kaiser window, beta = 2: I0(beta sqrt(1 - (2i / 7 - 1)^2)) / I0(beta), I0 by its power series
     auto i0 = [](double z) {
         double sum = 1.0, term = 1.0;
@@ -233,7 +317,6 @@ cudaError_t setup_bm3d_tables() {
         kai[i] = (float)(i0(2.0 * std::sqrt(1.0 - a * a)) / i0(2.0));
     }
     cudaError_t e = cudaMemcpyToSymbol(c_bm_dct, d, sizeof d);
-    if (!e) e = cudaMemcpyToSymbol(c_bm_haar, haar, sizeof haar);
     if (!e) e = cudaMemcpyToSymbol(c_bm_kaiser, kai, sizeof kai);
     return e;
 }
