@@ -163,7 +163,8 @@ abcs_status abcs_reconstruct(abcs_handle* h, const int32_t* counts, const int64_
  *   x^{t+1} = D_{sigma^t}(x^t + A^T z^t).
  *   counts, offsets, y [device] as written by abcs_sense (m_img = the image's
  *                      number of measurements)
- *   denoiser           abcs_denoiser; lambda is the TI-DCT threshold factor
+ *   denoiser           abcs_denoiser; lambda is the TI-DCT threshold factor (2.3 here) or
+ *                      BM3D's lambda_3D (2.7)
  *   cnn_weights        [device] packed weights of abcs_cnn_* (ABCS_DEN_CNN) or NULL
  *   x_out              [device] float [n_img][Hc][Wc], out: x^iters
  *   sigma_trace        [device] float [n_img][iters] or NULL, out: sigma^t
