@@ -227,10 +227,10 @@ __global__ void __launch_bounds__(kDampThreads) damp_div_kernel(const float* __r
     griddep_wait();
     const int k = blockIdx.y;
     const int64_t o = (int64_t)k * per_img;
-    double acc = 0.0;
+    float a = 0.f;                                  // a thread's few terms in FP32, the CTA sum in FP64
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_img; i += (int64_t)gridDim.x * blockDim.x)
-        acc += (double)__ldg(probe + o + i) * ((double)xp[o + i] - (double)x[o + i]);
-    acc = block_sum(acc, sh);
+        a = fmaf(__ldg(probe + o + i), xp[o + i] - x[o + i], a);
+    const double acc = block_sum((double)a, sh);
     if (threadIdx.x == 0) partial[(int64_t)k * gridDim.x + blockIdx.x] = acc;
 }
 

@@ -59,22 +59,31 @@ __global__ void __launch_bounds__(256) thi_hist_kernel(const float* __restrict__
 // histogram is cleared for the next pass.
 __global__ void __launch_bounds__(256) thi_pick_kernel(int pass, uint32_t* __restrict__ prefix,
                                                        int64_t* __restrict__ rem, uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[256];
     griddep_wait();
     const int k = blockIdx.x, t = threadIdx.x;
-    h[t] = hist[(int64_t)k * 256 + t];
+    __shared__ unsigned long long warp_tot[8];
+    const unsigned hv = hist[(int64_t)k * 256 + t];
     hist[(int64_t)k * 256 + t] = 0u;
+    // suffix sums: above(d) = sum of bins > d; digit d holds the rem-th largest key
+    // when above(d) < rem <= above(d) + h[d] (digit 0 if none above)
+    const int lane = t & 31, warp = t >> 5;
+    unsigned long long incl = hv;                                   // within the warp, from higher digits down
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v = __shfl_down_sync(0xffffffffu, incl, o);
+        if (lane + o < 32) incl += v;
+    }
+    if (lane == 0) warp_tot[warp] = incl;
     __syncthreads();
-    if (t == 0) {
-        const int64_t r = rem[k];
-        int64_t above = 0;
-        int d = 255;
-        for (; d > 0; --d) {
-            if (above + h[d] >= r) break;
-            above += h[d];
-        }
-        rem[k] = r - above;
-        prefix[k] = (pass ? prefix[k] : 0u) | ((uint32_t)d << (24 - 8 * pass));
+    unsigned long long higher = 0;
+    for (int w = warp + 1; w < 8; ++w) higher += warp_tot[w];
+    const unsigned long long above = incl - hv + higher;           // bins > t
+    const int64_t r = rem[k];
+    __syncthreads();                                                // every thread has read rem[k]
+    const bool here = (int64_t)above < r && (r <= (int64_t)(above + hv) || t == 0);
+    if (here) {
+        rem[k] = r - (int64_t)above;
+        prefix[k] = (pass ? prefix[k] : 0u) | ((uint32_t)t << (24 - 8 * pass));
     }
 }
 
