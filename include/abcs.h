@@ -116,7 +116,14 @@ typedef struct abcs_plan_info {
 
 /* Create a handle bound to the current CUDA device.  It owns a device
  * status word and a workspace grown on demand (cudaMalloc; growing waits
- * for the device).  Uploads the DCT and zigzag tables to this device. */
+ * for the device).  Uploads the DCT and zigzag tables to this device.
+ * Failure-detection test hooks, read from the environment at each call
+ * (host-side; nothing faults or hangs):
+ *   ABCS_FAULT_WS_LIMIT=n     a workspace larger than n bytes fails with
+ *                             ABCS_ERR_OOM, as a failed allocation would;
+ *   ABCS_FAULT_SKIP_ARRIVE=k  in abcs_ida_batch, CTA k waits at its first
+ *                             grid barrier without arriving, so the bounded
+ *                             waits expire (ABCS_DEV_TIMEOUT). */
 abcs_status abcs_create(abcs_handle** out);
 
 /* Free the handle's device memory.  Waits for the device first.  NULL is a no-op. */

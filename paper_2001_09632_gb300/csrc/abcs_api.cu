@@ -135,6 +135,11 @@ struct Carver {
 
 abcs_status ensure_ws(abcs_handle* h, size_t bytes) {
     if (bytes <= h->ws_bytes) return ABCS_OK;
+    // Failure-detection test hook: ABCS_FAULT_WS_LIMIT=n makes any workspace
+    // larger than n bytes fail as an allocation failure would (host side only)
+    if (const char* lim = getenv("ABCS_FAULT_WS_LIMIT"))
+        if (bytes > (size_t)strtoull(lim, nullptr, 10))
+            return fail(ABCS_ERR_OOM, "workspace of %zu bytes refused (ABCS_FAULT_WS_LIMIT)", bytes);
     if (h->ws) {
         cudaDeviceSynchronize();
         cudaFree(h->ws);

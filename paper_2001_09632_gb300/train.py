@@ -136,7 +136,34 @@ def make_pairs(h, n_images=512, H=512, W=512, captures=(0, 1, 2, 4, 8, 16, 29), 
     return torch.cat(R), torch.cat(C), torch.cat(S), torch.cat(D)
 
 
-def train(h, R, C, S, D, steps=4000, batch=128, lr=1e-3, seed=1, params=None, log=print):
+def save_checkpoint(path: str, state: dict) -> None:
+    """Write `state` (numpy arrays and scalars) to path atomically: into
+    path + '.tmp', flushed to disk, then renamed over path, so a process
+    killed while writing leaves the previous checkpoint intact."""
+    tmp = path + ".tmp"
+    with open(tmp, "wb") as f:
+        np.savez(f, **state)
+        f.flush()
+        os.fsync(f.fileno())
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path: str):
+    """The state written by save_checkpoint, or None if there is none."""
+    if not path or not os.path.exists(path):
+        return None
+    with np.load(path, allow_pickle=False) as z:
+        return {k: z[k] for k in z.files}
+
+
+def train(h, R, C, S, D, steps=4000, batch=128, lr=1e-3, seed=1, params=None, log=print, ckpt=None,
+          ckpt_every=500, until=None):
+    """Adam on the crops (R, C, S, D) with a cosine learning-rate decay over
+    `steps`.  With `ckpt`, the FP32 parameters, Adam's moments, the step and
+    the state of the crop sampler are saved every `ckpt_every` steps and
+    where the run stops, and a run finding that file resumes after its
+    step.  `until` stops after that step of the same schedule (a job cut
+    into pieces)."""
     n, crop = R.shape[0], R.shape[1]
     p = torch.tensor(init_params(seed) if params is None else params, device="cuda")
     m, v = torch.zeros_like(p), torch.zeros_like(p)
@@ -145,7 +172,24 @@ def train(h, R, C, S, D, steps=4000, batch=128, lr=1e-3, seed=1, params=None, lo
     gen = torch.Generator(device="cuda").manual_seed(seed)
     hist = []
     t0 = time.time()
-    for step in range(1, steps + 1):
+    first = 1
+    st = load_checkpoint(ckpt)
+    if st is not None:
+        p.copy_(torch.from_numpy(st["params"]))
+        m.copy_(torch.from_numpy(st["m"]))
+        v.copy_(torch.from_numpy(st["v"]))
+        gen.set_state(torch.from_numpy(st["gen"]))
+        first = int(st["step"]) + 1
+        hist = [tuple(x) for x in st["hist"].tolist()]
+        log(f"resumed after step {first - 1}")
+
+    def save(step):
+        save_checkpoint(ckpt, {"params": p.cpu().numpy(), "m": m.cpu().numpy(), "v": v.cpu().numpy(),
+                               "gen": gen.get_state().numpy(), "step": np.int64(step),
+                               "hist": np.asarray(hist, dtype=np.float64).reshape(-1, 2)})
+
+    last = steps if until is None else min(until, steps)
+    for step in range(first, last + 1):
         idx = torch.randint(0, n, (batch,), device="cuda", generator=gen)
         rb, cb, sb, db = R[idx].contiguous(), C[idx].contiguous(), S[idx].contiguous(), D[idx].contiguous()
         lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * (step - 1) / steps))     # cosine decay
@@ -154,6 +198,8 @@ def train(h, R, C, S, D, steps=4000, batch=128, lr=1e-3, seed=1, params=None, lo
             l = loss.item()
             hist.append((step, l))
             log(f"step {step:5d}  loss {l:.6f}  (rmse {255 * math.sqrt(l):.2f})  {time.time() - t0:.1f}s")
+        if ckpt and (step % ckpt_every == 0 or step == last):
+            save(step)
     torch.cuda.synchronize()
     assert abcs.abcs_sync_status(h) == 0
     return p.cpu().numpy(), hist, time.time() - t0

@@ -176,3 +176,23 @@ def test_ida_with_cnn_runs_and_matches_oracle_first_iterations(handle):
     assert abs(tr.cpu().numpy()[0, 0] - sig[0]) <= 1e-5 * sig[0]
     err = np.linalg.norm(x.cpu().numpy()[0] - xr) / np.linalg.norm(xr)
     assert err <= 2e-2, err
+
+
+def test_training_resumes_bit_identically(handle, tmp_path):
+    """Six Adam steps in one run, and the same six cut after step 3 and
+    resumed from the checkpoint, end with identical parameters (the sampler
+    state and Adam's moments are in the checkpoint; the gradient reductions
+    have a fixed order)."""
+    from paper_2001_09632_gb300 import train
+    n, H, W = 32, 32, 32
+    clean, r = _noisy(n, H, W, 60, 18.0)
+    d = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    R, C, S = d(r), d(clean), d(np.full(n, 18.0))
+    D = d(_density(n, H, W, 61))
+    quiet = lambda *a: None
+    pa, _, _ = train.train(handle, R, C, S, D, steps=6, batch=8, seed=4, log=quiet)
+    ck = str(tmp_path / "ck.npz")
+    train.train(handle, R, C, S, D, steps=6, batch=8, seed=4, log=quiet, ckpt=ck, ckpt_every=2, until=3)
+    assert int(train.load_checkpoint(ck)["step"]) == 3
+    pb, _, _ = train.train(handle, R, C, S, D, steps=6, batch=8, seed=4, log=quiet, ckpt=ck, ckpt_every=2)
+    assert np.array_equal(pa, pb)
