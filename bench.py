@@ -570,6 +570,16 @@ def main():
         sweep[name] = {"sense_ms": statistics.median(sm), "reconstruct_ms": statistics.median(rm),
                        "Mpixel_per_s": world * N_IMG * plan["N"] / ((statistics.median(sm) +
                                                                     statistics.median(rm)) * 1e-3) / 1e6}
+    # the tcgen05 reconstruct kernel (basis images in tensor memory), same workload
+    os.environ["ABCS_RECON_TC"] = "umma"
+    for _ in range(3):
+        step(prec)
+    sm, rm = timed_steps(min(K, 200), prec)
+    del os.environ["ABCS_RECON_TC"]
+    assert abcs.abcs_sync_status(h, s) == 0
+    sweep["tensor_memory_reconstruct"] = {
+        "precision": a.precision, "reconstruct_ms": statistics.median(rm),
+        "kernel": "recon_umma_kernel (ABCS_RECON_TC=umma; not the default)"}
     step(prec)
     torch.cuda.synchronize()
 

@@ -157,6 +157,8 @@ ABCS_D void cp_async16(float* s, const float* g) {
 }
 ABCS_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 ABCS_D void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+template <int N>
+ABCS_D void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 ABCS_D void stage_in_async(float* stage, const float* __restrict__ src, int64_t start, int n) {
     const int sh = (int)(start & 3);

@@ -19,6 +19,7 @@
 #include <cuda_fp16.h>
 
 #include "abcs_common.cuh"
+#include "umma.cuh"
 
 namespace abcs {
 
@@ -749,69 +750,14 @@ struct T5Tile {
 // mbarriers in the misc area: full[3], empty[3], acc_full[2], acc_empty[2]
 constexpr uint32_t T5_FULL = 0, T5_EMPTY = 24, T5_AFULL = 48, T5_AEMPTY = 64, T5_SLOT = 80, T5_ABORT = 84;
 
-ABCS_D uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// shared-memory matrix descriptor: K-major, no swizzle; lbo = byte distance
-// of adjacent 16-byte K chunks, sbo = byte distance of adjacent 8-row groups
-ABCS_D uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;                                // descriptor version of tcgen05
-    return d;                                              // base offset 0, no swizzle
-}
-
 // instruction descriptor, kind::f16: D F32, A and B BF16, both K-major, M = 128, N = n
-__host__ __device__ constexpr uint32_t t5_idesc(uint32_t n) { return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24); }
+__host__ __device__ constexpr uint32_t t5_idesc(uint32_t n) { return umma_idesc_f16(n, true); }
 
 ABCS_D void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
-}
-
-ABCS_D void umma_commit(uint32_t mbar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
-                 : "memory");
-}
-
-ABCS_D void tc5_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
-ABCS_D void tc5_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
-
-ABCS_D void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-          "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-          "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-}
-
-ABCS_D bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait for the phase of `parity`; false (and the abort flag set) on
-// expiry or when another role has aborted
-ABCS_D bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
-    for (int it = 0; it < (1 << 22); ++it) {
-        if (mbar_try_wait(mbar, parity)) return true;
-        if (*abort_flag) return false;
-    }
-    *abort_flag = 1;
-    set_status(status, ABCS_DEV_TIMEOUT);
-    return false;
 }
 
 // NC = 32: a 32 -> 32 layer (bias, ReLU, BF16 chunk-planar out).  NC = 16: the last

@@ -14,10 +14,14 @@
 //   TC_BF16    single BF16 product hi*hi
 // Pixels are integers <= 255, exact in FP16 and BF16, so the sensing input
 // needs no split.
+#include <cstdlib>
+#include <cstring>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "abcs_common.cuh"
+#include "umma.cuh"
 
 namespace abcs {
 ABCS_TU_TABLES(tc)
@@ -235,8 +239,21 @@ ABCS_D void frag_b(int set, uint32_t (&h)[2][2], uint32_t (&l)[2][2]) {
 // is copied (cp.async) while the current one is transformed, and each warp
 // transforms four blocks of the segment.
 // ---------------------------------------------------------------------------
+#ifndef ABCS_RECON_RSEG
+#define ABCS_RECON_RSEG 32
+#endif
+#ifndef ABCS_RECON_DEPTH
+#define ABCS_RECON_DEPTH 1
+#endif
+#ifndef ABCS_SENSE_DEPTH
+#define ABCS_SENSE_DEPTH 1
+#endif
 constexpr int SEG = 32;                        // sensing segment (blocks)
-constexpr int RSEG = 32;                       // reconstruction segment (blocks)
+constexpr int SDEPTH = ABCS_SENSE_DEPTH;       // sensing segments staged ahead
+constexpr int SNB = SDEPTH + 1, SNM = SDEPTH + 2;   // pixel buffers, metadata slots
+constexpr int RSEG = ABCS_RECON_RSEG;          // reconstruction segment (blocks)
+constexpr int RDEPTH = ABCS_RECON_DEPTH;       // reconstruction segments staged ahead
+constexpr int RNB = RDEPTH + 1, RNM = RDEPTH + 2;   // stage buffers, metadata slots
 template <int S>
 constexpr int seg_floats() { return S * 256 + 4; }   // packed range of a segment + alignment shift
 constexpr int kSegFloats = seg_floats<SEG>();
@@ -352,14 +369,14 @@ ABCS_D void recon_meta_store(const ReconArgs& a, const SegGeom& sg, const MetaRa
 // gathered by zigzag rank from the staged segment); stage 2 X = Y D (A = Y
 // straight from stage 1's accumulators, B = D constant).
 // ---------------------------------------------------------------------------
-constexpr size_t kReconSmem = 2 * kRSegFloats * sizeof(float) + 3 * sizeof(SegMeta<RSEG>);
-constexpr size_t kSenseSmem = 2 * 16 * SEG * 16 + kSegFloats * sizeof(float) + 3 * sizeof(SegMeta<SEG>);
+constexpr size_t kReconSmem = RNB * kRSegFloats * sizeof(float) + RNM * sizeof(SegMeta<RSEG>);
+constexpr size_t kSenseSmem = SNB * 16 * SEG * 16 + kSegFloats * sizeof(float) + SNM * sizeof(SegMeta<SEG>);
 
 template <int P>
 __global__ void __launch_bounds__(256, 3) recon_tc_kernel(ReconArgs a, int64_t ntot) {
     extern __shared__ __align__(16) unsigned char smem[];
     float (*stage)[kRSegFloats] = reinterpret_cast<float (*)[kRSegFloats]>(smem);
-    SegMeta<RSEG>* meta = reinterpret_cast<SegMeta<RSEG>*>(smem + 2 * kRSegFloats * sizeof(float));
+    SegMeta<RSEG>* meta = reinterpret_cast<SegMeta<RSEG>*>(smem + RNB * kRSegFloats * sizeof(float));
     const int warp = threadIdx.x >> 5;
     const Frag f;
     uint32_t ATh[4], ATl[4], DBh[2][2], DBl[2][2];
@@ -379,29 +396,38 @@ __global__ void __launch_bounds__(256, 3) recon_tc_kernel(ReconArgs a, int64_t n
     const int nseg = (int)((r1 - r0 + RSEG - 1) / RSEG);
     if (nseg <= 0) return;
     const int lo = f.g * g.Wc + 2 * f.q;
+    // segments j + 1 .. j + RDEPTH are in flight while segment j is
+    // transformed: RDEPTH + 1 stage buffers, RDEPTH + 2 metadata slots (warp 0
+    // stores segment j + RDEPTH's metadata while the other warps may still
+    // read segment j - 1's), metadata loads one segment further ahead
     MetaRaw raw;
     if (warp == 0) {
-        recon_meta_store(a, seg_geom<RSEG>(r0, r1, 0), recon_meta_load(a, seg_geom<RSEG>(r0, r1, 0)), meta[0]);
-        if (1 < nseg) raw = recon_meta_load(a, seg_geom<RSEG>(r0, r1, 1));
+        for (int d = 0; d < RDEPTH && d < nseg; ++d)
+            recon_meta_store(a, seg_geom<RSEG>(r0, r1, d), recon_meta_load(a, seg_geom<RSEG>(r0, r1, d)), meta[d]);
+        if (RDEPTH < nseg) raw = recon_meta_load(a, seg_geom<RSEG>(r0, r1, RDEPTH));
     }
     __syncthreads();
-    stage_in_async(stage[0], a.coeffs, meta[0].start, meta[0].n);
-    cp_async_commit();
-    int mi = 0;                                 // meta slot of segment j (j mod 3)
+#pragma unroll
+    for (int d = 0; d < RDEPTH; ++d) {
+        if (d < nseg) stage_in_async(stage[d], a.coeffs, meta[d].start, meta[d].n);
+        cp_async_commit();
+    }
+    int mi = 0, bi = 0;                         // metadata slot (j mod RNM) and stage buffer (j mod RNB) of segment j
+    int mn = RDEPTH % RNM, bn = RDEPTH % RNB;   // the same for segment j + RDEPTH
     for (int j = 0; j < nseg; ++j) {
-        const int mn = mi == 2 ? 0 : mi + 1;
-        if (j + 1 < nseg && warp == 0) {
-            recon_meta_store(a, seg_geom<RSEG>(r0, r1, j + 1), raw, meta[mn]);
-            if (j + 2 < nseg) raw = recon_meta_load(a, seg_geom<RSEG>(r0, r1, j + 2));
+        const int jn = j + RDEPTH;
+        if (jn < nseg && warp == 0) {
+            recon_meta_store(a, seg_geom<RSEG>(r0, r1, jn), raw, meta[mn]);
+            if (jn + 1 < nseg) raw = recon_meta_load(a, seg_geom<RSEG>(r0, r1, jn + 1));
         }
-        cp_async_wait_all();
+        cp_async_wait_group<RDEPTH - 1>();      // this thread's copies of segment j have landed
         __syncthreads();
-        if (j + 1 < nseg) stage_in_async(stage[(j + 1) & 1], a.coeffs, meta[mn].start, meta[mn].n);
+        if (jn < nseg) stage_in_async(stage[bn], a.coeffs, meta[mn].start, meta[mn].n);
         cp_async_commit();
 
         const SegMeta<RSEG>& M = meta[mi];
         const SegGeom sg = M.sg;
-        const float* st = stage[j & 1] + M.sh;
+        const float* st = stage[bi] + M.sh;
 #pragma unroll
         for (int c = warp; c < sg.nblk; c += 8) {
             const int m = M.cnt[c];
@@ -445,9 +471,447 @@ __global__ void __launch_bounds__(256, 3) recon_tc_kernel(ReconArgs a, int64_t n
                 *reinterpret_cast<uint16_t*>(a.out_u8 + o8 + 8) = (uint16_t)(u8(X[1][2]) | (u8(X[1][3]) << 8));
             }
         }
-        mi = mn;
+        mi = mi + 1 == RNM ? 0 : mi + 1;
+        bi = bi + 1 == RNB ? 0 : bi + 1;
+        mn = mn + 1 == RNM ? 0 : mn + 1;
+        bn = bn + 1 == RNB ? 0 : bn + 1;
     }
     cp_async_wait_all();
+}
+
+// ---------------------------------------------------------------------------
+// reconstruct on the 5th-generation tensor cores (the alternative to
+// recon_tc_kernel, selected with ABCS_RECON_TC=umma).  With phi_k the DCT
+// basis image of zigzag rank k (phi_k[16 r + c] = D[u_k][r] D[v_k][c]),
+// block b's pixels are x_b = sum_{k < m_b} y_b[k] phi_k (the inverse of
+// Eq. 1 with the unmeasured coefficients zero).  For a tile of KR_BLK blocks
+// and pixel half h this is one GEMM,
+//   X_h[p][i] = sum_k 16 phi_k[128 h + p] * y_i[k]     (M = 128 pixels, N = KR_BLK blocks, K = rank)
+// A = 16 Phi_h (hi + lo words) stays in tensor memory for the whole launch
+// (column k/2 of lane p holds ranks k, k + 1), B = the tile's coefficients
+// (hi + lo) goes through shared memory in K stages of KR_KS ranks, and the
+// FP32 accumulators are in tensor memory.  K stops at the tile's largest
+// count, so the MMA work follows the measurements.  The three split products
+// A_hi B_hi + A_lo B_hi + A_hi B_lo restore FP32 accuracy (one product for
+// plain BF16); the factor 16 keeps the low words of Phi out of the FP16
+// subnormal range and is divided out exactly in the epilogue.
+// One CTA per SM; CTA c computes pixel half c & 1 of tiles c/2, c/2 + G/2, ...
+//   warp 0      tensor-memory allocation; lane 0 issues the MMAs
+//   warp 1      loader: the tile's packed coefficients (one contiguous range)
+//               by one bulk copy into a ring of spans (up to 8 tiles in
+//               flight); per-block offsets and counts, loaded a tile ahead,
+//               and the tile's stage count
+//   warps 2-9   converters: thread (block i, part) splits its share of the
+//               stage's ranks into hi + lo and writes them K-major (no
+//               swizzle) into the stage buffers
+//   warps 10-13 epilogue (and, first, the tensor-memory copy of A from the
+//               table staged by one bulk copy): warp w reads lanes
+//               32 (w % 4) .. (its pixels) of the tile's columns (blocks);
+//               each store of a warp covers two pixel rows of one block
+// Every wait is bounded (ABCS_DEV_TIMEOUT and an abort flag that ends every
+// role); copies and MMAs in flight are drained before the CTA frees its
+// tensor memory and leaves.
+// Measured on 64 x 512^2 (BBV r 0.3, FP16x2): 36 us against 23 us for
+// recon_tc_kernel.  The MMAs keep the tensor pipe busy only ~14% of the
+// time; each K stage costs a hand-off between eight converter warps and the
+// MMA thread that the per-block mma.sync kernel does not pay, and both pixel
+// halves convert the same coefficients, padded to the tile's largest count.
+// ---------------------------------------------------------------------------
+#ifndef ABCS_KR_BLK
+#define ABCS_KR_BLK 128
+#endif
+#ifndef ABCS_KR_KS
+#define ABCS_KR_KS 64
+#endif
+#ifndef ABCS_KR_NB
+#define ABCS_KR_NB 2
+#endif
+constexpr int KR_BLK = ABCS_KR_BLK;                 // blocks per tile (the MMA's N: 64 or 128)
+constexpr int KR_KS = ABCS_KR_KS;                   // ranks per K stage (32 or 64)
+constexpr int KR_NB = ABCS_KR_NB;                   // stage buffers (a power of 2)
+constexpr int KR_CH = KR_KS / 8;                    // 8-rank chunks per stage
+constexpr int KR_TPB = 256 / KR_BLK;                // converter threads per block
+constexpr int KR_CPT = KR_CH / KR_TPB;              // chunks per converter thread and stage
+constexpr int KR_NACC = 256 / KR_BLK;               // accumulators (256 tensor-memory columns)
+constexpr int KR_NSLOT = 8;                         // tiles in flight between loader and converters
+constexpr int KR_RING = KR_BLK == 64 ? 2 * (KR_BLK * 256 + 8) : KR_BLK * 256 + 8;   // floats of the ring
+constexpr uint32_t KR_CHUNK = KR_BLK * 16;          // one 8-rank chunk of all the tile's blocks
+constexpr uint32_t KR_STAGE = 2 * KR_CH * KR_CHUNK; // hi chunks, then lo chunks
+static_assert(KR_CPT >= 1 && KR_CH % KR_TPB == 0 && (KR_NB & (KR_NB - 1)) == 0, "stage geometry");
+constexpr float KR_SCALE = 16.f;
+struct KrInfo {
+    int rel[KR_BLK];   // ring index of the block's first coefficient
+    int m[KR_BLK];     // the block's count (0 for rows past the batch or flagged)
+    int nst;           // K stages of the tile
+    int pad[3];
+};
+constexpr uint32_t KR_OFF_STAGE = 0;
+constexpr uint32_t KR_OFF_RAW = KR_NB * KR_STAGE;
+constexpr uint32_t KR_OFF_INFO = KR_OFF_RAW + KR_RING * 4;
+constexpr uint32_t KR_OFF_BAR = KR_OFF_INFO + KR_NSLOT * sizeof(KrInfo);
+// mbarriers: ring full/empty per slot, stage full/empty per buffer, acc full/empty, drain
+constexpr uint32_t KR_RAWF = 0, KR_RAWE = 8 * KR_NSLOT, KR_BF = 16 * KR_NSLOT, KR_BE = KR_BF + 8 * KR_NB,
+                   KR_ACCF = KR_BE + 8 * KR_NB, KR_ACCE = KR_ACCF + 8 * KR_NACC, KR_DRAIN = KR_ACCE + 8 * KR_NACC,
+                   KR_TAB = KR_DRAIN + 8;
+constexpr uint32_t KR_OFF_SPAN = KR_OFF_BAR + KR_TAB + 8;    // ring start of each slot's span (int64, loader only)
+constexpr uint32_t KR_OFF_MISC = KR_OFF_SPAN + 8 * KR_NSLOT;   // stage flags, tensor-memory address, abort flag
+constexpr size_t KR_SMEM = KR_OFF_MISC + 4 * KR_NB + 16;
+constexpr int KR_THREADS = 14 * 32;
+static_assert(KR_OFF_RAW % 1024 == 0 && KR_OFF_BAR % 8 == 0 && KR_RING >= KR_BLK * 256 + 8, "shared layout");
+static_assert(KR_SMEM <= 232448, "shared memory of the tensor-memory reconstruct kernel");
+static_assert(KR_RING * 4 >= 2 * 128 * 128 * 4, "the ring holds the operand table while tensor memory is filled");
+
+// 16 phi_k[p] as split operand words, [precision][pixel half][hi, lo][rank pair q][pixel p % 128]:
+// one contiguous 128 KB slice per CTA (64 KB of hi words for plain BF16)
+__device__ __align__(16) uint32_t g_kron[3][2][2][128][128];
+
+template <int P>
+ABCS_D void kron_setup_p(int q, int p) {
+    const int r = p >> 4, c = p & 15;
+    double v[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int z = zz_pos<16>(2 * q + e);
+        v[e] = (double)KR_SCALE * Dd<16>(z >> 4, r) * Dd<16>(z & 15, c);
+    }
+    uint32_t h, l;
+    split2d<P>(v[0], v[1], h, l);
+    g_kron[pidx<P>()][p >> 7][0][q][p & 127] = h;
+    g_kron[pidx<P>()][p >> 7][1][q][p & 127] = l;
+}
+
+__global__ void kron_setup_kernel() {     // grid 128 (rank pairs), block 256 (pixels)
+    kron_setup_p<kP16>(blockIdx.x, threadIdx.x);
+    kron_setup_p<kPB16>(blockIdx.x, threadIdx.x);
+    kron_setup_p<kPB1>(blockIdx.x, threadIdx.x);
+}
+
+template <int P>
+__global__ void __launch_bounds__(KR_THREADS, 1) recon_umma_kernel(ReconArgs a, int64_t ntot) {
+    extern __shared__ __align__(1024) unsigned char kr_smem[];
+    unsigned char* smem = kr_smem;
+    constexpr bool kSplit = P != kPB1;
+    constexpr uint32_t IDESC = umma_idesc_f16(KR_BLK, P != kP16);
+    const uint32_t sb = smem_u32(smem), bar = sb + KR_OFF_BAR;
+    KrInfo* info = reinterpret_cast<KrInfo*>(smem + KR_OFF_INFO);
+    volatile int* sflag = reinterpret_cast<volatile int*>(smem + KR_OFF_MISC);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + KR_OFF_MISC + 4 * KR_NB);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + KR_OFF_MISC + 4 * KR_NB + 4);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int half = blockIdx.x & 1, G2 = gridDim.x >> 1;
+    const int64_t T = (ntot + KR_BLK - 1) / KR_BLK, t0 = blockIdx.x >> 1;
+    const int my_n = t0 < T ? (int)((T - t0 + G2 - 1) / G2) : 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (t == 32) {
+        for (int b = 0; b < KR_NSLOT; ++b) {
+            mbar_init(bar + KR_RAWF + 8 * b, 1);
+            mbar_init(bar + KR_RAWE + 8 * b, 8);
+        }
+        for (int b = 0; b < KR_NB; ++b) {
+            mbar_init(bar + KR_BF + 8 * b, 8);
+            mbar_init(bar + KR_BE + 8 * b, 1);
+        }
+        for (int b = 0; b < KR_NACC; ++b) {
+            mbar_init(bar + KR_ACCF + 8 * b, 1);
+            mbar_init(bar + KR_ACCE + 8 * b, 4);
+        }
+        mbar_init(bar + KR_DRAIN, 1);
+        mbar_init(bar + KR_TAB, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        *abort_flag = 0;
+    }
+    tc5_fence_before();
+    __syncthreads();
+    tc5_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // A = 16 Phi_h into tensor memory (hi words in columns 0..127, lo words
+    // in 128..255): the CTA's table slice is staged in the (still unused)
+    // coefficient ring by one bulk copy
+    constexpr uint32_t kTabBytes = (kSplit ? 2 : 1) * 128 * 128 * 4;
+    if (t == 32) {
+        mbar_arrive_tx(bar + KR_TAB, kTabBytes);
+        bulk_g2s(sb + KR_OFF_RAW, &g_kron[pidx<P>()][half][0][0][0], kTabBytes, bar + KR_TAB);
+    }
+    if (warp >= 10) {
+        const int sp = warp & 3;
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait(bar + KR_TAB, 0, abort_flag, a.status);
+        if (__shfl_sync(0xffffffffu, ok, 0)) {
+            const uint32_t* tab = reinterpret_cast<const uint32_t*>(smem + KR_OFF_RAW) + 32 * sp + lane;
+#pragma unroll 1
+            for (int part = 0; part < (kSplit ? 2 : 1); ++part)
+#pragma unroll 1
+                for (int cb = 0; cb < 4; ++cb) {
+                    uint32_t v[32];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] = tab[(part * 128 + cb * 32 + i) * 128];
+                    tmem_st32(tmem + ((uint32_t)(32 * sp) << 16) + part * 128 + cb * 32, v);
+                }
+            tmem_wait_st();
+        }
+    }
+    tc5_fence_before();
+    __syncthreads();
+    tc5_fence_after();
+    griddep_wait();
+
+    if (warp == 1) {
+        // ---- loader: tile j's packed coefficients [s0, e) as the 16-byte span
+        // [lo4, hi4) placed contiguously in the ring; the converters release
+        // tiles in order, and a tile waits for its slot and its ring space
+        const bool al16 = (reinterpret_cast<uintptr_t>(a.coeffs) & 15) == 0;
+        volatile int64_t* span = reinterpret_cast<volatile int64_t*>(smem + KR_OFF_SPAN);
+        float* ring = reinterpret_cast<float*>(smem + KR_OFF_RAW);
+        const int64_t total = __ldg(a.offsets + ntot);       // end of the packed vector
+        int64_t rpos = 0;                                       // ring position (monotonic, floats) of the next span
+        int oldest = 0;                                      // oldest tile not yet released
+        constexpr int BPL = KR_BLK / 32;                     // blocks per lane
+        int64_t noff[BPL];
+        int nm[BPL];
+        auto fetch = [&](int jt) {                           // offsets and counts, one tile ahead
+            const int64_t fb = (t0 + (int64_t)jt * G2) * KR_BLK;
+            const int fn = (int)(ntot - fb < KR_BLK ? ntot - fb : KR_BLK);
+#pragma unroll
+            for (int h2 = 0; h2 < BPL; ++h2) {
+                const int i = lane + 32 * h2;
+                noff[h2] = i < fn ? __ldg(a.offsets + fb + i) : 0;
+                nm[h2] = i < fn ? __ldg(a.counts + fb + i) : 0;
+            }
+        };
+        if (my_n > 0) fetch(0);
+        int j = 0;
+        for (; j < my_n; ++j) {
+            const int slot = j & (KR_NSLOT - 1);
+            const int64_t b0 = (t0 + (int64_t)j * G2) * KR_BLK;
+            const int n = (int)(ntot - b0 < KR_BLK ? ntot - b0 : KR_BLK);
+            int64_t off[BPL];
+            int m[BPL], rel[BPL];
+#pragma unroll
+            for (int h2 = 0; h2 < BPL; ++h2) {
+                off[h2] = noff[h2];
+                m[h2] = nm[h2];
+            }
+            if (j + 1 < my_n) fetch(j + 1);
+            const int64_t start = __shfl_sync(0xffffffffu, off[0], 0);
+            bool bad = false;
+            int end_rel = 0, kmax = 0;
+#pragma unroll
+            for (int h2 = 0; h2 < BPL; ++h2) {
+                rel[h2] = 0;
+                if (lane + 32 * h2 >= n) {
+                    m[h2] = 0;
+                    continue;
+                }
+                const int64_t r = off[h2] - start;
+                if (start < 0 || m[h2] < 0 || m[h2] > 256 || r < 0 || r + m[h2] > KR_BLK * 256 ||
+                    start + r + m[h2] > total) {
+                    bad = true;
+                    m[h2] = 0;
+                } else {
+                    rel[h2] = (int)r;
+                }
+                end_rel = max(end_rel, rel[h2] + m[h2]);
+                kmax = max(kmax, m[h2]);
+            }
+            if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(a.status, ABCS_DEV_BADCOUNT);
+            end_rel = warp_max(end_rel);
+            kmax = warp_max(kmax);
+            const int64_t s0 = start < 0 ? 0 : start;
+            const int sh = (int)(s0 & 3);
+            const int64_t lo4 = s0 - sh, e = s0 + end_rel, hi4 = (e + 3) & ~(int64_t)3, sz = hi4 - lo4;
+            if ((rpos % KR_RING) + sz > KR_RING) rpos += KR_RING - (rpos % KR_RING);
+            bool ok = true;
+            while (oldest < j && (j - oldest >= KR_NSLOT || rpos + sz - span[oldest & (KR_NSLOT - 1)] > KR_RING)) {
+                int w = 1;
+                if (lane == 0)
+                    w = mbar_wait(bar + KR_RAWE + 8 * (oldest & (KR_NSLOT - 1)), (oldest / KR_NSLOT) & 1, abort_flag,
+                                  a.status);
+                if (!__shfl_sync(0xffffffffu, w, 0)) {
+                    ok = false;
+                    break;
+                }
+                ++oldest;
+            }
+            if (!ok) break;
+            const int ro = (int)(rpos % KR_RING);
+            KrInfo& I = info[slot];
+#pragma unroll
+            for (int h2 = 0; h2 < BPL; ++h2) {
+                I.rel[lane + 32 * h2] = ro + sh + rel[h2];
+                I.m[lane + 32 * h2] = m[h2];
+            }
+            if (lane == 0) {
+                I.nst = kmax > 0 ? (kmax + KR_KS - 1) / KR_KS : 1;
+                span[slot] = rpos;
+            }
+            // bulk part [lo4, x1); plain loads for the last ragged 16 bytes of
+            // the packed vector (a rounded span would read past it) or for an
+            // unaligned coefficient pointer
+            int64_t x1 = hi4 > total ? (e & ~(int64_t)3) : hi4;
+            if (!al16) x1 = lo4;
+            for (int64_t x = (x1 > s0 ? x1 : s0) + lane; x < e; x += 32) ring[ro + (x - lo4)] = __ldg(a.coeffs + x);
+            __syncwarp();
+            if (lane == 0) {
+                const uint32_t full = bar + KR_RAWF + 8 * slot;
+                if (x1 > lo4) {
+                    const uint32_t bytes = (uint32_t)(x1 - lo4) * 4u;
+                    mbar_arrive_tx(full, bytes);
+                    bulk_g2s(sb + KR_OFF_RAW + (uint32_t)ro * 4u, a.coeffs + lo4, bytes, full);
+                } else {
+                    mbar_arrive(full);
+                }
+            }
+            rpos += sz;
+        }
+        // copies still in flight land before the CTA leaves
+        if (lane == 0)
+            for (int jj = j > KR_NSLOT ? j - KR_NSLOT : 0; jj < j; ++jj)
+                mbar_drain(bar + KR_RAWF + 8 * (jj & (KR_NSLOT - 1)), (jj / KR_NSLOT) & 1, a.status);
+    } else if (warp >= 2 && warp < 10) {
+        // ---- converters
+        const int i = (t - 64) % KR_BLK, part = (t - 64) / KR_BLK;
+        int g = 0;
+        for (int j = 0; j < my_n; ++j) {
+            const int slot = j & (KR_NSLOT - 1);
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(bar + KR_RAWF + 8 * slot, (j / KR_NSLOT) & 1, abort_flag, a.status);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            const KrInfo& I = info[slot];
+            const int nst = I.nst, m = I.m[i];
+            const float* raw = reinterpret_cast<const float*>(smem + KR_OFF_RAW) + I.rel[i];
+            bool alive = true;
+            for (int s = 0; s < nst; ++s, ++g) {
+                const int b = g & (KR_NB - 1);
+                if (lane == 0) ok = mbar_wait(bar + KR_BE + 8 * b, ((g / KR_NB) & 1) ^ 1, abort_flag, a.status);
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    alive = false;
+                    break;
+                }
+#pragma unroll
+                for (int cc = 0; cc < KR_CPT; ++cc) {
+                    const int c = part * KR_CPT + cc, k0 = KR_KS * s + 8 * c;
+                    float v[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) v[e] = k0 + e < m ? raw[k0 + e] : 0.f;
+                    uint32_t hi[4], lo[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if constexpr (kSplit) split2<P>(v[2 * q], v[2 * q + 1], hi[q], lo[q]);
+                        else hi[q] = pk<P>(v[2 * q], v[2 * q + 1]);
+                    }
+                    unsigned char* st = smem + KR_OFF_STAGE + b * KR_STAGE + c * KR_CHUNK + i * 16;
+                    *reinterpret_cast<uint4*>(st) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    if constexpr (kSplit)
+                        *reinterpret_cast<uint4*>(st + KR_CH * KR_CHUNK) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    if (warp == 2) sflag[b] = (s == 0 ? 1 : 0) | (s == nst - 1 ? 2 : 0);
+                    mbar_arrive(bar + KR_BF + 8 * b);
+                }
+            }
+            if (!alive) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar + KR_RAWE + 8 * slot);
+        }
+    } else if (warp == 0) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            int g = 0;
+            bool alive = true;
+            for (int j = 0; j < my_n && alive; ++j) {
+                const int acc = j & (KR_NACC - 1);
+                if (!mbar_wait(bar + KR_ACCE + 8 * acc, ((j / KR_NACC) & 1) ^ 1, abort_flag, a.status)) break;
+                tc5_fence_after();
+                const uint32_t d = tmem + 256 + KR_BLK * acc;
+                for (int s = 0;; ++s) {
+                    const int b = g & (KR_NB - 1);
+                    if (!mbar_wait(bar + KR_BF + 8 * b, (g / KR_NB) & 1, abort_flag, a.status)) {
+                        alive = false;
+                        break;
+                    }
+                    tc5_fence_after();
+                    const int f = sflag[b];
+                    const uint32_t st = sb + KR_OFF_STAGE + b * KR_STAGE;
+#pragma unroll
+                    for (int kk = 0; kk < KR_KS / 16; ++kk) {
+                        const uint32_t ah = tmem + 8 * ((KR_KS / 16 * s + kk) & 15);
+                        const uint64_t bh = umma_desc(st + 2 * kk * KR_CHUNK, KR_CHUNK, 128);
+                        umma_tmem_a(d, ah, bh, IDESC, (f & 1) && kk == 0 ? 0u : 1u);
+                        if constexpr (kSplit) {
+                            const uint64_t bl = umma_desc(st + KR_CH * KR_CHUNK + 2 * kk * KR_CHUNK, KR_CHUNK, 128);
+                            umma_tmem_a(d, ah + 128, bh, IDESC, 1u);
+                            umma_tmem_a(d, ah, bl, IDESC, 1u);
+                        }
+                    }
+                    umma_commit(bar + KR_BE + 8 * b);     // the stage buffer is free once these complete
+                    ++g;
+                    if ((f & 2) || s == 256 / KR_KS - 1) {
+                        umma_commit(bar + KR_ACCF + 8 * acc);   // the tile's accumulator is ready
+                        break;
+                    }
+                }
+            }
+            umma_commit(bar + KR_DRAIN);
+            mbar_drain(bar + KR_DRAIN, 0, a.status);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue
+        const int sp = warp & 3, p = 128 * half + 32 * sp + lane;
+        const ImgGeom& G = a.g;
+        const int64_t pix = (int64_t)(p >> 4) * G.Wc + (p & 15);
+        auto u8 = [](float v) { return (uint8_t)fminf(fmaxf(rintf(v), 0.f), 255.f); };
+        for (int j = 0; j < my_n; ++j) {
+            const int acc = j & (KR_NACC - 1);
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(bar + KR_ACCF + 8 * acc, (j / KR_NACC) & 1, abort_flag, a.status);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            tc5_fence_after();
+            const uint32_t ta = tmem + ((uint32_t)(32 * sp) << 16) + 256 + KR_BLK * acc;
+            const int64_t b0 = (t0 + (int64_t)j * G2) * KR_BLK;
+            const int n = (int)(ntot - b0 < KR_BLK ? ntot - b0 : KR_BLK);
+            int k, bi, bj;
+            block_coords(G, b0, k, bi, bj);
+            int64_t pos = (int64_t)k * G.Hc * G.Wc + (int64_t)(bi * 16) * G.Wc + bj * 16 + pix;
+#pragma unroll 1
+            for (int g32 = 0; g32 < KR_BLK / 32; ++g32) {
+                uint32_t v[32];
+                tmem_ld32(ta + 32 * g32, v);
+                if (g32 == KR_BLK / 32 - 1) {       // the accumulator is free for the next tile
+                    tc5_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar + KR_ACCE + 8 * acc);
+                }
+#pragma unroll
+                for (int ii = 0; ii < 32; ++ii) {
+                    if (32 * g32 + ii < n) {
+                        const float x = __uint_as_float(v[ii]) * (1.f / KR_SCALE);
+                        if (a.out) a.out[pos] = x;
+                        if (a.out_u8) a.out_u8[pos] = u8(x);
+                    }
+                    pos += 16;
+                    if (++bj == G.nbw) {          // next block row (or the next image's first)
+                        bj = 0;
+                        pos += 15 * (int64_t)G.Wc;
+                    }
+                }
+            }
+        }
+    }
+    tc5_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc5_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512) : "memory");
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -537,8 +1001,8 @@ template <int P>
 __global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int64_t ntot) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint8_t (*pix)[16 * SEG * 16] = reinterpret_cast<uint8_t (*)[16 * SEG * 16]>(smem);
-    float* ost = reinterpret_cast<float*>(smem + 2 * 16 * SEG * 16);
-    SegMeta<SEG>* meta = reinterpret_cast<SegMeta<SEG>*>(smem + 2 * 16 * SEG * 16 + kSegFloats * sizeof(float));
+    float* ost = reinterpret_cast<float*>(smem + SNB * 16 * SEG * 16);
+    SegMeta<SEG>* meta = reinterpret_cast<SegMeta<SEG>*>(smem + SNB * 16 * SEG * 16 + kSegFloats * sizeof(float));
     const int warp = threadIdx.x >> 5;
     const Frag f;
     uint32_t DAh[4], DAl[4], DTh[2][2], DTl[2][2];
@@ -558,29 +1022,35 @@ __global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int64_t n
     const int nseg = (int)((r1 - r0 + SEG - 1) / SEG);
     if (nseg <= 0) return;
     griddep_wait();
+    // pixels of segments j + 1 .. j + SDEPTH are in flight while segment j is
+    // transformed (the same rings as in reconstruct)
     MetaRaw raw;
     if (warp == 0) {
-        sense_meta_store(seg_geom<SEG>(r0, r1, 0), sense_meta_load(a, seg_geom<SEG>(r0, r1, 0)), meta[0]);
-        if (1 < nseg) raw = sense_meta_load(a, seg_geom<SEG>(r0, r1, 1));
+        for (int d = 0; d < SDEPTH && d < nseg; ++d)
+            sense_meta_store(seg_geom<SEG>(r0, r1, d), sense_meta_load(a, seg_geom<SEG>(r0, r1, d)), meta[d]);
+        if (SDEPTH < nseg) raw = sense_meta_load(a, seg_geom<SEG>(r0, r1, SDEPTH));
     }
     __syncthreads();
-    sense_pixels(a, meta[0], pix[0], vec);
-    cp_async_commit();
-    int mi = 0;
+#pragma unroll
+    for (int d = 0; d < SDEPTH; ++d) {
+        if (d < nseg) sense_pixels(a, meta[d], pix[d], vec);
+        cp_async_commit();
+    }
+    int mi = 0, bi = 0, mn = SDEPTH % SNM, bn = SDEPTH % SNB;
     for (int j = 0; j < nseg; ++j) {
-        const int mn = mi == 2 ? 0 : mi + 1;
-        if (j + 1 < nseg && warp == 0) {
-            sense_meta_store(seg_geom<SEG>(r0, r1, j + 1), raw, meta[mn]);
-            if (j + 2 < nseg) raw = sense_meta_load(a, seg_geom<SEG>(r0, r1, j + 2));
+        const int jn = j + SDEPTH;
+        if (jn < nseg && warp == 0) {
+            sense_meta_store(seg_geom<SEG>(r0, r1, jn), raw, meta[mn]);
+            if (jn + 1 < nseg) raw = sense_meta_load(a, seg_geom<SEG>(r0, r1, jn + 1));
         }
-        cp_async_wait_all();
+        cp_async_wait_group<SDEPTH - 1>();
         __syncthreads();
-        if (j + 1 < nseg) sense_pixels(a, meta[mn], pix[(j + 1) & 1], vec);
+        if (jn < nseg) sense_pixels(a, meta[mn], pix[bn], vec);
         cp_async_commit();
 
         const SegMeta<SEG>& M = meta[mi];
         const int nblk = M.sg.nblk;
-        const uint8_t* px = pix[j & 1];
+        const uint8_t* px = pix[bi];
         float* os = ost + M.sh;
 #pragma unroll 2
         for (int c = warp; c < nblk; c += 8) {
@@ -629,7 +1099,10 @@ __global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int64_t n
             a.offsets[b] = start + M.rel[threadIdx.x];
             if (b == ntot - 1) a.offsets[ntot] = start + M.n;
         }
-        mi = mn;
+        mi = mi + 1 == SNM ? 0 : mi + 1;
+        bi = bi + 1 == SNB ? 0 : bi + 1;
+        mn = mn + 1 == SNM ? 0 : mn + 1;
+        bn = bn + 1 == SNB ? 0 : bn + 1;
     }
     cp_async_wait_all();
 }
@@ -650,7 +1123,29 @@ cudaError_t grid_segs(K kernel, int64_t ntot, int seg, size_t smem, int* grid) {
 }
 
 template <int P>
+cudaError_t launch_recon_umma_p(const ReconArgs& a, cudaStream_t s) {
+    const int64_t ntot = (int64_t)a.g.n_img * a.g.n_blocks;
+    if (ntot <= 0) return cudaSuccess;
+    int dev, sms;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!e) e = cudaFuncSetAttribute(recon_umma_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KR_SMEM);
+    if (e) return e;
+    const int64_t T = (ntot + KR_BLK - 1) / KR_BLK;
+    const int pairs = (int)(T < sms / 2 ? T : (sms / 2 > 0 ? sms / 2 : 1));
+    return launch_pdl(recon_umma_kernel<P>, dim3(2 * pairs), dim3(KR_THREADS), KR_SMEM, s, a, ntot);
+}
+
+// ABCS_RECON_TC=umma selects the tensor-memory kernel (measured slower than
+// the mma.sync one on the 64 x 512^2 workload, so not the default)
+inline bool recon_umma_selected() {
+    const char* v = getenv("ABCS_RECON_TC");
+    return v && strcmp(v, "umma") == 0;
+}
+
+template <int P>
 cudaError_t launch_recon_tc_p(const ReconArgs& a, cudaStream_t s) {
+    if (recon_umma_selected()) return launch_recon_umma_p<P>(a, s);
     const int64_t ntot = (int64_t)a.g.n_img * a.g.n_blocks;
     int grid = 0;
     cudaError_t e = grid_segs(recon_tc_kernel<P>, ntot, RSEG, kReconSmem, &grid);
@@ -670,6 +1165,7 @@ cudaError_t launch_sense_tc_p(const SenseArgs& a, cudaStream_t s) {
 
 cudaError_t setup_tc_fragments() {
     tc_frag_setup_kernel<<<1, 32>>>();
+    kron_setup_kernel<<<128, 256>>>();
     cudaError_t e = cudaGetLastError();
     if (!e) e = cudaDeviceSynchronize();
     return e;

@@ -4,6 +4,7 @@
   python -m paper_2001_09632_gb300.profile_cases bm3d   # abcs_denoise_bm3d, 16 x 512x512, sigma 20
   python -m paper_2001_09632_gb300.profile_cases thi    # abcs_thi, 64 x 512x512, M = floor(0.3 N)
   python -m paper_2001_09632_gb300.profile_cases damp   # abcs_damp, 16 x 512x512, DD r 0.1, 3 iterations
+  python -m paper_2001_09632_gb300.profile_cases recon  # abcs_reconstruct FP16x2, 64 x 512x512, BBV r 0.3
 """
 from __future__ import annotations
 
@@ -73,12 +74,28 @@ def damp(h):
     return {"case": "damp", "ms": _timed(run)}
 
 
+def recon(h):
+    n, H, W, B, r = 64, 512, 512, 16, 0.3
+    d = torch.from_numpy(synth.gen_batch(n, H, W, 1234)).cuda()
+    plan = abcs.abcs_plan(H, W, B, r, abcs.BBV)
+    nB = plan["n_blocks"]
+    c = torch.empty(n * nB, dtype=torch.int32, device="cuda")
+    o = torch.empty(n * nB + 1, dtype=torch.int64, device="cuda")
+    y = torch.empty(n * plan["M"], dtype=torch.float32, device="cuda")
+    abcs.abcs_sense(h, d, n, H, W, W, H * W, B, r, abcs.BBV, abcs.TC_FP16X2, c, o, y, n * plan["M"])
+    x = torch.empty((n, H, W), device="cuda")
+    run = lambda: abcs.abcs_reconstruct(h, c, o, y, n, H, W, B, abcs.TC_FP16X2, x)
+    for _ in range(3):
+        run()
+    return {"case": "recon", "ms": _timed(run)}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["bm3d", "thi", "damp"])
+    ap.add_argument("case", choices=["bm3d", "thi", "damp", "recon"])
     a = ap.parse_args()
     h = abcs.abcs_create()
-    res = {"bm3d": bm3d, "thi": thi, "damp": damp}[a.case](h)
+    res = {"bm3d": bm3d, "thi": thi, "damp": damp, "recon": recon}[a.case](h)
     res["status"] = abcs.abcs_sync_status(h)
     print(json.dumps(res))
     abcs.abcs_destroy(h)

@@ -52,6 +52,33 @@ def test_tc_sense_and_reconstruct(handle, prec, variant, shape):
         assert ex <= BOUND[prec], ex
 
 
+@pytest.mark.parametrize("prec", [abcs.TC_FP16X2, abcs.TC_BF16X2, abcs.TC_BF16])
+@pytest.mark.parametrize("variant,shape", [(O.BBV, (2, 96, 336)), (O.DD, (5, 160, 208)), (O.ZZ, (3, 48, 48)),
+                                           (O.BBV, (9, 512, 512))])
+def test_tc_reconstruct_tensor_memory_kernel(handle, monkeypatch, prec, variant, shape):
+    """The tcgen05 reconstruct kernel (ABCS_RECON_TC=umma: basis images in
+    tensor memory, 128-block tiles) against the oracle; the shapes leave a
+    partial last tile, and 9 x 512^2 spans several tiles per CTA."""
+    n, H, W = shape
+    B, r = 16, 0.3
+    imgs = np.stack([synth.gen_image(H, W, 500 + k) for k in range(n)])
+    outs, c_ref, _ = _oracle(imgs, B, r, variant)
+    got = G.sense(handle, imgs, B, r, variant, precision=prec)
+    assert np.array_equal(got["counts"], c_ref)
+    monkeypatch.setenv("ABCS_RECON_TC", "umma")
+    rec, rec8, bits = G.reconstruct(handle, *got["d"], n, H, W, B, precision=prec, u8=True)
+    monkeypatch.delenv("ABCS_RECON_TC")
+    assert bits == 0
+    # uint8 output: the rounded, clamped FP32 pixels (a value within rounding of .5 may go either way)
+    assert np.max(np.abs(rec8.astype(int) - np.clip(np.rint(rec), 0, 255))) <= 1
+    rec_mma, _, _ = G.reconstruct(handle, *got["d"], n, H, W, B, precision=prec)
+    Hc, Wc = (H // B) * B, (W // B) * B
+    for k in range(n):
+        ref = O.reconstruct(outs[k]["counts"], outs[k]["y"], Hc, Wc, B)
+        assert G.rel_l2(rec[k], ref) <= BOUND[prec]
+        assert G.rel_l2(rec[k], rec_mma[k]) <= BOUND[prec]
+
+
 def test_precision_table(handle, capsys):
     """Relative L2 error vs FP64 and PSNR of the reconstruction for each
     precision on 8 images of 512x512, BBV, r = 0.3 (printed; asserted bounds)."""
