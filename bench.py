@@ -38,8 +38,12 @@ IDA_ITERS, LAMBDA, DF = 10, 2.3, 2.0
 FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one reconstruct launch on
 # this workload, from an ncu capture of the current kernel (None where none
-# was taken); must be re-measured whenever the kernel changes
-RECON_TRAFFIC = {"fp16x2": 28773120}
+# was taken); must be re-measured whenever the kernel changes.  Taken with
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+#       --clock-control none -k regex:recon_tc_kernel -s 2 -c 1
+#       python -m paper_2001_09632_gb300.profile_cases recon
+# (the same 64 x 512x512 BBV r 0.3 coefficients): 18,112,000 + 10,390,016 bytes
+RECON_TRAFFIC = {"fp16x2": 28502016}
 
 
 def _args():

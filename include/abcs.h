@@ -160,7 +160,12 @@ abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int
  *   out     [device] float [n_img][Hc][Wc] (Hc = floor(H/B) B, Wc = floor(W/B) B), or NULL
  *   out_u8  [device] uint8 [n_img][Hc][Wc] rounded half-to-even and clipped to [0,255], or NULL
  * At least one of out / out_u8 must be non-NULL.  Counts outside [0, B^2]
- * are clamped and flagged (ABCS_DEV_BADCOUNT). */
+ * are clamped and flagged (ABCS_DEV_BADCOUNT).
+ * Tensor-core precisions (B = 16) run the per-block mma.sync transform; with
+ * the environment variable ABCS_RECON_TC=umma (read at each call) they run
+ * the tcgen05 kernel instead, which computes each 128-block tile as one GEMM
+ * against the DCT basis images held in tensor memory (same results within
+ * the precision's bound; slower on the measured workloads). */
 abcs_status abcs_reconstruct(abcs_handle* h, const int32_t* counts, const int64_t* offsets,
                              const float* coeffs, int n_img, int H, int W, int B, int precision,
                              float* out, uint8_t* out_u8, void* stream);
