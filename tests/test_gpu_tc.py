@@ -134,3 +134,51 @@ def test_tc_rejects_other_block_sizes(handle):
     with pytest.raises(abcs.AbcsError) as e:
         abcs.abcs_sense(handle, d, 1, 64, 64, 64, 4096, 8, 0.3, O.ZZ, abcs.TC_FP16X2, c, o, y, 4096)
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("prec", [abcs.TC_FP16X2, abcs.TC_BF16X2, abcs.TC_BF16])
+@pytest.mark.parametrize("variant,r", [(O.ZZ, 1.0), (O.DD, 1.0), (O.ZZ, 0.01), (O.DD, 0.01), (O.BBV, 0.01)])
+def test_tc_extreme_subrates(handle, monkeypatch, prec, variant, r):
+    """Every coefficient measured (r = 1: full staging buffers in sense and
+    reconstruct; for the tensor-memory kernel a worst-case span per tile and,
+    on 10 x 512^2 = 80 tiles, two tiles per CTA through its ring) and almost
+    none (r = 0.01: m1 = 1 for DD, the L-DCT-ZZ fallback for BBV since
+    n_S = 0).  Counts bit-exact; coefficients and both reconstruct kernels
+    within the precision's bound."""
+    n, H, W, B = 10, 512, 512, 16
+    imgs = synth.gen_batch(n, H, W, 2024)
+    outs, c_ref, y_ref = _oracle(imgs, B, r, variant)
+    got = G.sense(handle, imgs, B, r, variant, precision=prec)
+    assert got["bits"] == 0
+    assert np.array_equal(got["counts"], c_ref)
+    assert G.rel_l2(got["y"], y_ref) <= BOUND[prec]
+    refs = [O.reconstruct(o["counts"], o["y"], H, W, B) for o in outs]
+    rec, _, bits = G.reconstruct(handle, *got["d"], n, H, W, B, precision=prec)
+    assert bits == 0
+    monkeypatch.setenv("ABCS_RECON_TC", "umma")
+    rec_u, _, bits_u = G.reconstruct(handle, *got["d"], n, H, W, B, precision=prec)
+    monkeypatch.delenv("ABCS_RECON_TC")
+    assert bits_u == 0
+    for k in (0, 5, 9):
+        assert G.rel_l2(rec[k], refs[k]) <= BOUND[prec]
+        assert G.rel_l2(rec_u[k], refs[k]) <= BOUND[prec]
+
+
+def test_empty_batch_is_rejected(handle):
+    import torch
+    d = torch.zeros(64 * 64, dtype=torch.uint8, device="cuda")
+    c = torch.zeros(16, dtype=torch.int32, device="cuda")
+    o = torch.zeros(17, dtype=torch.int64, device="cuda")
+    y = torch.zeros(4096, dtype=torch.float32, device="cuda")
+    x = torch.zeros(4096, dtype=torch.float32, device="cuda")
+    for prec in (abcs.FP32, abcs.TC_FP16X2):
+        with pytest.raises(abcs.AbcsError) as e:
+            abcs.abcs_sense(handle, d, 0, 64, 64, 64, 4096, 16, 0.3, O.BBV, prec, c, o, y, 4096)
+        assert e.value.status == 1
+        with pytest.raises(abcs.AbcsError) as e:
+            abcs.abcs_reconstruct(handle, c, o, y, 0, 64, 64, 16, prec, x)
+        assert e.value.status == 1
+    with pytest.raises(abcs.AbcsError) as e:
+        abcs.abcs_ida(handle, c, o, y, 0, 64, 64, 16, 2, 2.0, abcs.DEN_TIDCT, 2.3, None, x)
+    assert e.value.status == 1
+    assert abcs.abcs_sync_status(handle) == 0
