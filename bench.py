@@ -284,7 +284,7 @@ def images_learned_vs_plain(h, n=32):
 
 
 def video_stream(h, n_frames=120, H=1088, W=1920, fpb=30):
-    """C5 as a stream (SURVEY next row 4): 120 frames of 1920x1088 in pinned
+    """The video clip as a stream: 120 frames of 1920x1088 in pinned
     host memory, 30 per batch, each batch copied to the device, sensed with
     AL-DCT-DD at r = 0.25 and reconstructed by IDA; Mpixel/s from the first
     copy to the last image, with the stages of consecutive batches run one
@@ -327,7 +327,7 @@ def video_stream(h, n_frames=120, H=1088, W=1920, fpb=30):
     return out
 
 
-def bm3d_judge(h, n=16, H=512, W=512, B=16, iters=(10, 30)):
+def bm3d_comparison(h, n=16, H=512, W=512, B=16, iters=(10, 30)):
     """BM3D (hard-thresholding step) as IDA's plain denoiser, the one the
     paper pairs with IDA (Sec. VII, Fig. 7a), beside TI-DCT and the learned
     CNN: mean PSNR on n held-out 512x512 images (DD and BBV at r = 0.1 and
@@ -690,7 +690,7 @@ def main():
             extras["thi"] = thi_correlation(h)
             extras["damp_vs_ida"] = damp_vs_ida(h)
             extras["video_stream"] = video_stream(h)
-            extras["bm3d_judge"] = bm3d_judge(h)
+            extras["bm3d_comparison"] = bm3d_comparison(h)
 
     if rank != 0:
         abcs.abcs_destroy(h)

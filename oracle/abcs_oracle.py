@@ -10,7 +10,7 @@ Everything here is written straight from the paper's definitions, in float64
 (or exact Python integers), with no blocking, fusion or reordering beyond
 what the cited passage states.  Library primitives (numpy matmul) serve as
 steps.  Where the paper is silent, ambiguous or contradicts itself, the
-reading taken is stated at the function (and collected in the design doc).
+reading taken is stated at the function.
 
 Functions and the passages they follow:
   dct_matrix, dct2_blocks ......... Sec. IV (orthonormal 2D-DCT dictionary), Sec. V-C
