@@ -105,6 +105,10 @@ struct ImgGeom {
 // while its predecessor in the stream drains; it must call griddep_wait()
 // before touching any global memory the predecessor may write (all inputs).
 ABCS_D void griddep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+// Lets the next kernel of the stream (launched with launch_pdl) start its
+// CTAs before this grid ends.  Called only after this kernel's own
+// griddep_wait(), so everything before it in the stream is complete by then.
+ABCS_D void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,

@@ -103,6 +103,10 @@ __global__ void __launch_bounds__(1024) bbv_image_kernel(SenseArgs a) {
     __shared__ int64_t sh[33];
     __shared__ bool s_last;
     griddep_wait();
+    // one CTA per image leaves most SMs free: the sensing kernel may start on
+    // them now and stage its first pixels (it waits for this grid before it
+    // reads any count or offset)
+    griddep_launch();
     const int k = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
     const int64_t nB = a.g.n_blocks;
     const int64_t ch = (nB + nt - 1) / nt;                 // <= CH (host)

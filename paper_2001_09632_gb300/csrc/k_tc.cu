@@ -962,6 +962,17 @@ ABCS_D MetaRaw sense_meta_load(const SenseArgs& a, const SegGeom& sg) {
     return r;
 }
 
+// pixel positions only (they do not depend on the allocation)
+ABCS_D void sense_pos_store(const SenseArgs& a, const SegGeom& sg, SegMeta<SEG>& M) {
+    const int lane = threadIdx.x & 31;
+    if (lane < sg.nblk) {
+        int k, bi, bj;
+        block_coords(a.g, sg.b0 + lane, k, bi, bj);
+        M.pos[lane] = (int64_t)k * a.g.img_stride + (int64_t)(bi * 16) * a.g.pitch + bj * 16;
+    }
+    if (lane == 0) M.sg = sg;
+}
+
 ABCS_D void sense_meta_store(const SegGeom& sg, const MetaRaw& r, SegMeta<SEG>& M) {
     const int lane = threadIdx.x & 31;
     const int64_t start = __shfl_sync(0xffffffffu, r.off, 0);
@@ -1021,7 +1032,15 @@ __global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int64_t n
     cta_range(ntot, &r0, &r1);
     const int nseg = (int)((r1 - r0 + SEG - 1) / SEG);
     if (nseg <= 0) return;
+    // the first segment's pixels do not depend on the allocation: they are
+    // staged before the wait for the pilot kernel, which lets this grid start
+    // once it has passed its own wait (so the images are final by then)
+    if (warp == 0) sense_pos_store(a, seg_geom<SEG>(r0, r1, 0), meta[0]);
+    __syncthreads();
+    sense_pixels(a, meta[0], pix[0], vec);
+    cp_async_commit();
     griddep_wait();
+    __syncthreads();                            // meta[0] is rewritten below
     // pixels of segments j + 1 .. j + SDEPTH are in flight while segment j is
     // transformed (the same rings as in reconstruct)
     MetaRaw raw;
@@ -1032,7 +1051,7 @@ __global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int64_t n
     }
     __syncthreads();
 #pragma unroll
-    for (int d = 0; d < SDEPTH; ++d) {
+    for (int d = 1; d < SDEPTH; ++d) {
         if (d < nseg) sense_pixels(a, meta[d], pix[d], vec);
         cp_async_commit();
     }
