@@ -4,9 +4,14 @@
 // One warp owns one 16x16 block at a time and keeps it in MMA fragments
 // through both transform stages (the accumulator layout of the first
 // product is the A-operand layout of the second), so no shared-memory
-// transpose and no CTA barrier is needed.  Warps walk blocks grid-stride and
-// prefetch the next block's input with cp.async while transforming the
-// current one.
+// transpose is needed.  Persistent CTAs walk equal contiguous block ranges
+// in 32-block segments whose input is staged with cp.async while the
+// previous segment is transformed.
+//
+// The file also holds recon_umma_kernel, the reconstruction as one tcgen05
+// GEMM per 128-block tile against the DCT basis images kept in tensor
+// memory (selected with ABCS_RECON_TC=umma; slower than the per-block
+// kernel on the measured workloads).
 //
 // Precisions (abcs_precision):
 //   TC_FP16X2  operands split v = hi + lo in FP16; products hi*hi + lo*hi + hi*lo
