@@ -142,3 +142,50 @@ def test_sense_packing_zigzag_order(golden):
         ref = scipy.fft.dctn(img[:, blk * 8:(blk + 1) * 8].astype(float), type=2, norm="ortho")
         by_rank = np.empty(64); by_rank[tab.reshape(-1)] = ref.reshape(-1)
         assert np.allclose(out["y"][blk * m:(blk + 1) * m], by_rank[:m], atol=1e-10)
+
+
+def test_reconstruct_is_a_sum_of_basis_images():
+    """The decoder output of a block (IDCT of the zero-filled coefficients)
+    equals sum_{k < m} y_k phi_k, with phi_k the basis image of zigzag rank
+    k written from the cosine definition (not the oracle's DCT matrix).
+
+    The same sum with 16 phi_k and y split into FP16 hi + lo words (products
+    hi*hi + lo*hi + hi*lo, then / 16) stays within 1e-7 relative L2. The
+    factor 16 keeps the low words of phi out of the FP16 subnormal range; it
+    beats the unscaled split.  This is the arithmetic of the tensor-memory
+    reconstruct kernel."""
+    from paper_2001_09632_gb300 import synth
+    B = 16
+    n = np.arange(B)
+    k = np.arange(B)[:, None]
+    D = np.where(k == 0, math.sqrt(1 / B), math.sqrt(2 / B)) * np.cos(np.pi * (2 * n + 1) * k / (2 * B))
+    Phi = np.stack([np.outer(D[u], D[v]).reshape(-1) for u, v in np.asarray(O.zigzag(B))], axis=1)
+    img = synth.gen_image(64, 96, 21)
+    out = O.sense(img, B, 0.3, O.BBV)
+    ref = O.reconstruct(out["counts"], out["y"], 64, 96, B)
+
+    def f16_split(x):
+        h = x.astype(np.float16).astype(np.float64)
+        return h, (x - h).astype(np.float16).astype(np.float64)
+
+    def basis_sum(scale=None):
+        rec = np.zeros_like(ref)
+        off = 0
+        for b, m in enumerate(out["counts"]):
+            y = np.zeros(B * B)
+            y[:m] = out["y"][off:off + m]
+            off += m
+            if scale is None:
+                x = Phi @ y
+            else:
+                Ah, Al = f16_split(scale * Phi)
+                yh, yl = f16_split(y.astype(np.float32).astype(np.float64))
+                x = (Ah @ yh + Al @ yh + Ah @ yl) / scale
+            bi, bj = divmod(b, 96 // B)
+            rec[bi * B:(bi + 1) * B, bj * B:(bj + 1) * B] = x.reshape(B, B)
+        return rec
+
+    assert np.max(np.abs(basis_sum() - ref)) < 1e-9
+    e16 = np.linalg.norm(basis_sum(16.0) - ref) / np.linalg.norm(ref)
+    e1 = np.linalg.norm(basis_sum(1.0) - ref) / np.linalg.norm(ref)
+    assert e16 <= 1e-7 and e16 < e1
