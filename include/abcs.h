@@ -346,22 +346,37 @@ abcs_status abcs_thi(abcs_handle* h, const float* coeffs, int n_img, int H, int 
  * this is a library service).  For callers that may not call cudaMalloc
  * while running: a sensing loop whose device memory is reserved once at
  * start-up, or a real-time loop that cannot afford cudaMalloc's implicit
- * device synchronisation.  Same arguments and results as abcs_sense, but no
- * handle: the scratch lives in one static device array of 4,784,640 bytes
- * that every GPU loading the library holds until the process exits.
- * Limits: n_img <= 4096 (else ABCS_ERR_INVALID_ARG); n_img * n_B <=
- * 1,048,576 blocks unless `pilot` is given, and at most 65,536 pilot partial
- * sums (n_img * ceil(n_B / 256) for BBV, n_img * nbh * ceil(nbw * B / 256)
- * for DD) (else ABCS_ERR_CAPACITY).
+ * device synchronisation.  The arguments and results are those of
+ * abcs_sense, with two differences: there is no handle, and only
+ * precision ABCS_FP32 is built (a tensor-core precision returns
+ * ABCS_ERR_UNSUPPORTED, a value outside abcs_precision ABCS_ERR_INVALID_ARG).
+ * The scratch lives in one static device array of 4,784,640 bytes that
+ * every GPU loading the library holds until the process exits.
+ * Limits: n_img <= 4096 and n_img * n_B < 2^31 (else ABCS_ERR_INVALID_ARG);
+ * n_img * n_B <= 1,048,576 blocks unless `pilot` is given, and at most
+ * 65,536 pilot partial sums (n_img * ceil(n_B / 256) for BBV,
+ * n_img * nbh * ceil(nbw * B / 256) for DD) (else ABCS_ERR_CAPACITY).
  * The first call on a device, with that device current, uploads the
- * transform tables and looks up the array's device address; make that
- * first call before any stream capture.  All calls share the array: calls
- * that overlap on the GPU (e.g. on two streams) race; serialise them.
- * Device status bits of these calls are not reported. */
+ * transform tables, looks up the array's device address and clears its
+ * status word; make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (e.g. on two streams)
+ * race; serialise them.  Device status bits of these calls (an undecidable
+ * DD decision, a bad count) collect in the array's status word until
+ * abcs_sense_noalloc_status reads them. */
 abcs_status abcs_sense_noalloc(const uint8_t* img, int n_img, int H, int W, int64_t pitch,
                                int64_t img_stride, int B, double subrate, int variant,
                                int precision, int32_t* counts, int64_t* offsets, float* coeffs,
                                int64_t coeff_capacity, int32_t* pilot, void* stream);
+
+/* Wait for `stream`, then read and clear the device status word that the
+ * abcs_sense_noalloc calls on the current device have set (no allocation).
+ * Returns ABCS_OK if no bit was set, else ABCS_ERR_DEVICE with the bits
+ * (ABCS_DEV_*) in *bits (bits may be NULL); ABCS_ERR_INVALID_ARG before the
+ * first abcs_sense_noalloc call on the device.  Failure-detection test
+ * hook, read on the host at each abcs_sense_noalloc call:
+ * ABCS_FAULT_NOALLOC_BITS=n ORs the bits n into the word after the call's
+ * kernels. */
+abcs_status abcs_sense_noalloc_status(void* stream, uint32_t* bits);
 
 /* Wait for `stream`, read and clear the device status word.  Returns
  * ABCS_OK if no bit was set, else ABCS_ERR_DEVICE with the bits in *bits

@@ -66,6 +66,7 @@ _SIGS = {
     "abcs_denoise_bm3d": [_P, _P, _I, _I, _I, _P, _D, _P, _P],
     "abcs_sync_status": [_P, _P, C.POINTER(C.c_uint32)],
     "abcs_sense_noalloc": [_P, _I, _I, _I, _L, _L, _I, _D, _I, _I, _P, _P, _P, _L, _P, _P],
+    "abcs_sense_noalloc_status": [_P, C.POINTER(C.c_uint32)],
     "abcs_ida_batch": [_P, _P, _I, _P, _P, _P, _L, _I, _D, _I, _D, _P, _P, _P],
     "abcs_ida_capture": [_P, _P, _P, _P, _I, _I, _I, _I, _I, _D, _I, _D, _P, _P, _P, _P],
     "abcs_cnn_param_count": [],
@@ -179,6 +180,16 @@ def abcs_sense_noalloc(img, n_img, H, W, pitch, img_stride, B, subrate, variant,
     _check(lib.abcs_sense_noalloc(_ptr(img), n_img, H, W, pitch, img_stride, B, subrate, variant,
                                   precision, _ptr(counts), _ptr(offsets), _ptr(coeffs),
                                   coeff_capacity, _ptr(pilot), _stream(stream)))
+
+
+def abcs_sense_noalloc_status(stream=None) -> int:
+    """Waits for the stream; returns and clears the device status bits of the
+    abcs_sense_noalloc calls on the current device (0 = clean)."""
+    bits = C.c_uint32(0)
+    st = lib.abcs_sense_noalloc_status(_stream(stream), C.byref(bits))
+    if st not in (0, 8):
+        _check(st)
+    return bits.value
 
 
 def abcs_cnn_param_count() -> int:

@@ -10,6 +10,7 @@
 // instead, so a call allocates nothing.  The caller still provides the
 // image and every output buffer.
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
 
 #include "abcs_common.cuh"
@@ -36,6 +37,8 @@ constexpr size_t kScratchBytes = kOffW + 4 * (size_t)kNoAllocMaxBlocks;   // 4,7
 // Held by every GPU that loads the library, until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+__global__ void or_status_kernel(uint32_t* st, uint32_t bits) { set_status(st, bits); }
+
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 unsigned char* g_scratch_dev[kMaxDevices];       // device address of the array, per device
@@ -61,9 +64,23 @@ abcs_status setup_device(int dev, unsigned char** out) {
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr)
         return record_error(ABCS_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
+    // the status word accumulates the device bits of every call until
+    // abcs_sense_noalloc_status reads and clears it: start it at zero once
+    e = cudaMemset(p, 0, 2 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return record_error(ABCS_ERR_CUDA, cudaGetErrorString(e));
     g_scratch_dev[dev] = static_cast<unsigned char*>(p);
     *out = g_scratch_dev[dev];
     return ABCS_OK;
+}
+
+// The scratch array of the current device, set up by an earlier call.
+unsigned char* current_scratch(int* dev_out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    *dev_out = dev;
+    return g_scratch_dev[dev];
 }
 
 }  // namespace
@@ -79,7 +96,13 @@ extern "C" abcs_status abcs_sense_noalloc(const uint8_t* img, int n_img, int H, 
     if (n_img < 1 || n_img > kNoAllocMaxImages)
         return err(ABCS_ERR_INVALID_ARG, "n_img must be in [1, %lld] for abcs_sense_noalloc",
                    kNoAllocMaxImages);
+    if (precision < ABCS_FP32 || precision > ABCS_TC_BF16)
+        return err(ABCS_ERR_INVALID_ARG, "bad precision %lld", precision);
+    if (precision != ABCS_FP32)
+        return err(ABCS_ERR_UNSUPPORTED,
+                   "abcs_sense_noalloc computes in FP32 only (precision %lld requested)", precision);
     const int64_t nb_all = (int64_t)n_img * p.n_blocks;
+    if (nb_all >= (1LL << 31)) return err(ABCS_ERR_INVALID_ARG, "more than 2^31 - 1 blocks in one call");
     if (!pilot && nb_all > kNoAllocMaxBlocks)
         return err(ABCS_ERR_CAPACITY,
                    "abcs_sense_noalloc: %lld blocks exceed the static scratch limit of %lld "
@@ -100,8 +123,6 @@ extern "C" abcs_status abcs_sense_noalloc(const uint8_t* img, int n_img, int H, 
     if (pitch < W) return err(ABCS_ERR_INVALID_ARG, "pitch %lld < W %lld", pitch, W);
     if (n_img > 1 && img_stride < pitch * H)
         return err(ABCS_ERR_INVALID_ARG, "img_stride smaller than pitch * H");
-    if (precision != ABCS_FP32)
-        return err(ABCS_ERR_UNSUPPORTED, "precision %lld is not built for sensing", precision);
     if (coeff_capacity < (int64_t)n_img * p.M)
         return err(ABCS_ERR_CAPACITY, "coeff_capacity %lld < n_img * M = %lld", coeff_capacity,
                    (int64_t)n_img * p.M);
@@ -129,9 +150,10 @@ extern "C" abcs_status abcs_sense_noalloc(const uint8_t* img, int n_img, int H, 
     a.w = pilot ? pilot : reinterpret_cast<int32_t*>(scratch + kOffW);
 
     // The array keeps the previous call's contents.  Pilot values, partial
-    // sums, totals and bases are fully overwritten by every call; the status
-    // word and the allocation CTA counter must start at zero.
-    cudaError_t e = cudaMemsetAsync(a.status, 0, 2 * sizeof(uint32_t), s);
+    // sums, totals and bases are fully overwritten by every call; the
+    // allocation CTA counter must start at zero.  The status word is left
+    // as it is: it collects the bits of every call until it is read.
+    cudaError_t e = cudaMemsetAsync(a.done, 0, sizeof(uint32_t), s);
     int mode = 0;
     if (e == cudaSuccess) {
         if (variant == ABCS_BBV && p.nS > 0) {
@@ -147,6 +169,34 @@ extern "C" abcs_status abcs_sense_noalloc(const uint8_t* img, int n_img, int H, 
     }
     if (e == cudaSuccess) e = launch_allocate(a, mode, s);
     if (e == cudaSuccess) e = launch_sense_pack(a, s);
+    // Failure-detection test hook (host side): ABCS_FAULT_NOALLOC_BITS=n ORs
+    // the bits n into the status word after the call's kernels, as a device
+    // condition (an undecidable DD tie, a bad count) would.
+    if (e == cudaSuccess)
+        if (const char* f = getenv("ABCS_FAULT_NOALLOC_BITS")) {
+            or_status_kernel<<<1, 1, 0, s>>>(a.status, (uint32_t)strtoul(f, nullptr, 0));
+            e = cudaGetLastError();
+        }
     if (e != cudaSuccess) return record_error(ABCS_ERR_CUDA, cudaGetErrorString(e));
+    return ABCS_OK;
+}
+
+extern "C" abcs_status abcs_sense_noalloc_status(void* stream, uint32_t* bits) {
+    int dev = 0;
+    unsigned char* scratch = current_scratch(&dev);
+    if (bits) *bits = 0;
+    if (!scratch)
+        return err(ABCS_ERR_INVALID_ARG,
+                   "abcs_sense_noalloc_status: no abcs_sense_noalloc call on the current device yet");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(s);
+    uint32_t v = 0;
+    // a plain copy into a host variable and a memset: neither allocates
+    if (e == cudaSuccess) e = cudaMemcpy(&v, scratch + kOffStatus, sizeof v, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(scratch + kOffStatus, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return record_error(ABCS_ERR_CUDA, cudaGetErrorString(e));
+    if (bits) *bits = v;
+    if (v) return err(ABCS_ERR_DEVICE, "device status bits 0x%llx", (long long)v);
     return ABCS_OK;
 }
