@@ -481,19 +481,45 @@ def haar_matrix(n: int) -> np.ndarray:
     return H
 
 
+def bm3d_group(r: np.ndarray, y: int, x: int, sigma: float, N1: int = 8, N2: int = 16, Ns: int = 39):
+    """Block matching of BM3D's hard-thresholding step for the reference
+    patch at (y, x): the list of (d, row, column) of the group, the
+    reference first.
+
+    Candidates are the patches whose top-left corner lies within Ns // 2
+    rows and columns of the reference's, inside the image; d = ||P_ref -
+    P||^2 / N1^2 on the noisy patches; a candidate joins when d <= tau, with
+    tau = 2500 for sigma <= 40, else 5000 (reading: no prefiltering).  The
+    matches follow the reference in (d, row, column) order, and the group
+    keeps the first min(N2, count) rounded down to a power of two.
+    """
+    H, W = r.shape
+    tau = 2500.0 if sigma <= 40.0 else 5000.0
+    half = Ns // 2
+    ref = r[y:y + N1, x:x + N1]
+    cands = []
+    for yy in range(max(0, y - half), min(H - N1, y + half) + 1):
+        for xx in range(max(0, x - half), min(W - N1, x + half) + 1):
+            if (yy, xx) == (y, x):
+                continue
+            d = float(np.sum((ref - r[yy:yy + N1, xx:xx + N1]) ** 2)) / (N1 * N1)
+            if d <= tau:
+                cands.append((d, yy, xx))
+    cands.sort()
+    cands = [(0.0, y, x)] + cands                                        # the reference first
+    n = 1
+    while 2 * n <= min(N2, len(cands)):
+        n *= 2
+    return cands[:n]
+
+
 def bm3d_ht(r: np.ndarray, sigma: float, lam3d: float = 2.7, N1: int = 8, N2: int = 16, Ns: int = 39,
             Nstep: int = 3, beta: float = 2.0) -> np.ndarray:
     """BM3D's basic estimate of r (noise level sigma).
 
     - Reference patches (N1 x N1) at rows 0, Nstep, 2 Nstep, ... and the
       last row H - N1 (the same for columns).
-    - Candidates: every patch whose top-left corner lies within Ns // 2 of
-      the reference's, inside the image.
-    - Distance d = ||P_ref - P||^2 / N1^2 on the noisy patches.  Reading:
-      no prefiltering; tau = 2500 for sigma <= 40, else 5000.
-    - The group: the reference first, then the other candidates with
-      d <= tau ordered by (d, row, column); the first min(N2, count) rounded
-      down to a power of two.
+    - The group of each reference by block matching (bm3d_group).
     - 3D transform: orthonormal 2D DCT of every patch, then the orthonormal
       Haar transform along the group.
     - Hard threshold: zero the coefficients with |c| <= lam3d sigma.  Reading:
@@ -505,32 +531,17 @@ def bm3d_ht(r: np.ndarray, sigma: float, lam3d: float = 2.7, N1: int = 8, N2: in
     r = np.asarray(r, dtype=np.float64)
     H, W = r.shape
     D = dct_matrix(N1)
-    tau = 2500.0 if sigma <= 40.0 else 5000.0
     k1 = np.kaiser(N1, beta)
     K = np.outer(k1, k1)
     num = np.zeros((H, W))
     den = np.zeros((H, W))
     ys = sorted(set(list(range(0, H - N1 + 1, Nstep)) + [H - N1]))
     xs = sorted(set(list(range(0, W - N1 + 1, Nstep)) + [W - N1]))
-    half = Ns // 2
     thr = lam3d * sigma
     for y in ys:
         for x in xs:
-            ref = r[y:y + N1, x:x + N1]
-            cands = []
-            for yy in range(max(0, y - half), min(H - N1, y + half) + 1):
-                for xx in range(max(0, x - half), min(W - N1, x + half) + 1):
-                    if (yy, xx) == (y, x):
-                        continue
-                    d = float(np.sum((ref - r[yy:yy + N1, xx:xx + N1]) ** 2)) / (N1 * N1)
-                    if d <= tau:
-                        cands.append((d, yy, xx))
-            cands.sort()
-            cands = [(0.0, y, x)] + cands                                        # the reference first
-            n = 1
-            while 2 * n <= min(N2, len(cands)):
-                n *= 2
-            grp = cands[:n]
+            grp = bm3d_group(r, y, x, sigma, N1, N2, Ns)
+            n = len(grp)
             P = np.stack([r[yy:yy + N1, xx:xx + N1] for _, yy, xx in grp])       # n, N1, N1
             C = D @ P @ D.T                                                      # 2D DCT per patch
             Hn = haar_matrix(n)

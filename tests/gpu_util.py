@@ -13,6 +13,48 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
+def block_scale(y_ref, counts, offsets):
+    """Per coefficient: max(1, the largest |coefficient| of its block in y_ref)
+    (the block's DC for every block with m_i >= 1).  A coefficient's FP32
+    error is bounded relative to its block's energy, not to its own size."""
+    y_ref = np.abs(np.asarray(y_ref, dtype=np.float64))
+    counts = np.asarray(counts, dtype=np.int64)
+    starts = np.asarray(offsets, dtype=np.int64)[:-1] - int(offsets[0])
+    scale = np.ones(len(y_ref))
+    nz = counts > 0
+    if len(y_ref):
+        mx = np.maximum.reduceat(y_ref, starts[nz]) if nz.any() else np.zeros(0)
+        scale = np.repeat(np.maximum(1.0, mx), counts[nz])
+    return scale
+
+
+def check_coeffs(y, y_ref, counts, offsets, tol, tag=""):
+    """Packed measurements against the oracle's: relative L2 over all of them
+    <= tol, and every single coefficient within 10 tol of its block's scale
+    (a coefficient off by 1, or one block off by a few units, fails)."""
+    y = np.asarray(y, dtype=np.float64)
+    y_ref = np.asarray(y_ref, dtype=np.float64)
+    assert y.shape == y_ref.shape, (tag, y.shape, y_ref.shape)
+    e = rel_l2(y, y_ref)
+    assert e <= tol, (tag, "relL2", e)
+    if len(y):
+        worst = float(np.max(np.abs(y - y_ref) / block_scale(y_ref, counts, offsets)))
+        assert worst <= 10 * tol, (tag, "max per-coefficient error / block scale", worst)
+    return e
+
+
+def check_pixels(x, x_ref, tol, tag="", scale=255.0):
+    """Pixels against the oracle's: relative L2 <= tol and every pixel within
+    10 tol of the pixel range (one pixel off by 1 fails)."""
+    x = np.asarray(x, dtype=np.float64)
+    x_ref = np.asarray(x_ref, dtype=np.float64)
+    e = rel_l2(x, x_ref)
+    assert e <= tol, (tag, "relL2", e)
+    worst = float(np.max(np.abs(x - x_ref))) / scale
+    assert worst <= 10 * tol, (tag, "max per-pixel error / range", worst)
+    return e
+
+
 def sense(h, imgs, B, r, variant, precision=abcs.FP32, pitch=None):
     """imgs: (n, H, W) uint8 numpy.  Returns numpy counts, offsets, y, pilot, status bits."""
     imgs = np.ascontiguousarray(imgs)

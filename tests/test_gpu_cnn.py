@@ -108,6 +108,53 @@ def test_cnn_forward_parity(handle, n, H, W):
         assert err <= 2e-2, err
 
 
+# Output windows checked against the oracle on full-size images: corners,
+# the bottom rows, and windows across the 128-pixel tile columns and the
+# 4- and 8-row tile rows of the tensor-core layers, so tiles at x0 > 0,
+# several tiles per CTA (ring reuse, both tensor-memory accumulators,
+# mbarrier phase flips) and the persistent first layer are all compared.
+FULL_WINDOWS = {
+    (2, 512, 512): [(0, 0, 0, 16, 40), (0, 100, 120, 16, 24), (1, 250, 250, 12, 20), (1, 504, 480, 8, 32),
+                    (0, 300, 380, 10, 10), (1, 3, 509, 9, 3)],
+    (1, 1088, 1920): [(0, 0, 1880, 12, 40), (0, 540, 1020, 12, 16), (0, 1080, 0, 8, 30),
+                      (0, 1076, 1900, 12, 20), (0, 700, 1150, 10, 12)],
+}
+
+
+@pytest.mark.parametrize("n,H,W", list(FULL_WINDOWS))
+def test_cnn_forward_parity_full_size(handle, n, H, W):
+    """The learned denoiser on full-size images in the launch configuration
+    IDA and the benches use, against the FP64 oracle on output windows: the
+    receptive field of the 8 conv3x3 layers is +-8 pixels, so the oracle run
+    on the window plus an 8-pixel halo (clipped at the image border, where
+    the zero padding is the network's own) gives the window's outputs
+    exactly."""
+    params = _params(13)
+    ref_p = _bf16_mid(params)
+    _, packed = _pack(handle, params)
+    clean, r = _noisy(n, H, W, 70, 15.0)
+    dens = _density(n, H, W, 71)
+    sig = np.array([15.0, 24.0][:n])
+    d_in = torch.tensor(r, dtype=torch.float32, device="cuda")
+    d_out = torch.full_like(d_in, float("nan"))
+    abcs.abcs_cnn_denoise(handle, packed, d_in, torch.tensor(sig, dtype=torch.float32, device="cuda"),
+                          torch.tensor(dens, device="cuda"), n, H, W, d_out)
+    assert abcs.abcs_sync_status(handle) == 0
+    got = d_out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    r32 = d_in.cpu().numpy().astype(float)
+    for (k, y0, x0, h, w) in FULL_WINDOWS[(n, H, W)]:
+        ya, yb = max(0, y0 - 8), min(H, y0 + h + 8)
+        xa, xb = max(0, x0 - 8), min(W, x0 + w + 8)
+        ref = O.cnn_denoise(ref_p, r32[k, ya:yb, xa:xb], float(np.float32(sig[k])),
+                            dens[k, ya:yb, xa:xb].astype(float))[y0 - ya:y0 - ya + h, x0 - xa:x0 - xa + w]
+        rin = r32[k, y0:y0 + h, x0:x0 + w]
+        n_ref = (rin - ref) / 255.0
+        n_got = (rin - got[k, y0:y0 + h, x0:x0 + w]) / 255.0
+        err = np.linalg.norm(n_got - n_ref) / np.linalg.norm(n_ref)
+        assert err <= 2e-2, ((k, y0, x0), err)
+
+
 def test_cnn_gradient_parity(handle):
     params = _params(5)
     ref_p = _bf16_mid(params)

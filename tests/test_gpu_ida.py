@@ -53,7 +53,8 @@ def test_tidct_parity(handle, H, W, sigma, lam):
     r32 = d_in.cpu().numpy()[0].astype(float)
     ref = O.tidct_denoise(r32, float(np.float32(sigma)), lam)
     mask = _ambiguous_mask(r32, lam * float(np.float32(sigma))) if lam > 0 else np.zeros_like(r, bool)
-    assert mask.mean() < 0.1
+    # measured on these inputs: at most 3.5% of the pixels (100 x 250, sigma 8)
+    assert mask.mean() < 0.05, mask.mean()
     err = np.abs(got - ref)[~mask]
     assert err.max() <= 1e-5 * np.abs(ref).max()
     assert G.rel_l2(got[~mask], ref[~mask]) <= 1e-6
@@ -81,7 +82,27 @@ def test_ida_identity_denoiser_parity(handle, B, DF):
         # error relative to ||A^T y||: with D_F = 1 some iterates are exactly 0
         scale = np.linalg.norm(O.reconstruct(out["counts"], out["y"], Hc, Wc, B))
         assert np.linalg.norm(x[0] - xr) <= 1e-5 * scale, iters
+        assert np.max(np.abs(x[0] - xr)) <= 1e-4 * 255, iters       # every pixel
         np.testing.assert_allclose(tr[0, :iters], sig, rtol=1e-5, atol=1e-4 * max(sig))
+
+
+@pytest.mark.parametrize("variant", [O.BBV, O.DD])
+def test_ida_linear_step_full_size(handle, variant):
+    """The linear part of IDA (Eqs. 25, 28: residual, Onsager term, A^T z) on
+    2 x 512x512 images at B = 16, r = 0.3, in the launch configuration of the
+    batched workload: with D = identity every iterate is linear in y; every
+    pixel and sigma^t of iterations 1, 3 and 6 against the FP64 oracle."""
+    n, H, W, B, r = 2, 512, 512, 16, 0.3
+    imgs = synth.gen_batch(n, H, W, 611)
+    got = G.sense(handle, imgs, B, r, variant)
+    outs = [O.sense(im, B, r, variant) for im in imgs]
+    for iters in (1, 3, 6):
+        x, tr, bits = G.ida(handle, *got["d"], n, H, W, B, iters, 2.0, abcs.DEN_NONE)
+        assert bits == 0
+        for k in range(n):
+            xr, sig = O.ida(outs[k]["y"], outs[k]["counts"], H, W, B, iters, DF=2.0, denoiser=None)
+            G.check_pixels(x[k], xr, 1e-5, (iters, k))
+            np.testing.assert_allclose(tr[k, :iters], sig, rtol=1e-5)
 
 
 def test_ida_tidct_end_to_end(handle):

@@ -49,7 +49,7 @@ def test_sense_parity(handle, case, r, variant):
     if variant != O.ZZ:
         assert np.array_equal(got["pilot"], p_ref)
     assert len(got["y"]) == len(y_ref)
-    assert G.rel_l2(got["y"], y_ref) <= TOL
+    G.check_coeffs(got["y"], y_ref, c_ref, o_ref, TOL)
     # reconstruction of the same measurements
     rec, rec8, bits = G.reconstruct(handle, *got["d"], n, H, W, B, u8=True)
     assert bits == 0
@@ -58,7 +58,7 @@ def test_sense_parity(handle, case, r, variant):
         ref = O.reconstruct(c_ref[k * (Hc // B) * (Wc // B):(k + 1) * (Hc // B) * (Wc // B)],
                             y_ref[o_ref[k * (Hc // B) * (Wc // B)]:o_ref[(k + 1) * (Hc // B) * (Wc // B)]],
                             Hc, Wc, B)
-        assert G.rel_l2(rec[k], ref) <= TOL
+        G.check_pixels(rec[k], ref, TOL, k)
         ref8 = np.clip(np.round(ref), 0, 255)
         assert np.max(np.abs(rec8[k].astype(float) - ref8)) <= 1    # rounding ties may differ
 
@@ -67,7 +67,8 @@ def test_sense_pitched_rows(handle):
     imgs = np.stack([synth.gen_image(48, 200, 7)])
     ref = _oracle_batch(imgs, 16, 0.3, O.BBV)
     got = G.sense(handle, imgs, 16, 0.3, O.BBV, pitch=272)
-    assert np.array_equal(got["counts"], ref[0]) and G.rel_l2(got["y"], ref[2]) <= TOL
+    assert np.array_equal(got["counts"], ref[0])
+    G.check_coeffs(got["y"], ref[2], ref[0], ref[1], TOL)
 
 
 @pytest.mark.parametrize("B", [4, 8, 16, 32])
@@ -146,4 +147,4 @@ def test_full_size_batch_counts(handle, variant):
     assert np.array_equal(got["counts"], c_ref)
     assert np.array_equal(got["offsets"], o_ref)
     assert np.array_equal(got["pilot"], p_ref)
-    assert G.rel_l2(got["y"], y_ref) <= TOL
+    G.check_coeffs(got["y"], y_ref, c_ref, o_ref, TOL)

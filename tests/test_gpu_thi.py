@@ -6,6 +6,10 @@ FP64 ones.  The two rankings can differ only between coefficients within
 FP32 rounding of the threshold, so counts are compared bit-exactly when the
 M-th coefficient is the only one in that band, and otherwise checked to
 differ by at most the coefficients in the band (both keep exactly M).
+Whatever the band, the GPU's selection is checked in full on the FP32
+values it ranked (exactly M kept, nothing dropped above a kept magnitude,
+ties in index order, counts and masked values consistent), and rho and the
+THI image are compared with the oracle's on the GPU's kept set.
 """
 import numpy as np
 import pytest
@@ -45,6 +49,30 @@ def _band(img, B, M):
     return int(np.sum(np.abs(mag - t) <= 2e-6 * t + 2e-3))
 
 
+def _check_kept_set(Z, mk, counts, M, tag=""):
+    """Full validity of one image's selection, on the FP32 coefficients the
+    GPU ranked: exactly M kept; the masked output holds the kept
+    coefficients bit for bit and zeros elsewhere; every kept |c| >= every
+    dropped |c|; among magnitudes equal to the threshold the lowest
+    (block, zigzag rank) indices are kept; the counts are the per-block
+    numbers kept.  Returns the kept mask (n_B, B*B)."""
+    Z = np.asarray(Z, dtype=np.float32)
+    mk = np.asarray(mk, dtype=np.float32)
+    kept = mk != 0
+    assert np.all((mk == 0) | (mk == Z)), tag                    # kept values are the inputs, bit for bit
+    a = np.abs(Z).reshape(-1)
+    k = kept.reshape(-1)
+    t = a[k].min()
+    assert t > 0, tag                                            # no zero coefficient needs keeping here
+    assert int(k.sum()) == M, (tag, int(k.sum()), M)
+    assert np.all(a[~k] <= t), tag                               # nothing dropped above the threshold
+    tied = np.flatnonzero(a == t)
+    n_tied_kept = M - int(np.sum(a > t))
+    assert np.array_equal(np.flatnonzero(k & (a == t)), tied[:n_tied_kept]), tag   # ties in index order
+    assert np.array_equal(np.asarray(counts), kept.sum(axis=1)), tag
+    return kept
+
+
 def _check_counts(got, ref, amb):
     assert got.sum() == ref.sum()
     if amb <= 1:
@@ -69,14 +97,24 @@ def test_thi_counts_rho_and_image(handle, shape, B, variant):
     full = torch.full((n * nB,), B * B, dtype=torch.int32, device="cuda")
     rec, _, bits = G.reconstruct(handle, full, offs, mk, n, H, W, B)
     assert bits == 0
+    Zg = coeffs.cpu().numpy().reshape(n, nB, B * B)
+    Mk = mk.cpu().numpy().reshape(n, nB, B * B)
+    zr = O.zigzag_rank(B).reshape(-1)
     for k in range(n):
         ref = O.thi_counts(imgs[k], B, M)
         amb = _band(imgs[k], B, M)
         got = counts[k * nB:(k + 1) * nB]
         _check_counts(got, ref, amb)
+        kept = _check_kept_set(Zg[k], Mk[k], got, M, k)
+        # rho of the GPU's counts, and the image of the GPU's kept set with
+        # the oracle's FP64 coefficients
+        assert rho[k] == pytest.approx(O.pearson(got, ad["counts"][k * nB:(k + 1) * nB]), abs=1e-12)
+        Zo = np.where(kept, O.full_coefficients(imgs[k], B), 0.0)
+        img_kept = O.idct2_blocks(Zo[:, zr].reshape(Hc // B, Wc // B, B, B))
+        G.check_pixels(rec[k], img_kept, 1e-5, k)
         if amb <= 1:
             assert rho[k] == pytest.approx(O.pearson(ref, ad["counts"][k * nB:(k + 1) * nB]), abs=1e-12)
-            assert G.rel_l2(rec[k], O.thi_reconstruct(imgs[k], B, M)[:Hc, :Wc]) <= 1e-5
+            G.check_pixels(rec[k], O.thi_reconstruct(imgs[k], B, M)[:Hc, :Wc], 1e-5, k)
 
 
 def test_thi_ties_follow_block_order(handle):
@@ -123,9 +161,15 @@ def test_thi_full_batch(handle):
     coeffs, nB = _full(handle, imgs, B)
     ad = G.sense(handle, imgs, B, r, O.BBV, precision=abcs.TC_FP16X2)
     M = O.plan(512, 512, B, r, O.BBV)["M"]
-    counts, rho, _ = _thi(handle, coeffs, n, 512, 512, B, M, adaptive=ad["d"][0], masked=False)
+    counts, rho, mk = _thi(handle, coeffs, n, 512, 512, B, M, adaptive=ad["d"][0], masked=True)
     assert np.all(counts.reshape(n, nB).sum(axis=1) == M)
     assert np.all((rho > 0.0) & (rho <= 1.0))
+    Zg = coeffs.cpu().numpy().reshape(n, nB, B * B)
+    Mk = mk.cpu().numpy().reshape(n, nB, B * B)
+    for k in range(n):                                   # every image: a valid selection of exactly M
+        _check_kept_set(Zg[k], Mk[k], counts[k * nB:(k + 1) * nB], M, k)
+        assert rho[k] == pytest.approx(O.pearson(counts[k * nB:(k + 1) * nB], ad["counts"][k * nB:(k + 1) * nB]),
+                                       abs=1e-12)
     for k in (0, 31, 63):
         ref = O.thi_counts(imgs[k], B, M)
         amb = _band(imgs[k], B, M)

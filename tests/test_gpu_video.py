@@ -1,12 +1,16 @@
 """The streaming video pipeline (paper_2001_09632_gb300.video): copy, sense
 and IDA of consecutive frame batches on three streams give exactly the
 images of the same calls run one after another, and those of per-batch
-abcs_sense / abcs_ida calls; a ragged last batch included."""
+abcs_sense / abcs_ida calls; a ragged last batch included.  With the
+identity denoiser, every streamed frame is also compared with the FP64
+oracle."""
 import numpy as np
 import pytest
 import torch
 
+import oracle as O
 from paper_2001_09632_gb300 import abcs, synth
+from tests import gpu_util as G
 from paper_2001_09632_gb300.video import VideoPipeline
 
 pytestmark = pytest.mark.gpu
@@ -39,5 +43,12 @@ def test_overlapped_equals_sequential(den):
             assert abcs.abcs_sync_status(h) == 0
             assert torch.equal(x, a[f0:f0 + n])
         abcs.abcs_destroy(h)
+        if den == abcs.DEN_NONE:
+            # with the identity denoiser every streamed frame is linear in its
+            # measurements: each against the FP64 oracle's sensing and IDA
+            for f in range(F):
+                ref = O.sense(frames[f].numpy(), B, 0.25, O.DD)
+                xr, _ = O.ida(ref["y"], ref["counts"], vp.Hc, vp.Wc, B, 4, DF=2.0, denoiser=None)
+                G.check_pixels(a[f].cpu().numpy(), xr, 1e-5, f)
     finally:
         vp.close()

@@ -51,3 +51,84 @@ def test_denoises_a_noisy_step():
     noisy = clean + rng.normal(0, 20, clean.shape)
     out = O.bm3d_ht(noisy, 20.0)
     assert np.mean((out - clean) ** 2) < 0.5 * np.mean((noisy - clean) ** 2)
+
+
+def _scene(seed=0, H=80, W=80):
+    """iid uniform noise: two unrelated 8x8 patches differ by d ~ 2 * 255^2 / 12
+    ~ 10800 on average, far above both thresholds, so only planted patches match."""
+    return np.random.default_rng(seed).uniform(0, 255, (H, W))
+
+
+def _plant(r, y, x, P):
+    r[y:y + 8, x:x + 8] = P
+
+
+def test_block_matching_window_threshold_ties_and_power_of_two():
+    """Hand-built group for the reference at (30, 30): copies of its patch
+    planted at known offsets and known distances d = ||P_ref - P||^2 / 64.
+      B (11, 49): +1 everywhere, d = 1, offset (-19, +19), inside the window
+      A (49, 30): +1 everywhere, d = 1, offset (+19, 0), inside, ties with B
+      C (30, 50): exact copy, d = 0, offset (0, +20), outside the window
+      E (40, 12): d = 2501 (one pixel carries the extra 64), offset (+10, -18)
+    sigma <= 40 (tau 2500): matches B, A -> 3 candidates -> a group of 2, and
+    of the tie the lower row (B) comes first; sigma > 40 (tau 5000): B, A, E
+    -> 4 -> the reference, B, A, E."""
+    r = _scene(0)
+    P = r[30:38, 30:38].copy()
+    _plant(r, 11, 49, P + 1.0)
+    _plant(r, 49, 30, P + 1.0)
+    _plant(r, 30, 50, P)
+    Q = P + 50.0
+    Q[3, 4] = P[3, 4] + math.sqrt(2564.0)       # 63 * 2500 + 2564 = 64 * 2501
+    _plant(r, 40, 12, Q)
+    for s in (5.0, 40.0):
+        g = O.bm3d_group(r, 30, 30, s)
+        assert [(yy, xx) for _, yy, xx in g] == [(30, 30), (11, 49)], s
+        assert g[1][0] == pytest.approx(1.0, abs=1e-9)
+    g = O.bm3d_group(r, 30, 30, 40.5)
+    assert [(yy, xx) for _, yy, xx in g] == [(30, 30), (11, 49), (49, 30), (40, 12)]
+    assert [d for d, _, _ in g] == pytest.approx([0.0, 1.0, 1.0, 2501.0], abs=1e-9)
+
+
+def test_block_matching_threshold_is_inclusive():
+    """d = 2500 exactly joins at sigma = 40 (tau 2500, d <= tau)."""
+    r = _scene(1)
+    P = r[30:38, 30:38].copy()
+    _plant(r, 12, 14, P + 50.0)                  # d = 50^2, offset (-18, -16)
+    _plant(r, 45, 44, P + 2.0)                   # d = 4, offset (+15, +14)
+    g = O.bm3d_group(r, 30, 30, 40.0)
+    assert [(yy, xx) for _, yy, xx in g] == [(30, 30), (45, 44)]       # 3 candidates -> 2
+    assert O.bm3d_group(r, 30, 30, 40.0, N2=16)[1][0] == pytest.approx(4.0, abs=1e-9)
+    _plant(r, 45, 44, _scene(9)[0:8, 0:8])       # remove the close match: the reference and d = 2500 remain
+    g = O.bm3d_group(r, 30, 30, 40.0)
+    assert [(yy, xx) for _, yy, xx in g] == [(30, 30), (12, 14)]
+    assert g[1][0] == pytest.approx(2500.0, abs=1e-9)
+
+
+def test_block_matching_keeps_the_sixteen_closest():
+    """24 planted copies on a 9-pixel grid around the reference at (40, 40),
+    at distances d = delta^2 for distinct delta: the group is the reference and
+    the 15 closest (N2 = 16), in order of distance."""
+    r = _scene(2, 96, 96)
+    P = r[40:48, 40:48].copy()
+    deltas = np.random.default_rng(5).permutation(np.arange(1, 25)).astype(float)
+    pos = [(40 + 9 * i - 18, 40 + 9 * j - 18) for i in range(5) for j in range(5) if (i, j) != (2, 2)]
+    for (yy, xx), dl in zip(pos, deltas):
+        _plant(r, yy, xx, P + dl)
+    g = O.bm3d_group(r, 40, 40, 20.0)
+    assert len(g) == 16
+    order = np.argsort(deltas)[:15]
+    assert [(yy, xx) for _, yy, xx in g[1:]] == [pos[i] for i in order]
+    assert [d for d, _, _ in g[1:]] == pytest.approx(list(np.sort(deltas)[:15] ** 2), abs=1e-9)
+
+
+def test_block_matching_clips_the_window_at_the_border():
+    """Reference at (0, 0): the window covers rows and columns 0..19 only; a
+    copy at (19, 19) (inside) matches, one at (0, 20) does not."""
+    r = _scene(3, 48, 48)
+    P = r[0:8, 0:8].copy()
+    _plant(r, 19, 19, P + 3.0)
+    _plant(r, 0, 20, P)
+    g = O.bm3d_group(r, 0, 0, 10.0)
+    assert [(yy, xx) for _, yy, xx in g] == [(0, 0), (19, 19)]
+

@@ -53,3 +53,48 @@ def test_first_iteration_equals_ida():
     x1, s1, _ = O.damp(out["y"], out["counts"], 32, 48, 16, 1, b, DF=1.0, denoiser=den)
     xi, si = O.ida(out["y"], out["counts"], 32, 48, 16, 1, DF=2.0, denoiser=den)
     assert np.array_equal(x1, xi) and s1 == si
+
+
+def test_alpha_uses_the_divergence_at_the_previous_input():
+    """Eqs. 24 / 27: alpha^t = div D_{sigma^{t-1}}(r^{t-1}) / (M D_F).  With a
+    soft threshold at tau = sigma / 2 the divergence is #{|r_i| > tau}, which
+    changes from iterate to iterate; the denoiser logs its inputs, so the
+    expected alpha^t is counted by hand on r^{t-1}.  The Monte-Carlo
+    estimate differs from the exact count only for entries within eps of
+    tau (slack).  The counts of neighbouring iterates differ by more than
+    the slacks, so taking the divergence at r^t or at r^{t-2} fails."""
+    img = synth.gen_image(48, 64, 12)
+    out = O.sense(img, 16, 0.3, O.BBV)
+    b = _rademacher((48, 64), 13)
+    M = len(out["y"])
+    log = []
+
+    def soft(v, s):
+        log.append((np.array(v, copy=True), s))
+        return np.sign(v) * np.maximum(np.abs(v) - 0.5 * s, 0.0)
+
+    iters, DF = 6, 2.0
+    _, sigmas, alphas = O.damp(out["y"], out["counts"], 48, 64, 16, iters, b, DF=DF, denoiser=soft)
+    assert len(log) == 2 * iters - 1                       # D(r^t), then D(r^t + eps b) except at the end
+    r = [log[2 * t][0] for t in range(iters)]
+    for t in range(iters):
+        assert log[2 * t][1] == sigmas[t]
+        if t + 1 < iters:                                  # the probe call: same sigma, r^t + eps b
+            eps = 1e-3 * np.max(np.abs(r[t]))
+            assert log[2 * t + 1][1] == sigmas[t]
+            assert np.allclose(log[2 * t + 1][0], r[t] + eps * b, rtol=0, atol=1e-12 * np.max(np.abs(r[t])))
+
+    def count(t):
+        return int(np.sum(np.abs(r[t]) > 0.5 * sigmas[t]))
+
+    def slack(t):
+        eps = 1e-3 * np.max(np.abs(r[t]))
+        return int(np.sum(np.abs(np.abs(r[t]) - 0.5 * sigmas[t]) <= eps))
+
+    assert alphas[0] == 0.0
+    discriminating = 0
+    for t in range(1, iters):
+        assert abs(alphas[t] * M * DF - count(t - 1)) <= slack(t - 1) + 1e-6, t
+        if abs(count(t) - count(t - 1)) > slack(t) + slack(t - 1):
+            discriminating += 1
+    assert discriminating >= 3
