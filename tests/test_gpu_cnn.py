@@ -121,6 +121,21 @@ FULL_WINDOWS = {
 }
 
 
+def _quantised_denoise(params, r, sigma, density):
+    """The oracle's layers (cnn_input, conv3x3, ReLU) composed with the
+    storage roundings of the GPU path: the input planes and the first
+    layer's weights in FP16, every hidden activation stored in BF16 (the
+    mid-layer weights are already BF16 in `params`).  Only the FP32
+    accumulation order then separates it from the GPU's output."""
+    q = lambda a, dt: torch.tensor(a).to(dt).to(torch.float64).numpy()
+    h = q(O.cnn_input(r, sigma, density), torch.float16)
+    for l, (w, b) in enumerate(params):
+        h = O.conv3x3(h, q(w, torch.float16) if l == 0 else w, b)
+        if l < len(params) - 1:
+            h = q(np.maximum(h, 0.0), torch.bfloat16)
+    return np.asarray(r, dtype=np.float64) - 255.0 * h[0]
+
+
 @pytest.mark.parametrize("n,H,W", list(FULL_WINDOWS))
 def test_cnn_forward_parity_full_size(handle, n, H, W):
     """The learned denoiser on full-size images in the launch configuration
@@ -128,7 +143,12 @@ def test_cnn_forward_parity_full_size(handle, n, H, W):
     receptive field of the 8 conv3x3 layers is +-8 pixels, so the oracle run
     on the window plus an 8-pixel halo (clipped at the image border, where
     the zero padding is the network's own) gives the window's outputs
-    exactly."""
+    exactly.  Against the FP64 oracle: 2e-2 over all windows (the bar of the
+    small-image test) and 4e-2 per window (a flat 10x10 window, whose network
+    output is half the usual size, measures 2.5% from BF16 storage alone);
+    against the same layers with the GPU's storage roundings: 1e-2 per
+    window.  A wrong halo or tile offset puts whole rows or columns of a
+    window far off and fails both."""
     params = _params(13)
     ref_p = _bf16_mid(params)
     _, packed = _pack(handle, params)
@@ -143,16 +163,25 @@ def test_cnn_forward_parity_full_size(handle, n, H, W):
     got = d_out.cpu().numpy()
     assert np.all(np.isfinite(got))
     r32 = d_in.cpu().numpy().astype(float)
+    d_all, n_all = [], []
     for (k, y0, x0, h, w) in FULL_WINDOWS[(n, H, W)]:
         ya, yb = max(0, y0 - 8), min(H, y0 + h + 8)
         xa, xb = max(0, x0 - 8), min(W, x0 + w + 8)
-        ref = O.cnn_denoise(ref_p, r32[k, ya:yb, xa:xb], float(np.float32(sig[k])),
-                            dens[k, ya:yb, xa:xb].astype(float))[y0 - ya:y0 - ya + h, x0 - xa:x0 - xa + w]
+        sl = (slice(y0 - ya, y0 - ya + h), slice(x0 - xa, x0 - xa + w))
+        rc, dc, sg = r32[k, ya:yb, xa:xb], dens[k, ya:yb, xa:xb].astype(float), float(np.float32(sig[k]))
+        ref = O.cnn_denoise(ref_p, rc, sg, dc)[sl]
+        emu = _quantised_denoise(ref_p, rc, sg, dc)[sl]
         rin = r32[k, y0:y0 + h, x0:x0 + w]
-        n_ref = (rin - ref) / 255.0
-        n_got = (rin - got[k, y0:y0 + h, x0:x0 + w]) / 255.0
+        g = got[k, y0:y0 + h, x0:x0 + w]
+        n_ref, n_emu, n_got = (rin - ref) / 255.0, (rin - emu) / 255.0, (rin - g) / 255.0
         err = np.linalg.norm(n_got - n_ref) / np.linalg.norm(n_ref)
-        assert err <= 2e-2, ((k, y0, x0), err)
+        assert err <= 4e-2, ((k, y0, x0), err)
+        err_q = np.linalg.norm(n_got - n_emu) / np.linalg.norm(n_emu)
+        assert err_q <= 1e-2, ((k, y0, x0), err_q)
+        d_all.append((n_got - n_ref).ravel())
+        n_all.append(n_ref.ravel())
+    err = np.linalg.norm(np.concatenate(d_all)) / np.linalg.norm(np.concatenate(n_all))
+    assert err <= 2e-2, err
 
 
 def test_cnn_gradient_parity(handle):
