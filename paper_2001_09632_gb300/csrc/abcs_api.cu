@@ -155,6 +155,13 @@ abcs_status ensure_ws(abcs_handle* h, size_t bytes) {
     return ABCS_OK;
 }
 
+// ABCS_SENSE_TC=mma (read at each call) selects the per-block mma.sync
+// sensing kernel instead of the tcgen05 one for the tensor-core precisions.
+bool sense_mma_forced() {
+    const char* v = getenv("ABCS_SENSE_TC");
+    return v && strcmp(v, "mma") == 0;
+}
+
 template <typename T>
 T* at(abcs_handle* h, size_t off) {
     return reinterpret_cast<T*>(static_cast<char*>(h->ws) + off);
@@ -189,6 +196,8 @@ abcs_status abcs_create(abcs_handle** out) {
     ABCS_CUDA(upload_tables_tc(), "upload tables");
     ABCS_CUDA(setup_bm3d_tables(), "upload tables");
     ABCS_CUDA(setup_tc_fragments(), "tensor-core fragment setup");
+    ABCS_CUDA(upload_tables_su(), "upload tables");
+    ABCS_CUDA(setup_sense_umma(), "tensor-memory sensing table setup");
     abcs_handle* h = new abcs_handle;
     h->device = dev;
     if (cudaMalloc(&h->status, 256) != cudaSuccess) {
@@ -300,6 +309,8 @@ abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int
     }
     if (precision == ABCS_FP32)
         ABCS_CUDA(launch_sense_pack(a, s), "sense_pack launch");
+    else if (sense_umma_usable(a) && !sense_mma_forced())
+        ABCS_CUDA(launch_sense_umma(a, s), "sense_umma launch");
     else
         ABCS_CUDA(launch_sense_tc(a, s), "sense_tc launch");
     return ABCS_OK;

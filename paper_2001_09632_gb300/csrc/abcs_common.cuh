@@ -68,7 +68,9 @@ cudaError_t upload_tables_pilot();
 cudaError_t upload_tables_dct();
 cudaError_t upload_tables_ida();
 cudaError_t upload_tables_tc();
+cudaError_t upload_tables_su();
 cudaError_t setup_tc_fragments();   // after upload_tables_tc(), per device
+cudaError_t setup_sense_umma();     // after upload_tables_su(), per device
 
 // zigzag rank of (u, v) in a B x B block, JPEG orientation: diagonal s = u+v;
 // odd s runs with u increasing, even s with u decreasing.
@@ -195,6 +197,9 @@ struct ReconArgs {
 cudaError_t launch_reconstruct(const ReconArgs& a, cudaStream_t s);
 // tensor-core paths (B = 16; a.precision selects FP16x2 / BF16x2 / BF16)
 cudaError_t launch_sense_tc(const SenseArgs& a, cudaStream_t s);
+// tcgen05 sensing (k_sense_umma.cu): B = 16, 16-byte aligned images and rows
+bool sense_umma_usable(const SenseArgs& a);
+cudaError_t launch_sense_umma(const SenseArgs& a, cudaStream_t s);
 cudaError_t launch_recon_tc(const ReconArgs& a, cudaStream_t s);
 
 struct IdaLinArgs {

@@ -26,10 +26,16 @@ def _oracle(imgs, B, r, variant):
     return outs, counts, y
 
 
+@pytest.mark.parametrize("kernel", ["umma", "mma"])
 @pytest.mark.parametrize("prec", [abcs.TC_FP16X2, abcs.TC_BF16X2, abcs.TC_BF16])
 @pytest.mark.parametrize("variant", [O.ZZ, O.BBV, O.DD])
-@pytest.mark.parametrize("shape", [(2, 96, 336), (1, 64, 1040), (3, 48, 48), (5, 160, 208)])
-def test_tc_sense_and_reconstruct(handle, prec, variant, shape):
+@pytest.mark.parametrize("shape", [(2, 96, 336), (1, 64, 1040), (3, 48, 48), (5, 160, 208), (2, 80, 337)])
+def test_tc_sense_and_reconstruct(handle, monkeypatch, kernel, prec, variant, shape):
+    """Both sensing kernels: the tcgen05 one (the default for 16-byte aligned
+    rows; a row of 337 bytes falls back to the other) and the per-block
+    mma.sync one (ABCS_SENSE_TC=mma)."""
+    if kernel == "mma":
+        monkeypatch.setenv("ABCS_SENSE_TC", "mma")
     n, H, W = shape
     B, r = 16, 0.3
     imgs = np.stack([synth.gen_image(H, W, 300 + k) for k in range(n)])
@@ -106,6 +112,30 @@ def test_precision_table(handle, capsys):
         print("\n" + "\n".join(lines))
 
 
+@pytest.mark.parametrize("variant,r", [(O.BBV, 0.3), (O.DD, 0.3), (O.BBV, 0.5), (O.DD, 0.1)])
+def test_sense_kernels_agree_on_the_full_batch(handle, monkeypatch, variant, r):
+    """64 x 512x512 (the batched workload): the tcgen05 sensing kernel and
+    the per-block mma.sync kernel give the same counts and offsets, and
+    coefficients within the FP32 bar of each other and of the oracle on
+    sampled images (r = 0.5 BBV puts ranks >= 128 in every tile)."""
+    B, n = 16, 64
+    imgs = synth.gen_batch(n, 512, 512, 4242)
+    got_u = G.sense(handle, imgs, B, r, variant, precision=abcs.TC_FP16X2)
+    monkeypatch.setenv("ABCS_SENSE_TC", "mma")
+    got_m = G.sense(handle, imgs, B, r, variant, precision=abcs.TC_FP16X2)
+    monkeypatch.delenv("ABCS_SENSE_TC")
+    assert got_u["bits"] == 0 and got_m["bits"] == 0
+    assert np.array_equal(got_u["counts"], got_m["counts"])
+    assert np.array_equal(got_u["offsets"], got_m["offsets"])
+    G.check_coeffs(got_u["y"], got_m["y"], got_m["counts"], got_m["offsets"], 1e-5)
+    nB = got_u["plan"]["n_blocks"]
+    off = got_u["offsets"]
+    for k in (0, 33, 63):
+        ref = O.sense(imgs[k], B, r, variant)
+        assert np.array_equal(got_u["counts"][k * nB:(k + 1) * nB], ref["counts"])
+        G.check_coeffs(got_u["y"][off[k * nB]:off[(k + 1) * nB]], ref["y"], ref["counts"], ref["offsets"], 1e-5, k)
+
+
 def test_sense_full_batch_counts_and_samples(handle):
     """The bench workload (64 x 512x512, BBV r = 0.3, FP16x2) in the launch
     configuration the bench times: pilot values and counts of every image
@@ -142,9 +172,10 @@ def test_tc_rejects_other_block_sizes(handle):
     assert e.value.status == 2
 
 
+@pytest.mark.parametrize("kernel", ["umma", "mma"])
 @pytest.mark.parametrize("prec", [abcs.TC_FP16X2, abcs.TC_BF16X2, abcs.TC_BF16])
 @pytest.mark.parametrize("variant,r", [(O.ZZ, 1.0), (O.DD, 1.0), (O.ZZ, 0.01), (O.DD, 0.01), (O.BBV, 0.01)])
-def test_tc_extreme_subrates(handle, monkeypatch, prec, variant, r):
+def test_tc_extreme_subrates(handle, monkeypatch, kernel, prec, variant, r):
     """Every coefficient measured (r = 1: full staging buffers in sense and
     reconstruct; for the tensor-memory kernel a worst-case span per tile and,
     on 10 x 512^2 = 80 tiles, two tiles per CTA through its ring) and almost
@@ -154,7 +185,10 @@ def test_tc_extreme_subrates(handle, monkeypatch, prec, variant, r):
     n, H, W, B = 10, 512, 512, 16
     imgs = synth.gen_batch(n, H, W, 2024)
     outs, c_ref, y_ref = _oracle(imgs, B, r, variant)
+    if kernel == "mma":
+        monkeypatch.setenv("ABCS_SENSE_TC", "mma")
     got = G.sense(handle, imgs, B, r, variant, precision=prec)
+    monkeypatch.delenv("ABCS_SENSE_TC", raising=False)
     assert got["bits"] == 0
     assert np.array_equal(got["counts"], c_ref)
     G.check_coeffs(got["y"], y_ref, c_ref, np.concatenate([[0], np.cumsum(c_ref)]), BOUND[prec])
