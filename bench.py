@@ -51,15 +51,18 @@ RECON_TRAFFIC = {"fp16x2": 28502016}
 # the call a few times and times the last run with CUDA events.  They are
 # the programs the ncu summaries under profiles/ capture.
 # ---------------------------------------------------------------------------
-def _timed(fn):
+def _timed(fn, reps=10):
+    """Mean ms per call of `reps` calls queued back to back (the host runs
+    ahead of the device, so launch overheads between calls are hidden)."""
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
-    fn()
+    for _ in range(reps):
+        fn()
     e1.record()
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1)
+    return e0.elapsed_time(e1) / reps
 
 
 def case_bm3d(h):
@@ -76,7 +79,7 @@ def case_bm3d(h):
     run = lambda: abcs.abcs_denoise_bm3d(h, r, n, H, W, sig, 2.7, out)
     for _ in range(2):
         run()
-    return _timed(run)
+    return _timed(run, 1)
 
 
 def case_thi(h):
@@ -116,7 +119,7 @@ def case_damp(h):
     x = torch.empty((n, H, W), device="cuda")
     run = lambda: abcs.abcs_damp(h, c, o, y, n, H, W, B, 3, 2.0, abcs.DEN_TIDCT, 2.3, None, probe, x)
     run()
-    return _timed(run)
+    return _timed(run, 1)
 
 
 def _sense_case(h, variant, r, prec, seed=1234):
@@ -632,6 +635,109 @@ def thi_correlation(h, n=64, H=512, W=512, B=16, reps=5):
     out["thi_Mpx_per_s"] = n * H * W / (ms * 1e-3) / 1e6
     out["paper_table2_512_context"] = {"dd": [0.741, 0.818, 0.818, 0.807, 0.852],
                                        "bbv": [0.719, 0.784, 0.795, 0.786, 0.802]}
+    return out
+
+
+def subrate_sweep(h, prec, d_img, flush, hbm_peak, steps=30):
+    """The batched workload at every subrate and both adaptive variants
+    (64 x 512x512, B = 16, BBV and DD, r = 0.1 .. 0.5; the bench default
+    precision): abcs_sense and abcs_reconstruct timed with CUDA events on
+    the launching stream, L2 flushed before each step; Mpixel/s and the
+    step's HBM fraction against the algorithmic bytes 5 + 8 M/N per pixel
+    (uint8 image read, packed coefficients written and read back, counts
+    and offsets, FP32 image written)."""
+    import torch
+    from paper_2001_09632_gb300 import abcs
+    stream = torch.cuda.current_stream()
+    s = stream.cuda_stream
+    n = N_IMG
+    nB = (H // B) * (W // B)
+    cap = n * abcs.abcs_plan(H, W, B, 0.5, abcs.DD)["M"]
+    counts = torch.empty(n * nB, dtype=torch.int32, device="cuda")
+    offsets = torch.empty(n * nB + 1, dtype=torch.int64, device="cuda")
+    coeffs = torch.empty(cap, dtype=torch.float32, device="cuda")
+    rec = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
+    out = {}
+    for name, variant in (("bbv", abcs.BBV), ("dd", abcs.DD)):
+        for r in (0.1, 0.2, 0.3, 0.4, 0.5):
+            def sense():
+                abcs.abcs_sense(h, d_img, n, H, W, W, H * W, B, r, variant, prec, counts, offsets, coeffs, cap,
+                                None, s)
+
+            def recon():
+                abcs.abcs_reconstruct(h, counts, offsets, coeffs, n, H, W, B, prec, rec, None, s)
+            for _ in range(3):
+                sense()
+                recon()
+            ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+            for e0, e1, e2 in ev:
+                flush.fill_(1)
+                e0.record(stream)
+                sense()
+                e1.record(stream)
+                recon()
+                e2.record(stream)
+            torch.cuda.synchronize()
+            assert abcs.abcs_sync_status(h, s) == 0
+            sm = statistics.median(e0.elapsed_time(e1) for e0, e1, _ in ev)
+            rm = statistics.median(e1.elapsed_time(e2) for _, e1, e2 in ev)
+            total = int(offsets[-1].item())
+            px = n * nB * B * B
+            step_bytes = 2 * px + 8 * total + 24 * n * nB + 4 * px   # image, y twice, counts+offsets twice, FP32 out
+            out[f"{name}_r{r}"] = {"sense_ms": sm, "reconstruct_ms": rm,
+                                   "Mpixel_per_s": px / ((sm + rm) * 1e-3) / 1e6,
+                                   "measured_fraction": total / px,
+                                   "step_frac_hbm": step_bytes / ((sm + rm) * 1e-3) / 1e9 / hbm_peak}
+    return out
+
+
+def single_image_latency(h, iters=10):
+    """One 256x256 image (the single-image configuration: B = 16, BBV,
+    r = 0.3): abcs_sense + abcs_reconstruct + abcs_ida (10 plain TI-DCT
+    iterations) captured once into a CUDA graph and replayed; the median
+    latency of a replay (image already on the device)."""
+    import torch
+    from paper_2001_09632_gb300 import abcs, synth
+    H1 = W1 = 256
+    plan = abcs.abcs_plan(H1, W1, B, SUBRATE, abcs.BBV)
+    nB = plan["n_blocks"]
+    d_img = torch.from_numpy(synth.gen_image(H1, W1, 77)[None]).cuda()
+    counts = torch.empty(nB, dtype=torch.int32, device="cuda")
+    offsets = torch.empty(nB + 1, dtype=torch.int64, device="cuda")
+    coeffs = torch.empty(plan["M"], dtype=torch.float32, device="cuda")
+    rec = torch.empty((1, H1, W1), dtype=torch.float32, device="cuda")
+    x = torch.empty((1, H1, W1), dtype=torch.float32, device="cuda")
+    out = {}
+    for prec_name, prec in (("fp32", abcs.FP32), ("fp16x2", abcs.TC_FP16X2)):
+        side = torch.cuda.Stream()
+
+        def run(st):
+            abcs.abcs_sense(h, d_img, 1, H1, W1, W1, H1 * W1, B, SUBRATE, abcs.BBV, prec, counts, offsets, coeffs,
+                            plan["M"], None, st)
+            abcs.abcs_reconstruct(h, counts, offsets, coeffs, 1, H1, W1, B, prec, rec, None, st)
+            abcs.abcs_ida(h, counts, offsets, coeffs, 1, H1, W1, B, iters, DF, abcs.DEN_TIDCT, LAMBDA, None, x,
+                          None, st)
+        with torch.cuda.stream(side):
+            for _ in range(3):                   # workspace grown, kernels loaded, before the capture
+                run(side.cuda_stream)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            run(side.cuda_stream)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(20):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        assert abcs.abcs_sync_status(h) == 0
+        out[prec_name] = {"ms_median": statistics.median(ts), "ms_min": min(ts)}
+    out["workload"] = "1 x 256x256, B=16, BBV r 0.3: sense + IDCT + 10 plain IDA iterations (TI-DCT), CUDA graph replay"
     return out
 
 
