@@ -5,9 +5,9 @@
 // D[u_k][r] D[v_k][c], Eq. 1 and the zigzag order of Sec. IV), block b's
 // rank-k measurement (a row of Eq. 26's A applied to the block) is
 //   y_b[k] = sum_p phi_k[p] x_b[p].
-// For a tile of NT = 32 blocks and the ranks of one half h (k = 128 h + m):
+// For a tile of NT = 64 blocks and the ranks of one half h (k = 128 h + m):
 //   Y_h[m][n] = sum_p 16 phi_{128 h + m}[p] x_n[p] / 16
-//   (M = 128 ranks, N = 32 blocks, K = 256 pixels)
+//   (M = 128 ranks, N = 64 blocks, K = 256 pixels)
 // The pixels (uint8) are exact in FP16 and BF16, so only the constant
 // operand is split: 16 phi = hi + lo (hi + lo = 16 phi to about 22 bits in
 // FP16x2 / 16 bits in BF16x2, one BF16 word for plain BF16), and each half
@@ -18,32 +18,35 @@
 // Tensor memory (512 columns of 32 bits, 128 lanes):
 //   [0, 128)    A of half 0, hi words (lane m = rank m, column c = pixels 2c, 2c + 1)
 //   [128, 256)  A of half 0, lo words
-//   [256, 384)  A of half 1, hi words (ranks 128 .. 255)
-//   [384, 512)  two accumulators of 64 columns: half 0 (32 blocks) then half 1
-// The lo words of half 1 are the shared-memory A operand of its second
-// product.  Half 1 is computed only for tiles whose largest count exceeds
-// 128 (most tiles stop at rank 127 at subrates up to 0.3).
+//   [256, 384)  accumulator of MMA issuer 0: half 0 (64 blocks), then half 1
+//   [384, 512)  accumulator of MMA issuer 1
+// Half 1's A (ranks 128 .. 255, hi and lo) is a shared-memory operand.
+// Half 1 is computed only for tiles whose largest count exceeds 128 (a
+// third of the tiles at subrate 0.3).
 //
-// Roles (10 warps, one CTA per SM, tiles c, c + G, c + 2G, ...):
-//   warp 0      tensor-memory allocation; lane 0 loads the operand table
-//               and issues the MMAs
-//   warp 1      producer: pixel rows of a tile into a ring of raw slots by
-//               bulk copies (one per pixel row of each run of consecutive
-//               blocks in a block row); after the wait for the pilot kernel,
-//               each tile's counts, global offsets and largest count
-//   warps 2-5   converters: raw bytes -> FP16 / BF16 K-major B operand
-//               (lane = block, warp = pixel rows), one 16-byte store per
-//               8 pixels, no bank conflicts
-//   warps 6-9   epilogue: warp w reads lanes 32 (w % 4) .. (32 ranks) of
-//               the tile's 32 columns (blocks) and stores rank k of block n
-//               to y[offset_n + k] when k < m_n (a warp store covers 32
-//               consecutive coefficients of one block); it also writes the
-//               global offsets
-// The pixel staging and the half-0 products of the first tiles need no
+// A single thread issues one tcgen05.mma about every 50 cycles whatever N
+// is, while an M = 128, N = 64, K = 16 product takes the tensor pipe 32
+// cycles, so two issuing warps take alternate tiles (each with its own B
+// stage and accumulator) and keep the pipe busy.
+//
+// Roles (19 warps, one CTA per SM, tiles c, c + G, c + 2G, ...):
+//   warps 0, 1  MMA issuers (lane 0); warp 0 also allocates tensor memory
+//               and loads the operand table (bulk copies)
+//   warp 2      metadata, up to four tiles ahead: counts, global offsets
+//               (image-local offset + image base) and largest count
+//   warps 3-10  converters: 16-byte global loads of pixel rows one tile
+//               ahead (a warp reads 512 contiguous bytes of a row), FP16 /
+//               BF16 pairs into the tile's K-major B stage (conflict free)
+//   warps 11-18 epilogue: warp w reads lanes 32 (w % 4) .. (32 ranks) of
+//               32 of the tile's columns (blocks) and stores rank k of block
+//               n to y[offset_n + k] when k < m_n (a warp store covers 32
+//               consecutive coefficients of one block), predicated, without
+//               branches; it also writes the global offsets
+// The pixel loads and the half-0 products of the first tiles need no
 // allocation result, so they run while the pilot kernel finishes (PDL).
 // Every wait is bounded: on expiry ABCS_DEV_TIMEOUT is set and an abort flag
-// ends every role; copies and MMAs in flight are drained before the CTA
-// frees its tensor memory.
+// ends every role; MMAs in flight are drained before the CTA frees its
+// tensor memory.
 #include <cstdlib>
 #include <cstring>
 
@@ -99,45 +102,45 @@ ABCS_D void su_split(double a, double b, uint32_t& hi, uint32_t& lo) {
     lo = su_pk<P>((float)(a - ha), (float)(b - hb));
 }
 
-constexpr int NT = 32;                 // blocks per tile (the MMA's N)
-constexpr int SU_R = 4;                // raw pixel slots
-constexpr int SU_S = 3;                // B operand stages
+constexpr int NT = 64;                 // blocks per tile (the MMA's N)
 constexpr int SU_I = 4;                // metadata slots
 constexpr float SU_SCALE = 16.f;
 constexpr uint32_t SU_PART = 65536;    // bytes of one operand-table part
 constexpr uint32_t SU_STAGE = NT * 512;   // 32 K chunks of NT rows x 16 bytes
-constexpr uint32_t SU_RAW = NT * 256;     // 16 pixel rows of NT blocks x 16 bytes
+constexpr int SU_CONV = 8;             // converter warps
+constexpr int SU_EPI = 8;              // epilogue warps (two per tensor-memory lane quarter)
+// warp roles
+constexpr int W_MMA0 = 0, W_MMA1 = 1, W_META = 2, W_CONV = 3, W_EPI = W_CONV + SU_CONV;
+constexpr int SU_THREADS = 32 * (W_EPI + SU_EPI);
 
 struct SuInfo {
-    int64_t off[NT];   // global offset of the block's first coefficient
-    int m[NT];         // the block's count (0 past the batch or when flagged)
+    uint32_t pk[NT];   // per block: offset relative to base (low 16 bits) | count << 16
+    int64_t base;      // global offset of the tile's first block
     int kmax;          // largest count of the tile
     int pad;
 };
+static_assert(sizeof(SuInfo) % 16 == 0, "metadata slots stay 16-byte aligned");
 
-constexpr uint32_t SU_OFF_A1LO = 0;                               // also staging of the table parts
-constexpr uint32_t SU_OFF_B = SU_OFF_A1LO + SU_PART;
-constexpr uint32_t SU_OFF_RAW = SU_OFF_B + SU_S * SU_STAGE;
-constexpr uint32_t SU_OFF_INFO = SU_OFF_RAW + SU_R * SU_RAW;
+constexpr uint32_t SU_OFF_A1HI = 0;                               // also staging of the table parts
+constexpr uint32_t SU_OFF_A1LO = SU_PART;
+constexpr uint32_t SU_OFF_B = 2 * SU_PART;                        // stage i belongs to MMA issuer i
+constexpr uint32_t SU_OFF_INFO = SU_OFF_B + 2 * SU_STAGE;
 constexpr uint32_t SU_OFF_BAR = SU_OFF_INFO + SU_I * sizeof(SuInfo);
 // mbarriers
-constexpr uint32_t SU_RAWF = 0, SU_RAWE = SU_RAWF + 8 * SU_R, SU_BF = SU_RAWE + 8 * SU_R, SU_BE = SU_BF + 8 * SU_S,
-                   SU_ACCF = SU_BE + 8 * SU_S, SU_ACCE = SU_ACCF + 16, SU_INF = SU_ACCE + 16,
-                   SU_INE = SU_INF + 8 * SU_I, SU_TABF = SU_INE + 8 * SU_I, SU_TABE = SU_TABF + 8,
-                   SU_DRAIN = SU_TABE + 8, SU_NBAR = SU_DRAIN + 8;
+constexpr uint32_t SU_BF = 0, SU_BE = 16, SU_ACCF = 32, SU_ACCE = 48, SU_INF = 64, SU_INE = SU_INF + 8 * SU_I,
+                   SU_TABF = SU_INE + 8 * SU_I, SU_TABE = SU_TABF + 8, SU_TABR = SU_TABE + 8, SU_DRAIN = SU_TABR + 8,
+                   SU_NBAR = SU_DRAIN + 16;
 constexpr uint32_t SU_OFF_MISC = SU_OFF_BAR + SU_NBAR;            // tensor-memory address, abort flag
 constexpr size_t SU_SMEM = SU_OFF_MISC + 16;
-constexpr int SU_THREADS = 10 * 32;
-static_assert(SU_OFF_B % 1024 == 0 && SU_OFF_RAW % 16 == 0 && SU_OFF_INFO % 16 == 0 && SU_OFF_BAR % 8 == 0,
-              "shared layout");
+static_assert(SU_OFF_B % 1024 == 0 && SU_OFF_INFO % 16 == 0 && SU_OFF_BAR % 8 == 0, "shared layout");
 static_assert(SU_SMEM <= 232448, "shared memory of the tensor-memory sensing kernel");
 
 // Operand table per precision, four 64 KB parts of 16 phi (rows = ranks of
 // a half, K = pixels):
-//   parts 0, 1, 2: tensor-memory words of half 0 hi, half 0 lo, half 1 hi,
-//                  word [c][m] = (A[m][2c], A[m][2c + 1])
-//   part 3:        half 1 lo as its shared-memory K-major image,
-//                  byte 2048 kc + 16 m + 2 e = A[m][8 kc + e]
+//   parts 0, 1: tensor-memory words of half 0, hi and lo:
+//               word [c][m] = (A[m][2c], A[m][2c + 1])
+//   parts 2, 3: half 1 hi and lo as their shared-memory K-major images:
+//               byte 2048 kc + 16 m + 2 e = A[m][8 kc + e]
 __device__ __align__(16) uint32_t g_sphi[3][4][SU_PART / 4];
 
 template <int P>
@@ -157,8 +160,8 @@ ABCS_D void sphi_setup_p(int half, int m, int c) {
         t[0][c * 128 + m] = hi;
         t[1][c * 128 + m] = lo;
     } else {
-        t[2][c * 128 + m] = hi;
         // pixels 2c, 2c + 1: chunk kc = 2c / 8, word (2c % 8) / 2 of row m
+        t[2][(c >> 2) * 512 + m * 4 + (c & 3)] = hi;
         t[3][(c >> 2) * 512 + m * 4 + (c & 3)] = lo;
     }
 }
@@ -170,12 +173,33 @@ __global__ void sphi_setup_kernel() {     // grid (128 columns, 2 halves), block
     sphi_setup_p<kSPB1>(half, m, c);
 }
 
+// D (tensor memory) (+)= A (tensor memory) * B (shared-memory descriptor);
+// the accumulate flag is a compile-time constant
+template <int ACC>
+ABCS_D void mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "n"(ACC));
+}
+
 // D (tensor memory) (+)= A (shared-memory descriptor) * B (shared-memory descriptor)
-ABCS_D void umma_smem_a(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
+template <int ACC>
+ABCS_D void mma_sa(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+        "l"(adesc), "l"(bdesc), "r"(idesc), "n"(ACC));
+}
+
+// 16 consecutive columns of this warp's 32 lanes (thread i -> lane i)
+ABCS_D void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
 // two pixels (bytes 2 sel, 2 sel + 1 of w) as an operand pair; exact
@@ -216,6 +240,7 @@ __global__ void __launch_bounds__(SU_THREADS, 1) sense_umma_kernel(SenseArgs a, 
     const int64_t T = (ntot + NT - 1) / NT;
     const int my_n = blockIdx.x < T ? (int)((T - blockIdx.x + G - 1) / G) : 0;
     const ImgGeom& g = a.g;
+    auto tile_b0 = [&](int j) { return ((int64_t)blockIdx.x + (int64_t)j * G) * NT; };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
@@ -224,25 +249,20 @@ __global__ void __launch_bounds__(SU_THREADS, 1) sense_umma_kernel(SenseArgs a, 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (t == 32) {
-        for (int i = 0; i < SU_R; ++i) {
-            mbar_init(bar + SU_RAWF + 8 * i, 1);
-            mbar_init(bar + SU_RAWE + 8 * i, 4);
-        }
-        for (int i = 0; i < SU_S; ++i) {
-            mbar_init(bar + SU_BF + 8 * i, 4);
-            mbar_init(bar + SU_BE + 8 * i, 1);
-        }
         for (int i = 0; i < 2; ++i) {
+            mbar_init(bar + SU_BF + 8 * i, SU_CONV);
+            mbar_init(bar + SU_BE + 8 * i, 1);
             mbar_init(bar + SU_ACCF + 8 * i, 1);
-            mbar_init(bar + SU_ACCE + 8 * i, 4);
+            mbar_init(bar + SU_ACCE + 8 * i, SU_EPI);
+            mbar_init(bar + SU_DRAIN + 8 * i, 1);
         }
         for (int i = 0; i < SU_I; ++i) {
             mbar_init(bar + SU_INF + 8 * i, 1);
-            mbar_init(bar + SU_INE + 8 * i, 4);
+            mbar_init(bar + SU_INE + 8 * i, SU_EPI);
         }
         mbar_init(bar + SU_TABF, 1);
-        mbar_init(bar + SU_TABE, 4);
-        mbar_init(bar + SU_DRAIN, 1);
+        mbar_init(bar + SU_TABE, SU_EPI);
+        mbar_init(bar + SU_TABR, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         *abort_flag = 0;
     }
@@ -251,236 +271,260 @@ __global__ void __launch_bounds__(SU_THREADS, 1) sense_umma_kernel(SenseArgs a, 
     tc5_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0) {
-        // ---- operand table, then the MMA issuer
+    if (warp == W_MMA0 || warp == W_MMA1) {
+        // ---- operand table (issuer 0), then the MMA issuers: issuer i takes
+        // the tiles j = i mod 2 with B stage i and accumulator i
+        const int me = warp - W_MMA0;
         if (lane == 0) {
-            const uint32_t* tab = &g_sphi[su_pidx<P>()][0][0];
             bool alive = true;
-            // parts 0 .. 2 staged in the A1lo region and copied into tensor
-            // memory by the epilogue warps; part 3 lands there last
-            int ph = 0;
-            for (int part = 0; part < 4 && alive; ++part) {
-                if (!kSplit && (part == 1 || part == 3)) continue;
-                mbar_arrive_tx(bar + SU_TABF, SU_PART);
-                bulk_g2s(sb + SU_OFF_A1LO, tab + part * (SU_PART / 4), SU_PART, bar + SU_TABF);
-                if (!mbar_wait(bar + SU_TABF, ph & 1, abort_flag, a.status)) alive = false;
-                if (part != 3 && alive) {
-                    // the epilogue warps have copied this part into tensor memory
-                    if (!mbar_wait(bar + SU_TABE, ph & 1, abort_flag, a.status)) alive = false;
+            if (me == 0) {
+                const uint32_t* tab = &g_sphi[su_pidx<P>()][0][0];
+                // half 0 (parts 0, 1) staged in the half-1 regions and copied
+                // into tensor memory by the epilogue warps; then half 1
+                // (parts 2, 3) lands in its regions
+                const uint32_t n0 = kSplit ? 2 * SU_PART : SU_PART;
+                mbar_arrive_tx(bar + SU_TABF, n0);
+                bulk_g2s(sb + SU_OFF_A1HI, tab, SU_PART, bar + SU_TABF);
+                if (kSplit) bulk_g2s(sb + SU_OFF_A1LO, tab + SU_PART / 4, SU_PART, bar + SU_TABF);
+                alive = mbar_wait(bar + SU_TABF, 0, abort_flag, a.status) &&
+                        mbar_wait(bar + SU_TABE, 0, abort_flag, a.status);
+                if (alive) {
+                    mbar_arrive_tx(bar + SU_TABF, n0);
+                    bulk_g2s(sb + SU_OFF_A1HI, tab + 2 * (SU_PART / 4), SU_PART, bar + SU_TABF);
+                    if (kSplit) bulk_g2s(sb + SU_OFF_A1LO, tab + 3 * (SU_PART / 4), SU_PART, bar + SU_TABF);
+                    alive = mbar_wait(bar + SU_TABF, 1, abort_flag, a.status);
                 }
-                ++ph;
+                if (alive) mbar_arrive(bar + SU_TABR);
             }
+            // both issuers: half 0 in tensor memory (the epilogue's copies) and
+            // half 1 in shared memory are ready
+            if (alive && !mbar_wait(bar + SU_TABE, 0, abort_flag, a.status)) alive = false;
+            if (alive && !mbar_wait(bar + SU_TABR, 0, abort_flag, a.status)) alive = false;
             tc5_fence_after();
-            for (int j = 0; j < my_n && alive; ++j) {
-                const int acc = j & 1, st = j % SU_S, is = j % SU_I;
-                if (!mbar_wait(bar + SU_ACCE + 8 * acc, ((j >> 1) & 1) ^ 1, abort_flag, a.status)) break;
-                if (!mbar_wait(bar + SU_BF + 8 * st, (j / SU_S) & 1, abort_flag, a.status)) break;
+            const uint32_t d0 = tmem + 256 + 128 * me, d1 = d0 + 64;
+            const uint64_t bd0 = umma_desc(sb + SU_OFF_B + me * SU_STAGE, NT * 16, 128);
+            const uint64_t ah0 = umma_desc(sb + SU_OFF_A1HI, 2048, 128), al0 = umma_desc(sb + SU_OFF_A1LO, 2048, 128);
+            for (int j = me, u = 0; j < my_n && alive; j += 2, ++u) {
+                const int is = j % SU_I;
+                if (!mbar_wait(bar + SU_ACCE + 8 * me, (u & 1) ^ 1, abort_flag, a.status)) break;
+                if (!mbar_wait(bar + SU_BF + 8 * me, u & 1, abort_flag, a.status)) break;
                 tc5_fence_after();
-                const uint32_t d0 = tmem + 384 + 64 * acc, d1 = d0 + 32;
-                const uint32_t bst = sb + SU_OFF_B + st * SU_STAGE;
-#pragma unroll 4
-                for (int ks = 0; ks < 16; ++ks) {
-                    const uint64_t bd = umma_desc(bst + ks * 1024, 512, 128);
-                    umma_tmem_a(d0, tmem + 8 * ks, bd, IDESC, ks > 0 ? 1u : 0u);
-                    if constexpr (kSplit) umma_tmem_a(d0, tmem + 128 + 8 * ks, bd, IDESC, 1u);
+                // K step ks: pixel row ks = B chunks 2 ks, 2 ks + 1 (ks * 2 * NT * 16 bytes,
+                // i.e. ks * 2 * NT in the descriptor's 16-byte address units)
+                mma_ta<0>(d0, tmem, bd0, IDESC);
+                if constexpr (kSplit) mma_ta<1>(d0, tmem + 128, bd0, IDESC);
+#pragma unroll
+                for (int ks = 1; ks < 16; ++ks) {
+                    const uint64_t bd = bd0 + (uint64_t)(ks * 2 * NT);
+                    mma_ta<1>(d0, tmem + 8 * ks, bd, IDESC);
+                    if constexpr (kSplit) mma_ta<1>(d0, tmem + 128 + 8 * ks, bd, IDESC);
                 }
                 // half 1 only where some block of the tile needs ranks >= 128
                 if (!mbar_wait(bar + SU_INF + 8 * is, (j / SU_I) & 1, abort_flag, a.status)) break;
                 if (info[is].kmax > 128) {
-#pragma unroll 4
-                    for (int ks = 0; ks < 16; ++ks) {
-                        const uint64_t bd = umma_desc(bst + ks * 1024, 512, 128);
-                        umma_tmem_a(d1, tmem + 256 + 8 * ks, bd, IDESC, ks > 0 ? 1u : 0u);
-                        if constexpr (kSplit)
-                            umma_smem_a(d1, umma_desc(sb + SU_OFF_A1LO + ks * 4096, 2048, 128), bd, IDESC, 1u);
+                    mma_sa<0>(d1, ah0, bd0, IDESC);
+                    if constexpr (kSplit) mma_sa<1>(d1, al0, bd0, IDESC);
+#pragma unroll
+                    for (int ks = 1; ks < 16; ++ks) {
+                        const uint64_t bd = bd0 + (uint64_t)(ks * 2 * NT);
+                        mma_sa<1>(d1, ah0 + (uint64_t)(ks * 256), bd, IDESC);
+                        if constexpr (kSplit) mma_sa<1>(d1, al0 + (uint64_t)(ks * 256), bd, IDESC);
                     }
                 }
-                umma_commit(bar + SU_BE + 8 * st);        // the stage is free once these complete
-                umma_commit(bar + SU_ACCF + 8 * acc);     // the tile's accumulators are ready
+                umma_commit(bar + SU_BE + 8 * me);        // the stage is free once these complete
+                umma_commit(bar + SU_ACCF + 8 * me);      // the tile's accumulator is ready
             }
-            umma_commit(bar + SU_DRAIN);
-            mbar_drain(bar + SU_DRAIN, 0, a.status);
+            umma_commit(bar + SU_DRAIN + 8 * me);
+            mbar_drain(bar + SU_DRAIN + 8 * me, 0, a.status);
         }
         __syncwarp();
-    } else if (warp == 1) {
-        // ---- producer
-        const uint8_t* img = a.img;
-        auto pixels = [&](int j) -> bool {
-            const int slot = j % SU_R;
-            if (j >= SU_R) {
-                int ok = 1;
-                if (lane == 0) ok = mbar_wait(bar + SU_RAWE + 8 * slot, ((j / SU_R) & 1) ^ 1, abort_flag, a.status);
-                if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
-            }
-            const int64_t b0 = ((int64_t)blockIdx.x + (int64_t)j * G) * NT;
-            const int n = (int)(ntot - b0 < NT ? ntot - b0 : NT);
-            // lane = block of the tile; a run starts at the tile's first block
-            // and at every block-row start
-            int k = 0, bi = 0, bj = 0;
-            if (lane < n) su_coords(g, b0 + lane, k, bi, bj);
-            const bool start = lane < n && (lane == 0 || bj == 0);
-            const int len = start ? min(n - lane, g.nbw - bj) : 0;
-            if (lane == 0) mbar_arrive_tx(bar + SU_RAWF + 8 * slot, (uint32_t)n * 256u);
-            __syncwarp();
-            if (start) {
-                const uint8_t* src = img + (int64_t)k * g.img_stride + (int64_t)(bi * 16) * g.pitch + bj * 16;
-                const uint32_t dst = sb + SU_OFF_RAW + slot * SU_RAW + lane * 16;
-                for (int r = 0; r < 16; ++r)
-                    bulk_g2s(dst + r * (NT * 16), src + (int64_t)r * g.pitch, (uint32_t)len * 16u,
-                             bar + SU_RAWF + 8 * slot);
-            }
-            return true;
-        };
-        auto meta = [&](int j) -> bool {
+    } else if (warp == W_META) {
+        // ---- metadata, up to SU_I tiles ahead of the epilogue: lane = blocks lane, lane + 32
+        griddep_wait();
+        for (int j = 0; j < my_n; ++j) {
             const int is = j % SU_I;
             if (j >= SU_I) {
                 int ok = 1;
                 if (lane == 0) ok = mbar_wait(bar + SU_INE + 8 * is, ((j / SU_I) & 1) ^ 1, abort_flag, a.status);
-                if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
+                if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             }
-            const int64_t b0 = ((int64_t)blockIdx.x + (int64_t)j * G) * NT;
+            const int64_t b0 = tile_b0(j);
             const int n = (int)(ntot - b0 < NT ? ntot - b0 : NT);
-            int m = 0;
-            int64_t off = 0;
+            int m[2];
+            int64_t off[2];
             bool bad = false;
-            if (lane < n) {
-                int k, bi, bj;
-                su_coords(g, b0 + lane, k, bi, bj);
-                m = __ldg(a.counts + b0 + lane);
-                off = __ldg(a.offsets + b0 + lane) + __ldg(a.img_base + k);
-                if (m < 0 || m > 256 || off < 0) {
-                    bad = true;
-                    m = 0;
-                    off = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = lane + 32 * h;
+                m[h] = 0;
+                off[h] = 0;
+                if (i < n) {
+                    int k, bi, bj;
+                    su_coords(g, b0 + i, k, bi, bj);
+                    m[h] = __ldg(a.counts + b0 + i);
+                    off[h] = __ldg(a.offsets + b0 + i) + __ldg(a.img_base + k);
                 }
             }
-            if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(a.status, ABCS_DEV_BADCOUNT);
+            const int64_t base = __shfl_sync(0xffffffffu, off[0], 0);
             SuInfo& I = info[is];
-            I.m[lane] = m;
-            I.off[lane] = off;
-            int km = m;
+            int km = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = lane + 32 * h;
+                int64_t rel = off[h] - base;
+                if (i < n && (m[h] < 0 || m[h] > 256 || rel < 0 || rel + m[h] > NT * 256)) {
+                    bad = true;
+                    m[h] = 0;
+                    rel = 0;
+                }
+                if (i >= n) {
+                    m[h] = 0;
+                    rel = 0;
+                }
+                I.pk[i] = (uint32_t)rel | ((uint32_t)m[h] << 16);
+                km = max(km, m[h]);
+            }
+            if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(a.status, ABCS_DEV_BADCOUNT);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) km = max(km, __shfl_xor_sync(0xffffffffu, km, o));
-            if (lane == 0) I.kmax = km;
+            if (lane == 0) {
+                I.base = base;
+                I.kmax = km;
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(bar + SU_INF + 8 * is);
-            return true;
-        };
-        // the first slots' pixels do not depend on the allocation: they are
-        // copied before the wait for the pilot kernel (which lets this grid
-        // start once that kernel has passed its own wait)
-        int jp = 0;
-        bool ok = true;
-        for (; jp < SU_R && jp < my_n && ok; ++jp) ok = pixels(jp);
-        griddep_wait();
-        for (int j = 0; j < my_n && ok; ++j) {
-            ok = meta(j);
-            if (ok && jp < my_n) ok = pixels(jp++);
         }
-        // copies still in flight land before the CTA leaves
-        if (lane == 0)
-            for (int jj = jp > SU_R ? jp - SU_R : 0; jj < jp; ++jj)
-                mbar_drain(bar + SU_RAWF + 8 * (jj % SU_R), (jj / SU_R) & 1, a.status);
-    } else if (warp < 6) {
-        // ---- converters: warp wl = warp - 2 takes pixel rows wl, wl + 4, wl + 8, wl + 12 of
-        // every block (lane = block)
-        const int wl = warp - 2;
-        for (int j = 0; j < my_n; ++j) {
-            const int slot = j % SU_R, st = j % SU_S;
-            int ok = 1;
-            if (lane == 0) {
-                ok = mbar_wait(bar + SU_RAWF + 8 * slot, (j / SU_R) & 1, abort_flag, a.status);
-                if (ok) ok = mbar_wait(bar + SU_BE + 8 * st, ((j / SU_S) & 1) ^ 1, abort_flag, a.status);
+    } else if (warp < W_EPI) {
+        // ---- converters: warp c takes blocks lane + 32 (c & 1) of the tile
+        // and pixel rows (c >> 1) + 4 i; global 16-byte loads one tile ahead,
+        // FP16 / BF16 pairs into the K-major B stage of the tile's issuer
+        const int c = warp - W_CONV, nb = lane + 32 * (c & 1), r0 = c >> 1;
+        uint4 cur[4], nxt[4];
+        auto load = [&](int j, uint4 (&v)[4]) {
+            const int64_t b0 = tile_b0(j);
+            if (b0 + nb < ntot) {
+                int k, bi, bj;
+                su_coords(g, b0 + nb, k, bi, bj);
+                const uint8_t* src = a.img + (int64_t)k * g.img_stride + (int64_t)(bi * 16 + r0) * g.pitch + bj * 16;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = __ldg(reinterpret_cast<const uint4*>(src + (int64_t)(4 * i) * g.pitch));
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = make_uint4(0, 0, 0, 0);
             }
+        };
+        if (my_n > 0) load(0, cur);
+        for (int j = 0; j < my_n; ++j) {
+            if (j + 1 < my_n) load(j + 1, nxt);
+            const int st = j & 1, u = j >> 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(bar + SU_BE + 8 * st, (u & 1) ^ 1, abort_flag, a.status);
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-            const unsigned char* raw = smem + SU_OFF_RAW + slot * SU_RAW;
             unsigned char* bst = smem + SU_OFF_B + st * SU_STAGE;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int r = wl + 4 * i;
-                const uint4 w = *reinterpret_cast<const uint4*>(raw + r * (NT * 16) + lane * 16);
+                const int r = r0 + 4 * i;
+                const uint4 w = cur[i];
                 const uint4 lo = make_uint4(su_px2<P>(w.x, 0), su_px2<P>(w.x, 1), su_px2<P>(w.y, 0), su_px2<P>(w.y, 1));
                 const uint4 hi = make_uint4(su_px2<P>(w.z, 0), su_px2<P>(w.z, 1), su_px2<P>(w.w, 0), su_px2<P>(w.w, 1));
-                *reinterpret_cast<uint4*>(bst + (2 * r) * (NT * 16) + lane * 16) = lo;
-                *reinterpret_cast<uint4*>(bst + (2 * r + 1) * (NT * 16) + lane * 16) = hi;
+                *reinterpret_cast<uint4*>(bst + (2 * r) * (NT * 16) + nb * 16) = lo;
+                *reinterpret_cast<uint4*>(bst + (2 * r + 1) * (NT * 16) + nb * 16) = hi;
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(bar + SU_BF + 8 * st);
-                mbar_arrive(bar + SU_RAWE + 8 * slot);
-            }
+            if (lane == 0) mbar_arrive(bar + SU_BF + 8 * st);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) cur[i] = nxt[i];
         }
     } else {
-        // ---- epilogue warps; first they copy the operand table into tensor memory
-        const int q = warp & 3;
+        // ---- epilogue warps: lane quarter q = warp % 4 (tensor-memory
+        // access rule), column half ch; first they copy half 0 of the
+        // operand table into tensor memory
+        const int e = warp - W_EPI, q = warp & 3, ch = e >> 2;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         bool alive = true;
-        int ph = 0;
-        for (int part = 0; part < 3 && alive; ++part) {
-            if (!kSplit && part == 1) continue;
+        {
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(bar + SU_TABF, ph & 1, abort_flag, a.status);
-            if (!__shfl_sync(0xffffffffu, ok, 0)) {
-                alive = false;
-                break;
-            }
-            const uint32_t* tabs = reinterpret_cast<const uint32_t*>(smem + SU_OFF_A1LO) + 32 * q + lane;
+            if (lane == 0) ok = mbar_wait(bar + SU_TABF, 0, abort_flag, a.status);
+            alive = __shfl_sync(0xffffffffu, ok, 0) != 0;
+        }
+        if (alive) {
+            // part ch (0: hi, 1: lo) of half 0, staged at the region of half 1's part ch
+            if (kSplit || ch == 0) {
+                const uint32_t* tabs =
+                    reinterpret_cast<const uint32_t*>(smem + (ch ? SU_OFF_A1LO : SU_OFF_A1HI)) + 32 * q + lane;
 #pragma unroll 1
-            for (int cb = 0; cb < 4; ++cb) {
-                uint32_t v[32];
+                for (int cb = 0; cb < 4; ++cb) {
+                    uint32_t v[32];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = tabs[(cb * 32 + i) * 128];
-                tmem_st32(tmem + lane_base + part * 128 + cb * 32, v);
+                    for (int i = 0; i < 32; ++i) v[i] = tabs[(cb * 32 + i) * 128];
+                    tmem_st32(tmem + lane_base + ch * 128 + cb * 32, v);
+                }
+                tmem_wait_st();
             }
-            tmem_wait_st();
             tc5_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar + SU_TABE);
-            ++ph;
         }
         griddep_wait();
         const float inv = 1.f / SU_SCALE;
         for (int j = 0; j < my_n && alive; ++j) {
-            const int acc = j & 1, is = j % SU_I;
+            const int acc = j & 1, u = j >> 1, is = j % SU_I;
             int ok = 1;
             if (lane == 0) {
-                ok = mbar_wait(bar + SU_ACCF + 8 * acc, (j >> 1) & 1, abort_flag, a.status);
+                ok = mbar_wait(bar + SU_ACCF + 8 * acc, u & 1, abort_flag, a.status);
                 if (ok) ok = mbar_wait(bar + SU_INF + 8 * is, (j / SU_I) & 1, abort_flag, a.status);
             }
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             tc5_fence_after();
             const SuInfo& I = info[is];
             const int kmax = I.kmax;
-            const int64_t b0 = ((int64_t)blockIdx.x + (int64_t)j * G) * NT;
-            const int n = (int)(ntot - b0 < NT ? ntot - b0 : NT);
+            const int64_t base = I.base;
+            const uint32_t my_pk = I.pk[32 * ch + lane];      // for the offsets below
             for (int h = 0; h < 2; ++h) {
                 const int k0 = 128 * h + 32 * q;      // this warp's first rank
                 if (k0 >= kmax) continue;             // warp-uniform: no block needs these ranks
-                uint32_t v[32];
-                tmem_ld32(tmem + lane_base + 384 + 64 * acc + 32 * h, v);
                 const int rank = k0 + lane;
+                float* yb = a.coeffs + base + rank;
+                const int64_t lim = a.capacity - base - rank;
 #pragma unroll
-                for (int i = 0; i < NT; ++i) {
-                    const int m = I.m[i];
-                    if (k0 >= m) continue;            // warp-uniform
-                    const int64_t o = I.off[i] + rank;
-                    if (rank < m) {
-                        if (o < a.capacity) a.coeffs[o] = __uint_as_float(v[i]) * inv;
-                        else set_status(a.status, ABCS_DEV_CAPACITY);
+                for (int c16 = 0; c16 < 2; ++c16) {   // 16 blocks at a time
+                    const int n0 = 32 * ch + 16 * c16;
+                    uint32_t v[16], pk[16];
+                    tmem_ld16(tmem + lane_base + 256 + 128 * acc + 64 * h + n0, v);
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4) {
+                        const uint4 v4 = *reinterpret_cast<const uint4*>(&I.pk[n0 + i]);
+                        pk[i] = v4.x;
+                        pk[i + 1] = v4.y;
+                        pk[i + 2] = v4.z;
+                        pk[i + 3] = v4.w;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int m = (int)(pk[i] >> 16), rel = (int)(pk[i] & 0xFFFFu);
+                        if (rank < m && rel < lim) yb[rel] = __uint_as_float(v[i]) * inv;
                     }
                 }
-            }
-            // global offsets of the tile's blocks
-            if (q == 0 && lane < n) {
-                a.offsets[b0 + lane] = I.off[lane];
-                if (b0 + lane == ntot - 1) a.offsets[ntot] = I.off[lane] + I.m[lane];
             }
             tc5_fence_before();
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(bar + SU_ACCE + 8 * acc);
                 mbar_arrive(bar + SU_INE + 8 * is);
+            }
+            // global offsets of the tile's blocks (and the total after the last block)
+            if (q == 0) {
+                const int64_t b0 = tile_b0(j);
+                const int i = 32 * ch + lane;
+                if (b0 + i < ntot) {
+                    const int64_t o = base + (int64_t)(my_pk & 0xFFFFu);
+                    a.offsets[b0 + i] = o;
+                    if (b0 + i == ntot - 1) {
+                        a.offsets[ntot] = o + (int64_t)(my_pk >> 16);
+                        if (o + (int64_t)(my_pk >> 16) > a.capacity) set_status(a.status, ABCS_DEV_CAPACITY);
+                    }
+                }
             }
         }
     }
