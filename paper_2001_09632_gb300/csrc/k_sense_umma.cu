@@ -123,11 +123,12 @@ static_assert(sizeof(SuInfo) % 16 == 0, "metadata slots stay 16-byte aligned");
 
 constexpr uint32_t SU_OFF_A1HI = 0;                               // also staging of the table parts
 constexpr uint32_t SU_OFF_A1LO = SU_PART;
-constexpr uint32_t SU_OFF_B = 2 * SU_PART;                        // stage i belongs to MMA issuer i
-constexpr uint32_t SU_OFF_INFO = SU_OFF_B + 2 * SU_STAGE;
+constexpr int SU_S = 3;                // B stages (tile j uses stage j % 3)
+constexpr uint32_t SU_OFF_B = 2 * SU_PART;
+constexpr uint32_t SU_OFF_INFO = SU_OFF_B + SU_S * SU_STAGE;
 constexpr uint32_t SU_OFF_BAR = SU_OFF_INFO + SU_I * sizeof(SuInfo);
 // mbarriers
-constexpr uint32_t SU_BF = 0, SU_BE = 16, SU_ACCF = 32, SU_ACCE = 48, SU_INF = 64, SU_INE = SU_INF + 8 * SU_I,
+constexpr uint32_t SU_BF = 0, SU_BE = 24, SU_ACCF = 48, SU_ACCE = 64, SU_INF = 80, SU_INE = SU_INF + 8 * SU_I,
                    SU_TABF = SU_INE + 8 * SU_I, SU_TABE = SU_TABF + 8, SU_TABR = SU_TABE + 8, SU_DRAIN = SU_TABR + 8,
                    SU_NBAR = SU_DRAIN + 16;
 constexpr uint32_t SU_OFF_MISC = SU_OFF_BAR + SU_NBAR;            // tensor-memory address, abort flag
@@ -192,16 +193,6 @@ ABCS_D void mma_sa(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t ide
         "l"(adesc), "l"(bdesc), "r"(idesc), "n"(ACC));
 }
 
-// 16 consecutive columns of this warp's 32 lanes (thread i -> lane i)
-ABCS_D void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-}
-
 // two pixels (bytes 2 sel, 2 sel + 1 of w) as an operand pair; exact
 template <int P>
 ABCS_D uint32_t su_px2(uint32_t w, int sel) {
@@ -249,9 +240,11 @@ __global__ void __launch_bounds__(SU_THREADS, 1) sense_umma_kernel(SenseArgs a, 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (t == 32) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < SU_S; ++i) {
             mbar_init(bar + SU_BF + 8 * i, SU_CONV);
             mbar_init(bar + SU_BE + 8 * i, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             mbar_init(bar + SU_ACCF + 8 * i, 1);
             mbar_init(bar + SU_ACCE + 8 * i, SU_EPI);
             mbar_init(bar + SU_DRAIN + 8 * i, 1);
@@ -302,12 +295,12 @@ __global__ void __launch_bounds__(SU_THREADS, 1) sense_umma_kernel(SenseArgs a, 
             if (alive && !mbar_wait(bar + SU_TABR, 0, abort_flag, a.status)) alive = false;
             tc5_fence_after();
             const uint32_t d0 = tmem + 256 + 128 * me, d1 = d0 + 64;
-            const uint64_t bd0 = umma_desc(sb + SU_OFF_B + me * SU_STAGE, NT * 16, 128);
             const uint64_t ah0 = umma_desc(sb + SU_OFF_A1HI, 2048, 128), al0 = umma_desc(sb + SU_OFF_A1LO, 2048, 128);
             for (int j = me, u = 0; j < my_n && alive; j += 2, ++u) {
-                const int is = j % SU_I;
+                const int is = j % SU_I, st = j % SU_S;
+                const uint64_t bd0 = umma_desc(sb + SU_OFF_B + st * SU_STAGE, NT * 16, 128);
                 if (!mbar_wait(bar + SU_ACCE + 8 * me, (u & 1) ^ 1, abort_flag, a.status)) break;
-                if (!mbar_wait(bar + SU_BF + 8 * me, u & 1, abort_flag, a.status)) break;
+                if (!mbar_wait(bar + SU_BF + 8 * st, (j / SU_S) & 1, abort_flag, a.status)) break;
                 tc5_fence_after();
                 // K step ks: pixel row ks = B chunks 2 ks, 2 ks + 1 (ks * 2 * NT * 16 bytes,
                 // i.e. ks * 2 * NT in the descriptor's 16-byte address units)
@@ -331,7 +324,7 @@ __global__ void __launch_bounds__(SU_THREADS, 1) sense_umma_kernel(SenseArgs a, 
                         if constexpr (kSplit) mma_sa<1>(d1, al0 + (uint64_t)(ks * 256), bd, IDESC);
                     }
                 }
-                umma_commit(bar + SU_BE + 8 * me);        // the stage is free once these complete
+                umma_commit(bar + SU_BE + 8 * st);        // the stage is free once these complete
                 umma_commit(bar + SU_ACCF + 8 * me);      // the tile's accumulator is ready
             }
             umma_commit(bar + SU_DRAIN + 8 * me);
@@ -416,9 +409,9 @@ __global__ void __launch_bounds__(SU_THREADS, 1) sense_umma_kernel(SenseArgs a, 
         if (my_n > 0) load(0, cur);
         for (int j = 0; j < my_n; ++j) {
             if (j + 1 < my_n) load(j + 1, nxt);
-            const int st = j & 1, u = j >> 1;
+            const int st = j % SU_S;
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(bar + SU_BE + 8 * st, (u & 1) ^ 1, abort_flag, a.status);
+            if (lane == 0) ok = mbar_wait(bar + SU_BE + 8 * st, ((j / SU_S) & 1) ^ 1, abort_flag, a.status);
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             unsigned char* bst = smem + SU_OFF_B + st * SU_STAGE;
 #pragma unroll
@@ -481,38 +474,40 @@ __global__ void __launch_bounds__(SU_THREADS, 1) sense_umma_kernel(SenseArgs a, 
             const int kmax = I.kmax;
             const int64_t base = I.base;
             const uint32_t my_pk = I.pk[32 * ch + lane];      // for the offsets below
-            for (int h = 0; h < 2; ++h) {
-                const int k0 = 128 * h + 32 * q;      // this warp's first rank
-                if (k0 >= kmax) continue;             // warp-uniform: no block needs these ranks
-                const int rank = k0 + lane;
+            // the accumulator is read out first and released at once, so the
+            // next tile's products overlap these stores
+            const bool h0 = 32 * q < kmax, h1 = 128 + 32 * q < kmax;   // warp-uniform
+            uint32_t v0[32], v1[32];
+            const uint32_t ta = tmem + lane_base + 256 + 128 * acc + 32 * ch;
+            if (h0) tmem_ld32(ta, v0);
+            if (h1) tmem_ld32(ta + 64, v1);
+            tc5_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar + SU_ACCE + 8 * acc);
+            if (h0) {
+                const int rank = 32 * q + lane;
                 float* yb = a.coeffs + base + rank;
                 const int64_t lim = a.capacity - base - rank;
 #pragma unroll
-                for (int c16 = 0; c16 < 2; ++c16) {   // 16 blocks at a time
-                    const int n0 = 32 * ch + 16 * c16;
-                    uint32_t v[16], pk[16];
-                    tmem_ld16(tmem + lane_base + 256 + 128 * acc + 64 * h + n0, v);
-#pragma unroll
-                    for (int i = 0; i < 16; i += 4) {
-                        const uint4 v4 = *reinterpret_cast<const uint4*>(&I.pk[n0 + i]);
-                        pk[i] = v4.x;
-                        pk[i + 1] = v4.y;
-                        pk[i + 2] = v4.z;
-                        pk[i + 3] = v4.w;
-                    }
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int m = (int)(pk[i] >> 16), rel = (int)(pk[i] & 0xFFFFu);
-                        if (rank < m && rel < lim) yb[rel] = __uint_as_float(v[i]) * inv;
-                    }
+                for (int i = 0; i < 32; ++i) {
+                    const uint32_t pk = I.pk[32 * ch + i];
+                    const int m = (int)(pk >> 16), rel = (int)(pk & 0xFFFFu);
+                    if (rank < m && rel < lim) yb[rel] = __uint_as_float(v0[i]) * inv;
                 }
             }
-            tc5_fence_before();
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(bar + SU_ACCE + 8 * acc);
-                mbar_arrive(bar + SU_INE + 8 * is);
+            if (h1) {
+                const int rank = 128 + 32 * q + lane;
+                float* yb = a.coeffs + base + rank;
+                const int64_t lim = a.capacity - base - rank;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const uint32_t pk = I.pk[32 * ch + i];
+                    const int m = (int)(pk >> 16), rel = (int)(pk & 0xFFFFu);
+                    if (rank < m && rel < lim) yb[rel] = __uint_as_float(v1[i]) * inv;
+                }
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar + SU_INE + 8 * is);
             // global offsets of the tile's blocks (and the total after the last block)
             if (q == 0) {
                 const int64_t b0 = tile_b0(j);
