@@ -484,26 +484,29 @@ __global__ void __launch_bounds__(SU_THREADS, 1) sense_umma_kernel(SenseArgs a, 
             tc5_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar + SU_ACCE + 8 * acc);
+            // block i's (offset, count) comes from lane i by a shuffle, not a
+            // shared-memory load, so nothing orders it after the stores
+            float* const y = a.coeffs;
             if (h0) {
                 const int rank = 32 * q + lane;
-                float* yb = a.coeffs + base + rank;
-                const int64_t lim = a.capacity - base - rank;
+                const int64_t yb = base + rank;
+                const int lim = (int)min(a.capacity - yb, (int64_t)1 << 30);
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
-                    const uint32_t pk = I.pk[32 * ch + i];
+                    const uint32_t pk = __shfl_sync(0xffffffffu, my_pk, i);
                     const int m = (int)(pk >> 16), rel = (int)(pk & 0xFFFFu);
-                    if (rank < m && rel < lim) yb[rel] = __uint_as_float(v0[i]) * inv;
+                    if (rank < m && rel < lim) y[yb + rel] = __uint_as_float(v0[i]) * inv;
                 }
             }
             if (h1) {
                 const int rank = 128 + 32 * q + lane;
-                float* yb = a.coeffs + base + rank;
-                const int64_t lim = a.capacity - base - rank;
+                const int64_t yb = base + rank;
+                const int lim = (int)min(a.capacity - yb, (int64_t)1 << 30);
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
-                    const uint32_t pk = I.pk[32 * ch + i];
+                    const uint32_t pk = __shfl_sync(0xffffffffu, my_pk, i);
                     const int m = (int)(pk >> 16), rel = (int)(pk & 0xFFFFu);
-                    if (rank < m && rel < lim) yb[rel] = __uint_as_float(v1[i]) * inv;
+                    if (rank < m && rel < lim) y[yb + rel] = __uint_as_float(v1[i]) * inv;
                 }
             }
             __syncwarp();
