@@ -193,6 +193,12 @@ ABCS_D void mma_sa(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t ide
         "l"(adesc), "l"(bdesc), "r"(idesc), "n"(ACC));
 }
 
+// y[i] = v when pred, as one predicated store (no branch around it)
+ABCS_D void st_pred(float* p, float v, bool pred) {
+    asm volatile("{\n.reg .pred q;\nsetp.ne.b32 q, %2, 0;\n@q st.global.f32 [%0], %1;\n}\n" ::"l"(p), "f"(v),
+                 "r"((int)pred));
+}
+
 // two pixels (bytes 2 sel, 2 sel + 1 of w) as an operand pair; exact
 template <int P>
 ABCS_D uint32_t su_px2(uint32_t w, int sel) {
@@ -495,7 +501,7 @@ __global__ void __launch_bounds__(SU_THREADS, 1) sense_umma_kernel(SenseArgs a, 
                 for (int i = 0; i < 32; ++i) {
                     const uint32_t pk = __shfl_sync(0xffffffffu, my_pk, i);
                     const int m = (int)(pk >> 16), rel = (int)(pk & 0xFFFFu);
-                    if (rank < m && rel < lim) y[yb + rel] = __uint_as_float(v0[i]) * inv;
+                    st_pred(y + yb + rel, __uint_as_float(v0[i]) * inv, rank < m && rel < lim);
                 }
             }
             if (h1) {
@@ -506,7 +512,7 @@ __global__ void __launch_bounds__(SU_THREADS, 1) sense_umma_kernel(SenseArgs a, 
                 for (int i = 0; i < 32; ++i) {
                     const uint32_t pk = __shfl_sync(0xffffffffu, my_pk, i);
                     const int m = (int)(pk >> 16), rel = (int)(pk & 0xFFFFu);
-                    if (rank < m && rel < lim) y[yb + rel] = __uint_as_float(v1[i]) * inv;
+                    st_pred(y + yb + rel, __uint_as_float(v1[i]) * inv, rank < m && rel < lim);
                 }
             }
             __syncwarp();
