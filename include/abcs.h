@@ -149,7 +149,12 @@ abcs_status abcs_plan(int H, int W, int B, double subrate, int variant, abcs_pla
  * per image), else ABCS_ERR_CAPACITY before any work.  Counts are exact
  * integers; the DD decisions |c| > T are taken on the exact coefficient.
  * precision selects how the measured coefficients are computed; pilot
- * decisions do not depend on it. */
+ * decisions do not depend on it.  Tensor-core precisions (B = 16) run the
+ * per-block mma.sync transform; with the environment variable
+ * ABCS_SENSE_TC=umma (read at each call) and 16-byte aligned img, pitch and
+ * img_stride they run the tcgen05 kernel instead, which computes each
+ * 64-block tile as one GEMM against the zigzag-ordered DCT basis (the same
+ * results within the precision's bound; slower on the measured workloads). */
 abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int W,
                        int64_t pitch, int64_t img_stride, int B, double subrate,
                        int variant, int precision, int32_t* counts, int64_t* offsets,

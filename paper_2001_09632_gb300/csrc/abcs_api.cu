@@ -155,11 +155,12 @@ abcs_status ensure_ws(abcs_handle* h, size_t bytes) {
     return ABCS_OK;
 }
 
-// ABCS_SENSE_TC=mma (read at each call) selects the per-block mma.sync
-// sensing kernel instead of the tcgen05 one for the tensor-core precisions.
-bool sense_mma_forced() {
+// ABCS_SENSE_TC=umma (read at each call) selects the tcgen05 sensing
+// kernel instead of the per-block mma.sync one for the tensor-core
+// precisions (16-byte aligned rows only).
+bool sense_umma_selected() {
     const char* v = getenv("ABCS_SENSE_TC");
-    return v && strcmp(v, "mma") == 0;
+    return v && strcmp(v, "umma") == 0;
 }
 
 template <typename T>
@@ -309,7 +310,7 @@ abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int
     }
     if (precision == ABCS_FP32)
         ABCS_CUDA(launch_sense_pack(a, s), "sense_pack launch");
-    else if (sense_umma_usable(a) && !sense_mma_forced())
+    else if (sense_umma_usable(a) && sense_umma_selected())
         ABCS_CUDA(launch_sense_umma(a, s), "sense_umma launch");
     else
         ABCS_CUDA(launch_sense_tc(a, s), "sense_tc launch");

@@ -31,11 +31,11 @@ def _oracle(imgs, B, r, variant):
 @pytest.mark.parametrize("variant", [O.ZZ, O.BBV, O.DD])
 @pytest.mark.parametrize("shape", [(2, 96, 336), (1, 64, 1040), (3, 48, 48), (5, 160, 208), (2, 80, 337)])
 def test_tc_sense_and_reconstruct(handle, monkeypatch, kernel, prec, variant, shape):
-    """Both sensing kernels: the tcgen05 one (the default for 16-byte aligned
-    rows; a row of 337 bytes falls back to the other) and the per-block
-    mma.sync one (ABCS_SENSE_TC=mma)."""
-    if kernel == "mma":
-        monkeypatch.setenv("ABCS_SENSE_TC", "mma")
+    """Both sensing kernels: the per-block mma.sync one (the default) and the
+    tcgen05 one (ABCS_SENSE_TC=umma; 16-byte aligned rows only, a row of 337
+    bytes falls back to the other)."""
+    if kernel == "umma":
+        monkeypatch.setenv("ABCS_SENSE_TC", "umma")
     n, H, W = shape
     B, r = 16, 0.3
     imgs = np.stack([synth.gen_image(H, W, 300 + k) for k in range(n)])
@@ -120,9 +120,9 @@ def test_sense_kernels_agree_on_the_full_batch(handle, monkeypatch, variant, r):
     sampled images (r = 0.5 BBV puts ranks >= 128 in every tile)."""
     B, n = 16, 64
     imgs = synth.gen_batch(n, 512, 512, 4242)
-    got_u = G.sense(handle, imgs, B, r, variant, precision=abcs.TC_FP16X2)
-    monkeypatch.setenv("ABCS_SENSE_TC", "mma")
     got_m = G.sense(handle, imgs, B, r, variant, precision=abcs.TC_FP16X2)
+    monkeypatch.setenv("ABCS_SENSE_TC", "umma")
+    got_u = G.sense(handle, imgs, B, r, variant, precision=abcs.TC_FP16X2)
     monkeypatch.delenv("ABCS_SENSE_TC")
     assert got_u["bits"] == 0 and got_m["bits"] == 0
     assert np.array_equal(got_u["counts"], got_m["counts"])
@@ -185,8 +185,8 @@ def test_tc_extreme_subrates(handle, monkeypatch, kernel, prec, variant, r):
     n, H, W, B = 10, 512, 512, 16
     imgs = synth.gen_batch(n, H, W, 2024)
     outs, c_ref, y_ref = _oracle(imgs, B, r, variant)
-    if kernel == "mma":
-        monkeypatch.setenv("ABCS_SENSE_TC", "mma")
+    if kernel == "umma":
+        monkeypatch.setenv("ABCS_SENSE_TC", "umma")
     got = G.sense(handle, imgs, B, r, variant, precision=prec)
     monkeypatch.delenv("ABCS_SENSE_TC", raising=False)
     assert got["bits"] == 0
