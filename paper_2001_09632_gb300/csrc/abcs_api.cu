@@ -297,6 +297,11 @@ abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int
     a.done = h->status + 1;
     a.img_done = h->img_done;
     a.status = h->status;
+    // the tensor-core sensing kernels derive the image bases from the
+    // per-image totals (the allocation then skips its serial pass over
+    // the batch); the FP32 kernel reads them from the allocation
+    const bool umma = precision != ABCS_FP32 && sense_umma_usable(a) && sense_umma_selected();
+    a.pilot_bases = (precision == ABCS_FP32 || (!umma && !sense_tc_bases_in_kernel(a))) ? 1 : 0;
 
     // pilot kernels allocate in their fused tail; without a pilot the
     // stand-alone allocation kernel runs
@@ -310,7 +315,7 @@ abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int
     }
     if (precision == ABCS_FP32)
         ABCS_CUDA(launch_sense_pack(a, s), "sense_pack launch");
-    else if (sense_umma_usable(a) && sense_umma_selected())
+    else if (umma)
         ABCS_CUDA(launch_sense_umma(a, s), "sense_umma launch");
     else
         ABCS_CUDA(launch_sense_tc(a, s), "sense_tc launch");

@@ -174,6 +174,8 @@ struct SenseArgs {
     unsigned* done;      // allocation CTAs finished (reset by the last one)
     unsigned* img_done;  // per image: pilot CTAs finished (fused allocation; reset after use), or NULL
     uint32_t* status;
+    int pilot_bases;     // 1: the allocation writes img_base; 0: the sensing kernel derives the
+                         // image bases from img_total itself (tensor-core sensing kernels)
 };
 int pilot_ctas_per_image(const SenseArgs& a);
 cudaError_t launch_bbv_pilot(const SenseArgs& a, cudaStream_t s);
@@ -197,6 +199,9 @@ struct ReconArgs {
 cudaError_t launch_reconstruct(const ReconArgs& a, cudaStream_t s);
 // tensor-core paths (B = 16; a.precision selects FP16x2 / BF16x2 / BF16)
 cudaError_t launch_sense_tc(const SenseArgs& a, cudaStream_t s);
+// whether the mma.sync sensing kernel can derive the image bases itself
+// (its CTAs' block ranges span at most 64 images)
+bool sense_tc_bases_in_kernel(const SenseArgs& a);
 // tcgen05 sensing (k_sense_umma.cu): B = 16, 16-byte aligned images and rows
 bool sense_umma_usable(const SenseArgs& a);
 cudaError_t launch_sense_umma(const SenseArgs& a, cudaStream_t s);

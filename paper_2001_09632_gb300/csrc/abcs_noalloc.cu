@@ -148,6 +148,7 @@ extern "C" abcs_status abcs_sense_noalloc(const uint8_t* img, int n_img, int H, 
     a.img_base = reinterpret_cast<int64_t*>(scratch + kOffBase);
     a.wpart = reinterpret_cast<unsigned long long*>(scratch + kOffPart);
     a.w = pilot ? pilot : reinterpret_cast<int32_t*>(scratch + kOffW);
+    a.pilot_bases = 1;
 
     // The array keeps the previous call's contents.  Pilot values, partial
     // sums, totals and bases are fully overwritten by every call; the

@@ -186,7 +186,7 @@ ABCS_D void pilot_alloc_tail(const SenseArgs& a, int mode, int k, int cpi, int64
     if (threadIdx.x == 0) a.img_done[k] = 0u;
     alloc_image(a.w, a.wpart, cpi, a.g.n_blocks, alloc_params(a, mode), k, a.counts, a.offsets, a.img_total, sh,
                 sW);
-    alloc_finish(a.g.n_img, a.img_total, a.img_base, a.done, sh, s_last);
+    if (a.pilot_bases) alloc_finish(a.g.n_img, a.img_total, a.img_base, a.done, sh, s_last);
 }
 
 }  // namespace abcs

@@ -98,10 +98,93 @@ ABCS_D int bbv_block(const SenseArgs& a, int k, int64_t i) {
     return s;
 }
 
-template <int CH>
+// One pixel row of a block (B bytes) as 32-bit words, from a B-aligned
+// address (B >= 4).
+template <int B>
+ABCS_D void load_row_words(const uint8_t* p, uint32_t (&w)[B / 4]) {
+    if constexpr (B == 4) {
+        w[0] = __ldg(reinterpret_cast<const uint32_t*>(p));
+    } else if constexpr (B == 8) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+        w[0] = v.x; w[1] = v.y;
+    } else {
+#pragma unroll
+        for (int h = 0; h < B / 16; ++h) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + h);
+            w[4 * h] = v.x; w[4 * h + 1] = v.y; w[4 * h + 2] = v.z; w[4 * h + 3] = v.w;
+        }
+    }
+}
+
+template <int NW>
+ABCS_D int row_byte(const uint32_t (&w)[NW], int p) {
+    uint32_t v = w[0];
+#pragma unroll
+    for (int q = 1; q < NW; ++q) v = (p >> 2) == q ? w[q] : v;
+    return (int)((v >> (8 * (p & 3))) & 0xFFu);
+}
+
+// Eq. 19 split by the pixels each term reads: for block i with top-left
+// pixel (r0, c0) and samples a = X0 + j L (j < n_S), 1-based in the block,
+//   T_i = sum |P(r0, c0 + a) - P(r0, c0 + a - 1)|       (its top row)
+//   L_i = sum |P(r0 + a, c0) - P(r0 + a - 1, c0)|       (its left column)
+// and BBV_i = T_i + L_i + T_{block below} + L_{block to the right}, the
+// block's own last row / column standing in at the image's bottom / right
+// edge (EB_bj / ER_bi).  The pixel rows are read as whole B-byte vectors,
+// consecutive threads taking consecutive blocks of a block row.
+template <int B>
+ABCS_D void bbv_terms(const SenseArgs& a, int k, int i, int16_t* sT, int16_t* sL, int16_t* sEB, int16_t* sER) {
+    const ImgGeom& g = a.g;
+    const int L = a.L, X0 = a.X0, nS = a.nS;
+    const int bi = i / g.nbw, bj = i - bi * g.nbw;
+    const int64_t p = g.pitch;
+    const uint8_t* blk = a.img + (int64_t)k * g.img_stride + (int64_t)(bi * B) * p + bj * B;
+    constexpr int NW = B / 4;
+    uint32_t top[NW];
+    load_row_words<B>(blk, top);
+    const bool last_row = bi + 1 == g.nbh, last_col = bj + 1 == g.nbw;
+    int T = 0, Lc = 0, R = 0;
+    // the column pairs in chunks of 4 samples, their 8 row loads in flight together
+    for (int j0 = 0; j0 < nS; j0 += 4) {
+        uint32_t r_lo[4][NW], r_hi[4][NW];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int a1 = X0 + min(j0 + jj, nS - 1) * L;
+            load_row_words<B>(blk + (int64_t)(a1 - 1) * p, r_lo[jj]);
+            load_row_words<B>(blk + (int64_t)a1 * p, r_hi[jj]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            if (j0 + jj < nS) {
+                Lc += abs((int)(r_hi[jj][0] & 0xFFu) - (int)(r_lo[jj][0] & 0xFFu));
+                R += abs((int)(r_hi[jj][NW - 1] >> 24) - (int)(r_lo[jj][NW - 1] >> 24));
+            }
+        }
+    }
+    for (int j = 0; j < nS; ++j) {
+        const int a1 = X0 + j * L;
+        T += abs(row_byte(top, a1) - row_byte(top, a1 - 1));
+    }
+    sT[i] = (int16_t)T;
+    sL[i] = (int16_t)Lc;
+    if (last_col) sER[bi] = (int16_t)R;
+    if (last_row) {
+        uint32_t bot[NW];
+        load_row_words<B>(blk + (int64_t)(B - 1) * p, bot);
+        int Bt = 0;
+        for (int j = 0; j < nS; ++j) {
+            const int a1 = X0 + j * L;
+            Bt += abs(row_byte(bot, a1) - row_byte(bot, a1 - 1));
+        }
+        sEB[bj] = (int16_t)Bt;
+    }
+}
+
+template <int CH, int VB>
 __global__ void __launch_bounds__(1024) bbv_image_kernel(SenseArgs a) {
     __shared__ int64_t sh[33];
     __shared__ bool s_last;
+    extern __shared__ __align__(16) int16_t bbv_sm[];   // VB > 0: T, L (n_B each), EB (nbw), ER (nbh)
     griddep_wait();
     // one CTA per image leaves most SMs free: the sensing kernel may start on
     // them now and stage its first pixels (it waits for this grid before it
@@ -113,11 +196,31 @@ __global__ void __launch_bounds__(1024) bbv_image_kernel(SenseArgs a) {
     const int64_t i0 = min(nB, (int64_t)t * ch), i1 = min(nB, i0 + ch);
     int w[CH], m[CH];
     int64_t wsum = 0;
+    if constexpr (VB > 0) {
+        int16_t* sT = bbv_sm;
+        int16_t* sL = sT + nB;
+        int16_t* sEB = sL + nB;
+        int16_t* sER = sEB + a.g.nbw;
+        for (int i = t; i < (int)nB; i += nt) bbv_terms<VB>(a, k, i, sT, sL, sEB, sER);
+        __syncthreads();
 #pragma unroll
-    for (int c = 0; c < CH; ++c) {
-        const int64_t i = i0 + c;
-        w[c] = (i < i1) ? bbv_block(a, k, i) : 0;
-        wsum += w[c];
+        for (int c = 0; c < CH; ++c) {
+            const int i = (int)(i0 + c);
+            w[c] = 0;
+            if (i < i1) {
+                const int bi = i / a.g.nbw, bj = i - bi * a.g.nbw;
+                w[c] = sT[i] + sL[i] + (bi + 1 < a.g.nbh ? sT[i + a.g.nbw] : sEB[bj]) +
+                       (bj + 1 < a.g.nbw ? sL[i + 1] : sER[bi]);
+            }
+            wsum += w[c];
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int64_t i = i0 + c;
+            w[c] = (i < i1) ? bbv_block(a, k, i) : 0;
+            wsum += w[c];
+        }
     }
     const int64_t W = block_sum(wsum, sh);
     const int cap = a.cap;
@@ -179,7 +282,7 @@ __global__ void __launch_bounds__(1024) bbv_image_kernel(SenseArgs a) {
         }
     }
     if (t == 0) a.img_total[k] = total;
-    alloc_finish(a.g.n_img, a.img_total, a.img_base, a.done, sh, &s_last);
+    if (a.pilot_bases) alloc_finish(a.g.n_img, a.img_total, a.img_base, a.done, sh, &s_last);
 }
 
 // Pilot CTAs per image: the number of partial sums the allocation adds up.
@@ -196,16 +299,41 @@ cudaError_t launch_bbv_pilot(const SenseArgs& a, cudaStream_t s) {
     return launch_pdl(bbv_kernel, grid, dim3(256), 0, s, a, 0);
 }
 
+template <int CH, int VB>
+static cudaError_t launch_bbv_image(const SenseArgs& a, cudaStream_t s) {
+    const size_t smem = VB > 0 ? (size_t)(2 * a.g.n_blocks + a.g.nbw + a.g.nbh) * sizeof(int16_t) : 0;
+    cudaError_t e = cudaFuncSetAttribute(bbv_image_kernel<CH, VB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e) return e;
+    return launch_pdl(bbv_image_kernel<CH, VB>, dim3((unsigned)a.g.n_img), dim3(1024), smem, s, a);
+}
+
+template <int CH>
+static cudaError_t launch_bbv_image_b(const SenseArgs& a, cudaStream_t s) {
+    // vector row loads need rows and images aligned to min(B, 16) bytes
+    const uintptr_t al = reinterpret_cast<uintptr_t>(a.img) | (uintptr_t)a.g.pitch |
+                         (uintptr_t)(a.g.n_img > 1 ? a.g.img_stride : 0);
+    const uintptr_t need = (uintptr_t)(a.g.B >= 16 ? 16 : a.g.B) - 1;
+    if ((al & need) == 0) {
+        switch (a.g.B) {
+            case 4: return launch_bbv_image<CH, 4>(a, s);
+            case 8: return launch_bbv_image<CH, 8>(a, s);
+            case 16: return launch_bbv_image<CH, 16>(a, s);
+            case 32: return launch_bbv_image<CH, 32>(a, s);
+        }
+    }
+    return launch_bbv_image<CH, 0>(a, s);
+}
+
 // One CTA per image when its blocks fit 16 per thread (n_B <= 16384), else
 // the block-parallel pilot whose last CTA per image allocates it.
 cudaError_t launch_bbv_alloc(const SenseArgs& a, cudaStream_t s) {
     const int64_t ch = (a.g.n_blocks + 1023) / 1024;
-    const dim3 grid1((unsigned)a.g.n_img);
-    if (ch <= 1) return launch_pdl(bbv_image_kernel<1>, grid1, dim3(1024), 0, s, a);
-    if (ch <= 2) return launch_pdl(bbv_image_kernel<2>, grid1, dim3(1024), 0, s, a);
-    if (ch <= 4) return launch_pdl(bbv_image_kernel<4>, grid1, dim3(1024), 0, s, a);
-    if (ch <= 8) return launch_pdl(bbv_image_kernel<8>, grid1, dim3(1024), 0, s, a);
-    if (ch <= 16) return launch_pdl(bbv_image_kernel<16>, grid1, dim3(1024), 0, s, a);
+    if (ch <= 1) return launch_bbv_image_b<1>(a, s);
+    if (ch <= 2) return launch_bbv_image_b<2>(a, s);
+    if (ch <= 4) return launch_bbv_image_b<4>(a, s);
+    if (ch <= 8) return launch_bbv_image_b<8>(a, s);
+    if (ch <= 16) return launch_bbv_image_b<16>(a, s);
     dim3 grid((unsigned)((a.g.n_blocks + 255) / 256), (unsigned)a.g.n_img);
     return launch_pdl(bbv_kernel, grid, dim3(256), 0, s, a, 1);
 }

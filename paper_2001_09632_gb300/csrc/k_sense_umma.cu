@@ -338,8 +338,14 @@ __global__ void __launch_bounds__(SU_THREADS, 1) sense_umma_kernel(SenseArgs a, 
         }
         __syncwarp();
     } else if (warp == W_META) {
-        // ---- metadata, up to SU_I tiles ahead of the epilogue: lane = blocks lane, lane + 32
+        // ---- metadata, up to SU_I tiles ahead of the epilogue: lane = blocks
+        // lane, lane + 32.  Global offset = image-local offset + the image's
+        // base, derived from the per-image totals: a running base of the
+        // tile's first image (the gap to the next tile summed by the warp)
+        // plus a 64-wide prefix of the totals of the tile's images.
         griddep_wait();
+        int kc = 0;
+        int64_t basec = 0;
         for (int j = 0; j < my_n; ++j) {
             const int is = j % SU_I;
             if (j >= SU_I) {
@@ -349,6 +355,26 @@ __global__ void __launch_bounds__(SU_THREADS, 1) sense_umma_kernel(SenseArgs a, 
             }
             const int64_t b0 = tile_b0(j);
             const int n = (int)(ntot - b0 < NT ? ntot - b0 : NT);
+            const int kseg = (int)(b0 / g.n_blocks);
+            {
+                int64_t v = 0;
+                for (int k = kc + lane; k < kseg; k += 32) v += __ldg(a.img_total + k);
+                basec += warp_sum(v);
+                kc = kseg;
+            }
+            const int64_t ta = kseg + lane < g.n_img ? __ldg(a.img_total + kseg + lane) : 0;
+            const int64_t tb = kseg + 32 + lane < g.n_img ? __ldg(a.img_total + kseg + 32 + lane) : 0;
+            int64_t ia = ta, ib = tb;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t ua = __shfl_up_sync(0xffffffffu, ia, o), ub = __shfl_up_sync(0xffffffffu, ib, o);
+                if (lane >= o) {
+                    ia += ua;
+                    ib += ub;
+                }
+            }
+            ib += __shfl_sync(0xffffffffu, ia, 31);
+            const int64_t ea = ia - ta, eb = ib - tb;     // bases of images kseg + lane, kseg + 32 + lane (minus basec)
             int m[2];
             int64_t off[2];
             bool bad = false;
@@ -357,12 +383,16 @@ __global__ void __launch_bounds__(SU_THREADS, 1) sense_umma_kernel(SenseArgs a, 
                 const int i = lane + 32 * h;
                 m[h] = 0;
                 off[h] = 0;
+                int d = 0;
                 if (i < n) {
                     int k, bi, bj;
                     su_coords(g, b0 + i, k, bi, bj);
+                    d = k - kseg;                      // 0 .. 63
                     m[h] = __ldg(a.counts + b0 + i);
-                    off[h] = __ldg(a.offsets + b0 + i) + __ldg(a.img_base + k);
+                    off[h] = __ldg(a.offsets + b0 + i);
                 }
+                const int64_t xa = __shfl_sync(0xffffffffu, ea, d & 31), xb = __shfl_sync(0xffffffffu, eb, d & 31);
+                if (i < n) off[h] += basec + (d < 32 ? xa : xb);
             }
             const int64_t base = __shfl_sync(0xffffffffu, off[0], 0);
             SuInfo& I = info[is];

@@ -948,9 +948,34 @@ ABCS_D uint32_t px_pair(uint32_t w, int hi2) {
     }
 }
 
+// Image bases of the CTA's images k_first .. k_first + SK_MAX - 1 (when the
+// allocation does not write them): warp 0 sums the totals of the images
+// before k_first and scans those of the CTA's images into kbase[].
+constexpr int SK_MAX = 64;
+ABCS_D void cta_image_bases(const SenseArgs& a, int k_first, int64_t* kbase) {
+    const int lane = threadIdx.x & 31;
+    int64_t v = 0;
+    for (int k = lane; k < k_first; k += 32) v += __ldg(a.img_total + k);
+    int64_t carry = warp_sum(v);
+#pragma unroll
+    for (int h = 0; h < SK_MAX / 32; ++h) {
+        const int k = k_first + 32 * h + lane;
+        const int64_t t = k < a.g.n_img ? __ldg(a.img_total + k) : 0;
+        int64_t incl = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        kbase[32 * h + lane] = carry + incl - t;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+}
+
 // counts and image-local offsets from the allocation, image bases from its
-// last CTA; pos = byte offset of the block's top-left pixel in the input
-ABCS_D MetaRaw sense_meta_load(const SenseArgs& a, const SegGeom& sg) {
+// last CTA or from the CTA's own table; pos = byte offset of the block's
+// top-left pixel in the input
+ABCS_D MetaRaw sense_meta_load(const SenseArgs& a, const SegGeom& sg, const int64_t* kbase, int k_first) {
     const int lane = threadIdx.x & 31;
     MetaRaw r;
     r.off = 0;
@@ -960,7 +985,7 @@ ABCS_D MetaRaw sense_meta_load(const SenseArgs& a, const SegGeom& sg) {
         const int64_t b = sg.b0 + lane;
         int k, bi, bj;
         block_coords(a.g, b, k, bi, bj);
-        r.off = __ldg(a.offsets + b) + __ldg(a.img_base + k);
+        r.off = __ldg(a.offsets + b) + (a.pilot_bases ? __ldg(a.img_base + k) : kbase[k - k_first]);
         r.m = __ldg(a.counts + b);
         r.pos = (int64_t)k * a.g.img_stride + (int64_t)(bi * 16) * a.g.pitch + bj * 16;
     }
@@ -1045,14 +1070,18 @@ __global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int64_t n
     sense_pixels(a, meta[0], pix[0], vec);
     cp_async_commit();
     griddep_wait();
+    __shared__ int64_t kbase[SK_MAX];
+    const int k_first = (int)(r0 / g.n_blocks);
+    if (!a.pilot_bases && warp == 0) cta_image_bases(a, k_first, kbase);
     __syncthreads();                            // meta[0] is rewritten below
     // pixels of segments j + 1 .. j + SDEPTH are in flight while segment j is
     // transformed (the same rings as in reconstruct)
     MetaRaw raw;
     if (warp == 0) {
         for (int d = 0; d < SDEPTH && d < nseg; ++d)
-            sense_meta_store(seg_geom<SEG>(r0, r1, d), sense_meta_load(a, seg_geom<SEG>(r0, r1, d)), meta[d]);
-        if (SDEPTH < nseg) raw = sense_meta_load(a, seg_geom<SEG>(r0, r1, SDEPTH));
+            sense_meta_store(seg_geom<SEG>(r0, r1, d), sense_meta_load(a, seg_geom<SEG>(r0, r1, d), kbase, k_first),
+                             meta[d]);
+        if (SDEPTH < nseg) raw = sense_meta_load(a, seg_geom<SEG>(r0, r1, SDEPTH), kbase, k_first);
     }
     __syncthreads();
 #pragma unroll
@@ -1065,7 +1094,7 @@ __global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int64_t n
         const int jn = j + SDEPTH;
         if (jn < nseg && warp == 0) {
             sense_meta_store(seg_geom<SEG>(r0, r1, jn), raw, meta[mn]);
-            if (jn + 1 < nseg) raw = sense_meta_load(a, seg_geom<SEG>(r0, r1, jn + 1));
+            if (jn + 1 < nseg) raw = sense_meta_load(a, seg_geom<SEG>(r0, r1, jn + 1), kbase, k_first);
         }
         cp_async_wait_group<SDEPTH - 1>();
         __syncthreads();
@@ -1185,6 +1214,16 @@ cudaError_t launch_sense_tc_p(const SenseArgs& a, cudaStream_t s) {
     if (e) return e;
     return launch_pdl(sense_tc_kernel<P>, dim3(grid), dim3(256), kSenseSmem, s, a, ntot);
 }
+
+// The image bases of a CTA's range fit its table when no range of
+// ceil(ntot / grid) blocks spans more than SK_MAX images.
+bool sense_tc_bases_fit(const SenseArgs& a) {
+    const int64_t ntot = (int64_t)a.g.n_img * a.g.n_blocks;
+    int grid = 0;
+    if (grid_segs(sense_tc_kernel<kP16>, ntot, SEG, kSenseSmem, &grid) != cudaSuccess || grid <= 0) return false;
+    const int64_t per = (ntot + grid - 1) / grid;
+    return (per + a.g.n_blocks - 1) / a.g.n_blocks + 1 <= SK_MAX;
+}
 }  // namespace
 
 cudaError_t setup_tc_fragments() {
@@ -1204,6 +1243,8 @@ cudaError_t launch_recon_tc(const ReconArgs& a, cudaStream_t s) {
     }
     return cudaErrorInvalidValue;
 }
+
+bool sense_tc_bases_in_kernel(const SenseArgs& a) { return a.g.B == 16 && sense_tc_bases_fit(a); }
 
 cudaError_t launch_sense_tc(const SenseArgs& a, cudaStream_t s) {
     if (a.g.B != 16) return cudaErrorInvalidValue;
