@@ -345,7 +345,8 @@ def uneven_batch_ida(h, world, max_over_ranks, barrier, n=256, subrate=0.2, iter
     import torch
     from paper_2001_09632_gb300 import abcs, synth
     from paper_2001_09632_gb300.uneven import UnevenBatch
-    ub = UnevenBatch(h, synth.gen_uneven_batch(n, seed), subrate)
+    items = synth.gen_uneven_batch(n, seed)
+    ub = UnevenBatch(h, items, subrate)
     stream = torch.cuda.current_stream()
     for _ in range(2):                     # first call: autotune + capture
         ub.ida(h, iters, abcs.DEN_TIDCT, LAMBDA, DF)
@@ -362,17 +363,14 @@ def uneven_batch_ida(h, world, max_over_ranks, barrier, n=256, subrate=0.2, iter
     ms = max_over_ranks(statistics.median(a.elapsed_time(b) for a, b in ev))
     assert abcs.abcs_sync_status(h) == 0
     psnr = ub.psnr()
-    # the same images, one abcs_ida call per group
-    outs = []
-    for (H, W, B, ni, b0, c0, cap) in ub.groups:
-        Hc, Wc = (H // B) * B, (W // B) * B
-        outs.append(torch.empty((ni, Hc, Wc), dtype=torch.float32, device="cuda"))
+    # the same images, one abcs_sense and one abcs_ida call per (size, B) group
+    groups = ub.per_group_sensing(h, items)
+    outs = [torch.empty((len(ks), (H // B) * B, (W // B) * B), dtype=torch.float32, device="cuda")
+            for (H, W, B, ks, c, o, y) in groups]
 
     def per_group():
-        for (H, W, B, ni, b0, c0, cap), xo in zip(ub.groups, outs):
-            nb = ni * (H // B) * (W // B)
-            abcs.abcs_ida(h, ub.counts[b0:b0 + nb], ub.offsets[b0:b0 + nb + 1], ub.y[c0:c0 + cap], ni, H, W, B,
-                          iters, DF, abcs.DEN_TIDCT, LAMBDA, None, xo, None)
+        for (H, W, B, ks, c, o, y), xo in zip(groups, outs):
+            abcs.abcs_ida(h, c, o, y, len(ks), H, W, B, iters, DF, abcs.DEN_TIDCT, LAMBDA, None, xo, None)
     per_group()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -381,13 +379,30 @@ def uneven_batch_ida(h, world, max_over_ranks, barrier, n=256, subrate=0.2, iter
     e1.record(stream)
     torch.cuda.synchronize()
     ms_groups = max_over_ranks(e0.elapsed_time(e1))
-    same = all(torch.equal(ub.image(k), xo[j]) for ks, xo in zip(ub.members, outs) for j, k in enumerate(ks))
+    same = all(torch.equal(ub.image(k), xo[j]) for (H, W, B, ks, c, o, y), xo in zip(groups, outs)
+               for j, k in enumerate(ks))
+    # sensing the whole batch: one abcs_sense_batch call (two launches)
+    for _ in range(3):
+        ub.sense(h)
+    ev = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ub.sense(h)
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    sense_ms = max_over_ranks(statistics.median(a.elapsed_time(b) for a, b in ev))
+    assert abcs.abcs_sync_status(h) == 0
     return {"value": world * ub.pixels * iters / (ms * 1e-3) / 1e6, "unit": "Mpixel*iter/s",
             "images": n, "mix": "40% 256x256, 40% 512x512, 20% 1024x1024; B cycles 8, 16, 32",
             "subrate": subrate, "variant": "BBV", "iters": iters, "denoiser": "tidct", "lambda": LAMBDA,
             "pixels": ub.pixels, "measurements": ub.measurements, "ms_per_call": ms,
             "launch": "one persistent cooperative kernel per call, CUDA graph replay",
-            "per_group_calls": {"calls": len(ub.groups), "ms": ms_groups,
+            "sensing": {"ms_per_call": sense_ms, "Mpixel_per_s": world * ub.pixels / (sense_ms * 1e-3) / 1e6,
+                        "how": "one abcs_sense_batch call over the 256 images (pilot + allocation launch, "
+                               "sensing launch), FP32"},
+            "per_group_calls": {"calls": len(groups), "ms": ms_groups,
                                 "value": world * ub.pixels * iters / (ms_groups * 1e-3) / 1e6,
                                 "identical_output": same},
             "mean_psnr": sum(psnr) / len(psnr),

@@ -9,6 +9,8 @@
  *   abcs_sense ........... Alg. 1 (AL-DCT-BBV) / Alg. 2 (AL-DCT-DD) / L-DCT-ZZ (Sec. IV):
  *                          pilot estimate (Eq. 19 or Sec. V-B), allocation (Eqs. 22-23),
  *                          zigzag-ordered 2D-DCT measurements (Eq. 26 rows)
+ *   abcs_sense_batch ..... the same over images of different sizes, block sizes,
+ *                          variants and subrates, two launches per batch
  *   abcs_reconstruct ..... the real-time decoder output I_o of Fig. 1: block inverse
  *                          2D-DCT of the zero-filled measurements (Sec. VII-D)
  *   abcs_ida ............. IDA, Eqs. 13, 15, 25 with alpha = 1/D_F (Eq. 28)
@@ -159,6 +161,38 @@ abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int
                        int64_t pitch, int64_t img_stride, int B, double subrate,
                        int variant, int precision, int32_t* counts, int64_t* offsets,
                        float* coeffs, int64_t coeff_capacity, int32_t* pilot, void* stream);
+
+/* One image of an uneven sensing batch (abcs_sense_batch). */
+typedef struct abcs_sense_desc {
+    int32_t H, W, B;         /* image size in pixels, block size (4, 8, 16 or 32) */
+    int32_t variant;         /* abcs_variant */
+    double subrate;          /* (0, 1] */
+    int64_t img_offset;      /* byte offset of the image's first pixel from `img` */
+    int64_t pitch;           /* bytes between the image's rows (>= W) */
+} abcs_sense_desc;
+
+/* Sense a batch of images of different sizes, block sizes, variants and
+ * subrates (Alg. 1 / Alg. 2 per image, as abcs_sense computes them), in two
+ * launches for the whole batch: one for every image's pilot estimate and
+ * allocation (Eq. 19 or Sec. V-B; Eqs. 22-23), one for every image's
+ * measurements (Eq. 26 rows).
+ *   img      [device] uint8; image k at img + desc[k].img_offset, rows desc[k].pitch apart
+ *   desc     [host] n_img descriptors
+ *   counts   [device] int32  [total blocks]      out: m_i per block
+ *   offsets  [device] int64  [total blocks + 1]  out: exclusive prefix of counts over the batch
+ *   coeffs   [device] float  [coeff_capacity]    out: packed measurements
+ *   pilot    [device] int32  [total blocks] or NULL; out: BBV_i / n_i (0 for L-DCT-ZZ)
+ * Image k's blocks follow image k-1's (raster order within an image), so
+ * image k's first block is the sum of n_B over the images before it and its
+ * measurements start at offsets[that block]; total blocks = the sum of the
+ * images' n_B.  The layout is the one abcs_ida_batch reads (block_offset =
+ * the image's first block, coeff_base = 0).  precision: ABCS_FP32 only (a
+ * tensor-core precision returns ABCS_ERR_UNSUPPORTED).  coeff_capacity must
+ * be >= the sum of the images' plan.M, else ABCS_ERR_CAPACITY before any
+ * work.  A descriptor abcs_plan rejects fails the call with that status. */
+abcs_status abcs_sense_batch(abcs_handle* h, const uint8_t* img, const abcs_sense_desc* desc, int n_img,
+                             int precision, int32_t* counts, int64_t* offsets, float* coeffs,
+                             int64_t coeff_capacity, int32_t* pilot, void* stream);
 
 /* Block inverse 2D-DCT of the zero-filled measurements (A^T y, Fig. 1 I_o).
  *   counts, offsets, coeffs [device] as written by abcs_sense

@@ -37,6 +37,11 @@ class abcs_image_desc(C.Structure):
                 ("block_offset", C.c_int64), ("coeff_base", C.c_int64), ("pixel_offset", C.c_int64)]
 
 
+class abcs_sense_desc(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("B", C.c_int32), ("variant", C.c_int32),
+                ("subrate", C.c_double), ("img_offset", C.c_int64), ("pitch", C.c_int64)]
+
+
 class abcs_plan_info(C.Structure):
     _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("B", C.c_int32), ("variant", C.c_int32),
                 ("nbh", C.c_int32), ("nbw", C.c_int32), ("n_blocks", C.c_int64), ("N", C.c_int64),
@@ -60,6 +65,7 @@ _SIGS = {
     "abcs_last_error": [],
     "abcs_plan": [_I, _I, _I, _D, _I, C.POINTER(abcs_plan_info)],
     "abcs_sense": [_P, _P, _I, _I, _I, _L, _L, _I, _D, _I, _I, _P, _P, _P, _L, _P, _P],
+    "abcs_sense_batch": [_P, _P, _P, _I, _I, _P, _P, _P, _L, _P, _P],
     "abcs_reconstruct": [_P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P],
     "abcs_ida": [_P, _P, _P, _P, _I, _I, _I, _I, _I, _D, _I, _D, _P, _P, _P, _P],
     "abcs_denoise_tidct": [_P, _P, _I, _I, _I, _P, _D, _P, _P],
@@ -133,6 +139,14 @@ def abcs_sense(h, img, n_img, H, W, pitch, img_stride, B, subrate, variant, prec
     _check(lib.abcs_sense(h, _ptr(img), n_img, H, W, pitch, img_stride, B, subrate, variant,
                           precision, _ptr(counts), _ptr(offsets), _ptr(coeffs), coeff_capacity,
                           _ptr(pilot), _stream(stream)))
+
+
+def abcs_sense_batch(h, img, descs, precision, counts, offsets, coeffs, coeff_capacity, pilot=None,
+                     stream=None) -> None:
+    """descs: list of (H, W, B, variant, subrate, img_offset, pitch)."""
+    arr = (abcs_sense_desc * len(descs))(*[abcs_sense_desc(H, W, B, v, r, o, p) for (H, W, B, v, r, o, p) in descs])
+    _check(lib.abcs_sense_batch(h, _ptr(img), arr, len(descs), precision, _ptr(counts), _ptr(offsets),
+                                _ptr(coeffs), coeff_capacity, _ptr(pilot), _stream(stream)))
 
 
 def abcs_reconstruct(h, counts, offsets, coeffs, n_img, H, W, B, precision, out=None, out_u8=None,

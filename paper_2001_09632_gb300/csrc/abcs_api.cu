@@ -322,6 +322,90 @@ abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int
     return ABCS_OK;
 }
 
+abcs_status abcs_sense_batch(abcs_handle* h, const uint8_t* img, const abcs_sense_desc* desc, int n_img,
+                             int precision, int32_t* counts, int64_t* offsets, float* coeffs,
+                             int64_t coeff_capacity, int32_t* pilot, void* stream) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    if (!desc) return fail(ABCS_ERR_INVALID_ARG, "NULL descriptors");
+    if (n_img < 1 || n_img > 65535) return fail(ABCS_ERR_INVALID_ARG, "n_img must be in [1, 65535]");
+    if (!img || !counts || !offsets || !coeffs) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (precision < ABCS_FP32 || precision > ABCS_TC_BF16)
+        return fail(ABCS_ERR_INVALID_ARG, "bad precision %d", precision);
+    if (precision != ABCS_FP32)
+        return fail(ABCS_ERR_UNSUPPORTED, "abcs_sense_batch computes in FP32 (mixed block sizes)");
+    std::vector<SenseBatchImg> tab(n_img);
+    int64_t blk = 0, items = 0, tiles = 0, need = 0;
+    for (int k = 0; k < n_img; ++k) {
+        const abcs_sense_desc& d = desc[k];
+        abcs_plan_info p;
+        abcs_status st = make_plan(d.H, d.W, d.B, d.subrate, d.variant, &p);
+        if (st) {
+            const std::string msg = g_err;
+            return fail(st, "descriptor %d: %s", k, msg.c_str());
+        }
+        if (d.pitch < d.W) return fail(ABCS_ERR_INVALID_ARG, "descriptor %d: pitch < W", k);
+        if (d.img_offset < 0) return fail(ABCS_ERR_INVALID_ARG, "descriptor %d: negative img_offset", k);
+        SenseBatchImg& e = tab[k];
+        e.g = make_geom(1, d.H, d.W, d.B, d.pitch, d.pitch * d.H);
+        e.img_off = d.img_offset;
+        e.blk0 = blk;
+        e.variant = d.variant;
+        e.L = p.L; e.X0 = p.X0; e.nS = p.nS; e.m1 = p.m1; e.m_zz = p.m_zz; e.T = p.T; e.cap = p.cap;
+        e.R = p.R;
+        SenseArgs one{};
+        one.g = e.g;
+        one.variant = d.variant;
+        if (d.variant == ABCS_BBV && p.nS > 0) e.mode = 1;
+        else if (d.variant == ABCS_DD) e.mode = 2;
+        else e.mode = d.variant == ABCS_BBV ? 3 : 0;
+        e.cpi = (e.mode == 1 || e.mode == 2) ? pilot_ctas_per_image(one) : 1;
+        e.item0 = (int)items;
+        e.tile0 = (int)tiles;
+        const int NB = kTileCols / d.B;
+        items += e.cpi;
+        tiles += (int64_t)e.g.nbh * ((e.g.nbw + NB - 1) / NB);
+        blk += p.n_blocks;
+        need += p.M;
+        if (blk >= (1LL << 31) || items >= (1LL << 31) || tiles >= (1LL << 31))
+            return fail(ABCS_ERR_INVALID_ARG, "more than 2^31 - 1 blocks in one call");
+    }
+    if (coeff_capacity < need)
+        return fail(ABCS_ERR_CAPACITY, "coeff_capacity %lld < sum of the images' M = %lld",
+                    (long long)coeff_capacity, (long long)need);
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(ABCS_ERR_CUDA, "cannot select the handle's device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Carver c;
+    const size_t o_tab = c.take<SenseBatchImg>(n_img);
+    const size_t o_w = c.take<int32_t>(pilot ? 1 : blk);
+    const size_t o_part = c.take<unsigned long long>(items);
+    const size_t o_tot = c.take<int64_t>(n_img);
+    const size_t o_base = c.take<int64_t>(n_img + 1);
+    abcs_status st = ensure_ws(h, c.off);
+    if (st) return st;
+    ABCS_CUDA(cudaMemcpyAsync(at<SenseBatchImg>(h, o_tab), tab.data(), n_img * sizeof(SenseBatchImg),
+                              cudaMemcpyHostToDevice, s),
+              "upload batch table");
+    SenseBatchArgs b{};
+    b.imgs = at<SenseBatchImg>(h, o_tab);
+    b.n_img = n_img;
+    b.img = img;
+    b.counts = counts;
+    b.offsets = offsets;
+    b.coeffs = coeffs;
+    b.capacity = coeff_capacity;
+    b.w = pilot ? pilot : at<int32_t>(h, o_w);
+    b.wpart = at<unsigned long long>(h, o_part);
+    b.img_total = at<int64_t>(h, o_tot);
+    b.img_base = at<int64_t>(h, o_base);
+    b.done = h->status + 1;
+    b.img_done = h->img_done;
+    b.status = h->status;
+    ABCS_CUDA(launch_pilot_batch(b, (int)items, s), "batch pilot + allocation launch");
+    ABCS_CUDA(launch_sense_batch(b, (int)tiles, s), "batch sensing launch");
+    return ABCS_OK;
+}
+
 abcs_status abcs_reconstruct(abcs_handle* h, const int32_t* counts, const int64_t* offsets,
                              const float* coeffs, int n_img, int H, int W, int B, int precision,
                              float* out, uint8_t* out_u8, void* stream) {

@@ -177,6 +177,63 @@ struct SenseArgs {
     int pilot_bases;     // 1: the allocation writes img_base; 0: the sensing kernel derives the
                          // image bases from img_total itself (tensor-core sensing kernels)
 };
+// Uneven batch (abcs_sense_batch): one entry per image, in batch order.
+struct SenseBatchImg {
+    ImgGeom g;           // the image alone (n_img = 1)
+    int64_t img_off;     // byte offset of its first pixel
+    int64_t blk0;        // its first block in counts / offsets / pilot
+    int variant, L, X0, nS, m1, m_zz, T, cap;
+    int64_t R;
+    int mode;            // pilot: 1 BBV, 2 DD; allocation only: 0 (ZZ), 3 (BBV with n_S = 0)
+    int item0, cpi;      // its first pilot work item and their number
+    int tile0;           // its first sensing tile
+};
+
+struct SenseBatchArgs {
+    const SenseBatchImg* imgs;
+    int n_img;
+    const uint8_t* img;
+    int32_t* counts;
+    int64_t* offsets;
+    float* coeffs;
+    int64_t capacity;
+    int32_t* w;                 // pilot values, one per block
+    unsigned long long* wpart;  // one per pilot work item
+    int64_t* img_total;
+    int64_t* img_base;
+    unsigned* done;
+    unsigned* img_done;
+    uint32_t* status;
+};
+
+// The arguments of image k of a batch as a one-image SenseArgs: its blocks,
+// counts, offsets and pilot values start at the image's first block.
+ABCS_D SenseArgs batch_image_args(const SenseBatchArgs& b, const SenseBatchImg& e, int k) {
+    SenseArgs a{};
+    a.g = e.g;
+    a.img = b.img + e.img_off;
+    a.variant = e.variant;
+    a.precision = ABCS_FP32;
+    a.L = e.L; a.X0 = e.X0; a.nS = e.nS; a.m1 = e.m1; a.m_zz = e.m_zz; a.T = e.T; a.cap = e.cap;
+    a.R = e.R;
+    a.counts = b.counts + e.blk0;
+    a.offsets = b.offsets + e.blk0;
+    a.coeffs = b.coeffs;
+    a.capacity = b.capacity;
+    a.w = b.w + e.blk0;
+    a.wpart = b.wpart + e.item0;
+    a.pilot_cpi = e.cpi;
+    a.img_total = b.img_total + k;
+    a.img_base = b.img_base + k;
+    a.done = b.done;
+    a.img_done = b.img_done + k;
+    a.status = b.status;
+    a.pilot_bases = 0;
+    return a;
+}
+
+cudaError_t launch_pilot_batch(const SenseBatchArgs& b, int n_items, cudaStream_t s);
+cudaError_t launch_sense_batch(const SenseBatchArgs& b, int n_tiles, cudaStream_t s);
 int pilot_ctas_per_image(const SenseArgs& a);
 cudaError_t launch_bbv_pilot(const SenseArgs& a, cudaStream_t s);
 cudaError_t launch_dd_pilot(const SenseArgs& a, cudaStream_t s);

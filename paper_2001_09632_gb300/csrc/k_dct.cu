@@ -30,10 +30,11 @@ __device__ __noinline__ void sense_prologue(const SenseArgs& a, int k, int64_t g
 // measured coefficients scattered into the tile's packed range in smem ->
 // one contiguous, vectorised copy to global memory.
 // ---------------------------------------------------------------------------
+// One tile (block row bi, tile column tx) of image k; last_image: the tile
+// writes the batch total offsets[n_img n_B] after the image's last block.
 template <int B>
-__global__ void __launch_bounds__(256, (B == 16 ? 3 : 4)) sense_pack_kernel(SenseArgs a) {
+ABCS_D void sense_pack_tile(const SenseArgs& a, int k, int bi, int tx, bool last_image, unsigned char* smem) {
     using Tl = Tile<B>;
-    extern __shared__ __align__(16) unsigned char smem[];
     const TileSmem<B> sm(smem, 1);
     float* Ts = sm.Ts;
     float* Ps = sm.P[0];
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(256, (B == 16 ? 3 : 4)) sense_pack_kernel(Sens
     __shared__ int64_t s_gstart;
 
     const ImgGeom& g = a.g;
-    const int k = blockIdx.z, bi = blockIdx.y, bj0 = blockIdx.x * Tl::NB;
+    const int bj0 = tx * Tl::NB;
     const int nblk = min(Tl::NB, g.nbw - bj0);
     const int64_t gi0 = (int64_t)k * g.n_blocks + (int64_t)bi * g.nbw + bj0;
     const int t = threadIdx.x;
@@ -86,14 +87,47 @@ __global__ void __launch_bounds__(256, (B == 16 ? 3 : 4)) sense_pack_kernel(Sens
     }
     __syncthreads();
     if (t < nblk) a.offsets[gi0 + t] = gstart + rel[t];
-    if (k == g.n_img - 1 && bi == g.nbh - 1 && bj0 + nblk == g.nbw && t == 0)
-        a.offsets[(int64_t)g.n_img * g.n_blocks] = gstart + rel[nblk];
+    if (last_image && bi == g.nbh - 1 && bj0 + nblk == g.nbw && t == 0)
+        a.offsets[(int64_t)(k + 1) * g.n_blocks] = gstart + rel[nblk];
     const int total = rel[nblk];
     if (gstart + total > a.capacity) {
         if (t == 0) set_status(a.status, ABCS_DEV_CAPACITY);
         return;
     }
     stage_out(Ps, a.coeffs, gstart, total);
+}
+
+template <int B>
+__global__ void __launch_bounds__(256, (B == 16 ? 3 : 4)) sense_pack_kernel(SenseArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    sense_pack_tile<B>(a, blockIdx.z, blockIdx.y, blockIdx.x, blockIdx.z == a.g.n_img - 1, smem);
+}
+
+// ---------------------------------------------------------------------------
+// Uneven batch (abcs_sense_batch): one launch over the tiles of every image,
+// each CTA finds its image by a binary search over the images' first tiles
+// and runs the tile code of that image's block size with the image's own
+// arguments (blocks, counts and offsets at the image's first block).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) sense_batch_kernel(SenseBatchArgs b) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int lo = 0, hi = b.n_img - 1;               // last image with tile0 <= blockIdx.x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.imgs[mid].tile0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const int k = lo;
+    const SenseBatchImg& e = b.imgs[k];
+    const SenseArgs a = batch_image_args(b, e, k);
+    const int NB = kTileCols / e.g.B, ntx = (e.g.nbw + NB - 1) / NB;
+    const int j = (int)blockIdx.x - e.tile0, bi = j / ntx, tx = j - bi * ntx;
+    const bool last = k == b.n_img - 1;
+    switch (e.g.B) {
+        case 4: sense_pack_tile<4>(a, 0, bi, tx, last, smem); break;
+        case 8: sense_pack_tile<8>(a, 0, bi, tx, last, smem); break;
+        case 16: sense_pack_tile<16>(a, 0, bi, tx, last, smem); break;
+        default: sense_pack_tile<32>(a, 0, bi, tx, last, smem); break;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -181,6 +215,16 @@ cudaError_t launch_recon_B(const ReconArgs& a, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t launch_sense_batch(const SenseBatchArgs& b, int n_tiles, cudaStream_t s) {
+    size_t smem = Tile<4>::smem_bytes(1);
+    smem = Tile<8>::smem_bytes(1) > smem ? Tile<8>::smem_bytes(1) : smem;
+    smem = Tile<16>::smem_bytes(1) > smem ? Tile<16>::smem_bytes(1) : smem;
+    smem = Tile<32>::smem_bytes(1) > smem ? Tile<32>::smem_bytes(1) : smem;
+    cudaError_t e = cudaFuncSetAttribute(sense_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    return launch_pdl(sense_batch_kernel, dim3((unsigned)n_tiles), dim3(256), smem, s, b);
+}
 
 cudaError_t launch_sense_pack(const SenseArgs& a, cudaStream_t s) {
     switch (a.g.B) {

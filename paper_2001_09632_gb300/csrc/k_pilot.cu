@@ -22,15 +22,11 @@ namespace abcs {
 // The loop over the n_S sample positions is unrolled four-fold so that its
 // byte loads are in flight together.  With `fuse`, the last CTA of an image
 // allocates it (Eqs. 22-23) and the last image allocated writes the bases.
-__global__ void __launch_bounds__(256) bbv_kernel(SenseArgs a, int fuse) {
-    __shared__ unsigned long long sh[32];
-    __shared__ int64_t sh2[33];
-    __shared__ int64_t sW;
-    __shared__ bool s_last;
-    griddep_wait();
+// BBV of the blocks [c blockDim.x, (c + 1) blockDim.x) of image k; their sum
+// goes to partial c of the image's ncta partials.
+ABCS_D void bbv_item(const SenseArgs& a, int k, int c, int ncta, unsigned long long* sh) {
     const ImgGeom& g = a.g;
-    const int k = blockIdx.y;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)c * blockDim.x + threadIdx.x;
     unsigned long long v = 0;
     if (i < g.n_blocks) {
         const int B = g.B, L = a.L, X0 = a.X0, nS = a.nS;
@@ -57,8 +53,17 @@ __global__ void __launch_bounds__(256) bbv_kernel(SenseArgs a, int fuse) {
         v = (unsigned long long)s;
     }
     v = block_sum(v, sh);
-    if (threadIdx.x == 0) a.wpart[(int64_t)k * gridDim.x + blockIdx.x] = v;
-    if (fuse) pilot_alloc_tail(a, 1, k, gridDim.x, sh2, &sW, &s_last);
+    if (threadIdx.x == 0) a.wpart[(int64_t)k * ncta + c] = v;
+}
+
+__global__ void __launch_bounds__(256) bbv_kernel(SenseArgs a, int fuse) {
+    __shared__ unsigned long long sh[32];
+    __shared__ int64_t sh2[33];
+    __shared__ int64_t sW;
+    __shared__ bool s_last;
+    griddep_wait();
+    bbv_item(a, blockIdx.y, blockIdx.x, gridDim.x, sh);
+    if (fuse) pilot_alloc_tail(a, 1, blockIdx.y, gridDim.x, sh2, &sW, &s_last);
 }
 
 // ---------------------------------------------------------------------------
@@ -378,23 +383,18 @@ ABCS_D bool dd_exceeds_exact(const uint8_t* blk, int64_t pitch, int u, int v, in
     return d > 0.0;
 }
 
+// n_i of the blocks of tile (block row bi, tile column tx) of image k; their
+// sum goes to partial `slot`.  Ts and zz are the tile's shared buffers
+// (Tile<B>::FLOATS floats, B * B ranks, zz already loaded).
 template <int B>
-__global__ void __launch_bounds__(256, 4) dd_pilot_kernel(SenseArgs a, int fuse) {
+ABCS_D void dd_tile(const SenseArgs& a, int k, int bi, int tx, int64_t slot, float* Ts, const uint16_t* zz,
+                    unsigned long long* sh) {
     using Tl = Tile<B>;
-    __shared__ float Ts[Tl::FLOATS];
-    __shared__ uint16_t zz[B * B];
-    __shared__ unsigned long long sh[32];
-    __shared__ int64_t sh2[33];
-    __shared__ int64_t sW;
-    __shared__ bool s_last;
-
     const ImgGeom& g = a.g;
-    const int k = blockIdx.z, bi = blockIdx.y, bj0 = blockIdx.x * Tl::NB;
+    const int bj0 = tx * Tl::NB;
     const int nblk = min(Tl::NB, g.nbw - bj0);
     const int t = threadIdx.x;
     const uint8_t* img = a.img + (int64_t)k * g.img_stride + (int64_t)(bi * B) * g.pitch;
-    load_zz_table<B>(zz);
-    griddep_wait();
     {
         const int b = t / B, n = t % B;
         float x[B];
@@ -444,7 +444,22 @@ __global__ void __launch_bounds__(256, 4) dd_pilot_kernel(SenseArgs a, int fuse)
         }
     }
     mine = block_sum(mine, sh);
-    if (t == 0) a.wpart[(int64_t)k * gridDim.x * gridDim.y + (int64_t)blockIdx.y * gridDim.x + blockIdx.x] = mine;
+    if (t == 0) a.wpart[slot] = mine;
+}
+
+template <int B>
+__global__ void __launch_bounds__(256, 4) dd_pilot_kernel(SenseArgs a, int fuse) {
+    __shared__ float Ts[Tile<B>::FLOATS];
+    __shared__ uint16_t zz[B * B];
+    __shared__ unsigned long long sh[32];
+    __shared__ int64_t sh2[33];
+    __shared__ int64_t sW;
+    __shared__ bool s_last;
+    load_zz_table<B>(zz);
+    griddep_wait();
+    const int k = blockIdx.z;
+    dd_tile<B>(a, k, blockIdx.y, blockIdx.x,
+               (int64_t)k * gridDim.x * gridDim.y + (int64_t)blockIdx.y * gridDim.x + blockIdx.x, Ts, zz, sh);
     if (fuse) pilot_alloc_tail(a, 2, k, gridDim.x * gridDim.y, sh2, &sW, &s_last);
 }
 
@@ -466,6 +481,82 @@ static cudaError_t launch_dd(const SenseArgs& a, int fuse, cudaStream_t s) {
 }
 
 cudaError_t launch_dd_pilot(const SenseArgs& a, cudaStream_t s) { return launch_dd(a, 0, s); }
+
+// ---------------------------------------------------------------------------
+// Uneven batch (abcs_sense_batch): one launch over the pilot work items of
+// every image (BBV: 256 blocks per item; DD: one tile; L-DCT-ZZ and BBV with
+// n_S = 0: one allocation-only item).  Each CTA finds its image by a binary
+// search over the images' first items; the last item of an image to finish
+// allocates the image (Eqs. 22-23), and the last image allocated turns the
+// per-image totals into the image bases.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) pilot_batch_kernel(SenseBatchArgs b) {
+    extern __shared__ __align__(16) unsigned char pb_smem[];
+    __shared__ unsigned long long sh[32];
+    __shared__ int64_t sh2[33];
+    __shared__ int64_t sW;
+    __shared__ bool s_last;
+    int lo = 0, hi = b.n_img - 1;               // last image with item0 <= blockIdx.x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.imgs[mid].item0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const int k = lo;
+    const SenseBatchImg& e = b.imgs[k];
+    const SenseArgs a = batch_image_args(b, e, k);
+    const int j = (int)blockIdx.x - e.item0;
+    const int B = e.g.B;
+    uint16_t* zz = reinterpret_cast<uint16_t*>(pb_smem);                  // 1024 ranks
+    float* Ts = reinterpret_cast<float*>(pb_smem + 2048);
+    if (e.mode == 2) {
+        switch (B) {
+            case 4: load_zz_table<4>(zz); break;
+            case 8: load_zz_table<8>(zz); break;
+            case 16: load_zz_table<16>(zz); break;
+            default: load_zz_table<32>(zz); break;
+        }
+    }
+    griddep_wait();
+    bool alloc = true;
+    if (e.mode == 1 || e.mode == 2) {
+        if (e.mode == 1) {
+            bbv_item(a, 0, j, e.cpi, sh);
+        } else {
+            const int ntx = (e.g.nbw + kTileCols / B - 1) / (kTileCols / B);
+            const int bi = j / ntx, tx = j - bi * ntx;
+            switch (B) {
+                case 4: dd_tile<4>(a, 0, bi, tx, j, Ts, zz, sh); break;
+                case 8: dd_tile<8>(a, 0, bi, tx, j, Ts, zz, sh); break;
+                case 16: dd_tile<16>(a, 0, bi, tx, j, Ts, zz, sh); break;
+                default: dd_tile<32>(a, 0, bi, tx, j, Ts, zz, sh); break;
+            }
+        }
+        // the last of the image's items allocates it
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = atomicAdd(a.img_done, 1u) == (unsigned)e.cpi - 1;
+        }
+        __syncthreads();
+        alloc = s_last;
+        if (alloc) {
+            __threadfence();
+            if (threadIdx.x == 0) *a.img_done = 0u;
+        }
+    } else {
+        for (int64_t i = threadIdx.x; i < e.g.n_blocks; i += blockDim.x) a.w[i] = 0;   // no pilot values
+    }
+    if (!alloc) return;
+    alloc_image(a.w, a.wpart, e.cpi, e.g.n_blocks, alloc_params(a, e.mode), 0, a.counts, a.offsets, a.img_total,
+                sh2, &sW);
+    alloc_finish(b.n_img, b.img_total, b.img_base, b.done, sh2, &s_last);
+}
+
+cudaError_t launch_pilot_batch(const SenseBatchArgs& b, int n_items, cudaStream_t s) {
+    const size_t smem = 2048 + Tile<32>::FLOATS * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(pilot_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    return launch_pdl(pilot_batch_kernel, dim3((unsigned)n_items), dim3(256), smem, s, b);
+}
 cudaError_t launch_dd_alloc(const SenseArgs& a, cudaStream_t s) { return launch_dd(a, 1, s); }
 
 }  // namespace abcs

@@ -89,19 +89,26 @@ def test_batch_barrier_timeout_is_reported(handle):
 
 
 def test_uneven_batch_module_equals_per_group_ida(handle):
-    """The grouped layout of paper_2001_09632_gb300.uneven (one abcs_sense per
-    (size, B) group, spare offsets entry per group) gives the same images as
-    one abcs_ida call per group."""
+    """paper_2001_09632_gb300.uneven: the whole batch sensed by one
+    abcs_sense_batch call and reconstructed by one abcs_ida_batch call gives
+    the same counts, measurements and images as one abcs_sense and one
+    abcs_ida call per (size, B) group."""
     from paper_2001_09632_gb300.uneven import UnevenBatch
     items = synth.gen_uneven_batch(10, 700, sizes=((64, 64), (96, 128), (128, 192)))
     ub = UnevenBatch(handle, items, 0.2)
     ub.ida(handle, 5, abcs.DEN_TIDCT, 2.3)
     assert abcs.abcs_sync_status(handle) == 0
-    for (H, W, B, ni, b0, c0, cap), ks in zip(ub.groups, ub.members):
-        nb = ni * (H // B) * (W // B)
+    off = ub.offsets.cpu().numpy()
+    for (H, W, B, ks, c, o, y) in ub.per_group_sensing(handle, items):
+        ni, nB = len(ks), (H // B) * (W // B)
+        cg, og = c.cpu().numpy(), o.cpu().numpy()
+        for j, k in enumerate(ks):
+            b0 = ub.block0[k]
+            assert np.array_equal(ub.counts[b0:b0 + nB].cpu().numpy(), cg[j * nB:(j + 1) * nB]), k
+            yb = ub.y[off[b0]:off[b0 + nB]].cpu().numpy()
+            assert np.array_equal(yb, y[og[j * nB]:og[(j + 1) * nB]].cpu().numpy()), k
         xo = torch.empty((ni, (H // B) * B, (W // B) * B), dtype=torch.float32, device="cuda")
-        abcs.abcs_ida(handle, ub.counts[b0:b0 + nb], ub.offsets[b0:b0 + nb + 1], ub.y[c0:c0 + cap], ni, H, W, B,
-                      5, 2.0, abcs.DEN_TIDCT, 2.3, None, xo, None)
+        abcs.abcs_ida(handle, c, o, y, ni, H, W, B, 5, 2.0, abcs.DEN_TIDCT, 2.3, None, xo, None)
         for j, k in enumerate(ks):
             assert torch.equal(ub.image(k), xo[j]), (H, W, B, k)
     assert min(ub.psnr()) > 15.0
