@@ -36,14 +36,15 @@ METRIC = "Mpixel/s ABCS sense+recon and IDA/iter; learned vs plain IDA at equal 
 N_IMG, H, W, B, SUBRATE, SEED = 64, 512, 512, 16, 0.3, 1000
 IDA_ITERS, LAMBDA, DF = 10, 2.3, 2.0
 FLUSH_BYTES = 512 << 20
-# dram__bytes_read.sum + dram__bytes_write.sum of one reconstruct launch on
-# this workload, from an ncu capture of the current kernel (None where none
-# was taken); must be re-measured whenever the kernel changes.  Taken with
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the kernels of
+# one step on this workload, from an ncu capture of the current kernels
+# (None where none was taken); must be re-measured whenever a kernel
+# changes.  Taken with
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
-#       --clock-control none -k regex:recon_tc_kernel -s 2 -c 1
-#       python bench.py --case recon
-# (the same 64 x 512x512 BBV r 0.3 coefficients): 18,112,000 + 10,390,016 bytes
-RECON_TRAFFIC = {"fp16x2": 28502016}
+#       --clock-control none -k regex:"bbv_image|sense_tc_kernel|recon_tc_kernel" -s 3 -c 3
+#       python bench.py --case step
+# (64 x 512x512, BBV r 0.3, FP16x2; ncu flushes the caches before each launch)
+TRAFFIC = {"recon_fp16x2": None, "sense_fp16x2": None}
 
 
 # ---------------------------------------------------------------------------
@@ -158,6 +159,21 @@ def case_sense(h):
     return _timed(sense)
 
 
+def case_step(h):
+    """One step of the bench: abcs_sense + abcs_reconstruct FP16x2, 64 x 512x512, BBV r 0.3."""
+    import torch
+    from paper_2001_09632_gb300 import abcs
+    sense, (c, o, y, n, H, W, B) = _sense_case(h, abcs.BBV, 0.3, abcs.TC_FP16X2)
+    x = torch.empty((n, H, W), device="cuda")
+
+    def step():
+        sense()
+        abcs.abcs_reconstruct(h, c, o, y, n, H, W, B, abcs.TC_FP16X2, x)
+    for _ in range(3):
+        step()
+    return _timed(step)
+
+
 def case_sense_dd(h):
     """abcs_sense FP16x2, 64 x 512x512, DD r 0.3 (DD pilot + allocation + sensing)."""
     from paper_2001_09632_gb300 import abcs
@@ -168,7 +184,7 @@ def case_sense_dd(h):
 
 
 CASES = {"bm3d": case_bm3d, "thi": case_thi, "damp": case_damp, "recon": case_recon, "sense": case_sense,
-         "sense_dd": case_sense_dd}
+         "sense_dd": case_sense_dd, "step": case_step}
 
 
 def run_case(name):
@@ -857,6 +873,16 @@ def main():
         sweep[name] = {"sense_ms": statistics.median(sm), "reconstruct_ms": statistics.median(rm),
                        "Mpixel_per_s": world * N_IMG * plan["N"] / ((statistics.median(sm) +
                                                                     statistics.median(rm)) * 1e-3) / 1e6}
+    # the tcgen05 sensing kernel (basis in tensor memory), same workload
+    os.environ["ABCS_SENSE_TC"] = "umma"
+    for _ in range(3):
+        step(prec)
+    sm, rm = timed_steps(min(K, 200), prec)
+    del os.environ["ABCS_SENSE_TC"]
+    assert abcs.abcs_sync_status(h, s) == 0
+    sweep["tensor_memory_sense"] = {
+        "precision": a.precision, "sense_ms": statistics.median(sm),
+        "kernel": "sense_umma_kernel (ABCS_SENSE_TC=umma; not the default)"}
     # the tcgen05 reconstruct kernel (basis images in tensor memory), same workload
     os.environ["ABCS_RECON_TC"] = "umma"
     for _ in range(3):
@@ -933,6 +959,9 @@ def main():
     barrier()
     e2e_u8_ms = max_over_ranks(ep0.elapsed_time(ep1) / Ke)
     pipe8.close()
+    hbm_peak, peak_kind = _peaks()
+    sweep_sub = subrate_sweep(h, prec, d_img, flush, hbm_peak)
+    latency = single_image_latency(h)
     t_end3 = time.time()
     clocks = clk.stop(t_start, t_end3)
     extras = {}
@@ -953,12 +982,26 @@ def main():
             dist.destroy_process_group()
         return
 
-    hbm_peak, peak_kind = _peaks()
     recon_bytes = 4 * total_coeffs + 12 * N_IMG * nB + 4 * px
     sense_bytes = px + 4 * total_coeffs + 12 * N_IMG * nB
     recon_avg = sum(recon_ms) / K
     sense_avg = sum(sense_ms) / K
-    achieved = recon_bytes / (recon_avg * 1e-3) / 1e9
+    # the roofline object describes the longer of the step's two calls: the
+    # sensing call (pilot + allocation kernel, then the sensing kernel) or
+    # the reconstruct kernel; both are in `kernels`
+    sense_frac = sense_bytes / (sense_avg * 1e-3) / 1e9 / hbm_peak
+    recon_frac = recon_bytes / (recon_avg * 1e-3) / 1e9 / hbm_peak
+    if sense_avg >= recon_avg:
+        dom = {"kernel": "abcs_sense: bbv_image_kernel (pilot + allocation) then "
+                         + ("sense_tc_kernel" if prec != abcs.FP32 else "sense_pack_kernel<16>"),
+               "bytes": sense_bytes, "ms": sense_avg, "traffic": TRAFFIC.get("sense_" + a.precision),
+               "bytes_are": "uint8 image read once + packed FP32 coefficients written + counts and offsets "
+                            "(the pilot's reads of the same pixels are L2 hits and not counted)"}
+    else:
+        dom = {"kernel": "recon_tc_kernel" if prec != abcs.FP32 else "recon_kernel<16>",
+               "bytes": recon_bytes, "ms": recon_avg, "traffic": TRAFFIC.get("recon_" + a.precision),
+               "bytes_are": "packed FP32 coefficients + counts and offsets read, FP32 image written"}
+    achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": K,
         "warmup": a.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -968,17 +1011,21 @@ def main():
                    "precision": a.precision,
                    "value_is": "sense+reconstruct Mpixel/s", "l2": "flushed between timed steps (512 MB write)",
                    "measurements_per_step": total_coeffs, "parallelism": f"replicas x{world}"},
-        "roofline": {"kernel": "recon_tc_kernel" if prec != abcs.FP32 else "recon_kernel<16>", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": dom["kernel"], "bound": "hbm", "achieved": achieved,
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                     "peak_kind": peak_kind, "traffic": RECON_TRAFFIC.get(a.precision),
-                     "traffic_source": "DRAM read + write bytes of one launch of this kernel on this "
-                                       "workload in an ncu capture (most of the FP32 output is still "
-                                       "in L2 when the kernel ends)",
-                     "algorithmic_bytes_per_launch": recon_bytes},
+                     "peak_kind": peak_kind, "traffic": dom["traffic"],
+                     "traffic_source": "DRAM read + write bytes per call of these kernels on this workload "
+                                       "in an ncu capture (cold caches; the step's outputs are still in "
+                                       "L2 when a kernel ends, so they can read below the algorithmic bytes)",
+                     "algorithmic_bytes_per_launch": dom["bytes"], "algorithmic_bytes_are": dom["bytes_are"],
+                     "ms_per_launch": dom["ms"]},
         "kernels": {"sense_ms": sense_avg, "reconstruct_ms": recon_avg,
                     "sense_GBps_algorithmic": sense_bytes / (sense_avg * 1e-3) / 1e9,
-                    "sense_frac_hbm": sense_bytes / (sense_avg * 1e-3) / 1e9 / hbm_peak,
-                    "sense_plus_recon_frac_hbm": (sense_bytes + recon_bytes) / (step_ms * 1e-3) / 1e9 / hbm_peak},
+                    "sense_frac_hbm": sense_frac, "reconstruct_frac_hbm": recon_frac,
+                    "sense_plus_recon_frac_hbm": (sense_bytes + recon_bytes) / (step_ms * 1e-3) / 1e9 / hbm_peak,
+                    "step_bytes_per_pixel": (sense_bytes + recon_bytes) / px},
+        "subrate_sweep": sweep_sub,
+        "single_image_latency": latency,
         "precision_sweep": sweep,
         "ida": {"value": world * px * IDA_ITERS / (ida_ms * 1e-3) / 1e6, "unit": "Mpixel*iter/s",
                 "iters": IDA_ITERS, "denoiser": "tidct", "lambda": LAMBDA, "damping": DF,
