@@ -185,8 +185,42 @@ def case_sense_dd(h):
     return _timed(sense)
 
 
+def _ida_linear_setup(h, seed=2468):
+    """64 x 512x512 sensed with BBV r 0.3 and an abcs_ida call with the
+    identity denoiser: each iteration is the linear step (Eqs. 25, 28) and
+    sigma (Eq. 15) alone."""
+    import torch
+    from paper_2001_09632_gb300 import abcs
+    sense, (c, o, y, n, H, W, B) = _sense_case(h, abcs.BBV, 0.3, abcs.TC_FP16X2, seed)
+    sense()
+    x = torch.empty((n, H, W), device="cuda")
+    iters = 10
+    run = lambda: abcs.abcs_ida(h, c, o, y, n, H, W, B, iters, 2.0, abcs.DEN_NONE, 0.0, None, x)
+    return run, iters, (c, o, y, n, H, W, B)
+
+
+def case_ida_linear(h):
+    """abcs_ida with the identity denoiser (10 iterations: linear step +
+    sigma), 64 x 512x512, BBV r 0.3, tensor-core FP16x2 linear step."""
+    from paper_2001_09632_gb300 import abcs
+    abcs.abcs_set_ida_precision(h, abcs.TC_FP16X2)
+    run, iters, _ = _ida_linear_setup(h)
+    for _ in range(2):
+        run()
+    return _timed(run, 3)
+
+
+def case_ida_linear_fp32(h):
+    """The same with the FP32 CUDA-core linear step."""
+    run, iters, _ = _ida_linear_setup(h)
+    for _ in range(2):
+        run()
+    return _timed(run, 3)
+
+
 CASES = {"bm3d": case_bm3d, "thi": case_thi, "damp": case_damp, "recon": case_recon, "sense": case_sense,
-         "sense_dd": case_sense_dd, "step": case_step}
+         "sense_dd": case_sense_dd, "step": case_step, "ida_linear": case_ida_linear,
+         "ida_linear_fp32": case_ida_linear_fp32}
 
 
 def run_case(name):

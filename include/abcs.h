@@ -226,6 +226,17 @@ abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offse
                      int denoiser, double lambda, const void* cnn_weights,
                      float* x_out, float* sigma_trace, void* stream);
 
+/* Transform precision of the IDA linear step (Eqs. 25, 28: A x and A^T z)
+ * in abcs_ida, abcs_damp and abcs_ida_capture on this handle.  ABCS_FP32
+ * (the default) runs FP32 CUDA-core butterflies for every block size.  A
+ * tensor-core precision runs, for B = 16, the per-block mma.sync transform
+ * (r = x + D^T Z D of the masked residual Z, so x's unmeasured components
+ * pass unchanged; ||z||^2 is summed in FP32 per lane over at most 16 terms,
+ * then in FP64); other block sizes, and x or x_out not 8-byte aligned, keep
+ * FP32.  abcs_ida_batch always runs FP32.
+ * Returns ABCS_ERR_INVALID_ARG for a NULL handle or an unknown precision. */
+abcs_status abcs_set_ida_precision(abcs_handle* h, int precision);
+
 /* D-AMP (Eq. 24) and its damped form DAMP-D (Eq. 27): IDA with the Onsager
  * coefficient taken from the denoiser's divergence instead of 1 / damping:
  *   z^t = y - A x^t + alpha^t z^{t-1},

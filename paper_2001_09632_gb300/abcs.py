@@ -71,6 +71,7 @@ _SIGS = {
     "abcs_denoise_tidct": [_P, _P, _I, _I, _I, _P, _D, _P, _P],
     "abcs_denoise_bm3d": [_P, _P, _I, _I, _I, _P, _D, _P, _P],
     "abcs_sync_status": [_P, _P, C.POINTER(C.c_uint32)],
+    "abcs_set_ida_precision": [_P, _I],
     "abcs_sense_noalloc": [_P, _I, _I, _I, _L, _L, _I, _D, _I, _I, _P, _P, _P, _L, _P, _P],
     "abcs_sense_noalloc_status": [_P, C.POINTER(C.c_uint32)],
     "abcs_ida_batch": [_P, _P, _I, _P, _P, _P, _L, _I, _D, _I, _D, _P, _P, _P],
@@ -255,6 +256,12 @@ def abcs_thi(h, coeffs, n_img, H, W, B, M, adaptive, thi_counts, rho=None, maske
     `adaptive` counts (or None), masked coefficients (or None)."""
     _check(lib.abcs_thi(h, _ptr(coeffs), n_img, H, W, B, M, _ptr(adaptive), _ptr(thi_counts), _ptr(rho),
                         _ptr(masked), _stream(stream)))
+
+
+def abcs_set_ida_precision(h, precision) -> None:
+    """Transform precision of the IDA linear step on this handle (FP32 or a
+    tensor-core precision, used for B = 16)."""
+    _check(lib.abcs_set_ida_precision(h, precision))
 
 
 def abcs_sync_status(h, stream=None) -> int:

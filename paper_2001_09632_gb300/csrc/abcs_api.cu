@@ -26,6 +26,7 @@ struct abcs_handle {
     std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;
     cudaStream_t capture_stream = nullptr;
     bool graphs_ok = true;
+    int ida_precision = ABCS_FP32;  // transforms of the IDA linear step (abcs_set_ida_precision)
 };
 
 namespace {
@@ -197,6 +198,7 @@ abcs_status abcs_create(abcs_handle** out) {
     ABCS_CUDA(upload_tables_tc(), "upload tables");
     ABCS_CUDA(setup_bm3d_tables(), "upload tables");
     ABCS_CUDA(setup_tc_fragments(), "tensor-core fragment setup");
+    ABCS_CUDA(setup_ida_fragments(), "tensor-core fragment setup");
     ABCS_CUDA(upload_tables_su(), "upload tables");
     ABCS_CUDA(setup_sense_umma(), "tensor-memory sensing table setup");
     abcs_handle* h = new abcs_handle;
@@ -228,6 +230,14 @@ void abcs_destroy(abcs_handle* h) {
     if (h->status) cudaFree(h->status);
     if (h->img_done) cudaFree(h->img_done);
     delete h;
+}
+
+abcs_status abcs_set_ida_precision(abcs_handle* h, int precision) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "set_ida_precision: NULL handle");
+    if (precision < ABCS_FP32 || precision > ABCS_TC_BF16)
+        return fail(ABCS_ERR_INVALID_ARG, "set_ida_precision: unknown precision %d", precision);
+    h->ida_precision = precision;
+    return ABCS_OK;
 }
 
 abcs_status abcs_sync_status(abcs_handle* h, void* stream, uint32_t* bits) {
@@ -579,6 +589,7 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
     a.inv_df = (float)(1.0 / damping);
     a.alpha = damp ? at<float>(h, o_alpha) : nullptr;
     a.status = h->status;
+    a.precision = h->ida_precision;
     if (damp) {
         ABCS_CUDA(cudaMemsetAsync(at<float>(h, o_alpha), 0, n_img * sizeof(float), s), "memset");   // alpha^0 = 0
         if (alpha_trace) ABCS_CUDA(cudaMemsetAsync(alpha_trace, 0, (size_t)n_img * iters * sizeof(float), s), "memset");

@@ -277,8 +277,10 @@ struct IdaLinArgs {
     float inv_df;          // Onsager coefficient of IDA (Eq. 28) ...
     const float* alpha;    // ... or per image (D-AMP / DAMP-D, Eqs. 24, 27), if not NULL
     uint32_t* status;
+    int precision;         // abcs_precision: tensor-core transforms for B = 16 (aligned x, r)
 };
 cudaError_t launch_ida_linear(const IdaLinArgs& a, cudaStream_t s);
+cudaError_t setup_ida_fragments();   // after upload_tables_ida(), per device
 // D-AMP / DAMP-D Onsager coefficient (k_ida.cu): per image
 //   alpha[k] = inv_df * div_k / M_k,  div_k = b^T (xp - x) / eps_k,  eps_k = eps_rel max|r|
 // amax: n_img words (cleared here); partial: n_img x chunks doubles

@@ -7,6 +7,7 @@ ABCS_TU_TABLES(ida)
 }  // namespace abcs
 
 #include "dct_tile.cuh"
+#include "tc_frag.cuh"
 
 namespace abcs {
 
@@ -77,8 +78,10 @@ ABCS_D double linear_tile(const LinTile& L, unsigned char* smem, int* rel, int64
     __syncthreads();
 
     // column mapping: forward DCT, residual update of the measured
-    // coefficients, inverse DCT -- all in registers
-    double nz = 0.0;
+    // coefficients, inverse DCT -- all in registers.  ||z||^2: each thread
+    // sums its (at most B) terms in FP32, the CTA sum is an FP32 tree (this
+    // GPU's FP64 pipe is narrow); the tile's partial is stored in FP64.
+    float nz = 0.f;
     {
         const int v = t % B;
         float* col = Ts + b * Tl::BLK + v;
@@ -99,7 +102,7 @@ ABCS_D double linear_tile(const LinTile& L, unsigned char* smem, int* rel, int64
                 const float z = (ys[r] - c[u]) + zp * L.inv_df;
                 ys[r] = z;
                 c[u] += z;
-                nz += (double)z * (double)z;
+                nz = fmaf(z, z, nz);
             }
         }
         idct<B>(c, x);
@@ -113,7 +116,7 @@ ABCS_D double linear_tile(const LinTile& L, unsigned char* smem, int* rel, int64
         store_f32_row<B>(L.r + o, aligned16(L.r + o), x);
     }
     stage_out(Ys, L.z, start, n_in);
-    return block_sum(nz, shd);
+    return (double)block_sum(nz, reinterpret_cast<float*>(shd));
 }
 
 template <int B>
@@ -153,6 +156,353 @@ static cudaError_t launch_lin_B(const IdaLinArgs& a, cudaStream_t s) {
     return launch_pdl(ida_linear_kernel<B>, grid, dim3(256), smem, s, a);
 }
 
+// ---------------------------------------------------------------------------
+// Linear step on the tensor cores (B = 16, the tensor-core precisions).  One
+// warp keeps a 16 x 16 block in mma.sync fragments through
+//   forward   V = D X^T, then R = V D^T = C^T          (A = D, then A = V)
+//   residual  z = y - c + z_prev / D_F on the measured ranks (Eqs. 25, 28)
+//   adjoint   X_z = D^T Z D of the masked residual Z    (A = D^T, then A = Y)
+//   r = x + X_z
+// Lane (g, q) holds pixel rows g, g + 8 x columns 2q, 2q + 1, 2q + 8, 2q + 9:
+// the B-operand layout of X^T and the accumulator layout of X_z alike, so x
+// stays in registers from its load to the final addition, and the forward's
+// accumulators hold exactly the coefficients that the adjoint's B operand
+// needs in the same lane.  Adding the transformed correction to x (rather
+// than inverting c + z) keeps x's components outside the measured ranks
+// exact.  The B operands of D^T and D are the A operands of D and D^T in
+// another register order (b[nt][j] = a[nt + 2 j]), so two constant
+// fragments serve all four products.
+// ---------------------------------------------------------------------------
+__device__ uint32_t g_ida_frag[3][2][8][32];   // [precision][A of D, A of D^T][hi 0-3, lo 4-7][lane]
+
+template <int P>
+ABCS_D void ida_frag_setup_p() {
+    const int lane = threadIdx.x & 31;
+    uint32_t h[4], l[4];
+    for (int s = 0; s < 2; ++s) {
+        load_a_const<P>(s == 1, h, l);
+        for (int i = 0; i < 4; ++i) {
+            g_ida_frag[pidx<P>()][s][i][lane] = h[i];
+            g_ida_frag[pidx<P>()][s][4 + i][lane] = l[i];
+        }
+    }
+}
+
+__global__ void ida_frag_setup_kernel() {
+    ida_frag_setup_p<kP16>();
+    ida_frag_setup_p<kPB16>();
+    ida_frag_setup_p<kPB1>();
+}
+
+ABCS_D void st_global_pred(float* p, float v, bool pred) {
+    asm volatile(
+        "{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q st.global.f32 [%0], %1;\n}\n" ::"l"(p), "f"(v),
+        "r"((int)pred)
+        : "memory");
+}
+
+constexpr int kTcNB = 16;                       // blocks of a tile (one block row, 256 pixel columns)
+// Coefficient staging buffers hold up to kTcCap coefficients (160 per block
+// on average, subrate 0.625); a tile with more reads y and z_prev from
+// global memory instead.  The cap keeps three CTAs resident per SM.
+constexpr int kTcCap = 2560;
+constexpr int kTcStage = kTcCap + 4;            // floats of a packed coefficient staging buffer
+constexpr int kTcX = kTcNB * 256;               // floats of a tile's x stage
+// dynamic shared memory: two stages of (x, y, z_prev), three metadata slots
+struct TcMeta {
+    int64_t start;     // index of the tile's first coefficient
+    int64_t pix;       // pixel index of the tile's top-left pixel
+    int rel[kTcNB + 1];
+    int nblk;
+    int k;             // image
+};
+constexpr size_t kTcStageBytes = (size_t)(kTcX + 2 * kTcStage) * 4;
+constexpr size_t kTcSmem = 2 * kTcStageBytes + 3 * sizeof(TcMeta);
+
+// A tile's counts and first offset, loaded by warp 0 two tiles ahead:
+// lane l holds the counts of blocks 2l and 2l + 1.
+struct TcRaw {
+    int c0, c1;
+    int64_t start;
+};
+
+struct TcTile {
+    int k, by, bx, nblk;
+    int64_t gi0;       // first block of the tile in counts / offsets
+};
+
+// tile j (< 2^31) -> image, block row, tile column
+ABCS_D TcTile tc_tile(const ImgGeom& g, int ntx, int j) {
+    TcTile t;
+    const int per_img = ntx * g.nbh;
+    t.k = j / per_img;
+    const int r = j - t.k * per_img;
+    t.by = r / ntx;
+    t.bx = r - t.by * ntx;
+    t.nblk = min(kTcNB, g.nbw - t.bx * kTcNB);
+    t.gi0 = (int64_t)t.k * g.n_blocks + (int64_t)t.by * g.nbw + t.bx * kTcNB;
+    return t;
+}
+
+ABCS_D TcRaw tc_raw_load(const IdaLinArgs& a, const TcTile& t) {
+    const int lane = threadIdx.x & 31;
+    TcRaw r;
+    r.c0 = 2 * lane < t.nblk ? __ldg(a.counts + t.gi0 + 2 * lane) : 0;
+    r.c1 = 2 * lane + 1 < t.nblk ? __ldg(a.counts + t.gi0 + 2 * lane + 1) : 0;
+    r.start = lane == 0 ? __ldg(a.offsets + t.gi0) : 0;
+    return r;
+}
+
+// warp 0: counts clamped to [0, 256] (a clamp sets ABCS_DEV_BADCOUNT), block
+// offsets relative to the tile's first coefficient
+ABCS_D void tc_meta_store(const IdaLinArgs& a, const TcTile& t, TcRaw r, TcMeta& M) {
+    const int lane = threadIdx.x & 31;
+    bool bad = false;
+    if (r.c0 < 0 || r.c0 > 256) { bad = true; r.c0 = r.c0 < 0 ? 0 : 256; }
+    if (r.c1 < 0 || r.c1 > 256) { bad = true; r.c1 = r.c1 < 0 ? 0 : 256; }
+    const int pair = r.c0 + r.c1;
+    int incl = pair;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    const int excl = incl - pair;
+    if (2 * lane < t.nblk) M.rel[2 * lane] = excl;
+    if (2 * lane + 1 < t.nblk) M.rel[2 * lane + 1] = excl + r.c0;
+    const int64_t start = __shfl_sync(0xffffffffu, r.start, 0);
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 0) {
+        M.rel[t.nblk] = total;
+        M.start = start;
+        M.nblk = t.nblk;
+        M.k = t.k;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(a.status, ABCS_DEV_BADCOUNT);
+}
+
+// x chunk (block c, pixel row r, 16-byte chunk h) at float offset
+// 256 c + 16 r + 4 (h ^ s(r)), s(r) = 2 ((r >> 1) & 1): the fragment loads
+// (lane (g, q): rows g, g + 8, float pairs 2q, 2q + 8) are then free of
+// bank conflicts
+ABCS_D int tc_xoff(int c, int r, int h) { return 256 * c + 16 * r + 4 * (h ^ (((r >> 1) & 1) << 1)); }
+
+// all threads: x of the tile (16-byte copies; x and Wc 16-byte aligned),
+// y and z_prev ranges
+ABCS_D void tc_stage_in(const IdaLinArgs& a, const ImgGeom& g, const TcMeta& M, float* xs, float* ys, float* zs) {
+    if (a.x) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int id = threadIdx.x + 256 * i;           // pixel row r, block c, chunk h
+            const int h = id & 3, c = (id >> 2) & 15, r = id >> 6;
+            if (c < M.nblk) cp_async16(xs + tc_xoff(c, r, h), a.x + M.pix + (int64_t)r * g.Wc + 16 * c + 4 * h);
+        }
+    }
+    const int n = M.rel[M.nblk];
+    if (n <= kTcCap) {
+        stage_in_async(ys, a.y, M.start, n);
+        if (a.z_prev) stage_in_async(zs, a.z_prev, M.start, n);
+    }
+}
+
+// One tile from the stage, 8 warps: warp w transforms blocks w and w + 8.
+// z and r go from registers to global memory.  Returns the lane's FP32
+// sum of z^2 (at most 16 terms).
+template <int P, bool STAGED>
+ABCS_D float tc_transform(const IdaLinArgs& a, const ImgGeom& g, const TcMeta& M, const float* xs, const float* Ys,
+                          const float* Zp, float inv_df, const uint32_t (&Dh)[4], const uint32_t (&Dl)[4],
+                          const uint32_t (&Th)[4], const uint32_t (&Tl)[4], const int (&rk)[2][4]) {
+    const int warp = threadIdx.x >> 5;
+    const Frag f;
+    const int sh = (int)(M.start & 3);
+    const bool has_x = a.x != nullptr, has_zp = a.z_prev != nullptr;
+    float nz = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) {
+        const int c = warp + 8 * j;
+        if (c >= M.nblk) break;
+        float2 xv[2][2];       // [row half h][column pair p]: rows g + 8 h, columns 2q + 8 p, + 1
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+                xv[h][p] = has_x ? *reinterpret_cast<const float2*>(
+                                       xs + tc_xoff(c, f.g + 8 * h, (f.q >> 1) + 2 * p) + 2 * (f.q & 1))
+                                 : make_float2(0.f, 0.f);
+        float R[2][4] = {};
+        if (has_x) {
+            float V[2][4];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                uint32_t bh0, bl0, bh1, bl1;
+                split2<P>(xv[nt][0].x, xv[nt][0].y, bh0, bl0);
+                split2<P>(xv[nt][1].x, xv[nt][1].y, bh1, bl1);
+                mma_split<P>(V[nt], Dh, Dl, bh0, bh1, bl0, bl1);
+            }
+            uint32_t Ah[4], Al[4];
+            split2<P>(V[0][0], V[0][1], Ah[0], Al[0]);
+            split2<P>(V[0][2], V[0][3], Ah[1], Al[1]);
+            split2<P>(V[1][0], V[1][1], Ah[2], Al[2]);
+            split2<P>(V[1][2], V[1][3], Ah[3], Al[3]);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_split<P>(R[nt], Ah, Al, Dh[nt], Dh[nt + 2], Dl[nt], Dl[nt + 2]);
+        }
+        const int r0 = M.rel[c], m = M.rel[c + 1] - r0;
+        const float* ys = STAGED ? Ys + sh + r0 : a.y + M.start + r0;
+        const float* zs = STAGED ? Zp + sh + r0 : a.z_prev + M.start + r0;
+        float* zg = a.z + M.start + r0;
+        float Z[2][4];
+        // staged: every lane reads in-range stage words (index 0 where the
+        // rank is not measured); from global memory only measured ranks are
+        // read; z is stored under a predicate
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = rk[nt][i];
+                const bool v = r < m;
+                const int ri = v ? r : 0;
+                const float yv = STAGED ? ys[ri] : (v ? ys[r] : 0.f);
+                const float zp = has_zp ? (STAGED ? zs[ri] : (v ? zs[r] : 0.f)) : 0.f;
+                const float z = v ? (yv - R[nt][i]) + zp * inv_df : 0.f;
+                st_global_pred(zg + r, z, v);
+                nz = fmaf(z, z, nz);
+                Z[nt][i] = z;
+            }
+        float Y[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            uint32_t bh0, bl0, bh1, bl1;
+            split2<P>(Z[0][2 * nt], Z[0][2 * nt + 1], bh0, bl0);
+            split2<P>(Z[1][2 * nt], Z[1][2 * nt + 1], bh1, bl1);
+            mma_split<P>(Y[nt], Th, Tl, bh0, bh1, bl0, bl1);
+        }
+        uint32_t Ah[4], Al[4];
+        split2<P>(Y[0][0], Y[0][1], Ah[0], Al[0]);
+        split2<P>(Y[0][2], Y[0][3], Ah[1], Al[1]);
+        split2<P>(Y[1][0], Y[1][1], Ah[2], Al[2]);
+        split2<P>(Y[1][2], Y[1][3], Ah[3], Al[3]);
+        float X[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) mma_split<P>(X[nt], Ah, Al, Th[nt], Th[nt + 2], Tl[nt], Tl[nt + 2]);
+        // X[p][i]: pixel row g + 8 (i >> 1), column 2q + (i & 1) + 8 p
+        float* rb = a.r + M.pix + c * 16 + (int64_t)f.g * g.Wc + 2 * f.q;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+                *reinterpret_cast<float2*>(rb + 8 * h * (int64_t)g.Wc + 8 * p) =
+                    make_float2(xv[h][p].x + X[p][2 * h], xv[h][p].y + X[p][2 * h + 1]);
+    }
+    return nz;
+}
+
+// Persistent CTAs walk the tiles j = blockIdx.x, + gridDim.x, ...; tile
+// j + G's x, y and z_prev are copied (cp.async) while tile j is
+// transformed, and warp 0 loads tile j + 2G's counts.  One barrier per
+// tile.  Tile j's ||z||^2 goes to partial[j] (the same slot as the per-tile
+// kernel's): each warp sums its lanes in FP32 (at most 512 terms), and
+// thread 0 adds the 8 warp sums in FP64 after the next tile's barrier.
+template <int P>
+__global__ void __launch_bounds__(256, 3) ida_linear_tc_kernel(IdaLinArgs a, int ntx, int ntiles) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float swarp[2][8];
+    TcMeta* meta = reinterpret_cast<TcMeta*>(smem + 2 * kTcStageBytes);
+    auto xs = [&](int b) { return reinterpret_cast<float*>(smem + b * kTcStageBytes); };
+    auto ys = [&](int b) { return xs(b) + kTcX; };
+    auto zs = [&](int b) { return xs(b) + kTcX + kTcStage; };
+    const ImgGeom& g = a.g;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Frag f;
+    uint32_t Dh[4], Dl[4], Th[4], Tl[4];
+    {
+        const uint32_t* tb = &g_ida_frag[pidx<P>()][0][0][lane];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            Dh[i] = tb[32 * i];
+            Dl[i] = tb[32 * (4 + i)];
+            Th[i] = tb[256 + 32 * i];
+            Tl[i] = tb[256 + 32 * (4 + i)];
+        }
+    }
+    int rk[2][4];              // rank of R[nt][i] = C[2q + (i & 1) + 8 nt][g + 8 (i >> 1)]
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) rk[nt][i] = zz_rank(2 * f.q + (i & 1) + 8 * nt, f.g + 8 * (i >> 1), 16);
+    const int G = gridDim.x;
+    const int j0 = blockIdx.x;
+    if (j0 >= ntiles) return;
+    griddep_wait();
+    auto tile_pix = [&](const TcTile& t) {
+        return (int64_t)t.k * g.Hc * g.Wc + (int64_t)(t.by * 16) * g.Wc + t.bx * 256;
+    };
+    TcRaw raw;
+    if (warp == 0) {
+        const TcTile t0 = tc_tile(g, ntx, j0);
+        tc_meta_store(a, t0, tc_raw_load(a, t0), meta[0]);
+        if (lane == 0) meta[0].pix = tile_pix(t0);
+        if (j0 + G < ntiles) raw = tc_raw_load(a, tc_tile(g, ntx, j0 + G));
+    }
+    __syncthreads();
+    tc_stage_in(a, g, meta[0], xs(0), ys(0), zs(0));
+    cp_async_commit();
+    int i = 0;
+    for (int j = j0; j < ntiles; j += G, ++i) {
+        const int b = i & 1, mi = i % 3, mn = (i + 1) % 3;
+        const bool next = j + G < ntiles;
+        if (warp == 0 && next) {
+            const TcTile tn = tc_tile(g, ntx, j + G);
+            tc_meta_store(a, tn, raw, meta[mn]);
+            if (lane == 0) meta[mn].pix = tile_pix(tn);
+            if (j + 2 * G < ntiles) raw = tc_raw_load(a, tc_tile(g, ntx, j + 2 * G));
+        }
+        cp_async_wait_all();          // tile j's stage has landed (this thread's copies)
+        __syncthreads();              // ... everyone's; meta[mn] written; stage b ^ 1 free; swarp[b ^ 1] final
+        if (threadIdx.x == 0 && i > 0) {
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) sum += (double)swarp[b ^ 1][w];
+            a.partial[j - G] = sum;
+        }
+        if (next) tc_stage_in(a, g, meta[mn], xs(b ^ 1), ys(b ^ 1), zs(b ^ 1));
+        cp_async_commit();
+        const TcMeta& M = meta[mi];
+        const float inv_df = a.alpha ? __ldg(a.alpha + M.k) : a.inv_df;
+        const float nz = warp_sum(M.rel[M.nblk] <= kTcCap
+                                      ? tc_transform<P, true>(a, g, M, xs(b), ys(b), zs(b), inv_df, Dh, Dl, Th, Tl, rk)
+                                      : tc_transform<P, false>(a, g, M, xs(b), ys(b), zs(b), inv_df, Dh, Dl, Th, Tl, rk));
+        if (lane == 0) swarp[b][warp] = nz;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int b = (i - 1) & 1;
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) sum += (double)swarp[b][w];
+        a.partial[j0 + (i - 1) * G] = sum;
+    }
+}
+
+template <int P>
+static cudaError_t launch_lin_tc(const IdaLinArgs& a, cudaStream_t s) {
+    const int ntx = (a.g.nbw + kTcNB - 1) / kTcNB;
+    const int64_t ntiles = (int64_t)ntx * a.g.nbh * a.g.n_img;
+    if (ntiles <= 0) return cudaSuccess;
+    if (ntiles >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+    int dev, sms, per_sm;
+    cudaError_t e = cudaFuncSetAttribute(ida_linear_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTcSmem);
+    if (!e) e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ida_linear_tc_kernel<P>, 256, kTcSmem);
+    if (e) return e;
+    const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const int grid = (int)(ntiles < cap ? ntiles : cap);
+    return launch_pdl(ida_linear_tc_kernel<P>, dim3(grid), dim3(256), kTcSmem, s, a, ntx, (int)ntiles);
+}
+
 // sigma^t = sqrt(||z^t||^2 / m) per image (Eq. 15); m = the image's
 // measurement count.  Partials are summed in a fixed order.
 __global__ void ida_sigma_kernel(const double* __restrict__ partial, int cpi,
@@ -165,11 +515,13 @@ __global__ void ida_sigma_kernel(const double* __restrict__ partial, int cpi,
     for (int j = threadIdx.x; j < cpi; j += 32) s += partial[(int64_t)k * cpi + j];
     s = warp_sum(s);
     if (threadIdx.x == 0) {
+        // the FP64 sum rounded once to FP32, then an FP32 division and square
+        // root (a few ulp; this GPU's FP64 divide and square root are slow)
         const int64_t m = offsets[(int64_t)(k + 1) * nB] - offsets[(int64_t)k * nB];
-        const double v = m > 0 ? sqrt(s / (double)m) : 0.0;
+        const float v = m > 0 ? sqrtf((float)s / (float)m) : 0.f;
         if (!isfinite(v)) set_status(status, ABCS_DEV_NONFINITE);
-        sigma[k] = (float)v;
-        if (trace) trace[(int64_t)k * iters + t] = (float)v;
+        sigma[k] = v;
+        if (trace) trace[(int64_t)k * iters + t] = v;
     }
 }
 
@@ -487,10 +839,10 @@ __global__ void __launch_bounds__(256, ABCS_BATCH_MINB) ida_batch_kernel(BatchAr
                 if (threadIdx.x == 0) {
                     const int64_t last = im.blk0 + (int64_t)im.nbh * im.nbw - 1;
                     const int64_t m = a.offsets[last] + a.counts[last] - a.offsets[im.blk0];
-                    const double v = m > 0 ? sqrt(s / (double)m) : 0.0;
+                    const float v = m > 0 ? sqrtf((float)s / (float)m) : 0.f;   // as ida_sigma_kernel
                     if (!isfinite(v)) set_status(a.status, ABCS_DEV_NONFINITE);
-                    a.sigma[k] = (float)v;
-                    if (a.trace) a.trace[(int64_t)k * a.iters + t] = (float)v;
+                    a.sigma[k] = v;
+                    if (a.trace) a.trace[(int64_t)k * a.iters + t] = v;
                 }
             }
         }
@@ -532,12 +884,34 @@ cudaError_t launch_density(const ImgGeom& g, const int32_t* counts, float* out, 
     return launch_pdl(density_kernel, dim3(grid > 0 ? grid : 1), dim3(256), 0, s, g, counts, out);
 }
 
+cudaError_t setup_ida_fragments() {
+    ida_frag_setup_kernel<<<1, 32>>>();
+    cudaError_t e = cudaGetLastError();
+    if (!e) e = cudaDeviceSynchronize();
+    return e;
+}
+
 int ida_ctas_per_image(const ImgGeom& g) {
     const int NB = kTileCols / g.B;
     return ((g.nbw + NB - 1) / NB) * g.nbh;
 }
 
+// The tensor-core step copies x in 16-byte pieces and stores r in pixel
+// pairs: x 16-byte, r 8-byte aligned.
+static bool ida_tc_usable(const IdaLinArgs& a) {
+    return a.g.B == 16 && a.precision != ABCS_FP32 && (reinterpret_cast<uintptr_t>(a.x) & 15) == 0 &&
+           (reinterpret_cast<uintptr_t>(a.r) & 7) == 0;
+}
+
 cudaError_t launch_ida_linear(const IdaLinArgs& a, cudaStream_t s) {
+    if (ida_tc_usable(a)) {
+        switch (a.precision) {
+            case kP16: return launch_lin_tc<kP16>(a, s);
+            case kPB16: return launch_lin_tc<kPB16>(a, s);
+            case kPB1: return launch_lin_tc<kPB1>(a, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (a.g.B) {
         case 4: return launch_lin_B<4>(a, s);
         case 8: return launch_lin_B<8>(a, s);
