@@ -185,6 +185,41 @@ def case_sense_dd(h):
     return _timed(sense)
 
 
+def ida_linear_step(h, s, counts, offsets, coeffs, x, total_coeffs, iters=10, reps=5):
+    """The IDA linear step (Eqs. 25, 28) plus sigma (Eq. 15) per iteration on
+    the bench workload: abcs_ida with the identity denoiser, FP32 and the
+    tensor-core FP16x2 step.  Algorithmic bytes of an iteration with x and
+    z_prev: x read, r written (8 B/px), y and z_prev read, z written
+    (12 B per measurement)."""
+    import torch
+    from paper_2001_09632_gb300 import abcs
+    n, H, W = x.shape
+    px = n * H * W
+    out = {}
+    for name, prec in (("fp32", abcs.FP32), ("fp16x2", abcs.TC_FP16X2)):
+        abcs.abcs_set_ida_precision(h, prec)
+        run = lambda: abcs.abcs_ida(h, counts, offsets, coeffs, n, H, W, 16, iters, 2.0, abcs.DEN_NONE, 0.0,
+                                    None, x, None, s)
+        run()
+        ev = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(torch.cuda.current_stream())     # s is the current stream's handle
+            run()
+            e1.record(torch.cuda.current_stream())
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        out[name + "_us_per_iteration"] = 1e3 * statistics.median(a.elapsed_time(b) for a, b in ev) / iters
+    abcs.abcs_set_ida_precision(h, abcs.FP32)
+    assert abcs.abcs_sync_status(h, s) == 0
+    bytes_it = 8 * px + 12 * total_coeffs
+    out["bytes_per_iteration"] = bytes_it
+    out["hbm_floor_us"] = None
+    out["how"] = ("abcs_ida, identity denoiser, 10 iterations per call, median of 5 calls / 10; each iteration "
+                  "is the linear kernel and the sigma kernel; iteration 0 reads no x or z_prev")
+    return out
+
+
 def _ida_linear_setup(h, seed=2468):
     """64 x 512x512 sensed with BBV r 0.3 and an abcs_ida call with the
     identity denoiser: each iteration is the linear step (Eqs. 25, 28) and
@@ -951,6 +986,7 @@ def main():
     t_end2 = time.time()
     ida_ms = max_over_ranks(statistics.median(e0.elapsed_time(e1) for e0, e1 in ida_ms))
     assert abcs.abcs_sync_status(h, s) == 0
+    lin = ida_linear_step(h, s, counts, offsets, coeffs, x, total_coeffs)
 
     # ---- end to end through the C ABI with host buffers -------------------
     h_img = torch.from_numpy(imgs).pin_memory()
@@ -1066,6 +1102,9 @@ def main():
         "ida": {"value": world * px * IDA_ITERS / (ida_ms * 1e-3) / 1e6, "unit": "Mpixel*iter/s",
                 "iters": IDA_ITERS, "denoiser": "tidct", "lambda": LAMBDA, "damping": DF,
                 "ms_per_call": ida_ms},
+        "ida_linear": dict(lin, hbm_floor_us=lin["bytes_per_iteration"] / hbm_peak / 1e3,
+                           fp16x2_frac_hbm=lin["bytes_per_iteration"] / (lin["fp16x2_us_per_iteration"] * 1e-6)
+                           / 1e9 / hbm_peak),
         "e2e": {"value": world * px / (e2e_ms * 1e-3) / 1e6, "unit": "Mpixel/s",
                 "h2d_bytes_per_step": int(h_img.numel()), "d2h_bytes_per_step": int(h_rec.numel() * 4),
                 "ms_per_step": e2e_ms,

@@ -605,7 +605,7 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
         a.z = zbuf[t & 1];
         a.r = rbuf[t & 1];
         ABCS_CUDA(launch_ida_linear(a, s), "ida_linear launch");
-        ABCS_CUDA(launch_ida_sigma(g, offsets, a.partial, sig, sigma_trace, iters, t, h->status, s),
+        ABCS_CUDA(launch_ida_sigma(a, sig, sigma_trace, iters, t, s),
                   "ida_sigma launch");
         if (t == capture) {
             ABCS_CUDA(cudaMemcpyAsync(r_cap, a.r, npx * sizeof(float), cudaMemcpyDeviceToDevice, s), "copy r");

@@ -290,8 +290,8 @@ cudaError_t launch_damp_alpha(const ImgGeom& g, const int64_t* offsets, const fl
                               const float* x, const unsigned* amax, float eps_rel, float inv_df, double* partial,
                               float* alpha, float* alpha_trace, int iters, int t, uint32_t* status, cudaStream_t s);
 int damp_chunks(const ImgGeom& g);
-cudaError_t launch_ida_sigma(const ImgGeom& g, const int64_t* offsets, const double* partial,
-                             float* sigma, float* sigma_trace, int iters, int t, uint32_t* status,
+// sigma^t per image from the partials of the linear step just launched with `a`
+cudaError_t launch_ida_sigma(const IdaLinArgs& a, float* sigma, float* sigma_trace, int iters, int t,
                              cudaStream_t s);
 int ida_ctas_per_image(const ImgGeom& g);
 cudaError_t launch_tidct(const float* in, float* out, int n_img, int H, int W, const float* sigma,

@@ -194,11 +194,11 @@ __global__ void ida_frag_setup_kernel() {
     ida_frag_setup_p<kPB1>();
 }
 
-ABCS_D void st_global_pred(float* p, float v, bool pred) {
-    asm volatile(
-        "{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q st.global.f32 [%0], %1;\n}\n" ::"l"(p), "f"(v),
-        "r"((int)pred)
-        : "memory");
+// *p = v if r < m
+ABCS_D void st_global_lt(float* p, float v, int r, int m) {
+    asm volatile("{\n .reg .pred q;\n setp.lt.s32 q, %2, %3;\n @q st.global.f32 [%0], %1;\n}\n" ::"l"(p),
+                 "f"(v), "r"(r), "r"(m)
+                 : "memory");
 }
 
 constexpr int kTcNB = 16;                       // blocks of a tile (one block row, 256 pixel columns)
@@ -305,94 +305,128 @@ ABCS_D void tc_stage_in(const IdaLinArgs& a, const ImgGeom& g, const TcMeta& M, 
     }
 }
 
-// One tile from the stage, 8 warps: warp w transforms blocks w and w + 8.
-// z and r go from registers to global memory.  Returns the lane's FP32
-// sum of z^2 (at most 16 terms).
+// Lane constants of the transform, computed once per thread.
+struct TcLane {
+    uint32_t xo[2][2];     // byte offset in a block's x stage of rows g + 8 h, columns 2q + 8 p, + 1
+    uint32_t rk[2];        // ranks of R[nt][i] = C[2q + (i & 1) + 8 nt][g + 8 (i >> 1)], byte 4 nt + i
+    int ro;                // pixel offset of row g, column 2q in a block (row stride Wc)
+};
+
+ABCS_D int tc_rank(const TcLane& L, int nt, int i) { return (int)((L.rk[nt] >> (8 * i)) & 0xFFu); }
+
+ABCS_D float2 lds_f2(uint32_t a) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+ABCS_D float lds_f(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(a));
+    return v;
+}
+
+// One 16 x 16 block by one warp.  xb: shared address of its x stage
+// (tc_xoff layout, block 0); yb: shared address of its first staged
+// coefficient, z_prev zoff bytes further (STAGED), or yg / zpg: the same
+// coefficients in global memory; zg: its z; rb: r at its top-left pixel plus
+// the lane offset ro, rows 8 apart at rb8.  Returns the lane's FP32 sum of
+// z^2 (at most 8 terms).
 template <int P, bool STAGED>
-ABCS_D float tc_transform(const IdaLinArgs& a, const ImgGeom& g, const TcMeta& M, const float* xs, const float* Ys,
-                          const float* Zp, float inv_df, const uint32_t (&Dh)[4], const uint32_t (&Dl)[4],
-                          const uint32_t (&Th)[4], const uint32_t (&Tl)[4], const int (&rk)[2][4]) {
+ABCS_D float tc_block(uint32_t xb, uint32_t yb, uint32_t zoff, const float* yg, const float* zpg, float* zg,
+                      float* rb, float* rb8, int m, float inv_df, bool has_x, bool has_zp, const uint32_t (&Dh)[4],
+                      const uint32_t (&Dl)[4], const uint32_t (&Th)[4], const uint32_t (&Tl)[4], const TcLane& ln) {
+    float R[2][4] = {};
+    if (has_x) {
+        float V[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const float2 x0 = lds_f2(xb + ln.xo[nt][0]), x1 = lds_f2(xb + ln.xo[nt][1]);
+            uint32_t bh0, bl0, bh1, bl1;
+            split2<P>(x0.x, x0.y, bh0, bl0);
+            split2<P>(x1.x, x1.y, bh1, bl1);
+            mma_split<P>(V[nt], Dh, Dl, bh0, bh1, bl0, bl1);
+        }
+        uint32_t Ah[4], Al[4];
+        split2<P>(V[0][0], V[0][1], Ah[0], Al[0]);
+        split2<P>(V[0][2], V[0][3], Ah[1], Al[1]);
+        split2<P>(V[1][0], V[1][1], Ah[2], Al[2]);
+        split2<P>(V[1][2], V[1][3], Ah[3], Al[3]);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) mma_split<P>(R[nt], Ah, Al, Dh[nt], Dh[nt + 2], Dl[nt], Dl[nt + 2]);
+    }
+    float nz = 0.f;
+    float Z[2][4];
+    // staged: every lane reads in-range stage words (index 0 where the rank
+    // is not measured); from global memory only measured ranks are read; z
+    // is stored under a predicate
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = tc_rank(ln, nt, i);
+            const bool v = r < m;
+            float yv, zp;
+            if (STAGED) {
+                const uint32_t ad = yb + 4u * (uint32_t)(v ? r : 0);
+                yv = lds_f(ad);
+                zp = has_zp ? lds_f(ad + zoff) : 0.f;
+            } else {
+                yv = v ? yg[r] : 0.f;
+                zp = (has_zp && v) ? zpg[r] : 0.f;
+            }
+            const float z = v ? (yv - R[nt][i]) + zp * inv_df : 0.f;
+            st_global_lt(zg + r, z, r, m);
+            nz = fmaf(z, z, nz);
+            Z[nt][i] = z;
+        }
+    float Y[2][4];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        uint32_t bh0, bl0, bh1, bl1;
+        split2<P>(Z[0][2 * nt], Z[0][2 * nt + 1], bh0, bl0);
+        split2<P>(Z[1][2 * nt], Z[1][2 * nt + 1], bh1, bl1);
+        mma_split<P>(Y[nt], Th, Tl, bh0, bh1, bl0, bl1);
+    }
+    uint32_t Ah[4], Al[4];
+    split2<P>(Y[0][0], Y[0][1], Ah[0], Al[0]);
+    split2<P>(Y[0][2], Y[0][3], Ah[1], Al[1]);
+    split2<P>(Y[1][0], Y[1][1], Ah[2], Al[2]);
+    split2<P>(Y[1][2], Y[1][3], Ah[3], Al[3]);
+    float X[2][4];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) mma_split<P>(X[nt], Ah, Al, Th[nt], Th[nt + 2], Tl[nt], Tl[nt + 2]);
+    // r = x + X_z; X[p][i]: pixel row g + 8 (i >> 1), column 2q + (i & 1) + 8 p
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const float2 xv = has_x ? lds_f2(xb + ln.xo[h][p]) : make_float2(0.f, 0.f);
+            *reinterpret_cast<float2*>((h ? rb8 : rb) + 8 * p) =
+                make_float2(xv.x + X[p][2 * h], xv.y + X[p][2 * h + 1]);
+        }
+    return nz;
+}
+
+// One tile from the stage, 8 warps: warp w transforms blocks w and w + 8.
+// xs, ys: shared addresses of the stage's x and y buffers (z_prev follows y
+// at kTcStage floats).  Returns the lane's FP32 sum of z^2 (at most 16 terms).
+template <int P, bool STAGED>
+ABCS_D float tc_transform(const IdaLinArgs& a, const ImgGeom& g, const TcMeta& M, uint32_t xs, uint32_t ys,
+                          float inv_df, const uint32_t (&Dh)[4], const uint32_t (&Dl)[4], const uint32_t (&Th)[4],
+                          const uint32_t (&Tl)[4], const TcLane& ln) {
     const int warp = threadIdx.x >> 5;
-    const Frag f;
-    const int sh = (int)(M.start & 3);
-    const bool has_x = a.x != nullptr, has_zp = a.z_prev != nullptr;
+    const uint32_t sh = (uint32_t)(M.start & 3);
     float nz = 0.f;
 #pragma unroll 1
     for (int j = 0; j < 2; ++j) {
         const int c = warp + 8 * j;
         if (c >= M.nblk) break;
-        float2 xv[2][2];       // [row half h][column pair p]: rows g + 8 h, columns 2q + 8 p, + 1
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int p = 0; p < 2; ++p)
-                xv[h][p] = has_x ? *reinterpret_cast<const float2*>(
-                                       xs + tc_xoff(c, f.g + 8 * h, (f.q >> 1) + 2 * p) + 2 * (f.q & 1))
-                                 : make_float2(0.f, 0.f);
-        float R[2][4] = {};
-        if (has_x) {
-            float V[2][4];
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-                uint32_t bh0, bl0, bh1, bl1;
-                split2<P>(xv[nt][0].x, xv[nt][0].y, bh0, bl0);
-                split2<P>(xv[nt][1].x, xv[nt][1].y, bh1, bl1);
-                mma_split<P>(V[nt], Dh, Dl, bh0, bh1, bl0, bl1);
-            }
-            uint32_t Ah[4], Al[4];
-            split2<P>(V[0][0], V[0][1], Ah[0], Al[0]);
-            split2<P>(V[0][2], V[0][3], Ah[1], Al[1]);
-            split2<P>(V[1][0], V[1][1], Ah[2], Al[2]);
-            split2<P>(V[1][2], V[1][3], Ah[3], Al[3]);
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) mma_split<P>(R[nt], Ah, Al, Dh[nt], Dh[nt + 2], Dl[nt], Dl[nt + 2]);
-        }
         const int r0 = M.rel[c], m = M.rel[c + 1] - r0;
-        const float* ys = STAGED ? Ys + sh + r0 : a.y + M.start + r0;
-        const float* zs = STAGED ? Zp + sh + r0 : a.z_prev + M.start + r0;
-        float* zg = a.z + M.start + r0;
-        float Z[2][4];
-        // staged: every lane reads in-range stage words (index 0 where the
-        // rank is not measured); from global memory only measured ranks are
-        // read; z is stored under a predicate
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = rk[nt][i];
-                const bool v = r < m;
-                const int ri = v ? r : 0;
-                const float yv = STAGED ? ys[ri] : (v ? ys[r] : 0.f);
-                const float zp = has_zp ? (STAGED ? zs[ri] : (v ? zs[r] : 0.f)) : 0.f;
-                const float z = v ? (yv - R[nt][i]) + zp * inv_df : 0.f;
-                st_global_pred(zg + r, z, v);
-                nz = fmaf(z, z, nz);
-                Z[nt][i] = z;
-            }
-        float Y[2][4];
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            uint32_t bh0, bl0, bh1, bl1;
-            split2<P>(Z[0][2 * nt], Z[0][2 * nt + 1], bh0, bl0);
-            split2<P>(Z[1][2 * nt], Z[1][2 * nt + 1], bh1, bl1);
-            mma_split<P>(Y[nt], Th, Tl, bh0, bh1, bl0, bl1);
-        }
-        uint32_t Ah[4], Al[4];
-        split2<P>(Y[0][0], Y[0][1], Ah[0], Al[0]);
-        split2<P>(Y[0][2], Y[0][3], Ah[1], Al[1]);
-        split2<P>(Y[1][0], Y[1][1], Ah[2], Al[2]);
-        split2<P>(Y[1][2], Y[1][3], Ah[3], Al[3]);
-        float X[2][4];
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) mma_split<P>(X[nt], Ah, Al, Th[nt], Th[nt + 2], Tl[nt], Tl[nt + 2]);
-        // X[p][i]: pixel row g + 8 (i >> 1), column 2q + (i & 1) + 8 p
-        float* rb = a.r + M.pix + c * 16 + (int64_t)f.g * g.Wc + 2 * f.q;
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int p = 0; p < 2; ++p)
-                *reinterpret_cast<float2*>(rb + 8 * h * (int64_t)g.Wc + 8 * p) =
-                    make_float2(xv[h][p].x + X[p][2 * h], xv[h][p].y + X[p][2 * h + 1]);
+        float* rb = a.r + M.pix + c * 16 + ln.ro;
+        nz += tc_block<P, STAGED>(xs + 1024u * (uint32_t)c, ys + 4u * (sh + (uint32_t)r0), 4u * kTcStage,
+                                  a.y + M.start + r0, a.z_prev + M.start + r0, a.z + M.start + r0, rb,
+                                  rb + 8 * (int64_t)g.Wc, m, inv_df, a.x != nullptr, a.z_prev != nullptr, Dh, Dl,
+                                  Th, Tl, ln);
     }
     return nz;
 }
@@ -401,8 +435,9 @@ ABCS_D float tc_transform(const IdaLinArgs& a, const ImgGeom& g, const TcMeta& M
 // j + G's x, y and z_prev are copied (cp.async) while tile j is
 // transformed, and warp 0 loads tile j + 2G's counts.  One barrier per
 // tile.  Tile j's ||z||^2 goes to partial[j] (the same slot as the per-tile
-// kernel's): each warp sums its lanes in FP32 (at most 512 terms), and
-// thread 0 adds the 8 warp sums in FP64 after the next tile's barrier.
+// kernel's) in FP64: each warp sums its lanes in FP32 (at most 512 terms),
+// and thread 0 adds the 8 warp sums in FP32 after the next tile's barrier
+// (FP64 adds there held warp 0 back and the other warps at the barrier).
 template <int P>
 __global__ void __launch_bounds__(256, 3) ida_linear_tc_kernel(IdaLinArgs a, int ntx, int ntiles) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -425,11 +460,21 @@ __global__ void __launch_bounds__(256, 3) ida_linear_tc_kernel(IdaLinArgs a, int
             Tl[i] = tb[256 + 32 * (4 + i)];
         }
     }
-    int rk[2][4];              // rank of R[nt][i] = C[2q + (i & 1) + 8 nt][g + 8 (i >> 1)]
+    TcLane ln;
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
+    for (int nt = 0; nt < 2; ++nt) {
+        uint32_t w = 0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) rk[nt][i] = zz_rank(2 * f.q + (i & 1) + 8 * nt, f.g + 8 * (i >> 1), 16);
+        for (int i = 0; i < 4; ++i)
+            w |= (uint32_t)zz_rank(2 * f.q + (i & 1) + 8 * nt, f.g + 8 * (i >> 1), 16) << (8 * i);
+        ln.rk[nt] = w;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+            ln.xo[h][p] = 4u * (uint32_t)(tc_xoff(0, f.g + 8 * h, (f.q >> 1) + 2 * p) + 2 * (f.q & 1));
+    ln.ro = f.g * a.g.Wc + 2 * f.q;
     const int G = gridDim.x;
     const int j0 = blockIdx.x;
     if (j0 >= ntiles) return;
@@ -460,28 +505,29 @@ __global__ void __launch_bounds__(256, 3) ida_linear_tc_kernel(IdaLinArgs a, int
         cp_async_wait_all();          // tile j's stage has landed (this thread's copies)
         __syncthreads();              // ... everyone's; meta[mn] written; stage b ^ 1 free; swarp[b ^ 1] final
         if (threadIdx.x == 0 && i > 0) {
-            double sum = 0.0;
+            float sum = 0.f;
 #pragma unroll
-            for (int w = 0; w < 8; ++w) sum += (double)swarp[b ^ 1][w];
-            a.partial[j - G] = sum;
+            for (int w = 0; w < 8; ++w) sum += swarp[b ^ 1][w];
+            a.partial[j - G] = (double)sum;
         }
         if (next) tc_stage_in(a, g, meta[mn], xs(b ^ 1), ys(b ^ 1), zs(b ^ 1));
         cp_async_commit();
         const TcMeta& M = meta[mi];
         const float inv_df = a.alpha ? __ldg(a.alpha + M.k) : a.inv_df;
+        const uint32_t xsa = (uint32_t)__cvta_generic_to_shared(xs(b)), ysa = (uint32_t)__cvta_generic_to_shared(ys(b));
         const float nz = warp_sum(M.rel[M.nblk] <= kTcCap
-                                      ? tc_transform<P, true>(a, g, M, xs(b), ys(b), zs(b), inv_df, Dh, Dl, Th, Tl, rk)
-                                      : tc_transform<P, false>(a, g, M, xs(b), ys(b), zs(b), inv_df, Dh, Dl, Th, Tl, rk));
+                                      ? tc_transform<P, true>(a, g, M, xsa, ysa, inv_df, Dh, Dl, Th, Tl, ln)
+                                      : tc_transform<P, false>(a, g, M, xsa, ysa, inv_df, Dh, Dl, Th, Tl, ln));
         if (lane == 0) swarp[b][warp] = nz;
     }
     cp_async_wait_all();
     __syncthreads();
     if (threadIdx.x == 0) {
         const int b = (i - 1) & 1;
-        double sum = 0.0;
+        float sum = 0.f;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) sum += (double)swarp[b][w];
-        a.partial[j0 + (i - 1) * G] = sum;
+        for (int w = 0; w < 8; ++w) sum += swarp[b][w];
+        a.partial[j0 + (i - 1) * G] = (double)sum;
     }
 }
 
@@ -921,11 +967,12 @@ cudaError_t launch_ida_linear(const IdaLinArgs& a, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_ida_sigma(const ImgGeom& g, const int64_t* offsets, const double* partial,
-                             float* sigma, float* sigma_trace, int iters, int t, uint32_t* status,
+cudaError_t launch_ida_sigma(const IdaLinArgs& a, float* sigma, float* sigma_trace, int iters, int t,
                              cudaStream_t s) {
-    return launch_pdl(ida_sigma_kernel, dim3(g.n_img), dim3(32), 0, s, partial, ida_ctas_per_image(g), offsets,
-                      (int64_t)g.n_blocks, sigma, sigma_trace, iters, t, status);
+    const ImgGeom& g = a.g;
+    return launch_pdl(ida_sigma_kernel, dim3(g.n_img), dim3(32), 0, s, (const double*)a.partial,
+                      ida_ctas_per_image(g), a.offsets, (int64_t)g.n_blocks, sigma, sigma_trace, iters, t,
+                      a.status);
 }
 
 int damp_chunks(const ImgGeom& g) {

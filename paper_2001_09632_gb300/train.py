@@ -205,6 +205,24 @@ def train(h, R, C, S, D, steps=4000, batch=128, lr=1e-3, seed=1, params=None, lo
     return p.cpu().numpy(), hist, time.time() - t0
 
 
+def trajectory_psnr(h, weights, n=16, H=512, W=512, subrates=(0.1, 0.3), iters=(1, 2, 3, 4, 6),
+                    seed=TUNE_SEED + 500, log=print):
+    """Mean PSNR of learned IDA after each iteration count on n tuning images
+    (disjoint from the training and evaluation seeds): the check that the
+    network stays useful along its own trajectory."""
+    p = torch.tensor(weights, device="cuda")
+    packed = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
+    abcs.abcs_cnn_pack(h, p, packed)
+    imgs = synth.gen_batch(n, H, W, seed)
+    out = {}
+    for r in subrates:
+        sd = Sensed(h, imgs, 16, r, abcs.BBV)
+        out[str(r)] = {str(t): float(psnr(sd.ida(h, t, abcs.DEN_CNN, DEFAULT_LAMBDA, packed), sd.clean).mean())
+                       for t in iters}
+    log("trajectory psnr " + json.dumps(out))
+    return out
+
+
 def tune_lambda(h, n=16, H=512, W=512, iters=30, grid=None, log=print):
     grid = grid or [round(2.0 + 0.1 * i, 1) for i in range(16)]
     imgs = synth.gen_batch(n, H, W, TUNE_SEED)
@@ -378,8 +396,11 @@ def main():
     ap.add_argument("--report", default=None, help="write a JSON report here")
     ap.add_argument("--captures-a", default="0,0,0,1,2,3,5,8,15,29",
                     help="IDA iterations whose denoiser inputs form the phase-A crops (repeat to weight)")
-    ap.add_argument("--captures-b", default="0,0,1,2,3,5",
+    ap.add_argument("--captures-b", default="0,1,1,2,2,3,4,6",
                     help="iterations captured along the network's own trajectories (phase B)")
+    ap.add_argument("--rounds", type=int, default=3, help="phase B rounds (own trajectories, fine-tuning)")
+    ap.add_argument("--init", default=None, help="train: start phase B from these weights (no phase A)")
+    ap.add_argument("--round-steps", type=int, default=5000, help="Adam steps per phase B round")
     ap.add_argument("--large-every", type=int, default=3,
                     help="every n-th training batch of large images (0: none)")
     ap.add_argument("--large-size", default="1088,1920", help="H,W of the large training images")
@@ -395,24 +416,41 @@ def main():
         caps_a = tuple(int(x) for x in a.captures_a.split(","))
         caps_b = tuple(int(x) for x in a.captures_b.split(","))
         large = tuple(int(x) for x in a.large_size.split(","))
-        R, C, S, D = make_pairs(h, n_images=a.images, lam=a.lam, captures=caps_a, crops=48,
-                                large_every=a.large_every, large_size=large)
-        print(f"phase A: {R.shape[0]} training crops")
-        w, hist_a, secs_a = train(h, R, C, S, D, steps=a.steps)
-        # phase B: add inputs along the network's own IDA trajectories, fine-tune
+        if a.init:
+            # continue from trained weights: phase B rounds only
+            w, hist_a, secs_a = load_weights(a.init), [], 0.0
+            R = C = D = torch.empty((0, 64, 64), dtype=torch.float32, device="cuda")
+            S = torch.empty(0, dtype=torch.float32, device="cuda")
+        else:
+            R, C, S, D = make_pairs(h, n_images=a.images, lam=a.lam, captures=caps_a, crops=48,
+                                    large_every=a.large_every, large_size=large)
+            print(f"phase A: {R.shape[0]} training crops")
+            w, hist_a, secs_a = train(h, R, C, S, D, steps=a.steps)
+        report["train"] = {"phase_a_crops": int(R.shape[0]), "steps": [a.steps], "seconds": secs_a,
+                           "loss": {"A": hist_a}, "rounds": []}
+        report["train"]["rounds"].append({"round": 0, "trajectory_psnr": trajectory_psnr(h, w)})
+        # phase B, in rounds: inputs along the network's own IDA trajectories
+        # (Eq. 13 with the Onsager term of Eq. 28), captured with the current
+        # weights on fresh images, join the training set, and the network is
+        # fine-tuned; each round sees the trajectories its predecessor made
         pk = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
-        abcs.abcs_cnn_pack(h, torch.tensor(w, device="cuda"), pk)
-        R2, C2, S2, D2 = make_pairs(h, n_images=a.images // 2, lam=a.lam, captures=caps_b, crops=96,
-                                    seed=TRAIN_SEED + 5_000_000, packed=pk, large_every=a.large_every,
-                                    large_size=large)
-        R, C, S, D = torch.cat([R, R2]), torch.cat([C, C2]), torch.cat([S, S2]), torch.cat([D, D2])
-        del R2, C2, S2, D2
-        print(f"phase B: {R.shape[0]} training crops")
-        w, hist_b, secs_b = train(h, R, C, S, D, steps=a.steps, lr=3e-4, params=w, seed=2)
-        os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
-        w.astype("<f4").tofile(a.out)
-        report["train"] = {"crops": int(R.shape[0]), "steps": [a.steps, a.steps], "seconds": secs_a + secs_b,
-                           "loss": {"A": hist_a, "B": hist_b}}
+        for rnd in range(1, a.rounds + 1):
+            abcs.abcs_cnn_pack(h, torch.tensor(w, device="cuda"), pk)
+            R2, C2, S2, D2 = make_pairs(h, n_images=a.images // 2, lam=a.lam, captures=caps_b, crops=64,
+                                        seed=TRAIN_SEED + 5_000_000 * rnd, packed=pk, large_every=a.large_every,
+                                        large_size=large)
+            R, C, S, D = torch.cat([R, R2]), torch.cat([C, C2]), torch.cat([S, S2]), torch.cat([D, D2])
+            del R2, C2, S2, D2
+            print(f"phase B round {rnd}: {R.shape[0]} training crops")
+            w, hist_b, secs_b = train(h, R, C, S, D, steps=a.round_steps, lr=3e-4, params=w, seed=1 + rnd)
+            report["train"]["rounds"].append({"round": rnd, "crops": int(R.shape[0]), "seconds": secs_b,
+                                              "loss": hist_b, "trajectory_psnr": trajectory_psnr(h, w)})
+            report["train"]["seconds"] += secs_b
+            os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+            w.astype("<f4").tofile(a.out)
+            if a.report:
+                with open(a.report, "w") as f:
+                    json.dump(report, f, indent=1)
         del R, C, S, D
         torch.cuda.empty_cache()
     if a.cmd in ("eval", "all"):
