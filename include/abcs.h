@@ -322,10 +322,13 @@ abcs_status abcs_denoise_bm3d(abcs_handle* h, const float* in, int n_img, int H,
 /* Learned denoiser.  The paper plugs a pretrained 17-layer DnCNN into IDA
  * (Sec. VI-4); this library's learned denoiser is a smaller residual CNN of
  * the same kind, trained with the calls below:
- *   conv3x3 3->32 + ReLU, 6 x [conv3x3 32->32 + ReLU], conv3x3 32->1,
- *   x_hat = r - 255 * net(r / 255, sigma / 255, d)   (zero 'same' padding),
+ *   conv3x3 4->32 + ReLU, 6 x [conv3x3 32->32 + ReLU], conv3x3 32->1,
+ *   x_hat = r - 255 * net(r / 255, sigma / 255, d, tau)   (zero 'same' padding),
  *   d = the measured fraction m_i / B^2 of the pixel's block (abcs_density_map;
- *   abcs_ida builds it from the counts; NULL means d = 0).
+ *   abcs_ida builds it from the counts; NULL means d = 0),
+ *   tau = the iteration input, constant per image: abcs_ida and abcs_damp
+ *   pass tau = min(t, 8) / 8 in iteration t (0 for the first denoising of
+ *   A^T y); the calls below take it per image (NULL means 0).
  * Parameters are one FP32 vector of abcs_cnn_param_count() values, layer by
  * layer: w_l[co][ci][3][3] then b_l[co].  Inference runs from a packed
  * device copy (BF16 mid-layer weights) of abcs_cnn_packed_bytes() bytes. */
@@ -335,20 +338,22 @@ size_t abcs_cnn_packed_bytes(void);
 /* packed [device] <- params [device] (FP32 vector above). */
 abcs_status abcs_cnn_pack(abcs_handle* h, const float* params, void* packed, void* stream);
 
-/* out = x_hat(in, sigma[k], density) for every image k; in, out [device]
- * float [n_img][H][W] (in != out), sigma [device] float [n_img], density
- * [device] float [n_img][H][W] or NULL. */
+/* out = x_hat(in, sigma[k], density, tau[k]) for every image k; in, out
+ * [device] float [n_img][H][W] (in != out), sigma [device] float [n_img],
+ * density [device] float [n_img][H][W] or NULL, tau [device] float [n_img]
+ * or NULL. */
 abcs_status abcs_cnn_denoise(abcs_handle* h, const void* packed, const float* in, const float* sigma,
-                             const float* density, int n_img, int H, int W, float* out, void* stream);
+                             const float* density, const float* tau, int n_img, int H, int W, float* out,
+                             void* stream);
 
 /* Loss L = mean((x_hat - clean)^2) / 255^2 over the n crops and its
  * gradient with respect to the parameters of `packed`.
  *   r, clean [device] float [n][H][W]; sigma [device] float [n]
- *   density [device] float [n][H][W] or NULL
+ *   density [device] float [n][H][W] or NULL; tau [device] float [n] or NULL
  *   grad [device] float [abcs_cnn_param_count()]; loss [device] float [1] */
 abcs_status abcs_cnn_grad(abcs_handle* h, const void* packed, const float* r, const float* clean,
-                          const float* sigma, const float* density, int n, int H, int W, float* grad,
-                          float* loss, void* stream);
+                          const float* sigma, const float* density, const float* tau, int n, int H, int W,
+                          float* grad, float* loss, void* stream);
 
 /* One Adam step (beta = 0.9 / 0.999, eps = 1e-8, bias-corrected, `step`
  * counted from 1) on params [device] with moments adam_m, adam_v [device]
@@ -356,8 +361,8 @@ abcs_status abcs_cnn_grad(abcs_handle* h, const void* packed, const float* r, co
  * the gradient of the batch, updates params and the moments, re-packs. */
 abcs_status abcs_cnn_train_step(abcs_handle* h, float* params, float* adam_m, float* adam_v, int step,
                                 double lr, void* packed, const float* r, const float* clean,
-                                const float* sigma, const float* density, int n, int H, int W, float* loss,
-                                void* stream);
+                                const float* sigma, const float* density, const float* tau, int n, int H,
+                                int W, float* loss, void* stream);
 
 /* Per-pixel measured fraction of the block (the learned denoiser's third
  * input): out[k][y][x] = counts[k n_B + (y / B) nbw + x / B] / B^2 over the

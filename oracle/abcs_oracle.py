@@ -435,25 +435,30 @@ def tidct_denoise(r: np.ndarray, sigma: float, lam: float) -> np.ndarray:
 # Eqs. 13, 15, 25, 28: IDA.
 # --------------------------------------------------------------------------
 def ida(y: np.ndarray, counts: np.ndarray, Hc: int, Wc: int, B: int, iters: int,
-        DF: float = 2.0, denoiser=None, trace: bool = False):
+        DF: float = 2.0, denoiser=None, trace: bool = False, with_iteration: bool = False):
     """IDA: x^{t+1} = D_{sigma^t}(x^t + A^T z^t) (Eq. 13),
     z^t = y - A x^t + z^{t-1} / D_F (Eq. 25 plus the Onsager term of Eq. 28,
     alpha^t = 1/D_F), (sigma^t)^2 = ||z^t||^2 / m (Eq. 15), m = number of
     measurements of the image (len(y)).
 
     Reading: x^0 = 0 and z^{-1} = 0 (D-AMP's start; the paper states none).
-    `denoiser(r, sigma) -> x`; None means the identity (used by the pins).
-    Returns x^T and the list of sigma^t (and, with trace, every r^t, z^t).
+    `denoiser(r, sigma) -> x`, or `denoiser(r, sigma, t)` with
+    with_iteration (the learned denoiser); None means the identity (used by
+    the pins).  Returns x^T and the list of sigma^t (and, with trace, every
+    r^t, z^t).
     """
     m = len(y)
     x = np.zeros((Hc, Wc))
     z_prev = np.zeros(m)
     sigmas, rs, zs = [], [], []
-    for _ in range(iters):
+    for t in range(iters):
         z = y - A(x, counts, B) + z_prev / DF
         sigma = math.sqrt(float(np.dot(z, z)) / m)
         rt = x + At(z, counts, B, Hc, Wc)
-        x = rt if denoiser is None else denoiser(rt, sigma)
+        if denoiser is None:
+            x = rt
+        else:
+            x = denoiser(rt, sigma, t) if with_iteration else denoiser(rt, sigma)
         z_prev = z
         sigmas.append(sigma)
         if trace:
@@ -611,7 +616,7 @@ def damp(y: np.ndarray, counts: np.ndarray, Hc: int, Wc: int, B: int, iters: int
 # --------------------------------------------------------------------------
 # Learned denoiser: a DnCNN-style residual CNN (Sec. VI-4, ref. [21]).
 # --------------------------------------------------------------------------
-def cnn_init(c_in: int = 3, width: int = 32, depth: int = 8, seed: int = 0):
+def cnn_init(c_in: int = 4, width: int = 32, depth: int = 8, seed: int = 0):
     """He-normal weights, zero biases.  Layers: conv3x3 c_in->width + ReLU,
     (depth - 2) x [conv3x3 width->width + ReLU], conv3x3 width->1.
     Weight layout w[c_out, c_in, 3, 3]."""
@@ -649,16 +654,27 @@ def density_map(counts, H: int, W: int, B: int) -> np.ndarray:
     return np.kron(m, np.ones((B, B)))
 
 
-def cnn_input(r: np.ndarray, sigma: float, density=None) -> np.ndarray:
+def cnn_iter_input(t: int) -> float:
+    """The network's iteration input for IDA iteration t (t = 0 denoises
+    A^T y): tau_t = min(t, 8) / 8."""
+    return min(int(t), 8) / 8.0
+
+
+def cnn_input(r: np.ndarray, sigma: float, density=None, tau: float = 0.0) -> np.ndarray:
     """Network input: channel 0 = r / 255, channel 1 = sigma / 255
     everywhere, channel 2 = the measured fraction of the pixel's block
-    (zero when not given).  Readings: the noise level enters as a constant
-    map so one network serves every sigma of the IDA schedule; the density
-    tells it where coefficients are missing (the error of the first
-    iterate A^T y is the energy of the unmeasured coefficients)."""
+    (zero when not given), channel 3 = the iteration input tau everywhere.
+    Readings: the noise level enters as a constant map so one network serves
+    every sigma of the IDA schedule; the density tells it where coefficients
+    are missing (the error of the first iterate A^T y is the energy of the
+    unmeasured coefficients); tau tells it where in the iteration it is.
+    With the Onsager term of Eq. 28 the denoiser input of iteration t >= 1
+    carries z^{t-1} / D_F in the measured coefficients on top of the
+    estimate, a component the first input A^T y lacks, and a network that
+    cannot tell the two apart serves one of them badly."""
     d = np.zeros(np.shape(r)) if density is None else np.asarray(density, dtype=np.float64)
     return np.stack([np.asarray(r, dtype=np.float64) / 255.0,
-                     np.full(np.shape(r), sigma / 255.0), d])
+                     np.full(np.shape(r), sigma / 255.0), d, np.full(np.shape(r), float(tau))])
 
 
 def cnn_forward(params, x_in: np.ndarray):
@@ -673,9 +689,9 @@ def cnn_forward(params, x_in: np.ndarray):
     return h[0], acts
 
 
-def cnn_denoise(params, r: np.ndarray, sigma: float, density=None) -> np.ndarray:
-    """x_hat = r - 255 * net(r/255, sigma/255, density): residual learning (DnCNN)."""
-    n, _ = cnn_forward(params, cnn_input(r, sigma, density))
+def cnn_denoise(params, r: np.ndarray, sigma: float, density=None, tau: float = 0.0) -> np.ndarray:
+    """x_hat = r - 255 * net(r/255, sigma/255, density, tau): residual learning (DnCNN)."""
+    n, _ = cnn_forward(params, cnn_input(r, sigma, density, tau))
     return np.asarray(r, dtype=np.float64) - 255.0 * n
 
 
@@ -694,9 +710,9 @@ def conv3x3_backward(x: np.ndarray, w: np.ndarray, g: np.ndarray):
     return gxp[:, 1:-1, 1:-1], gw, gb
 
 
-def cnn_loss_and_grads(params, r: np.ndarray, sigma: float, clean: np.ndarray, density=None):
+def cnn_loss_and_grads(params, r: np.ndarray, sigma: float, clean: np.ndarray, density=None, tau: float = 0.0):
     """L = mean((x_hat - clean)^2) / 255^2 for one image, and dL/dparams."""
-    x_in = cnn_input(r, sigma, density)
+    x_in = cnn_input(r, sigma, density, tau)
     n, acts = cnn_forward(params, x_in)
     resid = (np.asarray(r, dtype=np.float64) - 255.0 * n - clean) / 255.0
     numel = resid.size

@@ -79,9 +79,9 @@ _SIGS = {
     "abcs_cnn_param_count": [],
     "abcs_cnn_packed_bytes": [],
     "abcs_cnn_pack": [_P, _P, _P, _P],
-    "abcs_cnn_denoise": [_P, _P, _P, _P, _P, _I, _I, _I, _P, _P],
-    "abcs_cnn_grad": [_P, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P, _P],
-    "abcs_cnn_train_step": [_P, _P, _P, _P, _I, _D, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P],
+    "abcs_cnn_denoise": [_P, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P],
+    "abcs_cnn_grad": [_P, _P, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P, _P],
+    "abcs_cnn_train_step": [_P, _P, _P, _P, _I, _D, _P, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P],
     "abcs_density_map": [_P, _P, _I, _I, _I, _I, _P, _P],
     "abcs_thi": [_P, _P, _I, _I, _I, _I, C.c_int64, _P, _P, _P, _P, _P],
     "abcs_damp": [_P, _P, _P, _P, _I, _I, _I, _I, _I, C.c_double, _I, C.c_double, _P, _P, _P, _P, _P, _P],
@@ -219,22 +219,23 @@ def abcs_cnn_pack(h, params, packed, stream=None) -> None:
     _check(lib.abcs_cnn_pack(h, _ptr(params), _ptr(packed), _stream(stream)))
 
 
-def abcs_cnn_denoise(h, packed, inp, sigma, density, n_img, H, W, out, stream=None) -> None:
-    """density: per-pixel measured fraction (abcs_density_map) or None."""
-    _check(lib.abcs_cnn_denoise(h, _ptr(packed), _ptr(inp), _ptr(sigma), _ptr(density), n_img, H, W, _ptr(out),
-                                _stream(stream)))
+def abcs_cnn_denoise(h, packed, inp, sigma, density, n_img, H, W, out, stream=None, tau=None) -> None:
+    """density: per-pixel measured fraction (abcs_density_map) or None;
+    tau: the iteration input per image or None (0)."""
+    _check(lib.abcs_cnn_denoise(h, _ptr(packed), _ptr(inp), _ptr(sigma), _ptr(density), _ptr(tau), n_img, H, W,
+                                _ptr(out), _stream(stream)))
 
 
-def abcs_cnn_grad(h, packed, r, clean, sigma, density, n, H, W, grad, loss, stream=None) -> None:
-    _check(lib.abcs_cnn_grad(h, _ptr(packed), _ptr(r), _ptr(clean), _ptr(sigma), _ptr(density), n, H, W,
-                             _ptr(grad), _ptr(loss), _stream(stream)))
+def abcs_cnn_grad(h, packed, r, clean, sigma, density, n, H, W, grad, loss, stream=None, tau=None) -> None:
+    _check(lib.abcs_cnn_grad(h, _ptr(packed), _ptr(r), _ptr(clean), _ptr(sigma), _ptr(density), _ptr(tau), n, H,
+                             W, _ptr(grad), _ptr(loss), _stream(stream)))
 
 
 def abcs_cnn_train_step(h, params, adam_m, adam_v, step, lr, packed, r, clean, sigma, density, n, H, W, loss,
-                        stream=None) -> None:
+                        stream=None, tau=None) -> None:
     _check(lib.abcs_cnn_train_step(h, _ptr(params), _ptr(adam_m), _ptr(adam_v), step, lr, _ptr(packed),
-                                   _ptr(r), _ptr(clean), _ptr(sigma), _ptr(density), n, H, W, _ptr(loss),
-                                   _stream(stream)))
+                                   _ptr(r), _ptr(clean), _ptr(sigma), _ptr(density), _ptr(tau), n, H, W,
+                                   _ptr(loss), _stream(stream)))
 
 
 def abcs_density_map(h, counts, n_img, H, W, B, out, stream=None) -> None:

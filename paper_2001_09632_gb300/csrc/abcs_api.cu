@@ -622,7 +622,8 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
                       "bm3d launch");
             x_cur = x_out;
         } else if (denoiser == ABCS_DEN_CNN) {
-            ABCS_CUDA(cnn_forward(cnn_weights, a.r, sig, dens, n_img, g.Hc, g.Wc, at<void>(h, o_act), 0, 0, x_out,
+            ABCS_CUDA(cnn_forward(cnn_weights, a.r, sig, dens, nullptr, cnn_iter_input(t), n_img, g.Hc, g.Wc,
+                                  at<void>(h, o_act), 0, 0, x_out,
                                   h->status, s),
                       "cnn launch");
             x_cur = x_out;
@@ -646,7 +647,8 @@ static abcs_status ida_run(abcs_handle* h, const int32_t* counts, const int64_t*
                           "bm3d launch");
                 xq = xp;
             } else if (denoiser == ABCS_DEN_CNN) {
-                ABCS_CUDA(cnn_forward(cnn_weights, rp, sig, dens, n_img, g.Hc, g.Wc, at<void>(h, o_act), 0, 0, xp,
+                ABCS_CUDA(cnn_forward(cnn_weights, rp, sig, dens, nullptr, cnn_iter_input(t), n_img, g.Hc, g.Wc,
+                                      at<void>(h, o_act), 0, 0, xp,
                                       h->status, s),
                           "cnn launch");
                 xq = xp;
@@ -893,7 +895,8 @@ abcs_status abcs_cnn_pack(abcs_handle* h, const float* params, void* packed, voi
 }
 
 abcs_status abcs_cnn_denoise(abcs_handle* h, const void* packed, const float* in, const float* sigma,
-                             const float* density, int n_img, int H, int W, float* out, void* stream) {
+                             const float* density, const float* tau, int n_img, int H, int W, float* out,
+                             void* stream) {
     if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
     if (!packed || !in || !sigma || !out) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
     if (in == out) return fail(ABCS_ERR_INVALID_ARG, "in and out must differ");
@@ -903,21 +906,22 @@ abcs_status abcs_cnn_denoise(abcs_handle* h, const void* packed, const float* in
     const size_t o_act = c.take<uint16_t>((size_t)2 * n_img * H * W * 32);
     abcs_status st = ensure_ws(h, c.off);
     if (st) return st;
-    ABCS_CUDA(cnn_forward(packed, in, sigma, density, n_img, H, W, at<void>(h, o_act), 0, 0, out, h->status,
-                          static_cast<cudaStream_t>(stream)),
+    ABCS_CUDA(cnn_forward(packed, in, sigma, density, tau, 0.f, n_img, H, W, at<void>(h, o_act), 0, 0, out,
+                          h->status, static_cast<cudaStream_t>(stream)),
               "cnn launch");
     return ABCS_OK;
 }
 
 abcs_status abcs_cnn_grad(abcs_handle* h, const void* packed, const float* r, const float* clean, const float* sigma,
-                          const float* density, int n, int H, int W, float* grad, float* loss, void* stream) {
+                          const float* density, const float* tau, int n, int H, int W, float* grad, float* loss,
+                          void* stream) {
     if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
     if (!packed || !r || !clean || !sigma || !grad || !loss) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
     if (n < 1 || n > 65535 || H < 1 || W < 1) return fail(ABCS_ERR_INVALID_ARG, "bad size");
     DeviceGuard dg(h->device);
     abcs_status st = ensure_ws(h, cnn_grad_ws_bytes(n, H, W));
     if (st) return st;
-    ABCS_CUDA(cnn_grad(packed, r, clean, sigma, density, n, H, W, h->ws, grad, loss, h->status,
+    ABCS_CUDA(cnn_grad(packed, r, clean, sigma, density, tau, n, H, W, h->ws, grad, loss, h->status,
                        static_cast<cudaStream_t>(stream)),
               "cnn grad launch");
     return ABCS_OK;
@@ -925,7 +929,8 @@ abcs_status abcs_cnn_grad(abcs_handle* h, const void* packed, const float* r, co
 
 abcs_status abcs_cnn_train_step(abcs_handle* h, float* params, float* adam_m, float* adam_v, int step, double lr,
                                 void* packed, const float* r, const float* clean, const float* sigma,
-                                const float* density, int n, int H, int W, float* loss, void* stream) {
+                                const float* density, const float* tau, int n, int H, int W, float* loss,
+                                void* stream) {
     if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
     if (!params || !adam_m || !adam_v || !packed || !r || !clean || !sigma || !loss)
         return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
@@ -939,7 +944,7 @@ abcs_status abcs_cnn_train_step(abcs_handle* h, float* params, float* adam_m, fl
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     float* grad = reinterpret_cast<float*>(static_cast<char*>(h->ws) + cnn_grad_ws_bytes(n, H, W));
     ABCS_CUDA(cnn_pack(params, packed, s), "cnn pack launch");
-    ABCS_CUDA(cnn_grad(packed, r, clean, sigma, density, n, H, W, h->ws, grad, loss, h->status, s),
+    ABCS_CUDA(cnn_grad(packed, r, clean, sigma, density, tau, n, H, W, h->ws, grad, loss, h->status, s),
               "cnn grad launch");
     ABCS_CUDA(cnn_adam(params, grad, adam_m, adam_v, step, (float)lr, s), "adam launch");
     ABCS_CUDA(cnn_pack(params, packed, s), "cnn pack launch");

@@ -335,10 +335,15 @@ cudaError_t launch_ida_batch(const BatchArgs& a, int th, int ctas_per_sm, size_t
 int cnn_param_count();
 size_t cnn_packed_bytes();
 cudaError_t cnn_pack(const float* params, void* packed, cudaStream_t s);
-cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, const float* dens, int n, int H,
-                        int W, void* act_buf, int keep_all, int mode, float* out, uint32_t* status, cudaStream_t s);
+// tau: the iteration input per image, or NULL for tau0 in every image
+cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, const float* dens, const float* tau,
+                        float tau0, int n, int H, int W, void* act_buf, int keep_all, int mode, float* out,
+                        uint32_t* status, cudaStream_t s);
 cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, const float* sigma, const float* dens,
-                     int n, int H, int W, void* ws, float* grad, float* loss, uint32_t* status, cudaStream_t s);
+                     const float* tau, int n, int H, int W, void* ws, float* grad, float* loss, uint32_t* status,
+                     cudaStream_t s);
+// the learned denoiser's iteration input in IDA iteration t
+inline float cnn_iter_input(int t) { return (float)(t < 8 ? t : 8) / 8.f; }
 // per-pixel measured fraction m_i / B^2 of the pixel's block (k_ida.cu)
 cudaError_t launch_density(const ImgGeom& g, const int32_t* counts, float* out, cudaStream_t s);
 // BM3D hard-thresholding step (k_bm3d.cu): in, out [n_img][H][W]; num, den

@@ -1,7 +1,8 @@
 // Learned residual denoiser for IDA (a DnCNN-style network, Sec. VI-4):
-//   conv3x3 3->32 + ReLU, 6 x [conv3x3 32->32 + ReLU], conv3x3 32->1,
-//   x_hat = r - 255 * net(r / 255, sigma / 255, d), zero 'same' padding,
-//   d = the measured fraction m_i / B^2 of the pixel's block (or 0).
+//   conv3x3 4->32 + ReLU, 6 x [conv3x3 32->32 + ReLU], conv3x3 32->1,
+//   x_hat = r - 255 * net(r / 255, sigma / 255, d, tau), zero 'same' padding,
+//   d = the measured fraction m_i / B^2 of the pixel's block (or 0),
+//   tau = the iteration input (min(t, 8) / 8 in IDA iteration t).
 // Activations and mid-layer weights are BF16 (activations chunk-planar:
 // four planes of 8 channels per image); every sum accumulates in FP32.  All
 // layers are implicit GEMMs on the tensor cores: the forward 32->32 layers
@@ -9,7 +10,7 @@
 // fed, TMEM accumulators, 128-pixel rows, operands read from shared memory by
 // descriptor), the input-gradient 32->32 layers on mma.sync (persistent
 // CTAs, weights resident, double-buffered tiles fed with ldmatrix), the
-// first layer (3 channels: r / 255, sigma / 255, d) in FP16 mma.sync.
+// first layer (4 channels: r / 255, sigma / 255, d, tau) in FP16 mma.sync.
 //
 // Training (fwd + bwd + Adam) reuses the same conv kernel for the input
 // gradient (weights transposed in (ci, co) and flipped in the tap, epilogue
@@ -26,13 +27,13 @@ namespace abcs {
 // ---------------------------------------------------------------------------
 // Parameter layout (FP32, the same as the FP64 oracle's):
 //   for l in 0..7: w_l[co][ci][3][3], then b_l[co]
-// channel plan: (3->32), 6 x (32->32), (32->1).
+// channel plan: (4->32), 6 x (32->32), (32->1).
 // ---------------------------------------------------------------------------
-constexpr int kC = 32, kMid = 6, kIn = 3;
+constexpr int kC = 32, kMid = 6, kIn = 4;
 constexpr int kW0 = kC * kIn * 9, kB0 = kC;
 constexpr int kWm = kC * kC * 9, kBm = kC;
 constexpr int kW7 = kC * 9, kB7 = 1;
-constexpr int kParams = kW0 + kB0 + kMid * (kWm + kBm) + kW7 + kB7;   // 56,673
+constexpr int kParams = kW0 + kB0 + kMid * (kWm + kBm) + kW7 + kB7;   // 56,961
 
 ABCS_HD int param_off_w(int l) {
     return l == 0 ? 0 : (l <= kMid ? kW0 + kB0 + (l - 1) * (kWm + kBm) : kW0 + kB0 + kMid * (kWm + kBm));
@@ -277,20 +278,24 @@ ABCS_D uint32_t pack_f16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// weight pair p = 2 tap + half of output channel co: (w[r], w[sigma]) or (w[d], 0)
+// weight pair p = 2 tap + half of output channel co: (w[r], w[sigma]) or (w[d], w[tau])
 ABCS_D uint32_t w0_pair(const CnnPacked* P, int co, int p) {
     if (p >= 18) return 0u;
     const int tap = p >> 1;
-    return (p & 1) ? pack_f16(__ldg(&P->w0[co][2][tap]), 0.f)
+    return (p & 1) ? pack_f16(__ldg(&P->w0[co][2][tap]), __ldg(&P->w0[co][3][tap]))
                    : pack_f16(__ldg(&P->w0[co][0][tap]), __ldg(&P->w0[co][1][tap]));
 }
 
+// the iteration input of image k: tau[k], or tau0 for every image
+ABCS_D float tau_of(const float* tau, float tau0, int k) { return tau ? __ldg(tau + k) : tau0; }
+
 __global__ void __launch_bounds__(256, 2) cnn_first_tc_kernel(const float* __restrict__ r,
                                                               const float* __restrict__ sigma,
-                                                              const float* __restrict__ dens, int n, int H, int W,
-                                                              const CnnPacked* __restrict__ P,
+                                                              const float* __restrict__ dens,
+                                                              const float* __restrict__ tau, float tau0, int n,
+                                                              int H, int W, const CnnPacked* __restrict__ P,
                                                               __nv_bfloat16* __restrict__ out) {
-    __shared__ uint32_t tin[IH * IW * 2];                 // per pixel: (r, sigma), (d, 0) as FP16x2
+    __shared__ uint32_t tin[IH * IW * 2];                 // per pixel: (r, sigma), (d, tau) as FP16x2
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = lane >> 2, q = lane & 3;
     const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH, per_img = tx * ty, ntiles = per_img * n;
     const int G = gridDim.x;
@@ -340,6 +345,7 @@ __global__ void __launch_bounds__(256, 2) cnn_first_tc_kernel(const float* __res
         int k, y0, x0;
         origin(tl, k, y0, x0);
         const float s255 = __ldg(sigma + k) * (1.f / 255.f);
+        const float tk = tau_of(tau, tau0, k);
         const float* rk = r + (int64_t)k * H * W;
         const float* dk = dens ? dens + (int64_t)k * H * W : nullptr;
 #pragma unroll
@@ -348,7 +354,7 @@ __global__ void __launch_bounds__(256, 2) cnn_first_tc_kernel(const float* __res
             const bool in_img = yy >= 0 && yy < H && xx >= 0 && xx < W;
             const int o = yy * W + xx;
             pre[e][0] = in_img ? pack_f16(__ldg(rk + o) * (1.f / 255.f), s255) : 0u;
-            pre[e][1] = (in_img && dk) ? pack_f16(__ldg(dk + o), 0.f) : 0u;
+            pre[e][1] = in_img ? pack_f16(dk ? __ldg(dk + o) : 0.f, tk) : 0u;
         }
     };
     fetch(tile);
@@ -547,25 +553,28 @@ __global__ void __launch_bounds__(256) wgrad32_kernel(const __nv_bfloat16* __res
     if ((t & 7) == 0) dst[kWm + co] = accb;
 }
 
-// Weight gradients of the first layer (inputs r/255, sigma/255, d; g: 32 ch).
+// Weight gradients of the first layer (inputs r/255, sigma/255, d, tau; g: 32 ch).
 __global__ void __launch_bounds__(256) wgrad_first_kernel(const float* __restrict__ r, const float* __restrict__ sigma,
-                                                          const float* __restrict__ dens,
-                                                          const __nv_bfloat16* __restrict__ g, int n, int H, int W,
-                                                          float* __restrict__ part) {
+                                                          const float* __restrict__ dens, const float* __restrict__ tau,
+                                                          float tau0, const __nv_bfloat16* __restrict__ g, int n, int H,
+                                                          int W, float* __restrict__ part) {
     __shared__ float tr[IH * IW];
     __shared__ float tv[IH * IW];        // 1 inside the image, 0 in the zero padding
     __shared__ float td[IH * IW];        // density, 0 in the padding
     __shared__ float tgg[TH * TW][33];
     const int t = threadIdx.x;
-    // thread t: co = t / 8; threads with t % 8 < 7 own 4 of the 27 (ci, tap) weights each
+    // thread t: co = t / 8; thread sub = t % 8 owns (ci, tap) weights 5 sub .. 5 sub + 4 of the 36
+    constexpr int kPer = 5;
+    static_assert(8 * kPer >= kIn * 9, "first-layer weights per output channel");
     const int co = t >> 3, sub = t & 7;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc[kPer] = {};
     float accb = 0.f;
     const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH, ntiles = tx * ty * n;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int k = tile / (tx * ty), rem = tile % (tx * ty);
         const int y0 = (rem / tx) * TH, x0 = (rem % tx) * TW;
         const float s255 = __ldg(sigma + k) * (1.f / 255.f);
+        const float tk = tau_of(tau, tau0, k);
         __syncthreads();
         for (int c = t; c < IH * IW; c += 256) {
             const int yy = y0 - 1 + c / IW, xx = x0 - 1 + c % IW;
@@ -586,28 +595,26 @@ __global__ void __launch_bounds__(256) wgrad_first_kernel(const float* __restric
             tgg[px][cp + 1] = v.y;
         }
         __syncthreads();
-        if (sub < 7) {
-            for (int p = 0; p < TH * TW; ++p) {
-                const float gv = tgg[p][co];
-                if (sub == 0) accb += gv;
-                const int py = p / TW, px = p % TW;
+        for (int p = 0; p < TH * TW; ++p) {
+            const float gv = tgg[p][co];
+            if (sub == 0) accb += gv;
+            const int py = p / TW, px = p % TW;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int idx = sub * 4 + e;            // 0..26 = ci * 9 + tap
-                    if (idx < kIn * 9) {
-                        const int ci = idx / 9, tap = idx % 9;
-                        const int ti = (py + tap / 3) * IW + px + tap % 3;
-                        const float in = ci == 0 ? tr[ti] : (ci == 1 ? s255 * tv[ti] : td[ti]);
-                        acc[e] = fmaf(gv, in, acc[e]);
-                    }
+            for (int e = 0; e < kPer; ++e) {
+                const int idx = sub * kPer + e;            // 0..35 = ci * 9 + tap
+                if (idx < kIn * 9) {
+                    const int ci = idx / 9, tap = idx % 9;
+                    const int ti = (py + tap / 3) * IW + px + tap % 3;
+                    const float in = ci == 0 ? tr[ti] : (ci == 1 ? s255 * tv[ti] : (ci == 2 ? td[ti] : tk * tv[ti]));
+                    acc[e] = fmaf(gv, in, acc[e]);
                 }
             }
         }
     }
     float* dst = part + (int64_t)blockIdx.x * (kW0 + kB0);
-    if (sub < 7)
-        for (int e = 0; e < 4; ++e)
-            if (sub * 4 + e < kIn * 9) dst[co * kIn * 9 + sub * 4 + e] = acc[e];
+#pragma unroll
+    for (int e = 0; e < kPer; ++e)
+        if (sub * kPer + e < kIn * 9) dst[co * kIn * 9 + sub * kPer + e] = acc[e];
     if (sub == 0) dst[kW0 + co] = accb;
 }
 
@@ -1024,8 +1031,9 @@ static cudaError_t conv32(int epi, const __nv_bfloat16* in, int n, int H, int W,
 
 // Forward through layers 0..6 into act[0..6] (each n*H*W*32 bf16), then the
 // last layer into out (mode 0: denoised image, mode 1: network output n).
-cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, const float* dens, int n, int H,
-                        int W, void* act_buf, int keep_all, int mode, float* out, uint32_t* status, cudaStream_t s) {
+cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, const float* dens, const float* tau,
+                        float tau0, int n, int H, int W, void* act_buf, int keep_all, int mode, float* out,
+                        uint32_t* status, cudaStream_t s) {
     const CnnPacked* P = static_cast<const CnnPacked*>(packed);
     const int64_t plane = (int64_t)n * H * W * kC;
     __nv_bfloat16* act = static_cast<__nv_bfloat16*>(act_buf);
@@ -1038,7 +1046,7 @@ cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, 
     const int64_t tiles = (int64_t)((W + TW - 1) / TW) * ((H + TH - 1) / TH) * n;
     const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
     e = launch_pdl(cnn_first_tc_kernel, dim3((unsigned)(tiles < cap ? tiles : cap)), dim3(256), 0, s, r, sigma,
-                   dens, n, H, W, P, A(0));
+                   dens, tau, tau0, n, H, W, P, A(0));
     for (int l = 1; l <= kMid && !e; ++l)
         e = conv32_tc5_launch(A(l - 1), n, H, W, &P->wc[l - 1][0][0][0], &P->bm[l - 1][0], A(l), status, s);
     if (e) return e;
@@ -1048,7 +1056,8 @@ cudaError_t cnn_forward(const void* packed, const float* r, const float* sigma, 
 // Loss and gradients (FP32, parameter layout) of a batch of n crops.
 // Workspace: act (7 planes), gbuf (2 planes), gn (n*H*W floats), parts.
 cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, const float* sigma, const float* dens,
-                     int n, int H, int W, void* ws, float* grad, float* loss, uint32_t* status, cudaStream_t s) {
+                     const float* tau, int n, int H, int W, void* ws, float* grad, float* loss, uint32_t* status,
+                     cudaStream_t s) {
     const CnnPacked* P = static_cast<const CnnPacked*>(packed);
     const int64_t px = (int64_t)n * H * W, plane = px * kC;
     char* w = static_cast<char*>(ws);
@@ -1059,7 +1068,7 @@ cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, con
     const int nparts = 304;
     float* part = gn + px;                                       // nparts * (kWm + kBm)
     double* lpart = reinterpret_cast<double*>(part + (size_t)nparts * (kWm + kBm));
-    cudaError_t e = cnn_forward(packed, r, sigma, dens, n, H, W, act, 1, 1, nout, status, s);
+    cudaError_t e = cnn_forward(packed, r, sigma, dens, tau, 0.f, n, H, W, act, 1, 1, nout, status, s);
     if (e) return e;
     cnn_loss_kernel<<<256, 256, 0, s>>>(nout, r, clean, px, gn, lpart);
     reduce_loss_kernel<<<1, 32, 0, s>>>(lpart, 256, loss);
@@ -1085,7 +1094,7 @@ cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, con
         if (e) return e;
         cur = 1 - cur;
     }
-    wgrad_first_kernel<<<np, 256, 0, s>>>(r, sigma, dens, gb + cur * plane, n, H, W, part);
+    wgrad_first_kernel<<<np, 256, 0, s>>>(r, sigma, dens, tau, 0.f, gb + cur * plane, n, H, W, part);
     reduce_parts_kernel<<<(kW0 + kB0 + 255) / 256, 256, 0, s>>>(part, np, kW0 + kB0, grad);
     return cudaGetLastError();
 }

@@ -34,6 +34,12 @@ DEFAULT_LAMBDA = 2.3   # tuned: tune_lambda() over 2.0..3.5 on held-out syntheti
 TRAIN_SEED, TUNE_SEED, EVAL_SEED = 10_000_000, 20_000_000, 30_000_000
 
 
+def iter_input(t: int) -> float:
+    """The learned denoiser's iteration input in IDA iteration t, as abcs_ida
+    passes it: min(t, 8) / 8."""
+    return min(int(t), 8) / 8.0
+
+
 def load_weights(path: str = WEIGHTS) -> np.ndarray:
     w = np.fromfile(path, dtype="<f4")
     if w.size != abcs.abcs_cnn_param_count():
@@ -44,7 +50,7 @@ def load_weights(path: str = WEIGHTS) -> np.ndarray:
 def init_params(seed: int) -> np.ndarray:
     """He-normal weights (last layer x 0.1), zero biases, in the ABI's layout."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    chans = [3] + [32] * 7 + [1]
+    chans = [4] + [32] * 7 + [1]
     out = []
     for l in range(8):
         ci, co = chans[l], chans[l + 1]
@@ -101,13 +107,14 @@ def psnr(x: torch.Tensor, ref: torch.Tensor) -> torch.Tensor:
 def make_pairs(h, n_images=512, H=512, W=512, captures=(0, 1, 2, 4, 8, 16, 29), crops=56, crop=64,
                batch=32, seed=TRAIN_SEED, lam=DEFAULT_LAMBDA, packed=None, large_every=0,
                large_size=(1024, 1024), log=print):
-    """(r^t, clean, sigma^t) crops; r^t from plain IDA, or from learned IDA
-    when `packed` weights are given (its own trajectories).  A capture index
+    """(r^t, clean, sigma^t, density, tau_t) crops; r^t from plain IDA, or
+    from learned IDA when `packed` weights are given (its own trajectories);
+    tau_t = min(t, 8) / 8 is the network's iteration input.  A capture index
     listed twice contributes twice the crops.  With large_every = n, every
     n-th batch uses 8 images of large_size instead."""
     subrates = (0.1, 0.2, 0.3, 0.4, 0.5)
     gen = torch.Generator(device="cuda").manual_seed(seed)
-    R, C, S, D = [], [], [], []
+    R, C, S, D, T = [], [], [], [], []
     t0 = time.time()
     for i0 in range(0, n_images, batch):
         j = i0 // batch
@@ -130,10 +137,11 @@ def make_pairs(h, n_images=512, H=512, W=512, captures=(0, 1, 2, 4, 8, 16, 29), 
             C.append(sd.clean[kk, rows, cols].reshape(-1, crop, crop))
             D.append(sd.density[kk, rows, cols].reshape(-1, crop, crop))
             S.append(s[:, None].expand(n, crops).reshape(-1))
+            T.append(torch.full((n * crops,), iter_input(t), dtype=torch.float32, device="cuda"))
         if j % 8 == 0:
             log(f"pairs: {i0 + batch}/{n_images} images, {sum(x.shape[0] for x in R)} crops, {time.time() - t0:.1f}s")
     assert abcs.abcs_sync_status(h) == 0
-    return torch.cat(R), torch.cat(C), torch.cat(S), torch.cat(D)
+    return torch.cat(R), torch.cat(C), torch.cat(S), torch.cat(D), torch.cat(T)
 
 
 def save_checkpoint(path: str, state: dict) -> None:
@@ -157,7 +165,7 @@ def load_checkpoint(path: str):
 
 
 def train(h, R, C, S, D, steps=4000, batch=128, lr=1e-3, seed=1, params=None, log=print, ckpt=None,
-          ckpt_every=500, until=None):
+          ckpt_every=500, until=None, T=None):
     """Adam on the crops (R, C, S, D) with a cosine learning-rate decay over
     `steps`.  With `ckpt`, the FP32 parameters, Adam's moments, the step and
     the state of the crop sampler are saved every `ckpt_every` steps and
@@ -192,8 +200,9 @@ def train(h, R, C, S, D, steps=4000, batch=128, lr=1e-3, seed=1, params=None, lo
     for step in range(first, last + 1):
         idx = torch.randint(0, n, (batch,), device="cuda", generator=gen)
         rb, cb, sb, db = R[idx].contiguous(), C[idx].contiguous(), S[idx].contiguous(), D[idx].contiguous()
+        tb = T[idx].contiguous() if T is not None else None
         lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * (step - 1) / steps))     # cosine decay
-        abcs.abcs_cnn_train_step(h, p, m, v, step, lr_t, packed, rb, cb, sb, db, batch, crop, crop, loss)
+        abcs.abcs_cnn_train_step(h, p, m, v, step, lr_t, packed, rb, cb, sb, db, batch, crop, crop, loss, tau=tb)
         if step % 200 == 0 or step == 1:
             l = loss.item()
             hist.append((step, l))
@@ -394,13 +403,13 @@ def main():
     ap.add_argument("--lam", type=float, default=DEFAULT_LAMBDA)
     ap.add_argument("--eval-images", type=int, default=128)
     ap.add_argument("--report", default=None, help="write a JSON report here")
-    ap.add_argument("--captures-a", default="0,0,0,1,2,3,5,8,15,29",
+    ap.add_argument("--captures-a", default="0,0,0,1,2,3,4,6,8",
                     help="IDA iterations whose denoiser inputs form the phase-A crops (repeat to weight)")
-    ap.add_argument("--captures-b", default="0,1,1,2,2,3,4,6",
+    ap.add_argument("--captures-b", default="0,0,1,2,2,3,3,4,4,5,6,8",
                     help="iterations captured along the network's own trajectories (phase B)")
-    ap.add_argument("--rounds", type=int, default=3, help="phase B rounds (own trajectories, fine-tuning)")
+    ap.add_argument("--rounds", type=int, default=8, help="phase B rounds (own trajectories, fine-tuning)")
     ap.add_argument("--init", default=None, help="train: start phase B from these weights (no phase A)")
-    ap.add_argument("--round-steps", type=int, default=5000, help="Adam steps per phase B round")
+    ap.add_argument("--round-steps", type=int, default=4000, help="Adam steps per phase B round")
     ap.add_argument("--large-every", type=int, default=3,
                     help="every n-th training batch of large images (0: none)")
     ap.add_argument("--large-size", default="1088,1920", help="H,W of the large training images")
@@ -420,12 +429,12 @@ def main():
             # continue from trained weights: phase B rounds only
             w, hist_a, secs_a = load_weights(a.init), [], 0.0
             R = C = D = torch.empty((0, 64, 64), dtype=torch.float32, device="cuda")
-            S = torch.empty(0, dtype=torch.float32, device="cuda")
+            S = T = torch.empty(0, dtype=torch.float32, device="cuda")
         else:
-            R, C, S, D = make_pairs(h, n_images=a.images, lam=a.lam, captures=caps_a, crops=48,
-                                    large_every=a.large_every, large_size=large)
+            R, C, S, D, T = make_pairs(h, n_images=a.images, lam=a.lam, captures=caps_a, crops=48,
+                                       large_every=a.large_every, large_size=large)
             print(f"phase A: {R.shape[0]} training crops")
-            w, hist_a, secs_a = train(h, R, C, S, D, steps=a.steps)
+            w, hist_a, secs_a = train(h, R, C, S, D, steps=a.steps, T=T)
         report["train"] = {"phase_a_crops": int(R.shape[0]), "steps": [a.steps], "seconds": secs_a,
                            "loss": {"A": hist_a}, "rounds": []}
         report["train"]["rounds"].append({"round": 0, "trajectory_psnr": trajectory_psnr(h, w)})
@@ -436,13 +445,14 @@ def main():
         pk = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
         for rnd in range(1, a.rounds + 1):
             abcs.abcs_cnn_pack(h, torch.tensor(w, device="cuda"), pk)
-            R2, C2, S2, D2 = make_pairs(h, n_images=a.images // 2, lam=a.lam, captures=caps_b, crops=64,
-                                        seed=TRAIN_SEED + 5_000_000 * rnd, packed=pk, large_every=a.large_every,
-                                        large_size=large)
-            R, C, S, D = torch.cat([R, R2]), torch.cat([C, C2]), torch.cat([S, S2]), torch.cat([D, D2])
-            del R2, C2, S2, D2
+            R2, C2, S2, D2, T2 = make_pairs(h, n_images=a.images // 2, lam=a.lam, captures=caps_b, crops=64,
+                                            seed=TRAIN_SEED + 5_000_000 * rnd, packed=pk,
+                                            large_every=a.large_every, large_size=large)
+            R, C, S, D, T = (torch.cat([R, R2]), torch.cat([C, C2]), torch.cat([S, S2]), torch.cat([D, D2]),
+                             torch.cat([T, T2]))
+            del R2, C2, S2, D2, T2
             print(f"phase B round {rnd}: {R.shape[0]} training crops")
-            w, hist_b, secs_b = train(h, R, C, S, D, steps=a.round_steps, lr=3e-4, params=w, seed=1 + rnd)
+            w, hist_b, secs_b = train(h, R, C, S, D, steps=a.round_steps, lr=3e-4, params=w, seed=1 + rnd, T=T)
             report["train"]["rounds"].append({"round": rnd, "crops": int(R.shape[0]), "seconds": secs_b,
                                               "loss": hist_b, "trajectory_psnr": trajectory_psnr(h, w)})
             report["train"]["seconds"] += secs_b
@@ -451,7 +461,7 @@ def main():
             if a.report:
                 with open(a.report, "w") as f:
                     json.dump(report, f, indent=1)
-        del R, C, S, D
+        del R, C, S, D, T
         torch.cuda.empty_cache()
     if a.cmd in ("eval", "all"):
         w = load_weights(a.out if a.cmd == "all" else a.weights)

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _params(seed=0, scale_last=1.0):
-    p = O.cnn_init(c_in=3, width=32, depth=8, seed=seed)
+    p = O.cnn_init(c_in=4, width=32, depth=8, seed=seed)
     rng = np.random.default_rng(seed + 1)
     out = []
     for l, (w, b) in enumerate(p):
@@ -92,16 +92,18 @@ def test_cnn_forward_parity(handle, n, H, W):
     clean, r = _noisy(n, H, W, 10, 12.0)
     dens = _density(n, H, W, 11)
     sig = np.array([12.0, 20.0][:n])
+    tau = np.array([0.25, 0.875][:n])
     d_in = torch.tensor(r, dtype=torch.float32, device="cuda")
     d_out = torch.full_like(d_in, float("nan"))
     d_sig = torch.tensor(sig, dtype=torch.float32, device="cuda")
     d_den = torch.tensor(dens, device="cuda")
-    abcs.abcs_cnn_denoise(handle, packed, d_in, d_sig, d_den, n, H, W, d_out)
+    abcs.abcs_cnn_denoise(handle, packed, d_in, d_sig, d_den, n, H, W, d_out,
+                          tau=torch.tensor(tau, dtype=torch.float32, device="cuda"))
     assert abcs.abcs_sync_status(handle) == 0
     got = d_out.cpu().numpy()
     r32 = d_in.cpu().numpy().astype(float)
     for k in range(n):
-        ref = O.cnn_denoise(ref_p, r32[k], float(np.float32(sig[k])), dens[k].astype(float))
+        ref = O.cnn_denoise(ref_p, r32[k], float(np.float32(sig[k])), dens[k].astype(float), tau[k])
         n_ref = (r32[k] - ref) / 255.0
         n_got = (r32[k] - got[k]) / 255.0
         err = np.linalg.norm(n_got - n_ref) / np.linalg.norm(n_ref)
@@ -121,14 +123,14 @@ FULL_WINDOWS = {
 }
 
 
-def _quantised_denoise(params, r, sigma, density):
+def _quantised_denoise(params, r, sigma, density, tau):
     """The oracle's layers (cnn_input, conv3x3, ReLU) composed with the
     storage roundings of the GPU path: the input planes and the first
     layer's weights in FP16, every hidden activation stored in BF16 (the
     mid-layer weights are already BF16 in `params`).  Only the FP32
     accumulation order then separates it from the GPU's output."""
     q = lambda a, dt: torch.tensor(a).to(dt).to(torch.float64).numpy()
-    h = q(O.cnn_input(r, sigma, density), torch.float16)
+    h = q(O.cnn_input(r, sigma, density, tau), torch.float16)
     for l, (w, b) in enumerate(params):
         h = O.conv3x3(h, q(w, torch.float16) if l == 0 else w, b)
         if l < len(params) - 1:
@@ -155,10 +157,12 @@ def test_cnn_forward_parity_full_size(handle, n, H, W):
     clean, r = _noisy(n, H, W, 70, 15.0)
     dens = _density(n, H, W, 71)
     sig = np.array([15.0, 24.0][:n])
+    tau = np.array([0.5, 0.125][:n])
     d_in = torch.tensor(r, dtype=torch.float32, device="cuda")
     d_out = torch.full_like(d_in, float("nan"))
     abcs.abcs_cnn_denoise(handle, packed, d_in, torch.tensor(sig, dtype=torch.float32, device="cuda"),
-                          torch.tensor(dens, device="cuda"), n, H, W, d_out)
+                          torch.tensor(dens, device="cuda"), n, H, W, d_out,
+                          tau=torch.tensor(tau, dtype=torch.float32, device="cuda"))
     assert abcs.abcs_sync_status(handle) == 0
     got = d_out.cpu().numpy()
     assert np.all(np.isfinite(got))
@@ -169,8 +173,8 @@ def test_cnn_forward_parity_full_size(handle, n, H, W):
         xa, xb = max(0, x0 - 8), min(W, x0 + w + 8)
         sl = (slice(y0 - ya, y0 - ya + h), slice(x0 - xa, x0 - xa + w))
         rc, dc, sg = r32[k, ya:yb, xa:xb], dens[k, ya:yb, xa:xb].astype(float), float(np.float32(sig[k]))
-        ref = O.cnn_denoise(ref_p, rc, sg, dc)[sl]
-        emu = _quantised_denoise(ref_p, rc, sg, dc)[sl]
+        ref = O.cnn_denoise(ref_p, rc, sg, dc, tau[k])[sl]
+        emu = _quantised_denoise(ref_p, rc, sg, dc, tau[k])[sl]
         rin = r32[k, y0:y0 + h, x0:x0 + w]
         g = got[k, y0:y0 + h, x0:x0 + w]
         n_ref, n_emu, n_got = (rin - ref) / 255.0, (rin - emu) / 255.0, (rin - g) / 255.0
@@ -191,17 +195,19 @@ def test_cnn_gradient_parity(handle):
     n, H, W = 2, 24, 40
     clean, r = _noisy(n, H, W, 20, 15.0)
     sig = np.array([15.0, 15.0])
+    tau = np.array([0.375, 1.0])
     dens = _density(n, H, W, 21)
     d = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
     d_r, d_c, d_s, d_d = d(r), d(clean), d(sig), d(dens)
     grad = torch.zeros(abcs.abcs_cnn_param_count(), dtype=torch.float32, device="cuda")
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
-    abcs.abcs_cnn_grad(handle, packed, d_r, d_c, d_s, d_d, n, H, W, grad, loss)
+    abcs.abcs_cnn_grad(handle, packed, d_r, d_c, d_s, d_d, n, H, W, grad, loss, tau=d(tau))
     assert abcs.abcs_sync_status(handle) == 0
     r32, c32 = d_r.cpu().numpy().astype(float), d_c.cpu().numpy().astype(float)
     ref_loss, ref_grads = 0.0, None
     for k in range(n):
-        lk, gk = O.cnn_loss_and_grads(ref_p, r32[k], float(np.float32(sig[k])), c32[k], dens[k].astype(float))
+        lk, gk = O.cnn_loss_and_grads(ref_p, r32[k], float(np.float32(sig[k])), c32[k], dens[k].astype(float),
+                                      tau[k])
         ref_loss += lk / n
         gk = [(gw / n, gb / n) for gw, gb in gk]
         ref_grads = gk if ref_grads is None else [(a + c, b + e) for (a, b), (c, e) in zip(ref_grads, gk)]
@@ -247,8 +253,8 @@ def test_ida_with_cnn_runs_and_matches_oracle_first_iterations(handle):
     abcs.abcs_ida(handle, *got["d"], 1, H, W, B, 2, 2.0, abcs.DEN_CNN, 0.0, packed, x, tr)
     assert abcs.abcs_sync_status(handle) == 0
     dmap = O.density_map(out["counts"], H, W, B)
-    xr, sig = O.ida(out["y"], out["counts"], H, W, B, 2, DF=2.0,
-                    denoiser=lambda rr, s: O.cnn_denoise(ref_p, rr, s, dmap))
+    xr, sig = O.ida(out["y"], out["counts"], H, W, B, 2, DF=2.0, with_iteration=True,
+                    denoiser=lambda rr, s, t: O.cnn_denoise(ref_p, rr, s, dmap, O.cnn_iter_input(t)))
     assert abs(tr.cpu().numpy()[0, 0] - sig[0]) <= 1e-5 * sig[0]
     err = np.linalg.norm(x.cpu().numpy()[0] - xr) / np.linalg.norm(xr)
     assert err <= 2e-2, err
