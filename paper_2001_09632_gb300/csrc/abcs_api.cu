@@ -318,7 +318,12 @@ abcs_status abcs_sense(abcs_handle* h, const uint8_t* img, int n_img, int H, int
     if (variant == ABCS_BBV && p.nS > 0) {
         ABCS_CUDA(launch_bbv_alloc(a, s), "bbv pilot + allocation launch");
     } else if (variant == ABCS_DD) {
-        ABCS_CUDA(launch_dd_alloc(a, s), "dd pilot + allocation launch");
+        // the tensor-core precisions take the DD pilot on the tensor cores too
+        // (its decisions are exact either way)
+        if (precision != ABCS_FP32 && dd_tc_usable(a))
+            ABCS_CUDA(launch_dd_tc_alloc(a, s), "dd pilot + allocation launch");
+        else
+            ABCS_CUDA(launch_dd_alloc(a, s), "dd pilot + allocation launch");
     } else {
         if (pilot) ABCS_CUDA(cudaMemsetAsync(pilot, 0, nb_all * sizeof(int32_t), s), "memset");
         ABCS_CUDA(launch_allocate(a, variant == ABCS_BBV ? 3 : 0, s), "allocate launch");

@@ -241,6 +241,9 @@ cudaError_t launch_allocate(const SenseArgs& a, int mode, cudaStream_t s);
 // pilot + allocation in one launch (needs a.img_done, zero on entry)
 cudaError_t launch_bbv_alloc(const SenseArgs& a, cudaStream_t s);
 cudaError_t launch_dd_alloc(const SenseArgs& a, cudaStream_t s);
+// DD pilot + allocation on the tensor cores (k_tc.cu; B = 16, 4-byte aligned pixel rows)
+bool dd_tc_usable(const SenseArgs& a);
+cudaError_t launch_dd_tc_alloc(const SenseArgs& a, cudaStream_t s);
 cudaError_t launch_sense_pack(const SenseArgs& a, cudaStream_t s);
 
 struct ReconArgs {

@@ -8,6 +8,7 @@ ABCS_TU_TABLES(pilot)
 
 #include "alloc_dev.cuh"
 #include "dct_tile.cuh"
+#include "dd_exact.cuh"
 
 namespace abcs {
 
@@ -351,38 +352,6 @@ cudaError_t launch_bbv_alloc(const SenseArgs& a, cudaStream_t s) {
 // in FP64, whose error is < 1e-11 here; an irrational coefficient within
 // 1e-9 of T is flagged ABCS_DEV_AMBIGUOUS and counted as not exceeding.
 // ---------------------------------------------------------------------------
-template <int B>
-ABCS_D int rational_sign(int u, int n) {
-    if (u == 0) return 1;
-    return (((n + 1) >> 1) & 1) ? -1 : 1;    // sign of cos(pi (2n+1) / 4)
-}
-
-// Exact decision |c(u,v)| > T for one block, re-reading its pixels.
-template <int B>
-ABCS_D bool dd_exceeds_exact(const uint8_t* blk, int64_t pitch, int u, int v, int T,
-                             uint32_t* status) {
-    constexpr int H2 = B / 2;
-    if ((u == 0 || u == H2) && (v == 0 || v == H2)) {
-        long long S = 0;
-        for (int n = 0; n < B; ++n)
-            for (int m = 0; m < B; ++m)
-                S += rational_sign<B>(u, n) * rational_sign<B>(v, m) * (int)__ldg(blk + n * pitch + m);
-        return llabs(S) > (long long)T * B;
-    }
-    double c = 0.0;
-    for (int n = 0; n < B; ++n) {
-        double row = 0.0;
-        for (int m = 0; m < B; ++m) row = fma((double)__ldg(blk + n * pitch + m), Dd<B>(v, m), row);
-        c = fma(Dd<B>(u, n), row, c);
-    }
-    const double d = fabs(c) - (double)T;
-    if (fabs(d) <= 1e-9) {
-        set_status(status, ABCS_DEV_AMBIGUOUS);
-        return false;
-    }
-    return d > 0.0;
-}
-
 // n_i of the blocks of tile (block row bi, tile column tx) of image k; their
 // sum goes to partial `slot`.  Ts and zz are the tile's shared buffers
 // (Tile<B>::FLOATS floats, B * B ranks, zz already loaded).

@@ -32,7 +32,9 @@ namespace abcs {
 ABCS_TU_TABLES(tc)
 }  // namespace abcs
 
+#include "alloc_dev.cuh"
 #include "dct_tile.cuh"
+#include "dd_exact.cuh"
 #include "tc_frag.cuh"
 
 namespace abcs {
@@ -1037,6 +1039,171 @@ __global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int64_t n
     cp_async_wait_all();
 }
 
+// ---------------------------------------------------------------------------
+// DD pilot on the tensor cores (Alg. 2, B = 16): n_i = #{rank j < m1 :
+// |c_j| > T}, decided on the exact coefficient.  One CTA per 32-block tile
+// of a block row (warp w takes blocks w, w + 8, w + 16, w + 24, all their
+// pixels loaded up front), one partial sum per tile, the fused allocation
+// of dd_pilot_kernel; each block's coefficients come from the sensing transform's
+// FP16x2 fragments (pixels exact in FP16, D split hi + lo).  A coefficient
+// within the band E_tc of T is recomputed in FP32 by the whole warp from the
+// block's pixels, which its lanes already hold (8 each): lane terms
+// fl(D_u,n D_v,m) x_n,m, summed in an FMA chain of 8 and a 5-level shuffle
+// tree; with the FP32 table's rounding that is within 16 2^-24 S of c, and
+// the band E_32 = 32 2^-24 S decides.  Inside E_32 the warp decides exactly
+// (dd_exact_warp16): integers at (u, v) in {0, 8}^2, else FP64 within
+// 1e-11, with the same 1e-9 ambiguity rule as the FP32 pilot.
+// Band: with S = 255 B bounding sum |D_u,n| |X_n,m| |D_v,m| (each row of D has
+// unit L2 norm, so its L1 norm is at most sqrt(B)), the hi + lo split of D
+// and of the stage-1 result (each within 2^-22 relative, or 2^-25 absolute in
+// FP16's subnormal range), the missing lo x lo product (2^-22) and FP32
+// accumulation of 32 + 48 terms (each addition within 2^-23 relative, which
+// also covers truncating adders) give |c_tc - c| <= 88 2^-23 S + 2^-25 16 S
+// / 255; E_tc doubles the first term and takes 0.01 for the second.
+// ---------------------------------------------------------------------------
+// Exact |c(u,v)| > T of the block whose pixels the warp holds (lane (g, q):
+// pw[h] = row g + 8 h, columns 4q .. 4q + 3); every lane returns the decision.
+ABCS_D bool dd_exact_warp16(int u, int v, const uint32_t (&pw)[2], int T, uint32_t* status) {
+    const Frag f;
+    if ((u == 0 || u == 8) && (v == 0 || v == 8)) {       // c = S / 16 with integer S
+        int S = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int su = rational_sign<16>(u, f.g + 8 * h);
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc)
+                S += su * rational_sign<16>(v, 4 * f.q + cc) * (int)((pw[h] >> (8 * cc)) & 0xFFu);
+        }
+        S = warp_sum(S);
+        return abs(S) > T * 16;
+    }
+    double c = 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const double du = Dd<16>(u, f.g + 8 * h);
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc)
+            c = fma(du * Dd<16>(v, 4 * f.q + cc), (double)((pw[h] >> (8 * cc)) & 0xFFu), c);
+    }
+    c = __shfl_sync(0xffffffffu, warp_sum(c), 0);
+    const double d = fabs(c) - (double)T;
+    if (fabs(d) <= 1e-9) {
+        if ((threadIdx.x & 31) == 0) set_status(status, ABCS_DEV_AMBIGUOUS);
+        return false;
+    }
+    return d > 0.0;
+}
+
+constexpr int kDdNB = 32, kDdBPW = kDdNB / 8;   // blocks of a CTA's tile (one block row), per warp
+
+__global__ void __launch_bounds__(256, 2) dd_pilot_tc_kernel(SenseArgs a) {
+    __shared__ unsigned long long sh[32];
+    __shared__ int64_t sh2[33];
+    __shared__ int64_t sW;
+    __shared__ bool s_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Frag f;
+    uint32_t DAh[4], DAl[4], DTh[2][2], DTl[2][2];
+    frag_a<kP16>(kSetSenseA, DAh, DAl);
+    frag_b<kP16>(kSetSenseB, DTh, DTl);
+    int rk[2][4];   // ranks of R[g + 8 (i>>1)][2q + (i&1) + 8 nt] = C[u = 2q + (i&1) + 8 nt][v = g + 8 (i>>1)]
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) rk[nt][i] = zz_rank(2 * f.q + (i & 1) + 8 * nt, f.g + 8 * (i >> 1), 16);
+    const ImgGeom& g = a.g;
+    const int k = blockIdx.z, bi = blockIdx.y, bj0 = blockIdx.x * kDdNB;
+    const int nblk = min(kDdNB, g.nbw - bj0);
+    const uint8_t* img = a.img + (int64_t)k * g.img_stride + (int64_t)(bi * 16) * g.pitch;
+    constexpr float kS = 255.f * 16.f;
+    const float band = 176.f * 1.1920929e-7f * kS + 0.01f;
+    const float band32 = 32.f * 5.9604645e-8f * kS;
+    const float T = (float)a.T;
+    const int m1 = a.m1;
+    griddep_wait();
+    // every block's pixels first (pwj[j][h]: block warp + 8 j, row g + 8 h, columns 4q .. 4q + 3)
+    uint32_t pwj[kDdBPW][2];
+#pragma unroll
+    for (int j = 0; j < kDdBPW; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            pwj[j][h] = warp + 8 * j < nblk
+                            ? __ldg(reinterpret_cast<const uint32_t*>(img + (bj0 + warp + 8 * j) * 16 +
+                                                                      (int64_t)(f.g + 8 * h) * g.pitch + 4 * f.q))
+                            : 0u;
+    unsigned long long mine = 0;
+#pragma unroll
+    for (int j = 0; j < kDdBPW; ++j) {
+        const int c = warp + 8 * j;
+        if (c >= nblk) break;
+        uint32_t xb[2][2], pw[2];       // pw[h]: pixels of row g + 8 h, columns 4q .. 4q + 3
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            pw[nt] = pwj[j][nt];
+            xb[nt][0] = px_pair<kP16>(pw[nt], 0);
+            xb[nt][1] = px_pair<kP16>(pw[nt], 1);
+        }
+        float V[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            mma0<kP16>(V[nt], DAh, xb[nt][0], xb[nt][1]);
+            mma<kP16>(V[nt], DAl, xb[nt][0], xb[nt][1]);
+        }
+        uint32_t Ah[4], Al[4];
+        split2<kP16>(V[0][0], V[0][1], Ah[0], Al[0]);
+        split2<kP16>(V[0][2], V[0][3], Ah[1], Al[1]);
+        split2<kP16>(V[1][0], V[1][1], Ah[2], Al[2]);
+        split2<kP16>(V[1][2], V[1][3], Ah[3], Al[3]);
+        float R[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+            mma_split<kP16>(R[nt], Ah, Al, DTh[nt][0], DTh[nt][1], DTl[nt][0], DTl[nt][1]);
+        int n = 0;
+        uint32_t pend = 0;              // bit 4 nt + i: coefficient inside the band
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (rk[nt][i] >= m1) continue;
+                const float v = fabsf(R[nt][i]);
+                if (v > T + band) ++n;
+                else if (v >= T - band) pend |= 1u << (4 * nt + i);
+            }
+        // in-band coefficients, one at a time over the warp
+        for (unsigned any = __ballot_sync(0xffffffffu, pend != 0); any;
+             any = __ballot_sync(0xffffffffu, pend != 0)) {
+            const int src = __ffs(any) - 1;
+            const uint32_t pb = __shfl_sync(0xffffffffu, pend, src);
+            const int e = __ffs(pb) - 1, nt = e >> 2, i = e & 3;
+            const int u = 2 * (src & 3) + (i & 1) + 8 * nt, vv = (src >> 2) + 8 * (i >> 1);
+            float p = 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float du = Dc<16>(u, f.g + 8 * h);
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc)
+                    p = fmaf(du * Dc<16>(vv, 4 * f.q + cc), (float)((pw[h] >> (8 * cc)) & 0xFFu), p);
+            }
+            const float v = fabsf(__shfl_sync(0xffffffffu, warp_sum(p), src));   // the same in every lane
+            bool hit = v > T + band32;
+            if (!hit && v >= T - band32) hit = dd_exact_warp16(u, vv, pw, a.T, a.status);
+            if (lane == src) {
+                n += hit ? 1 : 0;
+                pend &= ~(1u << e);
+            }
+        }
+        n = warp_sum(n);
+        if (lane == 0) {
+            a.w[(int64_t)k * g.n_blocks + (int64_t)bi * g.nbw + bj0 + c] = n;
+            mine += (unsigned long long)n;
+        }
+    }
+    mine = block_sum(mine, sh);
+    if (threadIdx.x == 0)
+        a.wpart[(int64_t)k * gridDim.x * gridDim.y + (int64_t)blockIdx.y * gridDim.x + blockIdx.x] = mine;
+    pilot_alloc_tail(a, 2, k, gridDim.x * gridDim.y, sh2, &sW, &s_last);
+}
+
 // one CTA per segment at most, and no more CTAs than fit on the GPU at once
 template <typename K>
 cudaError_t grid_segs(K kernel, int64_t ntot, int seg, size_t smem, int* grid) {
@@ -1119,6 +1286,19 @@ cudaError_t launch_recon_tc(const ReconArgs& a, cudaStream_t s) {
         case kPB1: return launch_recon_tc_p<kPB1>(a, s);
     }
     return cudaErrorInvalidValue;
+}
+
+// the tensor-core DD pilot reads each block row's 16 pixels as 4-byte words
+bool dd_tc_usable(const SenseArgs& a) {
+    const uintptr_t al = reinterpret_cast<uintptr_t>(a.img) | (uintptr_t)a.g.pitch |
+                         (uintptr_t)(a.g.n_img > 1 ? a.g.img_stride : 0);
+    return a.g.B == 16 && (al & 3) == 0;
+}
+
+cudaError_t launch_dd_tc_alloc(const SenseArgs& a, cudaStream_t s) {
+    if (!dd_tc_usable(a)) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((a.g.nbw + kDdNB - 1) / kDdNB), (unsigned)a.g.nbh, (unsigned)a.g.n_img);
+    return launch_pdl(dd_pilot_tc_kernel, grid, dim3(256), 0, s, a);
 }
 
 bool sense_tc_bases_in_kernel(const SenseArgs& a) { return a.g.B == 16 && sense_tc_bases_fit(a); }
