@@ -1096,7 +1096,7 @@ ABCS_D bool dd_exact_warp16(int u, int v, const uint32_t (&pw)[2], int T, uint32
 
 constexpr int kDdNB = 32, kDdBPW = kDdNB / 8;   // blocks of a CTA's tile (one block row), per warp
 
-__global__ void __launch_bounds__(256, 2) dd_pilot_tc_kernel(SenseArgs a) {
+__global__ void __launch_bounds__(256, 3) dd_pilot_tc_kernel(SenseArgs a) {
     __shared__ unsigned long long sh[32];
     __shared__ int64_t sh2[33];
     __shared__ int64_t sW;
@@ -1132,14 +1132,21 @@ __global__ void __launch_bounds__(256, 2) dd_pilot_tc_kernel(SenseArgs a) {
                                                                       (int64_t)(f.g + 8 * h) * g.pitch + 4 * f.q))
                             : 0u;
     unsigned long long mine = 0;
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < kDdBPW; ++j) {
         const int c = warp + 8 * j;
         if (c >= nblk) break;
         uint32_t xb[2][2], pw[2];       // pw[h]: pixels of row g + 8 h, columns 4q .. 4q + 3
+        // the next block's pixels move to the front (fixed register names)
+        pw[0] = pwj[0][0];
+        pw[1] = pwj[0][1];
+#pragma unroll
+        for (int jj = 0; jj + 1 < kDdBPW; ++jj) {
+            pwj[jj][0] = pwj[jj + 1][0];
+            pwj[jj][1] = pwj[jj + 1][1];
+        }
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt) {
-            pw[nt] = pwj[j][nt];
             xb[nt][0] = px_pair<kP16>(pw[nt], 0);
             xb[nt][1] = px_pair<kP16>(pw[nt], 1);
         }
