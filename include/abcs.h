@@ -18,6 +18,7 @@
  *                          BM3D / DnCNN; this library's plain stand-in is
  *                          shift-averaged 8x8 DCT hard thresholding)
  *   abcs_cnn_* ........... the learned residual CNN denoiser (DnCNN-style, Sec. VI-4)
+ *   abcs_psnr_ssim ....... the quality measures of the paper's tables (PSNR, SSIM of ref. [18])
  *
  * Conventions shared by every entry point:
  *   - Pointers marked [device] are CUDA device pointers (or managed memory)
@@ -225,6 +226,21 @@ abcs_status abcs_ida(abcs_handle* h, const int32_t* counts, const int64_t* offse
                      const float* y, int n_img, int H, int W, int B, int iters, double damping,
                      int denoiser, double lambda, const void* cnn_weights,
                      float* x_out, float* sigma_trace, void* stream);
+
+/* The paper's two quality measures (PSNR and SSIM, Tables 3, 6, 7) of
+ * reconstructions against the clean images, per image, with x clipped to
+ * [0, 255]:
+ *   PSNR = 10 log10(255^2 / MSE)  (+infinity when MSE = 0),
+ *   SSIM = mean over the valid (unpadded) region of Wang et al.'s map with
+ *          an 11 x 11 Gaussian window (sigma 1.5), K1 = 0.01, K2 = 0.03,
+ *          L = 255.
+ *   x          [device] float [n_img][H][W]
+ *   ref        [device] uint8: image k, row y at ref + k ref_stride + y ref_pitch
+ *   psnr, ssim [device] double [n_img], out
+ * H, W >= 11, ref_pitch >= W, ref_stride >= ref_pitch H (n_img > 1);
+ * otherwise ABCS_ERR_INVALID_ARG.  Uses the handle's workspace. */
+abcs_status abcs_psnr_ssim(abcs_handle* h, const float* x, const uint8_t* ref, int n_img, int H, int W,
+                           int64_t ref_pitch, int64_t ref_stride, double* psnr, double* ssim, void* stream);
 
 /* Transform precision of the IDA linear step (Eqs. 25, 28: A x and A^T z)
  * in abcs_ida, abcs_damp and abcs_ida_capture on this handle.  ABCS_FP32

@@ -72,6 +72,7 @@ _SIGS = {
     "abcs_denoise_bm3d": [_P, _P, _I, _I, _I, _P, _D, _P, _P],
     "abcs_sync_status": [_P, _P, C.POINTER(C.c_uint32)],
     "abcs_set_ida_precision": [_P, _I],
+    "abcs_psnr_ssim": [_P, _P, _P, _I, _I, _I, _L, _L, _P, _P, _P],
     "abcs_sense_noalloc": [_P, _I, _I, _I, _L, _L, _I, _D, _I, _I, _P, _P, _P, _L, _P, _P],
     "abcs_sense_noalloc_status": [_P, C.POINTER(C.c_uint32)],
     "abcs_ida_batch": [_P, _P, _I, _P, _P, _P, _L, _I, _D, _I, _D, _P, _P, _P],
@@ -257,6 +258,12 @@ def abcs_thi(h, coeffs, n_img, H, W, B, M, adaptive, thi_counts, rho=None, maske
     `adaptive` counts (or None), masked coefficients (or None)."""
     _check(lib.abcs_thi(h, _ptr(coeffs), n_img, H, W, B, M, _ptr(adaptive), _ptr(thi_counts), _ptr(rho),
                         _ptr(masked), _stream(stream)))
+
+
+def abcs_psnr_ssim(h, x, ref, n_img, H, W, ref_pitch, ref_stride, psnr, ssim, stream=None) -> None:
+    """psnr, ssim [n_img] float64 device tensors <- the quality of x against ref."""
+    _check(lib.abcs_psnr_ssim(h, _ptr(x), _ptr(ref), n_img, H, W, ref_pitch, ref_stride, _ptr(psnr), _ptr(ssim),
+                              _stream(stream)))
 
 
 def abcs_set_ida_precision(h, precision) -> None:

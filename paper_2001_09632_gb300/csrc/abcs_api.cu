@@ -199,6 +199,7 @@ abcs_status abcs_create(abcs_handle** out) {
     ABCS_CUDA(setup_bm3d_tables(), "upload tables");
     ABCS_CUDA(setup_tc_fragments(), "tensor-core fragment setup");
     ABCS_CUDA(setup_ida_fragments(), "tensor-core fragment setup");
+    ABCS_CUDA(setup_quality_tables(), "quality table setup");
     ABCS_CUDA(upload_tables_su(), "upload tables");
     ABCS_CUDA(setup_sense_umma(), "tensor-memory sensing table setup");
     abcs_handle* h = new abcs_handle;
@@ -230,6 +231,24 @@ void abcs_destroy(abcs_handle* h) {
     if (h->status) cudaFree(h->status);
     if (h->img_done) cudaFree(h->img_done);
     delete h;
+}
+
+abcs_status abcs_psnr_ssim(abcs_handle* h, const float* x, const uint8_t* ref, int n_img, int H, int W,
+                           int64_t ref_pitch, int64_t ref_stride, double* psnr, double* ssim, void* stream) {
+    if (!h) return fail(ABCS_ERR_INVALID_ARG, "NULL handle");
+    if (!x || !ref || !psnr || !ssim) return fail(ABCS_ERR_INVALID_ARG, "NULL buffer");
+    if (n_img < 1 || n_img > 65535 || H < 11 || W < 11)
+        return fail(ABCS_ERR_INVALID_ARG, "psnr_ssim: need 1..65535 images of at least 11 x 11 pixels");
+    if (ref_pitch < W || (n_img > 1 && ref_stride < ref_pitch * H))
+        return fail(ABCS_ERR_INVALID_ARG, "psnr_ssim: ref_pitch < W or ref_stride < ref_pitch * H");
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(ABCS_ERR_CUDA, "cannot select the handle's device");
+    abcs_status st = ensure_ws(h, quality_ws_bytes(n_img, H, W));
+    if (st) return st;
+    ABCS_CUDA(launch_psnr_ssim(x, ref, n_img, H, W, ref_pitch, ref_stride, psnr, ssim, h->ws,
+                               static_cast<cudaStream_t>(stream)),
+              "psnr_ssim launch");
+    return ABCS_OK;
 }
 
 abcs_status abcs_set_ida_precision(abcs_handle* h, int precision) {

@@ -347,6 +347,12 @@ cudaError_t cnn_grad(const void* packed, const float* r, const float* clean, con
                      cudaStream_t s);
 // the learned denoiser's iteration input in IDA iteration t
 inline float cnn_iter_input(int t) { return (float)(t < 8 ? t : 8) / 8.f; }
+// PSNR and SSIM per image (k_quality.cu): x [n][H][W] float, ref uint8 with
+// row pitch and image stride; psnr, ssim [n] double; H, W >= 11
+cudaError_t setup_quality_tables();
+size_t quality_ws_bytes(int n_img, int H, int W);
+cudaError_t launch_psnr_ssim(const float* x, const uint8_t* ref, int n_img, int H, int W, int64_t pitch,
+                             int64_t stride, double* psnr, double* ssim, void* ws, cudaStream_t s);
 // per-pixel measured fraction m_i / B^2 of the pixel's block (k_ida.cu)
 cudaError_t launch_density(const ImgGeom& g, const int32_t* counts, float* out, cudaStream_t s);
 // BM3D hard-thresholding step (k_bm3d.cu): in, out [n_img][H][W]; num, den
