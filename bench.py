@@ -511,11 +511,12 @@ def images_learned_vs_plain(h, n=128):
     from paper_2001_09632_gb300 import train
     out = train.evaluate(h, train.load_weights(), n=n, plain_iters=(10, 30), learned_iters=(1, 2, 3, 4, 6, 10),
                          log=lambda *_: None)
-    return {"images": n, "size": [512, 512], "variant": "BBV",
-            "per_subrate": {r: {"psnr_idct": v["psnr_idct"],
+    return {"images": n, "size": [512, 512], "variant": "BBV", "quality": "abcs_psnr_ssim",
+            "per_subrate": {r: {"psnr_idct": v["psnr_idct"], "ssim_idct": v["ssim_idct"],
                                 "psnr_plain30": v["plain"]["30"]["psnr"],
+                                "ssim_plain30": v["plain"]["30"]["ssim"],
                                 "Mpx_per_s_plain30": v["plain"]["30"]["Mpx_per_s"],
-                                "learned": {it: {"psnr": e["psnr"], "Mpx_per_s": e["Mpx_per_s"]}
+                                "learned": {it: {"psnr": e["psnr"], "ssim": e["ssim"], "Mpx_per_s": e["Mpx_per_s"]}
                                             for it, e in v["learned"].items()},
                                 "equal": v["equal"]} for r, v in out.items()}}
 
@@ -936,14 +937,29 @@ def main():
     value = world * px / (step_ms * 1e-3) / 1e6
 
     # ---- the other precisions of the block DCT (same workload) ------------
+    # with the mean PSNR / SSIM of the reconstructions (abcs_psnr_ssim) and
+    # their difference from the FP32 path's
+    qp = torch.empty(N_IMG, dtype=torch.float64, device=dev)
+    qs = torch.empty_like(qp)
+
+    def quality():
+        abcs.abcs_psnr_ssim(h, rec, d_img, N_IMG, H, W, W, H * W, qp, qs, s)
+        torch.cuda.synchronize()
+        return float(qp.mean()), float(qs.mean())
+
     sweep = {}
     for name, p in abcs.PRECISIONS.items():
         for _ in range(3):
             step(p)
         sm, rm = timed_steps(min(K, 200), p)
+        q_psnr, q_ssim = quality()
         sweep[name] = {"sense_ms": statistics.median(sm), "reconstruct_ms": statistics.median(rm),
                        "Mpixel_per_s": world * N_IMG * plan["N"] / ((statistics.median(sm) +
-                                                                    statistics.median(rm)) * 1e-3) / 1e6}
+                                                                    statistics.median(rm)) * 1e-3) / 1e6,
+                       "psnr": q_psnr, "ssim": q_ssim}
+    for name in abcs.PRECISIONS:
+        sweep[name]["dpsnr_vs_fp32"] = sweep[name]["psnr"] - sweep["fp32"]["psnr"]
+        sweep[name]["dssim_vs_fp32"] = sweep[name]["ssim"] - sweep["fp32"]["ssim"]
     # the tcgen05 sensing kernel (basis in tensor memory), same workload
     os.environ["ABCS_SENSE_TC"] = "umma"
     for _ in range(3):
@@ -968,7 +984,9 @@ def main():
     torch.cuda.synchronize()
 
     # ---- IDA, plain TI-DCT denoiser --------------------------------------
+    # the linear step in the step's precision (tensor cores unless FP32)
     x = torch.empty((N_IMG, H, W), dtype=torch.float32, device=dev)
+    abcs.abcs_set_ida_precision(h, prec)
     for _ in range(2):
         abcs.abcs_ida(h, counts, offsets, coeffs, N_IMG, H, W, B, IDA_ITERS, DF, abcs.DEN_TIDCT,
                       LAMBDA, None, x, None, s)
@@ -985,6 +1003,7 @@ def main():
     barrier()
     t_end2 = time.time()
     ida_ms = max_over_ranks(statistics.median(e0.elapsed_time(e1) for e0, e1 in ida_ms))
+    abcs.abcs_set_ida_precision(h, abcs.FP32)
     assert abcs.abcs_sync_status(h, s) == 0
     lin = ida_linear_step(h, s, counts, offsets, coeffs, x, total_coeffs)
 
@@ -1101,7 +1120,7 @@ def main():
         "precision_sweep": sweep,
         "ida": {"value": world * px * IDA_ITERS / (ida_ms * 1e-3) / 1e6, "unit": "Mpixel*iter/s",
                 "iters": IDA_ITERS, "denoiser": "tidct", "lambda": LAMBDA, "damping": DF,
-                "ms_per_call": ida_ms},
+                "linear_step": a.precision, "ms_per_call": ida_ms},
         "ida_linear": dict(lin, hbm_floor_us=lin["bytes_per_iteration"] / hbm_peak / 1e3,
                            fp16x2_frac_hbm=lin["bytes_per_iteration"] / (lin["fp16x2_us_per_iteration"] * 1e-6)
                            / 1e9 / hbm_peak),

@@ -347,10 +347,11 @@ cudaError_t launch_bbv_alloc(const SenseArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // DD pilot: n_i = #{ zigzag rank j < m1 : |c_j| > T }, decided on the exact
 // coefficient.  FP32 coefficients come with a rigorous error bound; any
-// coefficient within that band of T is re-evaluated: exactly in integers for
-// (u, v) in {0, B/2}^2 (those coefficients are S / B with integer S), else
-// in FP64, whose error is < 1e-11 here; an irrational coefficient within
-// 1e-9 of T is flagged ABCS_DEV_AMBIGUOUS and counted as not exceeding.
+// coefficient within that band of T is re-evaluated by the whole warp
+// (dd_exact_warp): exactly in integers for (u, v) in {0, B/2}^2 (those
+// coefficients are S / B with integer S), else in FP64, whose error is
+// < 1e-11 here; an irrational coefficient within 1e-9 of T is flagged
+// ABCS_DEV_AMBIGUOUS and counted as not exceeding.
 // ---------------------------------------------------------------------------
 // n_i of the blocks of tile (block row bi, tile column tx) of image k; their
 // sum goes to partial `slot`.  Ts and zz are the tile's shared buffers
@@ -396,14 +397,18 @@ ABCS_D void dd_tile(const SenseArgs& a, int k, int bi, int tx, int64_t slot, flo
         int n = 0;
         for (int j0 = 0; j0 < m1; j0 += 32) {
             const int j = j0 + lane;
-            bool hit = false;
+            bool hit = false, pend = false;
             if (j < m1) {
                 const float c = fabsf(blk[zz[j]]);
                 if (c > T + band) hit = true;
-                else if (c >= T - band) {
-                    const int p = zz_pos<B>(j);
-                    hit = dd_exceeds_exact<B>(img + (bj0 + b) * B, g.pitch, p / B, p % B, a.T, a.status);
-                }
+                else if (c >= T - band) pend = true;
+            }
+            // coefficients inside the band: decided exactly by the whole warp
+            for (unsigned any = __ballot_sync(0xffffffffu, pend); any; any &= any - 1) {
+                const int src = __ffs(any) - 1;
+                const int p = zz_pos<B>(j0 + src);
+                const bool ex = dd_exact_warp<B>(img + (bj0 + b) * B, g.pitch, p / B, p % B, a.T, a.status);
+                if (lane == src) hit = ex;
             }
             n += __popc(__ballot_sync(0xffffffffu, hit));
         }

@@ -97,6 +97,15 @@ class Sensed:
         return r, s
 
 
+def quality(h, x: torch.Tensor, sd: "Sensed"):
+    """Per-image PSNR and SSIM of x against the batch's clean images, from
+    the library (abcs_psnr_ssim): two float lists."""
+    ps = torch.empty(sd.n, dtype=torch.float64, device="cuda")
+    ss = torch.empty_like(ps)
+    abcs.abcs_psnr_ssim(h, x, sd.d_img, sd.n, sd.Hc, sd.Wc, sd.W, sd.H * sd.W, ps, ss)
+    return ps.tolist(), ss.tolist()
+
+
 def psnr(x: torch.Tensor, ref: torch.Tensor) -> torch.Tensor:
     """Per image 10 log10(255^2 / MSE) of x clipped to [0, 255]."""
     d = x.clamp(0, 255) - ref
@@ -266,33 +275,37 @@ def evaluate(h, weights, n=128, H=512, W=512, subrates=(0.1, 0.2, 0.3, 0.4, 0.5)
              plain_iters=(1, 3, 5, 10, 20, 30), learned_iters=(1, 2, 3, 4, 6, 10), lam=DEFAULT_LAMBDA,
              batch=32, seed=EVAL_SEED, log=print):
     """Plain IDA (TI-DCT) and learned IDA (CNN) on held-out images: mean PSNR
-    after each iteration count, and Mpixel/s of a full reconstruction with
-    that many iterations.  `equal` compares the fewest learned iterations
-    whose PSNR reaches the plain reference (its last iteration count) minus
-    0.1 dB with that reference."""
+    and SSIM after each iteration count, and Mpixel/s of a full
+    reconstruction with that many iterations.  `equal` compares the fewest
+    learned iterations whose PSNR reaches the plain reference (its last
+    iteration count) minus 0.1 dB with that reference."""
     p = torch.tensor(weights, device="cuda")
     packed = torch.empty(abcs.abcs_cnn_packed_bytes(), dtype=torch.uint8, device="cuda")
     abcs.abcs_cnn_pack(h, p, packed)
     out = {}
     for r in subrates:
-        ps = {("idct", 0): []}
+        ps, ss = {("idct", 0): []}, {("idct", 0): []}
         ms = {}
         px = 0
         for i0 in range(0, n, batch):
             imgs = synth.gen_batch(min(batch, n - i0), H, W, seed + i0)
             sd = Sensed(h, imgs, 16, r, variant)
             x0 = sd.ida(h, 1, abcs.DEN_NONE)      # one identity iteration = A^T y, the IDCT image
-            ps[("idct", 0)] += psnr(x0, sd.clean).tolist()
+            p_, s_ = quality(h, x0, sd)
+            ps[("idct", 0)] += p_
+            ss[("idct", 0)] += s_
             for kind, its, den, pk in (("plain", plain_iters, abcs.DEN_TIDCT, None),
                                        ("learned", learned_iters, abcs.DEN_CNN, packed)):
                 for it in its:
                     x, t_ms = timed_ida(h, sd, it, den, lam, pk, reps=2)
-                    ps.setdefault((kind, it), []).extend(psnr(x, sd.clean).tolist())
+                    p_, s_ = quality(h, x, sd)
+                    ps.setdefault((kind, it), []).extend(p_)
+                    ss.setdefault((kind, it), []).extend(s_)
                     ms[(kind, it)] = ms.get((kind, it), 0.0) + t_ms
             px += sd.n * sd.Hc * sd.Wc
-        res = {"psnr_idct": float(np.mean(ps[("idct", 0)]))}
+        res = {"psnr_idct": float(np.mean(ps[("idct", 0)])), "ssim_idct": float(np.mean(ss[("idct", 0)]))}
         for kind, its in (("plain", plain_iters), ("learned", learned_iters)):
-            res[kind] = {str(it): {"psnr": float(np.mean(ps[(kind, it)])),
+            res[kind] = {str(it): {"psnr": float(np.mean(ps[(kind, it)])), "ssim": float(np.mean(ss[(kind, it)])),
                                    "Mpx_per_s": px / (ms[(kind, it)] * 1e-3) / 1e6} for it in its}
         ref_it = str(plain_iters[-1])
         ref = res["plain"][ref_it]
