@@ -314,16 +314,6 @@ struct TcLane {
 
 ABCS_D int tc_rank(const TcLane& L, int nt, int i) { return (int)((L.rk[nt] >> (8 * i)) & 0xFFu); }
 
-ABCS_D float2 lds_f2(uint32_t a) {
-    float2 v;
-    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a));
-    return v;
-}
-ABCS_D float lds_f(uint32_t a) {
-    float v;
-    asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(a));
-    return v;
-}
 
 // One 16 x 16 block by one warp.  xb: shared address of its x stage
 // (tc_xoff layout, block 0); yb: shared address of its first staged

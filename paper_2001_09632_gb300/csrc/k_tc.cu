@@ -266,12 +266,13 @@ __global__ void __launch_bounds__(256, 3) recon_tc_kernel(ReconArgs a, int64_t n
     uint32_t ATh[4], ATl[4], DBh[2][2], DBl[2][2];
     frag_a<P>(kSetReconA, ATh, ATl);
     frag_b<P>(kSetReconB, DBh, DBl);
-    // ranks of the 8 coefficients this lane feeds into B = C: (2q + e, g + 8 nt), e in {0,1,8,9}
-    int rk[2][4];
+    // 4 x the ranks of the 8 coefficients this lane feeds into B = C: (2q + e, g + 8 nt), e in {0,1,8,9}
+    // (byte offsets in the staged segment)
+    int rkb[2][4];
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) rk[nt][i] = zz_rank(2 * f.q + (i & 1) + 8 * (i >> 1), f.g + 8 * nt, 16);
+        for (int i = 0; i < 4; ++i) rkb[nt][i] = 4 * zz_rank(2 * f.q + (i & 1) + 8 * (i >> 1), f.g + 8 * nt, 16);
 
     griddep_wait();
     const ImgGeom& g = a.g;
@@ -311,17 +312,17 @@ __global__ void __launch_bounds__(256, 3) recon_tc_kernel(ReconArgs a, int64_t n
 
         const SegMeta<RSEG>& M = meta[mi];
         const SegGeom sg = M.sg;
-        const float* st = stage[bi] + M.sh;
+        const uint32_t st = smem_u32(stage[bi] + M.sh);
 #pragma unroll
         for (int c = warp; c < sg.nblk; c += 8) {
-            const int m = M.cnt[c];
-            const float* sb = st + M.rel[c];
+            const int m4 = 4 * M.cnt[c];
+            const uint32_t sb = st + 4u * (uint32_t)M.rel[c];
             uint32_t bh[2][2], bl[2][2];
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
                 float cv[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) cv[i] = (rk[nt][i] < m) ? sb[rk[nt][i]] : 0.f;
+                for (int i = 0; i < 4; ++i) cv[i] = lds_f_lt(sb + (uint32_t)rkb[nt][i], rkb[nt][i], m4);
                 split2<P>(cv[0], cv[1], bh[nt][0], bl[nt][0]);
                 split2<P>(cv[2], cv[3], bh[nt][1], bl[nt][1]);
             }
@@ -928,11 +929,13 @@ __global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int64_t n
     uint32_t DAh[4], DAl[4], DTh[2][2], DTl[2][2];
     frag_a<P>(kSetSenseA, DAh, DAl);
     frag_b<P>(kSetSenseB, DTh, DTl);
-    int rk[2][4];   // ranks of R[g + 8 (i>>1)][2q + (i&1) + 8 nt] = C[u = 2q + (i&1) + 8 nt][v = g + 8 (i>>1)]
+    // 4 x the ranks of R[g + 8 (i>>1)][2q + (i&1) + 8 nt] = C[u = 2q + (i&1) + 8 nt][v = g + 8 (i>>1)]
+    // (byte offsets in the segment's packed staging buffer)
+    int rkb[2][4];
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) rk[nt][i] = zz_rank(2 * f.q + (i & 1) + 8 * nt, f.g + 8 * (i >> 1), 16);
+        for (int i = 0; i < 4; ++i) rkb[nt][i] = 4 * zz_rank(2 * f.q + (i & 1) + 8 * nt, f.g + 8 * (i >> 1), 16);
 
     const ImgGeom& g = a.g;
     const bool vec = ((reinterpret_cast<uintptr_t>(a.img) | (uintptr_t)g.pitch |
@@ -983,7 +986,7 @@ __global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int64_t n
         const SegMeta<SEG>& M = meta[mi];
         const int nblk = M.sg.nblk;
         const uint8_t* px = pix[bi];
-        float* os = ost + M.sh;
+        const uint32_t os = smem_u32(ost + M.sh);
 #pragma unroll 2
         for (int c = warp; c < nblk; c += 8) {
             uint32_t xb[2][2];
@@ -1009,13 +1012,12 @@ __global__ void __launch_bounds__(256, 4) sense_tc_kernel(SenseArgs a, int64_t n
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt)
                 mma_split<P>(R[nt], Ah, Al, DTh[nt][0], DTh[nt][1], DTl[nt][0], DTl[nt][1]);
-            const int m = M.cnt[c];
-            float* ob = os + M.rel[c];
+            const int m4 = 4 * M.cnt[c];
+            const uint32_t ob = os + 4u * (uint32_t)M.rel[c];
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (rk[nt][i] < m) ob[rk[nt][i]] = R[nt][i];
+                for (int i = 0; i < 4; ++i) sts_f_lt(ob + (uint32_t)rkb[nt][i], R[nt][i], rkb[nt][i], m4);
         }
         __syncthreads();
         // copy-out of the segment's packed range and its global offsets
