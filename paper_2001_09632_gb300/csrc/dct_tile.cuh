@@ -160,6 +160,35 @@ ABCS_D void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "m
 template <int N>
 ABCS_D void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Shared-memory accesses by 32-bit shared addresses (no generic-address
+// arithmetic).  The _lt forms take the predicate r < m inside the
+// instruction, so a per-coefficient condition costs no branch.
+ABCS_D float2 lds_f2(uint32_t a) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+ABCS_D float lds_f(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(a));
+    return v;
+}
+// *a if r < m, else 0
+ABCS_D float lds_f_lt(uint32_t a, int r, int m) {
+    float v;
+    // %0 is written before the inputs are read: early clobber
+    asm volatile("{\n .reg .pred q;\n setp.lt.s32 q, %2, %3;\n mov.f32 %0, 0f00000000;\n @q ld.shared.f32 %0, [%1];\n}\n"
+                 : "=&f"(v)
+                 : "r"(a), "r"(r), "r"(m));
+    return v;
+}
+// *a = v if r < m
+ABCS_D void sts_f_lt(uint32_t a, float v, int r, int m) {
+    asm volatile("{\n .reg .pred q;\n setp.lt.s32 q, %2, %3;\n @q st.shared.f32 [%0], %1;\n}\n" ::"r"(a), "f"(v),
+                 "r"(r), "r"(m)
+                 : "memory");
+}
+
 ABCS_D void stage_in_async(float* stage, const float* __restrict__ src, int64_t start, int n) {
     const int sh = (int)(start & 3);
     const float* g = src + start;

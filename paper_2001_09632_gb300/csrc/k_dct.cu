@@ -77,11 +77,11 @@ ABCS_D void sense_pack_tile(const SenseArgs& a, int k, int bi, int tx, bool last
         fdct<B>(x, c);
         if (b < nblk) {
             const int r0 = rel[b], m = rel[b + 1] - r0;
-            float* dst = Ps + sh + r0;
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(Ps + sh + r0);
 #pragma unroll
             for (int u = 0; u < B; ++u) {
                 const int r = rk[u * B + v];
-                if (r < m) dst[r] = c[u];
+                sts_f_lt(dst + 4u * (uint32_t)r, c[u], r, m);
             }
         }
     }
@@ -173,11 +173,11 @@ __global__ void __launch_bounds__(256, (B == 16 ? 3 : 4)) recon_kernel(ReconArgs
         const int b = t / B, v = t % B;
         float c[B], x[B];
         const int r0 = rel[min(b, nblk)], m = (b < nblk) ? rel[b + 1] - r0 : 0;
-        const float* src = Ps + sh + r0;
+        const uint32_t src = (uint32_t)__cvta_generic_to_shared(Ps + sh + r0);
 #pragma unroll
         for (int u = 0; u < B; ++u) {
             const int r = rk[u * B + v];
-            c[u] = (r < m) ? src[r] : 0.f;
+            c[u] = lds_f_lt(src + 4u * (uint32_t)r, r, m);
         }
         idct<B>(c, x);
         float* col = Ts + b * Tl::BLK + v;

@@ -321,10 +321,13 @@ ABCS_D int tc_rank(const TcLane& L, int nt, int i) { return (int)((L.rk[nt] >> (
 // coefficients in global memory; zg: its z; rb: r at its top-left pixel plus
 // the lane offset ro, rows 8 apart at rb8.  Returns the lane's FP32 sum of
 // z^2 (at most 8 terms).
-template <int P, bool STAGED>
+template <int P, bool STAGED, bool FULL>
 ABCS_D float tc_block(uint32_t xb, uint32_t yb, uint32_t zoff, const float* yg, const float* zpg, float* zg,
-                      float* rb, float* rb8, int m, float inv_df, bool has_x, bool has_zp, const uint32_t (&Dh)[4],
+                      float* rb, float* rb8, int m, float inv_df, bool has_x_, bool has_zp_, const uint32_t (&Dh)[4],
                       const uint32_t (&Dl)[4], const uint32_t (&Th)[4], const uint32_t (&Tl)[4], const TcLane& ln) {
+    // FULL: x and z_prev are both given (every iteration after the first),
+    // known at compile time so no per-coefficient test remains
+    const bool has_x = FULL || has_x_, has_zp = FULL || has_zp_;
     float R[2][4] = {};
     if (has_x) {
         float V[2][4];
@@ -400,7 +403,7 @@ ABCS_D float tc_block(uint32_t xb, uint32_t yb, uint32_t zoff, const float* yg, 
 // One tile from the stage, 8 warps: warp w transforms blocks w and w + 8.
 // xs, ys: shared addresses of the stage's x and y buffers (z_prev follows y
 // at kTcStage floats).  Returns the lane's FP32 sum of z^2 (at most 16 terms).
-template <int P, bool STAGED>
+template <int P, bool STAGED, bool FULL>
 ABCS_D float tc_transform(const IdaLinArgs& a, const ImgGeom& g, const TcMeta& M, uint32_t xs, uint32_t ys,
                           float inv_df, const uint32_t (&Dh)[4], const uint32_t (&Dl)[4], const uint32_t (&Th)[4],
                           const uint32_t (&Tl)[4], const TcLane& ln) {
@@ -413,7 +416,7 @@ ABCS_D float tc_transform(const IdaLinArgs& a, const ImgGeom& g, const TcMeta& M
         if (c >= M.nblk) break;
         const int r0 = M.rel[c], m = M.rel[c + 1] - r0;
         float* rb = a.r + M.pix + c * 16 + ln.ro;
-        nz += tc_block<P, STAGED>(xs + 1024u * (uint32_t)c, ys + 4u * (sh + (uint32_t)r0), 4u * kTcStage,
+        nz += tc_block<P, STAGED, FULL>(xs + 1024u * (uint32_t)c, ys + 4u * (sh + (uint32_t)r0), 4u * kTcStage,
                                   a.y + M.start + r0, a.z_prev + M.start + r0, a.z + M.start + r0, rb,
                                   rb + 8 * (int64_t)g.Wc, m, inv_df, a.x != nullptr, a.z_prev != nullptr, Dh, Dl,
                                   Th, Tl, ln);
@@ -428,7 +431,9 @@ ABCS_D float tc_transform(const IdaLinArgs& a, const ImgGeom& g, const TcMeta& M
 // kernel's) in FP64: each warp sums its lanes in FP32 (at most 512 terms),
 // and thread 0 adds the 8 warp sums in FP32 after the next tile's barrier
 // (FP64 adds there held warp 0 back and the other warps at the barrier).
-template <int P>
+// FULL: launched when x and z_prev are both given (every iteration after the
+// first), so the block transform tests neither.
+template <int P, bool FULL>
 __global__ void __launch_bounds__(256, 3) ida_linear_tc_kernel(IdaLinArgs a, int ntx, int ntiles) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float swarp[2][8];
@@ -506,8 +511,8 @@ __global__ void __launch_bounds__(256, 3) ida_linear_tc_kernel(IdaLinArgs a, int
         const float inv_df = a.alpha ? __ldg(a.alpha + M.k) : a.inv_df;
         const uint32_t xsa = (uint32_t)__cvta_generic_to_shared(xs(b)), ysa = (uint32_t)__cvta_generic_to_shared(ys(b));
         const float nz = warp_sum(M.rel[M.nblk] <= kTcCap
-                                      ? tc_transform<P, true>(a, g, M, xsa, ysa, inv_df, Dh, Dl, Th, Tl, ln)
-                                      : tc_transform<P, false>(a, g, M, xsa, ysa, inv_df, Dh, Dl, Th, Tl, ln));
+                                      ? tc_transform<P, true, FULL>(a, g, M, xsa, ysa, inv_df, Dh, Dl, Th, Tl, ln)
+                                      : tc_transform<P, false, FULL>(a, g, M, xsa, ysa, inv_df, Dh, Dl, Th, Tl, ln));
         if (lane == 0) swarp[b][warp] = nz;
     }
     cp_async_wait_all();
@@ -521,22 +526,27 @@ __global__ void __launch_bounds__(256, 3) ida_linear_tc_kernel(IdaLinArgs a, int
     }
 }
 
-template <int P>
-static cudaError_t launch_lin_tc(const IdaLinArgs& a, cudaStream_t s) {
+template <int P, bool FULL>
+static cudaError_t launch_lin_tc_k(const IdaLinArgs& a, cudaStream_t s) {
     const int ntx = (a.g.nbw + kTcNB - 1) / kTcNB;
     const int64_t ntiles = (int64_t)ntx * a.g.nbh * a.g.n_img;
     if (ntiles <= 0) return cudaSuccess;
     if (ntiles >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
     int dev, sms, per_sm;
-    cudaError_t e = cudaFuncSetAttribute(ida_linear_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(ida_linear_tc_kernel<P, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kTcSmem);
     if (!e) e = cudaGetDevice(&dev);
     if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ida_linear_tc_kernel<P>, 256, kTcSmem);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ida_linear_tc_kernel<P, FULL>, 256, kTcSmem);
     if (e) return e;
     const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
     const int grid = (int)(ntiles < cap ? ntiles : cap);
-    return launch_pdl(ida_linear_tc_kernel<P>, dim3(grid), dim3(256), kTcSmem, s, a, ntx, (int)ntiles);
+    return launch_pdl(ida_linear_tc_kernel<P, FULL>, dim3(grid), dim3(256), kTcSmem, s, a, ntx, (int)ntiles);
+}
+
+template <int P>
+static cudaError_t launch_lin_tc(const IdaLinArgs& a, cudaStream_t s) {
+    return a.x && a.z_prev ? launch_lin_tc_k<P, true>(a, s) : launch_lin_tc_k<P, false>(a, s);
 }
 
 // sigma^t = sqrt(||z^t||^2 / m) per image (Eq. 15); m = the image's

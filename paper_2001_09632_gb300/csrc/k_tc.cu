@@ -1201,7 +1201,7 @@ __global__ void __launch_bounds__(256, 3) dd_pilot_tc_kernel(SenseArgs a) {
                 pend &= ~(1u << e);
             }
         }
-        n = warp_sum(n);
+        n = __reduce_add_sync(0xffffffffu, n);
         if (lane == 0) {
             a.w[(int64_t)k * g.n_blocks + (int64_t)bi * g.nbw + bj0 + c] = n;
             mine += (unsigned long long)n;

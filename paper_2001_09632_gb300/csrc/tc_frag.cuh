@@ -134,35 +134,6 @@ ABCS_D void load_b_const(bool transpose, uint32_t (&h)[2][2], uint32_t (&l)[2][2
     }
 }
 
-// Shared-memory accesses by 32-bit shared addresses (no generic-address
-// arithmetic).  The _lt forms take the predicate r < m inside the
-// instruction, so a per-coefficient condition costs no branch.
-ABCS_D float2 lds_f2(uint32_t a) {
-    float2 v;
-    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a));
-    return v;
-}
-ABCS_D float lds_f(uint32_t a) {
-    float v;
-    asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(a));
-    return v;
-}
-// *a if r < m, else 0
-ABCS_D float lds_f_lt(uint32_t a, int r, int m) {
-    float v;
-    // %0 is written before the inputs are read: early clobber
-    asm volatile("{\n .reg .pred q;\n setp.lt.s32 q, %2, %3;\n mov.f32 %0, 0f00000000;\n @q ld.shared.f32 %0, [%1];\n}\n"
-                 : "=&f"(v)
-                 : "r"(a), "r"(r), "r"(m));
-    return v;
-}
-// *a = v if r < m
-ABCS_D void sts_f_lt(uint32_t a, float v, int r, int m) {
-    asm volatile("{\n .reg .pred q;\n setp.lt.s32 q, %2, %3;\n @q st.shared.f32 [%0], %1;\n}\n" ::"r"(a), "f"(v),
-                 "r"(r), "r"(m)
-                 : "memory");
-}
-
 // index of a tensor-core precision in per-precision tables
 template <int P>
 __host__ __device__ constexpr int pidx() { return P == kP16 ? 0 : (P == kPB16 ? 1 : 2); }
