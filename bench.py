@@ -44,9 +44,9 @@ FLUSH_BYTES = 512 << 20
 #       --clock-control none -k regex:"bbv_image|sense_tc_kernel|recon_tc_kernel" -s 3 -c 3
 #       python bench.py --case step
 # (64 x 512x512, BBV r 0.3, FP16x2; ncu flushes the caches before each launch)
-# (sense = bbv_image_kernel 10,558,976 + 0 and sense_tc_kernel 17,604,864 + 0 bytes;
-# reconstruct = recon_tc_kernel 18,112,768 + 7,954,432 bytes)
-TRAFFIC = {"recon_fp16x2": 26067200, "sense_fp16x2": 28163840}
+# (sense = bbv_image_kernel 10,559,232 + 0 and sense_tc_kernel 17,604,608 + 0 bytes;
+# reconstruct = recon_tc_kernel 18,111,744 + 7,710,208 bytes)
+TRAFFIC = {"recon_fp16x2": 25821952, "sense_fp16x2": 28163840}
 
 
 # ---------------------------------------------------------------------------
