@@ -125,6 +125,22 @@ def case_damp(h):
     return _timed(run, 1)
 
 
+def case_tidct(h):
+    """abcs_denoise_tidct (the plain denoiser alone), 64 x 512x512, sigma 20 per image."""
+    import torch
+    from paper_2001_09632_gb300 import abcs, synth
+    n, H, W = 64, 512, 512
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    r = torch.from_numpy(synth.gen_batch(n, H, W, 4321)).cuda().float()
+    r += 20.0 * torch.randn((n, H, W), device="cuda", generator=gen)
+    sig = torch.full((n,), 20.0, device="cuda")
+    x = torch.empty_like(r)
+    run = lambda: abcs.abcs_denoise_tidct(h, r, n, H, W, sig, 2.3, x)
+    for _ in range(3):
+        run()
+    return _timed(run)
+
+
 def _sense_case(h, variant, r, prec, seed=1234):
     import torch
     from paper_2001_09632_gb300 import abcs, synth
@@ -255,7 +271,7 @@ def case_ida_linear_fp32(h):
 
 CASES = {"bm3d": case_bm3d, "thi": case_thi, "damp": case_damp, "recon": case_recon, "sense": case_sense,
          "sense_dd": case_sense_dd, "step": case_step, "ida_linear": case_ida_linear,
-         "ida_linear_fp32": case_ida_linear_fp32}
+         "ida_linear_fp32": case_ida_linear_fp32, "tidct": case_tidct}
 
 
 def run_case(name):

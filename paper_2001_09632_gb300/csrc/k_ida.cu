@@ -667,10 +667,16 @@ __global__ void damp_alpha_kernel(const double* __restrict__ partial, int chunks
 //   (c) thread per output column: overlap-add of the 8 windows covering it
 //       and the column inverse, accumulated in 8 sliding registers; the top
 //       row is complete and written out.
-// Every output accumulates in a fixed order (deterministic).
+// Steps (b) and (c) carry the frequency rows u in pairs (2p, 2p + 1) through
+// packed FP32x2 arithmetic (one instruction, two FP32 operations, each
+// rounded as the scalar one), so the results are those of the scalar
+// transforms.  Every output accumulates in a fixed order (deterministic).
 // ---------------------------------------------------------------------------
-constexpr int kTW = 240, kWin = kTW + 7, kCols = kTW + 14, kQS = 65;
-constexpr size_t kTidctSmem = (8 * 256 + kWin * kQS) * sizeof(float);
+constexpr int kTW = 240, kWin = kTW + 7, kCols = kTW + 14, kQS2 = 33;
+// Vs: [4 row pairs][256 columns] float2; Qs: [kWin windows][kQS2] float2
+// (32 used: 4 row pairs x 8 positions; 33 keeps the per-window rows on
+// distinct bank pairs)
+constexpr size_t kTidctSmem = (4 * 256 + kWin * kQS2) * sizeof(float2);
 
 ABCS_D int reflect(int i, int n) {
     const int p = 2 * n;
@@ -679,12 +685,68 @@ ABCS_D int reflect(int i, int n) {
     return i < n ? i : p - 1 - i;
 }
 
+ABCS_D float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+ABCS_D float2 f2_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }   // exact a - b
+ABCS_D float2 f2_fma(float c, float2 x, float2 acc) { return __ffma2_rn(make_float2(c, c), x, acc); }
+ABCS_D float2 f2_mul(float c, float2 x) { return __fmul2_rn(make_float2(c, c), x); }
+
+// fdct_rec / idct_rec on two vectors at once, the same operations in the
+// same order per component
+template <int S, int N>
+ABCS_D void fdct8x2_rec(const float2* x, float2* c) {
+    if constexpr (N == 1) {
+        c[0] = f2_mul(Dc<8>(0, 0), x[0]);
+    } else {
+        constexpr int H = N / 2;
+        float2 sm[H], d[H];
+#pragma unroll
+        for (int n = 0; n < H; ++n) {
+            sm[n] = f2_add(x[n], x[N - 1 - n]);
+            d[n] = f2_sub(x[n], x[N - 1 - n]);
+        }
+        fdct8x2_rec<2 * S, H>(sm, c);
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int n = 0; n < H; ++n) acc = f2_fma(Dc<8>(S * (2 * j + 1), n), d[n], acc);
+            c[S * (2 * j + 1)] = acc;
+        }
+    }
+}
+
+template <int S, int N>
+ABCS_D void idct8x2_rec(const float2* c, float2* x) {
+    if constexpr (N == 2) {
+        // the DC product D[0][0] c[0] enters both sums unrounded (one FMA
+        // each), as the scalar transform is compiled
+        const float2 o = f2_fma(Dc<8>(S, 0), c[S], make_float2(0.f, 0.f));
+        const float d0 = Dc<8>(0, 0);
+        x[0] = __ffma2_rn(make_float2(d0, d0), c[0], o);
+        x[1] = __ffma2_rn(make_float2(d0, d0), c[0], make_float2(-o.x, -o.y));
+    } else if constexpr (N == 1) {
+        x[0] = f2_mul(Dc<8>(0, 0), c[0]);
+    } else {
+        constexpr int H = N / 2;
+        float2 e[H];
+        idct8x2_rec<2 * S, H>(c, e);
+#pragma unroll
+        for (int n = 0; n < H; ++n) {
+            float2 o = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < H; ++j) o = f2_fma(Dc<8>(S * (2 * j + 1), n), c[S * (2 * j + 1)], o);
+            x[n] = f2_add(e[n], o);
+            x[N - 1 - n] = f2_sub(e[n], o);
+        }
+    }
+}
+
 // One 240 x TH output tile of the plain denoiser (img, dst: one image).
 template <int TH>
 ABCS_D void tidct_tile(const float* __restrict__ img, float* __restrict__ dst, int H, int W, int x0, int y0,
                        float thr, unsigned char* smem) {
-    float* Vs = reinterpret_cast<float*>(smem);        // [8][256]
-    float* Qs = Vs + 8 * 256;                          // [kWin][kQS]
+    float2* Vs = reinterpret_cast<float2*>(smem);     // [4][256]
+    float2* Qs = Vs + 4 * 256;                         // [kWin][kQS2]
     const int t = threadIdx.x;
     __syncthreads();                                   // smem of a previous tile is free
 
@@ -706,38 +768,40 @@ ABCS_D void tidct_tile(const float* __restrict__ img, float* __restrict__ dst, i
             float V[8];
             fdct<8>(col, V);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) Vs[u * 256 + t] = V[u];
+            for (int p = 0; p < 4; ++p) Vs[p * 256 + t] = make_float2(V[2 * p], V[2 * p + 1]);
 #pragma unroll
             for (int i = 0; i < 7; ++i) col[i] = col[i + 1];
             if (wy + 8 < ylast + 7) col[7] = __ldg(img + (int64_t)reflect(wy + 8, H) * W + xc);
         }
         __syncthreads();
         if (t < kWin) {
-            float* q = Qs + t * kQS;
+            float2* q = Qs + t * kQS2;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                float vr[8];
+            for (int p = 0; p < 4; ++p) {
+                float2 vr[8], c[8], qr[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) vr[j] = Vs[u * 256 + t + j];
-                float c[8], qr[8];
-                fdct<8>(vr, c);
+                for (int j = 0; j < 8; ++j) vr[j] = Vs[p * 256 + t + j];
+                fdct8x2_rec<1, 8>(vr, c);
 #pragma unroll
-                for (int v = 0; v < 8; ++v)
-                    c[v] = (fabsf(c[v]) > thr || (u == 0 && v == 0)) ? c[v] : 0.f;
-                idct<8>(c, qr);
+                for (int v = 0; v < 8; ++v) {
+                    c[v].x = (fabsf(c[v].x) > thr || (p == 0 && v == 0)) ? c[v].x : 0.f;
+                    c[v].y = fabsf(c[v].y) > thr ? c[v].y : 0.f;
+                }
+                idct8x2_rec<1, 8>(c, qr);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) q[u * 8 + j] = qr[j];
+                for (int j = 0; j < 8; ++j) q[p * 8 + j] = qr[j];
             }
         }
         __syncthreads();
         if (t < kTW) {
             float S[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                float s = 0.f;
+            for (int p = 0; p < 4; ++p) {
+                float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int d = 0; d < 8; ++d) s += Qs[(t + d) * kQS + u * 8 + (7 - d)];
-                S[u] = s;
+                for (int d = 0; d < 8; ++d) s2 = f2_add(s2, Qs[(t + d) * kQS2 + p * 8 + (7 - d)]);
+                S[2 * p] = s2.x;
+                S[2 * p + 1] = s2.y;
             }
             float X[8];
             idct<8>(S, X);
