@@ -667,18 +667,21 @@ __global__ void damp_alpha_kernel(const double* __restrict__ partial, int chunks
 //   (c) thread per output column: overlap-add of the 8 windows covering it
 //       and the column inverse, accumulated in 8 sliding registers; the top
 //       row is complete and written out.
+// (b) and (c) run twice per window row, on frequency rows 0-3 and then 4-7.
 // Steps (b) and (c) carry the frequency rows u in pairs (2p, 2p + 1) through
 // packed FP32x2 arithmetic (one instruction, two FP32 operations, each
 // rounded as the scalar one), so the results are those of the scalar
 // transforms.  Every output accumulates in a fixed order (deterministic).
 // ---------------------------------------------------------------------------
-constexpr int kTW = 240, kWin = kTW + 7, kCols = kTW + 14, kQS2 = 33;
-// Vs: [4 row pairs][256 columns] float2; Qs: [kWin windows][kQS2] float2
-// (32 used: 4 row pairs x 8 positions; 33 keeps the per-window rows on
-// distinct bank pairs)
+constexpr int kTW = 240, kWin = kTW + 7, kCols = kTW + 14, kQS2 = 17;
+// Vs: [4 row pairs][256 columns] float2; Qs: [kWin windows][kQS2] float2 for
+// one half of the row pairs at a time (16 used: 2 row pairs x 8 positions;
+// 17 keeps the per-window rows on distinct bank pairs).  Halving Q keeps the
+// CTA at 42 KB, five CTAs per SM.
 constexpr size_t kTidctSmem = (4 * 256 + kWin * kQS2) * sizeof(float2);
 
 ABCS_D int reflect(int i, int n) {
+    if ((unsigned)i < (unsigned)n) return i;           // inside: no division
     const int p = 2 * n;
     i %= p;
     if (i < 0) i += p;
@@ -773,36 +776,42 @@ ABCS_D void tidct_tile(const float* __restrict__ img, float* __restrict__ dst, i
             for (int i = 0; i < 7; ++i) col[i] = col[i + 1];
             if (wy + 8 < ylast + 7) col[7] = __ldg(img + (int64_t)reflect(wy + 8, H) * W + xc);
         }
-        __syncthreads();
-        if (t < kWin) {
-            float2* q = Qs + t * kQS2;
+        float S[8];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                float2 vr[8], c[8], qr[8];
+        for (int half = 0; half < 2; ++half) {
+            __syncthreads();                           // Vs written (half 0); Q read by the last (c) (half 1)
+            if (t < kWin) {
+                float2* q = Qs + t * kQS2;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) vr[j] = Vs[p * 256 + t + j];
-                fdct8x2_rec<1, 8>(vr, c);
+                for (int pp = 0; pp < 2; ++pp) {
+                    const int p = 2 * half + pp;
+                    float2 vr[8], c[8], qr[8];
 #pragma unroll
-                for (int v = 0; v < 8; ++v) {
-                    c[v].x = (fabsf(c[v].x) > thr || (p == 0 && v == 0)) ? c[v].x : 0.f;
-                    c[v].y = fabsf(c[v].y) > thr ? c[v].y : 0.f;
+                    for (int j = 0; j < 8; ++j) vr[j] = Vs[p * 256 + t + j];
+                    fdct8x2_rec<1, 8>(vr, c);
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) {
+                        c[v].x = (fabsf(c[v].x) > thr || (p == 0 && v == 0)) ? c[v].x : 0.f;
+                        c[v].y = fabsf(c[v].y) > thr ? c[v].y : 0.f;
+                    }
+                    idct8x2_rec<1, 8>(c, qr);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) q[pp * 8 + j] = qr[j];
                 }
-                idct8x2_rec<1, 8>(c, qr);
+            }
+            __syncthreads();
+            if (t < kTW) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) q[p * 8 + j] = qr[j];
+                for (int pp = 0; pp < 2; ++pp) {
+                    float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int d = 0; d < 8; ++d) s2 = f2_add(s2, Qs[(t + d) * kQS2 + pp * 8 + (7 - d)]);
+                    S[4 * half + 2 * pp] = s2.x;
+                    S[4 * half + 2 * pp + 1] = s2.y;
+                }
             }
         }
-        __syncthreads();
         if (t < kTW) {
-            float S[8];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                float2 s2 = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int d = 0; d < 8; ++d) s2 = f2_add(s2, Qs[(t + d) * kQS2 + p * 8 + (7 - d)]);
-                S[2 * p] = s2.x;
-                S[2 * p + 1] = s2.y;
-            }
             float X[8];
             idct<8>(S, X);
 #pragma unroll
