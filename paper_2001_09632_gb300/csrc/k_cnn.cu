@@ -289,7 +289,7 @@ ABCS_D uint32_t w0_pair(const CnnPacked* P, int co, int p) {
 // the iteration input of image k: tau[k], or tau0 for every image
 ABCS_D float tau_of(const float* tau, float tau0, int k) { return tau ? __ldg(tau + k) : tau0; }
 
-__global__ void __launch_bounds__(256, 2) cnn_first_tc_kernel(const float* __restrict__ r,
+__global__ void __launch_bounds__(256, 3) cnn_first_tc_kernel(const float* __restrict__ r,
                                                               const float* __restrict__ sigma,
                                                               const float* __restrict__ dens,
                                                               const float* __restrict__ tau, float tau0, int n,
