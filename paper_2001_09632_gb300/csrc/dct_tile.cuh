@@ -204,6 +204,34 @@ ABCS_D void stage_in_async(float* stage, const float* __restrict__ src, int64_t 
     for (int e = head + 4 * nv + threadIdx.x; e < n; e += blockDim.x) cp_async4(stage + sh + e, g + e);
 }
 
+// The same range of two arrays into two stages in one pass (both sources
+// 16-byte aligned, else one array after the other).
+ABCS_D void stage_in_async2(float* st1, const float* __restrict__ src1, float* st2, const float* __restrict__ src2,
+                            int64_t start, int n) {
+    if ((reinterpret_cast<uintptr_t>(src1) | reinterpret_cast<uintptr_t>(src2)) & 15) {
+        stage_in_async(st1, src1, start, n);
+        stage_in_async(st2, src2, start, n);
+        return;
+    }
+    const int sh = (int)(start & 3);
+    const float* g1 = src1 + start;
+    const float* g2 = src2 + start;
+    const int head = min(n, (4 - sh) & 3);
+    for (int e = threadIdx.x; e < head; e += blockDim.x) {
+        cp_async4(st1 + sh + e, g1 + e);
+        cp_async4(st2 + sh + e, g2 + e);
+    }
+    const int nv = (n - head) >> 2;
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        cp_async16(st1 + sh + head + 4 * i, g1 + head + 4 * i);
+        cp_async16(st2 + sh + head + 4 * i, g2 + head + 4 * i);
+    }
+    for (int e = head + 4 * nv + threadIdx.x; e < n; e += blockDim.x) {
+        cp_async4(st1 + sh + e, g1 + e);
+        cp_async4(st2 + sh + e, g2 + e);
+    }
+}
+
 ABCS_D void stage_out(const float* stage, float* __restrict__ dst, int64_t start, int n) {
     const int sh = (int)(start & 3);
     if (reinterpret_cast<uintptr_t>(dst) & 15) {

@@ -291,17 +291,21 @@ ABCS_D int tc_xoff(int c, int r, int h) { return 256 * c + 16 * r + 4 * (h ^ (((
 // y and z_prev ranges
 ABCS_D void tc_stage_in(const IdaLinArgs& a, const ImgGeom& g, const TcMeta& M, float* xs, float* ys, float* zs) {
     if (a.x) {
+        // thread (row r0, block c, chunk h) copies rows r0 + 4 i (i < 4): the
+        // swizzle term of rows r0 + 4 i is that of r0, so they sit 64 i floats on
+        const int h = threadIdx.x & 3, c = (threadIdx.x >> 2) & 15, r0 = threadIdx.x >> 6;
+        if (c < M.nblk) {
+            const float* src = a.x + M.pix + (int64_t)r0 * g.Wc + 16 * c + 4 * h;
+            float* dst = xs + tc_xoff(c, r0, h);
+            const int64_t step = 4 * (int64_t)g.Wc;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int id = threadIdx.x + 256 * i;           // pixel row r, block c, chunk h
-            const int h = id & 3, c = (id >> 2) & 15, r = id >> 6;
-            if (c < M.nblk) cp_async16(xs + tc_xoff(c, r, h), a.x + M.pix + (int64_t)r * g.Wc + 16 * c + 4 * h);
+            for (int i = 0; i < 4; ++i) cp_async16(dst + 64 * i, src + i * step);
         }
     }
     const int n = M.rel[M.nblk];
     if (n <= kTcCap) {
-        stage_in_async(ys, a.y, M.start, n);
-        if (a.z_prev) stage_in_async(zs, a.z_prev, M.start, n);
+        if (a.z_prev) stage_in_async2(ys, a.y, zs, a.z_prev, M.start, n);
+        else stage_in_async(ys, a.y, M.start, n);
     }
 }
 
