@@ -37,9 +37,11 @@ def _ambiguous_mask(r, thr, band=2e-4):
     return mask
 
 
-@pytest.mark.parametrize("H,W", [(64, 64), (100, 250), (200, 520), (13, 300)])
+@pytest.mark.parametrize("H,W", [(64, 64), (100, 250), (200, 520), (13, 300), (3, 5), (1, 17), (7, 30)])
 @pytest.mark.parametrize("sigma,lam", [(8.0, 2.7), (25.0, 2.7), (3.0, 0.0)])
 def test_tidct_parity(handle, H, W, sigma, lam):
+    """Images narrower than a window (3 x 5, 1 x 17, 7 x 30) reflect each
+    window several times over."""
     rng = np.random.default_rng(H * W)
     clean = synth.gen_image(max(H, 8), max(W, 8), 5)[:H, :W].astype(float)
     r = clean + rng.standard_normal((H, W)) * sigma
