@@ -222,3 +222,27 @@ def test_empty_batch_is_rejected(handle):
         abcs.abcs_ida(handle, c, o, y, 0, 64, 64, 16, 2, 2.0, abcs.DEN_TIDCT, 2.3, None, x)
     assert e.value.status == 1
     assert abcs.abcs_sync_status(handle) == 0
+
+
+@pytest.mark.parametrize("prec", [abcs.FP32, abcs.TC_FP16X2])
+def test_blocks_with_no_measurement(handle, prec):
+    """Images whose left part is flat: BBV is 0 there, so those blocks get
+    m_i = 0 (Eq. 22) and the scatter / gather of every transform must leave
+    them out (no store, zero coefficients in the reconstruction), beside
+    textured blocks near the cap."""
+    n, H, W, B, r = 3, 96, 192, 16, 0.3
+    imgs = np.stack([synth.gen_image(H, W, 900 + k) for k in range(n)])
+    imgs[:, :, : W // 2] = 117                     # flat half: zero boundary variation
+    outs, c_ref, y_ref = _oracle(imgs, B, r, O.BBV)
+    assert (c_ref == 0).sum() > 0 and c_ref.max() > 100
+    got = G.sense(handle, imgs, B, r, O.BBV, precision=prec)
+    assert got["bits"] == 0
+    assert np.array_equal(got["counts"], c_ref)
+    o_ref = np.concatenate([[0], np.cumsum(c_ref)])
+    assert np.array_equal(got["offsets"], o_ref)
+    G.check_coeffs(got["y"], y_ref, c_ref, o_ref, BOUND[prec])
+    rec, _, bits = G.reconstruct(handle, *got["d"], n, H, W, B, precision=prec)
+    assert bits == 0
+    for k in range(n):
+        ref = O.reconstruct(outs[k]["counts"], outs[k]["y"], H, W, B)
+        G.check_pixels(rec[k], ref, BOUND[prec], k)
