@@ -140,3 +140,21 @@ def test_set_ida_precision_rejects_unknown(handle):
     with pytest.raises(abcs.AbcsError) as e:
         abcs.abcs_set_ida_precision(handle, 7)
     assert e.value.status == 1
+
+
+def test_ida_tc_blocks_with_no_measurement(tc):
+    """A flat half gives blocks with m_i = 0 beside textured blocks near the
+    cap: their residual is empty (no z, no correction) in every iteration."""
+    h = tc(abcs.TC_FP16X2)
+    H, W, B = 96, 192, 16
+    img = synth.gen_image(H, W, 933)
+    img[:, : W // 2] = 117
+    out = O.sense(img, B, 0.3, O.BBV)
+    assert (out["counts"] == 0).sum() > 0
+    got = G.sense(h, img[None], B, 0.3, O.BBV)
+    for iters in (1, 4):
+        x, tr, bits = G.ida(h, *got["d"], 1, H, W, B, iters, 2.0, abcs.DEN_NONE)
+        assert bits == 0
+        xr, sig = O.ida(out["y"], out["counts"], H, W, B, iters, DF=2.0, denoiser=None)
+        G.check_pixels(x[0], xr, 1e-5, iters)
+        np.testing.assert_allclose(tr[0, :iters], sig, rtol=1e-5)
